@@ -1,0 +1,255 @@
+"""ORACLE -- test infrastructure, not part of the library.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA library
+(``paper_2305_03317_b300``) and never imports it; the only module both sides
+use is ``bcgen`` (seeded inputs, no centrality arithmetic).
+
+Contents:
+  * ``bc`` / ``bc_ld`` / ``source_detail`` -- plain single-threaded Brandes in
+    double or long double (``brandes.c``), following the paper's computeBC
+    (Appendix A, BC listing) with iterateInBFS / iterateInReverse semantics
+    (Section 2.2): sigma summed over BFS-DAG predecessors, delta pulled from
+    DAG successors in reverse BFS order as (sigma_v/sigma_w)(1+delta_w), and
+    BC the raw sum of delta over the listed sources (source excluded).
+  * ``brute_force_bc`` -- exact rational BC from explicit enumeration of every
+    shortest path (tiny graphs only); the definition
+    BC(v) = sum_s sum_{t != s, v} sigma_st(v) / sigma_st written out.
+  * ``relabel`` / ``validate`` -- the ingest rules (degree-descending stable
+    relabelling; CSR validity) in their plain definitions.
+Every function here is pinned by ``tests/test_oracle*.py`` against closed
+forms, brute force and invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from collections import deque
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "brandes.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Detail(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("delta", ctypes.c_void_p),
+                ("edag", ctypes.c_int64), ("reached", ctypes.c_int64), ("sum_dm1", ctypes.c_int64),
+                ("max_level", ctypes.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    """Compile brandes.c into liboracle.so (plain -O2; no fast-math)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            for name in ("oracle_bc_f64", "oracle_bc_ld"):
+                f = getattr(lib, name)
+                f.restype = ctypes.c_int
+                f.argtypes = [i32, P, P, i32, P, P, P]
+            lib.oracle_bc_ld_out_f64.restype = ctypes.c_int
+            lib.oracle_bc_ld_out_f64.argtypes = [i32, P, P, i32, P, P]
+            lib.oracle_source_ld.restype = ctypes.c_int
+            lib.oracle_source_ld.argtypes = [i32, P, P, i32, P, P, P, P]
+            lib.oracle_bc_f64_threads.restype = ctypes.c_int
+            lib.oracle_bc_f64_threads.argtypes = [i32, P, P, i32, P, P, ctypes.c_int]
+            lib.oracle_relabel.restype = None
+            lib.oracle_relabel.argtypes = [i32, P, P, P, P, P, P]
+            lib.oracle_validate_csr.restype = ctypes.c_int
+            lib.oracle_validate_csr.argtypes = [i32, i64, P, P, ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(off, adj):
+    return (np.ascontiguousarray(off, dtype=np.int32), np.ascontiguousarray(adj, dtype=np.int32))
+
+
+def bc(off, adj, sources, threads: int = 1) -> np.ndarray:
+    """Raw BC (double) summed over ``sources`` (one entry per occurrence)."""
+    off, adj = _csr(off, adj)
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    n = off.shape[0] - 1
+    out = np.zeros(max(n, 1), dtype=np.float64)
+    if threads > 1:
+        rc = _L().oracle_bc_f64_threads(n, _p(off), _p(adj), src.shape[0], _p(src), _p(out), threads)
+    else:
+        rc = _L().oracle_bc_f64(n, _p(off), _p(adj), src.shape[0], _p(src), _p(out), None)
+    if rc:
+        raise ValueError(f"oracle rc={rc}")
+    return out[:n]
+
+
+def bc_ld(off, adj, sources) -> np.ndarray:
+    """Raw BC computed in long double (80-bit on x86-64), returned as np.longdouble."""
+    off, adj = _csr(off, adj)
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    n = off.shape[0] - 1
+    out = np.zeros(max(n, 1), dtype=np.longdouble)
+    rc = _L().oracle_bc_ld(n, _p(off), _p(adj), src.shape[0], _p(src), _p(out), None)
+    if rc:
+        raise ValueError(f"oracle rc={rc}")
+    return out[:n]
+
+
+def source_detail(off, adj, s: int, long_double: bool = False) -> dict:
+    """Levels, sigma, delta and counts for one source.
+
+    Returns dict(level int32[n] (-1 unreachable), sigma, delta (float64 or
+    longdouble), edag, reached, sum_dm1, max_level).
+    """
+    off, adj = _csr(off, adj)
+    n = off.shape[0] - 1
+    dt = np.longdouble if long_double else np.float64
+    level = np.empty(max(n, 1), np.int32)
+    sigma = np.empty(max(n, 1), dt)
+    delta = np.empty(max(n, 1), dt)
+    bcv = np.empty(max(n, 1), dt)
+    d = _Detail(level.ctypes.data, sigma.ctypes.data, delta.ctypes.data, 0, 0, 0, 0)
+    src = np.array([s], np.int32)
+    f = _L().oracle_bc_ld if long_double else _L().oracle_bc_f64
+    rc = f(n, _p(off), _p(adj), 1, _p(src), _p(bcv), ctypes.byref(d))
+    if rc:
+        raise ValueError(f"oracle rc={rc}")
+    return dict(level=level[:n], sigma=sigma[:n], delta=delta[:n], edag=int(d.edag),
+                reached=int(d.reached), sum_dm1=int(d.sum_dm1), max_level=int(d.max_level))
+
+
+def source_sigma_split(off, adj, s: int):
+    """Long-double levels / sigma as (mantissa in [0.5,1), exponent) / delta for one source."""
+    off, adj = _csr(off, adj)
+    n = off.shape[0] - 1
+    level = np.empty(max(n, 1), np.int32)
+    mant = np.empty(max(n, 1), np.float64)
+    ex = np.empty(max(n, 1), np.int32)
+    delta = np.empty(max(n, 1), np.float64)
+    rc = _L().oracle_source_ld(n, _p(off), _p(adj), s, _p(level), _p(mant), _p(ex), _p(delta))
+    if rc:
+        raise ValueError(f"oracle rc={rc}")
+    return level[:n], mant[:n], ex[:n], delta[:n]
+
+
+def relabel(off, adj):
+    """(perm, inv, new_off, new_adj): degree-descending, ties by id; rows sorted."""
+    off, adj = _csr(off, adj)
+    n = off.shape[0] - 1
+    m = adj.shape[0]
+    perm = np.empty(max(n, 1), np.int32)
+    inv = np.empty(max(n, 1), np.int32)
+    noff = np.empty(n + 1, np.int32)
+    nadj = np.empty(max(m, 1), np.int32)
+    _L().oracle_relabel(n, _p(off), _p(adj), _p(perm), _p(inv), _p(noff), _p(nadj))
+    return perm[:n], inv[:n], noff, nadj[:m]
+
+
+def validate(off, adj, undirected: bool = True) -> int:
+    """0 if the CSR is valid, else a reason code (1 offsets, 2 range, 3 self-loop,
+    4 duplicate, 5 asymmetric)."""
+    off, adj = _csr(off, adj)
+    n = off.shape[0] - 1
+    return int(_L().oracle_validate_csr(n, adj.shape[0], _p(off), _p(adj), 1 if undirected else 0))
+
+
+# ---------------------------------------------------------------------------
+# Brute force: explicit enumeration of every shortest path (tiny graphs only).
+# ---------------------------------------------------------------------------
+
+def _bfs_dist(off, adj, s):
+    n = len(off) - 1
+    d = [-1] * n
+    d[s] = 0
+    q = deque([s])
+    while q:
+        v = q.popleft()
+        for e in range(off[v], off[v + 1]):
+            w = adj[e]
+            if d[w] < 0:
+                d[w] = d[v] + 1
+                q.append(w)
+    return d
+
+
+def shortest_paths(off, adj, s, t):
+    """Every shortest s-t path as a tuple of vertices (DFS over distance layers)."""
+    off = [int(x) for x in off]
+    adj = [int(x) for x in adj]
+    ds = _bfs_dist(off, adj, s)
+    if ds[t] < 0:
+        return []
+    dt = _bfs_dist(off, adj, t)
+    out = []
+
+    def walk(path):
+        v = path[-1]
+        if v == t:
+            out.append(tuple(path))
+            return
+        for e in range(off[v], off[v + 1]):
+            w = adj[e]
+            if ds[w] == ds[v] + 1 and dt[w] == dt[v] - 1:
+                path.append(w)
+                walk(path)
+                path.pop()
+
+    walk([s])
+    return out
+
+
+def brute_force_bc(off, adj, sources):
+    """Exact rational BC: sum over s in sources, t != s of (#paths through v)/(#paths)."""
+    n = len(off) - 1
+    res = [Fraction(0)] * n
+    for s in sources:
+        s = int(s)
+        for t in range(n):
+            if t == s:
+                continue
+            ps = shortest_paths(off, adj, s, t)
+            if not ps:
+                continue
+            cnt = [0] * n
+            for p in ps:
+                for v in p[1:-1]:
+                    cnt[v] += 1
+            for v in range(n):
+                if cnt[v]:
+                    res[v] += Fraction(cnt[v], len(ps))
+    return res
+
+
+def brute_force_sigma(off, adj, s):
+    """(level, sigma) for one source by explicit path enumeration."""
+    n = len(off) - 1
+    level = [-1] * n
+    sigma = [0] * n
+    for t in range(n):
+        if t == s:
+            level[t], sigma[t] = 0, 1
+            continue
+        ps = shortest_paths(off, adj, s, t)
+        if ps:
+            level[t] = len(ps[0]) - 1
+            sigma[t] = len(ps)
+    return level, sigma
