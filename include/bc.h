@@ -1,0 +1,170 @@
+/*
+ * libbc -- exact betweenness centrality (Brandes) on one NVIDIA B300 (sm_103a).
+ *
+ * The operation is the paper's computeBC (Appendix A, BC listing): for each
+ * source s in a list, a level-synchronous BFS from s counts shortest paths
+ * (sigma, the iterateInBFS body), then a reverse level-by-level sweep over the
+ * BFS DAG accumulates the dependency
+ *     delta_s(v) = sum over DAG successors w of (sigma_v / sigma_w)(1 + delta_s(w))
+ * (the iterateInReverse body), and BC(v) += delta_s(v) for every v != s.
+ * The graph is undirected, unweighted, given as int32 CSR (Section 3.1: the
+ * backend keeps graphs in CSR).  The result is the raw sum over the listed
+ * sources: no halving for undirected graphs, no normalisation, no
+ * extrapolation from sampled sources.  A source listed twice counts twice.
+ *
+ * Numerics: path counts are exact unsigned 64-bit integers (exact to 2^64);
+ * counts beyond 2^64 switch the batch to an extended-range form (64-bit
+ * mantissa, 32-bit exponent).  delta and BC are IEEE double.  BC_W_SIGMA_INEXACT
+ * reports that some count reached 2^53 (the double conversion in the backward
+ * sweep then rounds).  Results are deterministic: every sum runs in a fixed
+ * order (CSR row order, in fixed 1024-arc chunks; sources in list order).
+ *
+ * Threading: a bc_graph may be used by one host thread at a time for
+ * bc_compute / bc_debug_source; bc_batch_submit / bc_poll are thread-safe.
+ * Error detail: bc_last_error() returns a thread-local message for the last
+ * failing call on the calling thread.
+ */
+#ifndef LIBBC_BC_H
+#define LIBBC_BC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t / CUstream (0 = the legacy default stream). */
+typedef struct CUstream_st* bc_stream_t;
+
+typedef struct bc_graph bc_graph;
+typedef uint64_t bc_job;
+
+typedef enum {
+    BC_OK = 0,
+    BC_PENDING = 1,            /* bc_poll: job not finished yet */
+    BC_W_SIGMA_INEXACT = 2,    /* finished; some path count >= 2^53, so delta used a rounded count */
+    BC_E_INVALID_ARG = -1,     /* null pointer, negative size, unknown flag or option value */
+    BC_E_INVALID_GRAPH = -2,   /* offsets not monotone / offsets[0] != 0 / offsets[n] != m, index out of
+                                  range, self-loop, duplicate arc, or an arc without its reverse */
+    BC_E_SOURCE = -3,          /* a source id outside [0, n) */
+    BC_E_NOMEM = -4,           /* device allocation failed (allocator hook returned NULL) */
+    BC_E_TIMEOUT = -5,         /* a bounded device wait (grid barrier) ran out; results not written */
+    BC_E_CUDA = -6,            /* a CUDA runtime call failed; bc_last_error() has the CUDA message */
+    BC_E_SIGMA_RANGE = -7,     /* a path count exceeded even the extended range (2^(2^31)) */
+    BC_E_LIMIT = -8            /* a size limit: BFS depth > 65534 levels, or n/m beyond int32 */
+} bc_status;
+
+/* bc_graph_create flags */
+#define BC_UNDIRECTED 1u        /* required: the CSR must be symmetric */
+#define BC_INPUT_ON_DEVICE 2u   /* offsets/indices are device pointers (else host pointers) */
+#define BC_SKIP_VALIDATION 4u   /* trust the input (self-loops/duplicates/asymmetry unchecked) */
+
+/*
+ * Device memory hook.  alloc(bytes, stream, ctx) returns device memory or NULL;
+ * free(ptr, stream, ctx) releases it.  Passing alloc = free = NULL restores the
+ * default (cudaMallocAsync / cudaFreeAsync on the given stream).  Applies to
+ * allocations made after the call; memory is released with the hook that
+ * allocated it.
+ */
+typedef void* (*bc_alloc_fn)(size_t bytes, bc_stream_t stream, void* ctx);
+typedef void (*bc_free_fn)(void* ptr, bc_stream_t stream, void* ctx);
+bc_status bc_set_allocator(bc_alloc_fn alloc, bc_free_fn free_fn, void* ctx);
+
+/*
+ * Ingest (paper Section 3.1: CSR graph copied to the device once).
+ * offsets[n+1], indices[m] (int32, host or device per flags) are copied; the
+ * caller keeps ownership.  On the device the graph is validated, relabelled
+ * by degree (descending, ties by original id) and stored with every row
+ * sorted ascending.  Blocks until the graph is ready.  n may be 0.
+ */
+bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_t n, int64_t m,
+                          uint32_t flags, bc_stream_t stream, bc_graph** out);
+bc_status bc_graph_destroy(bc_graph* g);
+
+/* Size facts of an ingested graph (any pointer may be NULL). */
+bc_status bc_graph_info(const bc_graph* g, int32_t* n, int64_t* m, int32_t* max_degree,
+                        int32_t* n_nonisolated);
+
+/*
+ * The relabelled graph, copied to HOST buffers: perm[n] (perm[r] = original id
+ * of new id r), offsets[n+1], indices[m] (new ids, rows sorted).  Any pointer
+ * may be NULL.  For inspection and tests.
+ */
+bc_status bc_graph_export(const bc_graph* g, int32_t* perm, int32_t* offsets, int32_t* indices);
+
+/* Tuning knobs; zero-initialise and set what you need (0 = automatic). */
+typedef struct {
+    int32_t batch_width;     /* sources per traversal: 1 (plain per-source), 32, 64 or 128; 0 = auto */
+    int32_t direction;       /* 0 = auto push/pull switching, 1 = push only, 2 = pull only */
+    float alpha;             /* switch to pull when frontier arcs * alpha > unvisited arcs (0 = 14) */
+    float beta;              /* back to push when frontier vertices * beta < non-isolated vertices (0 = 24) */
+    int32_t heavy_degree;    /* rows above this degree are processed by a whole thread block (0 = 4096) */
+    int32_t blocks_per_sm;   /* persistent-grid residency (0 = occupancy maximum, capped at 4) */
+    int64_t barrier_budget;  /* device cycles a grid-barrier wait may spin before BC_E_TIMEOUT
+                                (0 = about 20 s; tests may set 1 to force a timeout) */
+} bc_options;
+
+/*
+ * BC over a source list (paper Appendix A, computeBC; sources in ORIGINAL ids,
+ * host or device pointer).  out_bc: device array of n doubles, overwritten,
+ * in original ids.  Work is ordered on `stream`; the call returns after the
+ * results are final (it reads a device status word).  nsrc == 0 writes zeros.
+ * Returns BC_OK or BC_W_SIGMA_INEXACT on success.
+ */
+bc_status bc_compute(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc,
+                     bc_stream_t stream);
+bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc,
+                        bc_stream_t stream, const bc_options* opt);
+
+/* Per-call facts of the last bc_compute / bc_compute_ex on this graph. */
+typedef struct {
+    int32_t batch_width;     /* width used */
+    int32_t batches;         /* traversals run */
+    int32_t max_levels;      /* deepest BFS (levels, source = level 0) */
+    int32_t pull_levels;     /* forward levels run in pull (bottom-up) form, summed over batches */
+    int32_t push_levels;     /* forward levels run in push (top-down) form */
+    int32_t ext_batches;     /* batches rerun in the extended-range path-count form */
+    int32_t grid_blocks;     /* persistent grid size */
+    int32_t kernel_launches; /* kernels launched by the call */
+} bc_run_stats;
+bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
+
+/*
+ * Serving: continuous batching over resident graphs.  bc_batch_submit queues a
+ * job (sources copied from host memory at submit time; out_bc is a device
+ * array of n doubles that must stay alive until bc_poll returns a final
+ * status).  Jobs are admitted as execution slots and device memory free up;
+ * admitted jobs run concurrently on their own streams.  bc_poll returns
+ * BC_PENDING until done, then the job's final status once, releasing the id.
+ * A job's result is bitwise the same whether it runs alone or among others.
+ */
+bc_status bc_batch_submit(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc,
+                          bc_job* job);
+bc_status bc_poll(bc_job job);
+/* As bc_poll; on a final status also writes the job's submit-to-completion time in seconds. */
+bc_status bc_poll_ex(bc_job job, double* latency_s);
+/* Blocks until the job is final (timeout_ms < 0: no limit; when it passes: BC_PENDING), then
+ * returns and releases like bc_poll. */
+bc_status bc_wait(bc_job job, int64_t timeout_ms);
+bc_status bc_wait_ex(bc_job job, int64_t timeout_ms, double* latency_s);
+/* Serving facts: jobs admitted concurrently at peak, total completed. */
+bc_status bc_server_stats(int32_t* peak_concurrency, int64_t* completed);
+/* Slots (concurrent jobs) and device-memory budget for admission (bytes; 0 = 80% of free). */
+bc_status bc_server_config(int32_t slots, int64_t memory_budget);
+
+/*
+ * Test/inspection: levels and path counts of ONE source (original id) in
+ * original ids.  level[v] = BFS depth or -1; sigma(v) = sigma_mant[v] *
+ * 2^sigma_exp[v] exactly when the count is below 2^53 (mantissa in [0.5,1)).
+ * Host output buffers of n entries; any may be NULL.
+ */
+bc_status bc_debug_source(bc_graph* g, int32_t s, int32_t* level, double* sigma_mant, int32_t* sigma_exp);
+
+const char* bc_status_string(bc_status st);
+const char* bc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBBC_BC_H */

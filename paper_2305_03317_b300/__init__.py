@@ -1,0 +1,250 @@
+"""Python binding of libbc (exact Brandes betweenness centrality on one B300).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libbc.so`` built from ``csrc/`` (see ``include/bc.h`` for the C ABI,
+whose names this module mirrors).  PyTorch provides device memory for outputs
+and the CUDA stream handles.  There is no fallback: if the library is missing
+or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbc.so")
+
+BC_OK = 0
+BC_PENDING = 1
+BC_W_SIGMA_INEXACT = 2
+BC_E_INVALID_ARG = -1
+BC_E_INVALID_GRAPH = -2
+BC_E_SOURCE = -3
+BC_E_NOMEM = -4
+BC_E_TIMEOUT = -5
+BC_E_CUDA = -6
+BC_E_SIGMA_RANGE = -7
+BC_E_LIMIT = -8
+
+BC_UNDIRECTED = 1
+BC_INPUT_ON_DEVICE = 2
+BC_SKIP_VALIDATION = 4
+
+_lib = None
+
+
+class BCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status) if _lib else status}: {msg}")
+        self.status = status
+
+
+class bc_options(ctypes.Structure):
+    _fields_ = [("batch_width", ctypes.c_int32), ("direction", ctypes.c_int32), ("alpha", ctypes.c_float),
+                ("beta", ctypes.c_float), ("heavy_degree", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("barrier_budget", ctypes.c_int64)]
+
+
+class bc_run_stats(ctypes.Structure):
+    _fields_ = [("batch_width", ctypes.c_int32), ("batches", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("pull_levels", ctypes.c_int32), ("push_levels", ctypes.c_int32), ("ext_batches", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32)]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libbc.so and declare its signatures (raises if the file is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbc.so not built ({path}); run python -m paper_2305_03317_b300.build")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+    st = ctypes.c_int
+    sig = {
+        "bc_set_allocator": [P, P, P],
+        "bc_graph_create": [P, P, i32, i64, u32, P, ctypes.POINTER(P)],
+        "bc_graph_destroy": [P],
+        "bc_graph_info": [P, P, P, P, P],
+        "bc_graph_export": [P, P, P, P],
+        "bc_compute": [P, P, i32, P, P],
+        "bc_compute_ex": [P, P, i32, P, P, ctypes.POINTER(bc_options)],
+        "bc_last_run_stats": [P, ctypes.POINTER(bc_run_stats)],
+        "bc_batch_submit": [P, P, i32, P, ctypes.POINTER(u64)],
+        "bc_poll": [u64],
+        "bc_poll_ex": [u64, ctypes.POINTER(ctypes.c_double)],
+        "bc_wait": [u64, i64],
+        "bc_wait_ex": [u64, i64, ctypes.POINTER(ctypes.c_double)],
+        "bc_server_stats": [P, P],
+        "bc_server_config": [i32, i64],
+        "bc_debug_source": [P, i32, P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = st
+    lib.bc_status_string.argtypes = [st]
+    lib.bc_status_string.restype = ctypes.c_char_p
+    lib.bc_last_error.argtypes = []
+    lib.bc_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load().bc_status_string(s).decode()
+
+
+def last_error() -> str:
+    return load().bc_last_error().decode()
+
+
+def _check(s: int, allow=(BC_OK, BC_W_SIGMA_INEXACT)) -> int:
+    if s not in allow:
+        raise BCError(s, last_error())
+    return s
+
+
+def _ptr(x) -> int:
+    """Data pointer of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def server_config(slots: int = 4, memory_budget: int = 0) -> None:
+    _check(load().bc_server_config(slots, memory_budget))
+
+
+def server_stats():
+    peak = ctypes.c_int32()
+    done = ctypes.c_int64()
+    _check(load().bc_server_stats(ctypes.byref(peak), ctypes.byref(done)))
+    return int(peak.value), int(done.value)
+
+
+@dataclass
+class Job:
+    id: int
+    graph: "Graph"
+    out: object
+    sources: np.ndarray
+
+    def poll(self):
+        """None while pending, else (status, latency_seconds)."""
+        lat = ctypes.c_double()
+        s = load().bc_poll_ex(self.id, ctypes.byref(lat))
+        if s == BC_PENDING:
+            return None
+        _check(s)
+        return s, float(lat.value)
+
+    def wait(self, timeout_ms: int = -1):
+        lat = ctypes.c_double()
+        s = load().bc_wait_ex(self.id, timeout_ms, ctypes.byref(lat))
+        if s == BC_PENDING:
+            return None
+        _check(s)
+        return s, float(lat.value)
+
+
+class Graph:
+    """A graph resident on the device (relabelled CSR; see bc_graph_create)."""
+
+    def __init__(self, off, adj, validate: bool = True, stream=None):
+        lib = load()
+        self._h = ctypes.c_void_p()
+        flags = BC_UNDIRECTED | (0 if validate else BC_SKIP_VALIDATION)
+        if isinstance(off, np.ndarray):
+            off = np.ascontiguousarray(off, dtype=np.int32)
+            adj = np.ascontiguousarray(adj, dtype=np.int32)
+            self._keep = (off, adj)
+            n, m = off.shape[0] - 1, adj.shape[0]
+        else:  # torch tensors on the device
+            flags |= BC_INPUT_ON_DEVICE
+            n, m = off.numel() - 1, adj.numel()
+            self._keep = (off, adj)
+        st = _stream_handle(stream) if _has_cuda() else 0
+        _check(lib.bc_graph_create(_ptr(off), _ptr(adj) if m > 0 else None, n, m, flags, st,
+                                   ctypes.byref(self._h)))
+        self._keep = None
+        n_, m_, md, nnz = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.bc_graph_info(self._h, ctypes.byref(n_), ctypes.byref(m_), ctypes.byref(md), ctypes.byref(nnz)))
+        self.n, self.m, self.max_degree, self.n_nonisolated = n_.value, m_.value, md.value, nnz.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().bc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compute(self, sources, out=None, stream=None, batch_width: int = 0, direction: int = 0,
+                alpha: float = 0.0, beta: float = 0.0, heavy_degree: int = 0, blocks_per_sm: int = 0,
+                barrier_budget: int = 0):
+        """BC over ``sources`` (host numpy or device int32 tensor). Returns (out, status)."""
+        import torch
+        if out is None:
+            out = torch.empty(max(self.n, 1), dtype=torch.float64, device="cuda")[: self.n]
+        if isinstance(sources, np.ndarray):
+            sources = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc = int(sources.shape[0]) if isinstance(sources, np.ndarray) else int(sources.numel())
+        opt = bc_options(batch_width, direction, alpha, beta, heavy_degree, blocks_per_sm, barrier_budget)
+        s = load().bc_compute_ex(self._h, _ptr(sources) if nsrc else None, nsrc, _ptr(out) if self.n else None,
+                                 _stream_handle(stream), ctypes.byref(opt))
+        _check(s)
+        return out, s
+
+    def stats(self) -> dict:
+        st = bc_run_stats()
+        _check(load().bc_last_run_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def export(self):
+        perm = np.empty(max(self.n, 1), np.int32)
+        off = np.empty(self.n + 1, np.int32)
+        adj = np.empty(max(self.m, 1), np.int32)
+        _check(load().bc_graph_export(self._h, perm.ctypes.data, off.ctypes.data, adj.ctypes.data))
+        return perm[: self.n], off, adj[: self.m]
+
+    def debug_source(self, s: int):
+        """(level int32[n], sigma_mant float64[n], sigma_exp int32[n]) for one source."""
+        lev = np.empty(max(self.n, 1), np.int32)
+        mant = np.empty(max(self.n, 1), np.float64)
+        ex = np.empty(max(self.n, 1), np.int32)
+        r = load().bc_debug_source(self._h, int(s), lev.ctypes.data, mant.ctypes.data, ex.ctypes.data)
+        _check(r)
+        return lev[: self.n], mant[: self.n], ex[: self.n], r
+
+    def submit(self, sources, out) -> Job:
+        """Queue a serving job (host sources); ``out`` is a device float64 tensor of n."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        jid = ctypes.c_uint64()
+        _check(load().bc_batch_submit(self._h, src.ctypes.data if src.size else None, int(src.size),
+                                      _ptr(out) if self.n else None, ctypes.byref(jid)))
+        return Job(int(jid.value), self, out, src)
+
+
+def _has_cuda() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+__all__ = ["Graph", "Job", "BCError", "load", "status_string", "last_error", "server_config", "server_stats"]

@@ -1,0 +1,916 @@
+// libbc host runtime: the C ABI declared in include/bc.h.
+//
+// Owns graph lifetime (device-resident relabelled CSR), per-graph workspaces
+// sized for a batch width, the batching of a source list into traversals of
+// K columns, and the launch of the persistent kernel.  No computation of the
+// method happens on the host: it only marshals sizes, pointers and statuses.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/bc.h"
+#include "bc_internal.cuh"
+
+using namespace bcx;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_err;
+
+static bc_status fail(bc_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+static bc_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(BC_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ allocator hook
+struct AllocHook {
+    bc_alloc_fn alloc = nullptr;
+    bc_free_fn free_fn = nullptr;
+    void* ctx = nullptr;
+};
+static std::mutex g_alloc_mu;
+static AllocHook g_hook;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    AllocHook hook;  // the hook that allocated it
+};
+
+static void* dev_alloc_raw(size_t bytes, cudaStream_t st, AllocHook* used) {
+    AllocHook h;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        h = g_hook;
+    }
+    if (used) *used = h;
+    if (bytes == 0) bytes = 16;
+    if (h.alloc) return h.alloc(bytes, (bc_stream_t)st, h.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void dev_free_raw(void* p, cudaStream_t st, const AllocHook& h) {
+    if (!p) return;
+    if (h.alloc) {
+        if (h.free_fn) h.free_fn(p, (bc_stream_t)st, h.ctx);
+    } else {
+        cudaFreeAsync(p, st);
+    }
+}
+
+// for ingest (plain function pointers; the hook in force at the call is used)
+static void* ingest_alloc(size_t b, cudaStream_t st) { return dev_alloc_raw(b, st, nullptr); }
+static void ingest_free(void* p, cudaStream_t st) {
+    AllocHook h;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        h = g_hook;
+    }
+    dev_free_raw(p, st, h);
+}
+
+static bool buf_ensure(DevBuf& b, size_t bytes, cudaStream_t st) {
+    if (b.p && b.bytes >= bytes) return true;
+    if (b.p) dev_free_raw(b.p, st, b.hook);
+    b.p = dev_alloc_raw(bytes, st, &b.hook);
+    b.bytes = b.p ? bytes : 0;
+    return b.p != nullptr;
+}
+
+static void buf_release(DevBuf& b, cudaStream_t st) {
+    if (b.p) dev_free_raw(b.p, st, b.hook);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// ------------------------------------------------------------------ graph
+struct Workspace {
+    int K = 0;
+    int n_heavy = -1;
+    bool has_ext = false;
+    DevBuf V, F[3], lvl, sig, sig_e, rho, rho_e, ent, hent, stamp;
+    DevBuf cnt, hcnt, start, hstart, dsum, fulldeg, ctl, bstat, bc, src, bad, jobptr, coljob;
+    long long cap = 0, hcap = 0;
+    void release(cudaStream_t st) {
+        DevBuf* all[] = {&V, &F[0], &F[1], &F[2], &lvl, &sig, &sig_e, &rho, &rho_e, &ent, &hent, &stamp,
+                         &cnt, &hcnt, &start, &hstart, &dsum, &fulldeg, &ctl, &bstat, &bc, &src, &bad,
+                         &jobptr, &coljob};
+        for (DevBuf* b : all) buf_release(*b, st);
+    }
+    size_t bytes() const {
+        const DevBuf* all[] = {&V, &F[0], &F[1], &F[2], &lvl, &sig, &sig_e, &rho, &rho_e, &ent, &hent, &stamp,
+                               &cnt, &hcnt, &start, &hstart, &dsum, &fulldeg, &ctl, &bstat, &bc, &src, &bad,
+                               &jobptr, &coljob};
+        size_t t = 0;
+        for (const DevBuf* b : all) t += b->bytes;
+        return t;
+    }
+};
+
+// Bytes a workspace needs for n vertices at width K (plus the extended arrays).
+static size_t ws_need(int n, int K, int n_heavy, bool ext, int nbatch, int njobs) {
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    const int W = K >= 32 ? K / 32 : 1;
+    size_t b = 4 * sizeof(uint32_t) * nn * W + sizeof(uint16_t) * nn * K + 2 * sizeof(double) * nn * K;
+    if (ext) b += 2 * sizeof(int) * nn * K;
+    b += sizeof(int) * nn * K + sizeof(int) * (size_t)(n_heavy > 0 ? n_heavy : 1) * K + sizeof(int) * nn;
+    b += (4 * sizeof(int) + 2 * sizeof(long long)) * kLevelSlots + sizeof(Ctl);
+    b += sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * (1 + 2 * K) + sizeof(double) * nn;
+    b += sizeof(double*) * (size_t)(njobs > 0 ? njobs : 1);
+    return b;
+}
+
+struct bc_graph {
+    int n = 0;
+    long long m = 0;
+    int max_deg = 0;
+    int n_nz = 0;
+    DevBuf off, adj, perm, inv;
+    AllocHook hook;
+    std::mutex mu;
+    std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
+    bool sticky_ext = false;
+    bc_run_stats last{};
+    cudaStream_t last_stream = nullptr;
+};
+
+// ------------------------------------------------------------------ helpers
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int heavy_count(bc_graph* g, int threshold, cudaStream_t st, bc_status* err) {
+    // degrees are non-increasing in new ids: binary search over the offsets
+    // using a handful of device reads.
+    int lo = 0, hi = g->n_nz;  // first r with deg(r) <= threshold
+    const int* off = (const int*)g->off.p;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        int two[2];
+        cudaError_t e = cudaMemcpyAsync(two, off + mid, sizeof two, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            *err = cuda_fail(e, "heavy-row count");
+            return -1;
+        }
+        if (two[1] - two[0] > threshold) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+static bool ws_ensure(Workspace* w, int n_vert, int K, int n_heavy, bool ext, int nbatch, int njobs,
+                      cudaStream_t st) {
+    w->K = K;
+    const size_t n = (size_t)(n_vert > 0 ? n_vert : 1);
+    const int W = K >= 32 ? K / 32 : 1;
+    const long long cap = (long long)n * K;
+    const long long hcap = (long long)(n_heavy > 0 ? n_heavy : 1) * K;
+    const size_t nb = (size_t)(nbatch > 0 ? nbatch : 1);
+    bool ok = true;
+    ok &= buf_ensure(w->V, sizeof(uint32_t) * n * W, st);
+    for (int i = 0; i < 3; ++i) ok &= buf_ensure(w->F[i], sizeof(uint32_t) * n * W, st);
+    ok &= buf_ensure(w->lvl, sizeof(uint16_t) * n * K, st);
+    ok &= buf_ensure(w->sig, sizeof(unsigned long long) * n * K, st);
+    ok &= buf_ensure(w->rho, sizeof(double) * n * K, st);
+    if (ext) {
+        ok &= buf_ensure(w->sig_e, sizeof(int) * n * K, st);
+        ok &= buf_ensure(w->rho_e, sizeof(int) * n * K, st);
+    }
+    ok &= buf_ensure(w->ent, sizeof(int) * (size_t)cap, st);
+    ok &= buf_ensure(w->hent, sizeof(int) * (size_t)hcap, st);
+    ok &= buf_ensure(w->stamp, sizeof(int) * n, st);
+    ok &= buf_ensure(w->cnt, sizeof(int) * kLevelSlots, st);
+    ok &= buf_ensure(w->hcnt, sizeof(int) * kLevelSlots, st);
+    ok &= buf_ensure(w->start, sizeof(int) * kLevelSlots, st);
+    ok &= buf_ensure(w->hstart, sizeof(int) * kLevelSlots, st);
+    ok &= buf_ensure(w->dsum, sizeof(long long) * kLevelSlots, st);
+    ok &= buf_ensure(w->fulldeg, sizeof(long long) * kLevelSlots, st);
+    ok &= buf_ensure(w->ctl, sizeof(Ctl), st);
+    ok &= buf_ensure(w->bstat, sizeof(int) * nb, st);
+    ok &= buf_ensure(w->bc, sizeof(double) * n, st);
+    ok &= buf_ensure(w->src, sizeof(int) * nb * K, st);
+    ok &= buf_ensure(w->coljob, sizeof(int) * nb * K, st);
+    ok &= buf_ensure(w->bad, sizeof(int), st);
+    ok &= buf_ensure(w->jobptr, sizeof(double*) * (size_t)(njobs > 0 ? njobs : 1), st);
+    if (!ok) {
+        fail(BC_E_NOMEM, "device allocation failed for a batch-width-%d workspace (n=%d)", K, n_vert);
+        return false;
+    }
+    w->cap = cap;
+    w->hcap = hcap;
+    w->n_heavy = n_heavy;
+    w->has_ext = w->sig_e.p != nullptr;
+    return true;
+}
+
+static KParams make_params(bc_graph* g, Workspace* w, int n_heavy, int nbatch, const bc_options& o, bool ext) {
+    KParams p;
+    memset(&p, 0, sizeof p);
+    p.n = g->n;
+    p.n_nz = g->n_nz;
+    p.n_heavy = n_heavy;
+    p.m_nz = g->m;
+    p.off = (const int*)g->off.p;
+    p.adj = (const int*)g->adj.p;
+    p.src = (const int*)w->src.p;
+    p.nbatch = nbatch;
+    p.V = (uint32_t*)w->V.p;
+    for (int i = 0; i < 3; ++i) p.F[i] = (uint32_t*)w->F[i].p;
+    p.lvl = (uint16_t*)w->lvl.p;
+    p.sig = (unsigned long long*)w->sig.p;
+    p.sig_e = (int*)w->sig_e.p;
+    p.rho = (double*)w->rho.p;
+    p.rho_e = (int*)w->rho_e.p;
+    p.ent = (int*)w->ent.p;
+    p.hent = (int*)w->hent.p;
+    p.cap = w->cap;
+    p.hcap = w->hcap;
+    p.stamp = (int*)w->stamp.p;
+    p.la.cnt = (int*)w->cnt.p;
+    p.la.hcnt = (int*)w->hcnt.p;
+    p.la.start = (int*)w->start.p;
+    p.la.hstart = (int*)w->hstart.p;
+    p.la.dsum = (long long*)w->dsum.p;
+    p.la.fulldeg = (long long*)w->fulldeg.p;
+    p.ctl = (Ctl*)w->ctl.p;
+    p.batch_status = (int*)w->bstat.p;
+    p.job_bc = (double* const*)w->jobptr.p;
+    p.col_job = nullptr;
+    p.direction = o.direction;
+    p.alpha = o.alpha > 0 ? o.alpha : 14.0f;
+    p.beta = o.beta > 0 ? o.beta : 24.0f;
+    p.budget = o.barrier_budget > 0 ? o.barrier_budget : 40000000000ll;
+    p.ext = ext ? 1 : 0;
+    p.forward_only = 0;
+    return p;
+}
+
+static int choose_width(int n, int nsrc, int requested) {
+    if (requested > 0) return requested;
+    // automatic: wide batches amortise row reads over more sources; keep the
+    // per-batch state within a few GB and do not pad tiny requests.
+    if (nsrc <= 1) return 1;
+    if (nsrc <= 32) return 32;
+    const double bytes128 = (double)n * 128 * 20;
+    if (nsrc >= 256 && bytes128 < 16e9) return 128;
+    return 64;
+}
+
+static bc_status check_opts(const bc_options& o) {
+    if (o.batch_width != 0 && o.batch_width != 1 && o.batch_width != 32 && o.batch_width != 64 &&
+        o.batch_width != 128)
+        return fail(BC_E_INVALID_ARG, "batch_width must be 0, 1, 32, 64 or 128 (got %d)", o.batch_width);
+    if (o.direction < 0 || o.direction > 2) return fail(BC_E_INVALID_ARG, "direction must be 0, 1 or 2");
+    if (o.heavy_degree < 0 || o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0)
+        return fail(BC_E_INVALID_ARG, "negative option value");
+    return BC_OK;
+}
+
+static int grid_blocks(int K, int blocks_per_sm, int share) {
+    int per_sm = 0;
+    const int maxb = max_coop_blocks(K, &per_sm);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int bps = blocks_per_sm > 0 ? blocks_per_sm : (per_sm < 4 ? per_sm : 4);
+    if (bps > per_sm) bps = per_sm;
+    int blocks = bps * sms;
+    if (blocks > maxb) blocks = maxb;
+    if (share > 1) blocks = blocks / share;
+    return blocks;
+}
+
+// One traversal run of a source list (original ids, device) on workspace w:
+// map sources, launch the persistent kernel over all batches, read the status.
+// job_bc buffers (relabelled, one per job) are accumulated, not cleared.
+struct RunOut {
+    bool need_ext = false;
+    bool inexact = false;
+    Ctl ctl{};
+};
+
+static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int nsrc, int K, int n_heavy, int blocks,
+                          const bc_options& o, bool ext, const std::vector<double*>& job_bc,
+                          const std::vector<int>* col_job, bool forward_only, cudaStream_t st, RunOut* ro) {
+    const int nbatch = (nsrc + K - 1) / K;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w->bad.p, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_map_sources(d_src_orig, nsrc, (const int*)g->inv.p, g->n, K, (int*)w->src.p, nbatch,
+                                (int*)w->bad.p, st)) != cudaSuccess)
+        return cuda_fail(e, "map sources");
+    if ((e = cudaMemcpyAsync(w->jobptr.p, job_bc.data(), sizeof(double*) * job_bc.size(), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+        return cuda_fail(e, "job table");
+    if (col_job && (e = cudaMemcpyAsync(w->coljob.p, col_job->data(), sizeof(int) * col_job->size(),
+                                        cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "column table");
+    int bad = 0;
+    if ((e = cudaMemcpyAsync(&bad, w->bad.p, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "source check");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "source check");
+    if (bad) return fail(BC_E_SOURCE, "a source id is outside [0, %d)", g->n);
+    if ((e = cudaMemsetAsync(w->ctl.p, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(w->bstat.p, 0, sizeof(int) * nbatch, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    KParams p = make_params(g, w, n_heavy, nbatch, o, ext);
+    p.forward_only = forward_only ? 1 : 0;
+    if (col_job) p.col_job = (const int*)w->coljob.p;
+    if ((e = launch_batches(K, p, blocks, st)) != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+    std::vector<int> bst(nbatch);
+    if ((e = cudaMemcpyAsync(&ro->ctl, w->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    if ((e = cudaMemcpyAsync(bst.data(), w->bstat.p, sizeof(int) * nbatch, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+        return cuda_fail(e, "status read");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "persistent kernel");
+    const Ctl& ctl = ro->ctl;
+    if (ctl.err & ERR_TIMEOUT) return fail(BC_E_TIMEOUT, "a grid-barrier wait exceeded its cycle budget");
+    if (ctl.err & ERR_LIMIT) return fail(BC_E_LIMIT, "BFS deeper than %d levels", kMaxLevel);
+    if (ctl.err & ERR_CAPACITY) return fail(BC_E_CUDA, "internal: level-list capacity exceeded");
+    if (ctl.err) return fail(BC_E_CUDA, "internal device error 0x%x", ctl.err);
+    ro->need_ext = false;
+    ro->inexact = false;
+    for (int b = 0; b < nbatch; ++b) {
+        if (bst[b] & BST_NEED_EXT) ro->need_ext = true;
+        else if (!(bst[b] & BST_DONE)) return fail(BC_E_CUDA, "internal: batch %d not completed", b);
+        if (bst[b] & BST_INEXACT) ro->inexact = true;
+    }
+    return BC_OK;
+}
+
+// A full call: batches of K, extended-form rerun when a count overflows 64
+// bits, accumulation into job buffers.  `zero` clears each job buffer first.
+static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc, const bc_options& o, int blocks_share,
+                          const std::vector<double*>& job_bc, const std::vector<int>* col_job, bool forward_only,
+                          cudaStream_t st, bc_run_stats* stats, int* K_out, int* nheavy_out, bool* ext_out) {
+    const int K = choose_width(g->n, nsrc, o.batch_width);
+    const int nbatch = (nsrc + K - 1) / K;
+    const int heavy_thr = o.heavy_degree > 0 ? o.heavy_degree : 4096;
+    bc_status err = BC_OK;
+    const int n_heavy = heavy_count(g, heavy_thr, st, &err);
+    if (n_heavy < 0) return err;
+    const int blocks = grid_blocks(K, o.blocks_per_sm, blocks_share);
+    if (blocks < 1) return fail(BC_E_CUDA, "persistent kernel cannot be resident (occupancy 0)");
+    bool ext = g->sticky_ext;
+    bc_run_stats s{};
+    s.batch_width = K;
+    s.batches = nbatch;
+    s.grid_blocks = blocks;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (!ws_ensure(w, g->n, K, n_heavy, ext, nbatch, (int)job_bc.size(), st)) return BC_E_NOMEM;
+        for (double* jb : job_bc) {
+            cudaError_t e = cudaMemsetAsync(jb, 0, sizeof(double) * (size_t)(g->n > 0 ? g->n : 1), st);
+            if (e != cudaSuccess) return cuda_fail(e, "memset");
+        }
+        RunOut ro;
+        bc_status r = run_core(g, w, d_src, nsrc, K, n_heavy, blocks, o, ext, job_bc, col_job, forward_only, st, &ro);
+        if (r != BC_OK) return r;
+        s.kernel_launches += 2;
+        s.max_levels = ro.ctl.max_levels;
+        s.pull_levels += ro.ctl.pull_levels;
+        s.push_levels += ro.ctl.push_levels;
+        if (ro.need_ext && !ext) {
+            // rerun the whole call in the extended form, so that every source is
+            // accumulated in list order exactly as in a single pass
+            ext = true;
+            g->sticky_ext = true;
+            continue;
+        }
+        if (ro.need_ext) return fail(BC_E_SIGMA_RANGE, "path count beyond the extended range");
+        if (ext) s.ext_batches = nbatch;
+        if (stats) *stats = s;
+        if (K_out) *K_out = K;
+        if (nheavy_out) *nheavy_out = n_heavy;
+        if (ext_out) *ext_out = ext;
+        return ro.inexact ? BC_W_SIGMA_INEXACT : BC_OK;
+    }
+    return fail(BC_E_CUDA, "internal: extended rerun did not settle");
+}
+
+// ------------------------------------------------------------------ serving
+// Continuous batching: worker threads (one CUDA stream and one workspace each)
+// take queued jobs in arrival order as soon as a worker is free and the
+// device-memory budget admits its workspace; small jobs queued on the same
+// graph are packed into the same traversal (their columns side by side).
+namespace {
+
+struct Job {
+    bc_job id = 0;
+    bc_graph* g = nullptr;
+    std::vector<int> src;
+    double* out = nullptr;
+    bc_status result = BC_PENDING;
+    bool done = false;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+struct Server {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Job>> queue;
+    std::map<bc_job, std::shared_ptr<Job>> jobs;
+    std::vector<std::thread> workers;
+    int slots = 4;
+    long long budget = 0;  // bytes; 0 = decided at start
+    long long reserved = 0;
+    int running = 0, peak = 0;
+    long long completed = 0;
+    bc_job next_id = 1;
+    bool started = false;
+    int pack_limit = 256;  // sources per packed traversal
+};
+
+Server& server() {
+    static Server* s = new Server();  // never destroyed: workers may outlive static teardown
+    return *s;
+}
+
+void worker_main(int slot) {
+    Server& S = server();
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    Workspace ws;
+    DevBuf dsrc, jobbufs;
+    long long my_reserved = 0;
+    for (;;) {
+        std::vector<std::shared_ptr<Job>> batch;
+        long long grow = 0;
+        {
+            std::unique_lock<std::mutex> lk(S.mu);
+            for (;;) {
+                // first admissible job in arrival order
+                size_t lead = S.queue.size();
+                for (size_t i = 0; i < S.queue.size(); ++i) {
+                    const auto& j = S.queue[i];
+                    const int K = choose_width(j->g->n, (int)j->src.size(), 0);
+                    const long long need =
+                        (long long)ws_need(j->g->n, K, j->g->n_nz, j->g->sticky_ext, 64, 64) +
+                        (long long)sizeof(double) * j->g->n * 64;
+                    grow = need > my_reserved ? need - my_reserved : 0;
+                    if (S.reserved + grow <= S.budget || S.running == 0) { lead = i; break; }
+                }
+                if (lead < S.queue.size()) {
+                    auto L = S.queue[lead];
+                    batch.push_back(L);
+                    S.queue.erase(S.queue.begin() + (long)lead);
+                    int total = (int)L->src.size();
+                    for (size_t i = 0; i < S.queue.size() && total < S.pack_limit && batch.size() < 64;) {
+                        auto& j = S.queue[i];
+                        if (j->g == L->g && total + (int)j->src.size() <= S.pack_limit) {
+                            total += (int)j->src.size();
+                            batch.push_back(j);
+                            S.queue.erase(S.queue.begin() + (long)i);
+                        } else {
+                            ++i;
+                        }
+                    }
+                    S.reserved += grow;
+                    my_reserved += grow;
+                    S.running++;
+                    if (S.running > S.peak) S.peak = S.running;
+                    break;
+                }
+                S.cv_work.wait(lk);
+            }
+        }
+        // run the packed jobs
+        bc_graph* g = batch[0]->g;
+        std::vector<int> all;
+        std::vector<int> owner;  // job index per source
+        for (size_t j = 0; j < batch.size(); ++j) {
+            all.insert(all.end(), batch[j]->src.begin(), batch[j]->src.end());
+            owner.insert(owner.end(), batch[j]->src.size(), (int)j);
+        }
+        const int nsrc = (int)all.size();
+        bc_options o;
+        memset(&o, 0, sizeof o);
+        const int K = choose_width(g->n, nsrc, 0);
+        const int nbatch = (nsrc + K - 1) / K;
+        std::vector<int> col_job((size_t)nbatch * K, 0);
+        for (int i = 0; i < nbatch * K; ++i) col_job[i] = i < nsrc ? owner[i] : (int)batch.size() - 1;
+        bc_status r = BC_OK;
+        const size_t nn = (size_t)(g->n > 0 ? g->n : 1);
+        if (!buf_ensure(dsrc, sizeof(int) * (size_t)nsrc, st) ||
+            !buf_ensure(jobbufs, sizeof(double) * nn * batch.size(), st)) {
+            r = fail(BC_E_NOMEM, "serving buffers");
+        }
+        if (r == BC_OK) {
+            cudaError_t e = cudaMemcpyAsync(dsrc.p, all.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) r = cuda_fail(e, "source copy");
+        }
+        std::vector<double*> jb;
+        for (size_t j = 0; j < batch.size(); ++j) jb.push_back((double*)jobbufs.p + nn * j);
+        if (r == BC_OK) {
+            std::lock_guard<std::mutex> glk(g->mu);
+            r = run_jobs(g, &ws, (const int*)dsrc.p, nsrc, o, S.slots, jb, &col_job, false, st, nullptr, nullptr,
+                         nullptr, nullptr);
+        }
+        if (r >= 0) {
+            for (size_t j = 0; j < batch.size(); ++j) {
+                cudaError_t e = launch_unpermute(jb[j], (const int*)g->inv.p, batch[j]->out, g->n, st);
+                if (e != cudaSuccess) { r = cuda_fail(e, "unpermute"); break; }
+            }
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess && r >= 0) r = cuda_fail(e, "serving run");
+        }
+        const long long have = (long long)(ws.bytes() + dsrc.bytes + jobbufs.bytes);
+        {
+            std::lock_guard<std::mutex> lk(S.mu);
+            const auto now = std::chrono::steady_clock::now();
+            for (auto& j : batch) {
+                j->result = r;
+                j->done = true;
+                j->t_done = now;
+            }
+            S.running--;
+            S.completed += (long long)batch.size();
+            S.reserved += have - my_reserved;
+            my_reserved = have;
+        }
+        S.cv_done.notify_all();
+        S.cv_work.notify_all();
+        (void)slot;
+    }
+}
+
+void server_start_locked(Server& S) {
+    if (S.started) return;
+    if (S.budget <= 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        S.budget = (long long)(0.8 * (double)fr);
+    }
+    for (int i = 0; i < S.slots; ++i) {
+        S.workers.emplace_back(worker_main, i);
+        S.workers.back().detach();
+    }
+    S.started = true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+bc_status bc_set_allocator(bc_alloc_fn alloc, bc_free_fn free_fn, void* ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(BC_E_INVALID_ARG, "alloc and free must be both set or both NULL");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_hook.alloc = alloc;
+    g_hook.free_fn = free_fn;
+    g_hook.ctx = ctx;
+    return BC_OK;
+}
+
+bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_t n, int64_t m, uint32_t flags,
+                          bc_stream_t stream, bc_graph** out) {
+    if (!out) return fail(BC_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || m < 0) return fail(BC_E_INVALID_ARG, "negative size (n=%d, m=%lld)", n, (long long)m);
+    if (!offsets || (m > 0 && !indices)) return fail(BC_E_INVALID_ARG, "offsets/indices NULL");
+    if (flags & ~(BC_UNDIRECTED | BC_INPUT_ON_DEVICE | BC_SKIP_VALIDATION))
+        return fail(BC_E_INVALID_ARG, "unknown flag bits 0x%x", flags);
+    if (!(flags & BC_UNDIRECTED))
+        return fail(BC_E_INVALID_ARG, "only undirected graphs are supported (set BC_UNDIRECTED)");
+    if (m >= (1ll << 31) - 1 || n >= (1 << 30)) return fail(BC_E_LIMIT, "graph beyond int32 CSR limits");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::unique_ptr<bc_graph> g(new bc_graph());
+    g->n = n;
+    g->m = m;
+    const int* d_off = offsets;
+    const int* d_adj = indices;
+    DevBuf in_off, in_adj;
+    if (!(flags & BC_INPUT_ON_DEVICE)) {
+        if (!buf_ensure(in_off, sizeof(int) * ((size_t)n + 1), st) ||
+            !buf_ensure(in_adj, sizeof(int) * (size_t)(m > 0 ? m : 1), st)) {
+            buf_release(in_off, st);
+            buf_release(in_adj, st);
+            return fail(BC_E_NOMEM, "device allocation failed for the input copy");
+        }
+        cudaError_t e = cudaMemcpyAsync(in_off.p, offsets, sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && m > 0)
+            e = cudaMemcpyAsync(in_adj.p, indices, sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            buf_release(in_off, st);
+            buf_release(in_adj, st);
+            return cuda_fail(e, "input copy");
+        }
+        d_off = (const int*)in_off.p;
+        d_adj = (const int*)in_adj.p;
+    }
+    IngestOut io;
+    bool oom = false;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        g->hook = g_hook;
+    }
+    cudaError_t e = ingest(d_off, d_adj, n, m, !(flags & BC_SKIP_VALIDATION), st, ingest_alloc, ingest_free, &io, &oom);
+    buf_release(in_off, st);
+    buf_release(in_adj, st);
+    auto adopt = [&](DevBuf& b, void* p, size_t bytes) { b.p = p; b.bytes = bytes; b.hook = g->hook; };
+    adopt(g->off, io.off, sizeof(int) * ((size_t)n + 1));
+    adopt(g->adj, io.adj, sizeof(int) * (size_t)(m > 0 ? m : 1));
+    adopt(g->perm, io.perm, sizeof(int) * (size_t)(n > 0 ? n : 1));
+    adopt(g->inv, io.inv, sizeof(int) * (size_t)(n > 0 ? n : 1));
+    auto drop = [&]() {
+        buf_release(g->off, st); buf_release(g->adj, st); buf_release(g->perm, st); buf_release(g->inv, st);
+    };
+    if (oom) { drop(); return fail(BC_E_NOMEM, "device allocation failed during ingest"); }
+    if (e != cudaSuccess) { drop(); return cuda_fail(e, "ingest"); }
+    if (io.reason) {
+        static const char* why[] = {"", "offsets not monotone, offsets[0] != 0 or offsets[n] != m",
+                                    "an index outside [0, n)", "a self-loop", "a duplicate arc",
+                                    "an arc without its reverse (graph not symmetric)"};
+        drop();
+        return fail(BC_E_INVALID_GRAPH, "invalid CSR: %s", why[io.reason]);
+    }
+    g->max_deg = io.max_deg;
+    g->n_nz = io.n_nz;
+    *out = g.release();
+    return BC_OK;
+}
+
+bc_status bc_graph_destroy(bc_graph* g) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    cudaStream_t st = g->last_stream;
+    cudaStreamSynchronize(st);
+    for (auto& kv : g->ws) kv.second->release(st);
+    buf_release(g->off, st);
+    buf_release(g->adj, st);
+    buf_release(g->perm, st);
+    buf_release(g->inv, st);
+    cudaStreamSynchronize(st);
+    delete g;
+    return BC_OK;
+}
+
+bc_status bc_graph_info(const bc_graph* g, int32_t* n, int64_t* m, int32_t* max_degree, int32_t* n_nonisolated) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (max_degree) *max_degree = g->max_deg;
+    if (n_nonisolated) *n_nonisolated = g->n_nz;
+    return BC_OK;
+}
+
+bc_status bc_graph_export(const bc_graph* g, int32_t* perm, int32_t* offsets, int32_t* indices) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    cudaError_t e = cudaSuccess;
+    if (perm && g->n > 0) e = cudaMemcpy(perm, g->perm.p, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && offsets)
+        e = cudaMemcpy(offsets, g->off.p, sizeof(int) * ((size_t)g->n + 1), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && indices && g->m > 0)
+        e = cudaMemcpy(indices, g->adj.p, sizeof(int) * (size_t)g->m, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "export");
+    return BC_OK;
+}
+
+bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream,
+                        const bc_options* opt) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    if (nsrc < 0) return fail(BC_E_INVALID_ARG, "nsrc < 0");
+    if (nsrc > 0 && !sources) return fail(BC_E_INVALID_ARG, "sources is NULL");
+    if (!out_bc && g->n > 0) return fail(BC_E_INVALID_ARG, "out_bc is NULL");
+    bc_options o;
+    memset(&o, 0, sizeof o);
+    if (opt) o = *opt;
+    bc_status cs = check_opts(o);
+    if (cs != BC_OK) return cs;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->last_stream = st;
+    if (g->n == 0) return BC_OK;
+    if (nsrc == 0) {
+        cudaError_t e = cudaMemsetAsync(out_bc, 0, sizeof(double) * (size_t)g->n, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "zero output");
+        g->last = bc_run_stats{};
+        return BC_OK;
+    }
+    const int* d_src = sources;
+    DevBuf tmp;
+    if (!is_device_ptr(sources)) {
+        for (int i = 0; i < nsrc; ++i)
+            if (sources[i] < 0 || sources[i] >= g->n)
+                return fail(BC_E_SOURCE, "source %d (entry %d) is outside [0, %d)", sources[i], i, g->n);
+        if (!buf_ensure(tmp, sizeof(int) * (size_t)nsrc, st)) return fail(BC_E_NOMEM, "source buffer");
+        cudaError_t e = cudaMemcpyAsync(tmp.p, sources, sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            buf_release(tmp, st);
+            return cuda_fail(e, "source copy");
+        }
+        d_src = (const int*)tmp.p;
+    }
+    const int K = choose_width(g->n, nsrc, o.batch_width);
+    auto& slot = g->ws[K];
+    if (!slot) slot.reset(new Workspace());
+    Workspace* w = slot.get();
+    if (!buf_ensure(w->bc, sizeof(double) * (size_t)g->n, st)) {
+        buf_release(tmp, st);
+        return fail(BC_E_NOMEM, "output buffer");
+    }
+    std::vector<double*> jb{(double*)w->bc.p};
+    bc_run_stats stats{};
+    bc_status r = run_jobs(g, w, d_src, nsrc, o, 1, jb, nullptr, false, st, &stats, nullptr, nullptr, nullptr);
+    if (r >= 0) {
+        cudaError_t e = launch_unpermute((const double*)w->bc.p, (const int*)g->inv.p, out_bc, g->n, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "unpermute");
+        stats.kernel_launches += 1;
+        g->last = stats;
+    }
+    buf_release(tmp, st);
+    return r;
+}
+
+bc_status bc_compute(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream) {
+    return bc_compute_ex(g, sources, nsrc, out_bc, stream, nullptr);
+}
+
+bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st) {
+    if (!g || !st) return fail(BC_E_INVALID_ARG, "NULL argument");
+    *st = g->last;
+    return BC_OK;
+}
+
+bc_status bc_debug_source(bc_graph* g, int32_t s, int32_t* level, double* sigma_mant, int32_t* sigma_exp) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    if (s < 0 || s >= g->n) return fail(BC_E_SOURCE, "source %d outside [0, %d)", s, g->n);
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaStream_t st = nullptr;
+    g->last_stream = st;
+    DevBuf dsrc, dlev, dsig, dsige;
+    const size_t n = (size_t)g->n;
+    if (!buf_ensure(dsrc, sizeof(int), st) || !buf_ensure(dlev, sizeof(int) * n, st) ||
+        !buf_ensure(dsig, sizeof(unsigned long long) * n, st) || !buf_ensure(dsige, sizeof(int) * n, st)) {
+        buf_release(dsrc, st); buf_release(dlev, st); buf_release(dsig, st); buf_release(dsige, st);
+        return fail(BC_E_NOMEM, "debug buffers");
+    }
+    cudaMemcpyAsync(dsrc.p, &s, sizeof(int), cudaMemcpyHostToDevice, st);
+    bc_options o;
+    memset(&o, 0, sizeof o);
+    o.batch_width = 32;
+    auto& slot = g->ws[32];
+    if (!slot) slot.reset(new Workspace());
+    Workspace* w = slot.get();
+    int K = 0, n_heavy = 0;
+    bool ext = false;
+    bc_status r = buf_ensure(w->bc, sizeof(double) * n, st) ? BC_OK : fail(BC_E_NOMEM, "debug buffers");
+    if (r == BC_OK) {
+        std::vector<double*> jb{(double*)w->bc.p};
+        r = run_jobs(g, w, (const int*)dsrc.p, 1, o, 1, jb, nullptr, true, st, nullptr, &K, &n_heavy, &ext);
+    }
+    KParams p = make_params(g, w, n_heavy, 1, o, ext);
+    if (r < 0) {
+        buf_release(dsrc, st); buf_release(dlev, st); buf_release(dsig, st); buf_release(dsige, st);
+        return r;
+    }
+    cudaError_t e = launch_debug_extract(p, 32, (int*)dlev.p, (unsigned long long*)dsig.p, (int*)dsige.p, st);
+    std::vector<int> lev(n), sige(n), perm(n);
+    std::vector<unsigned long long> sig(n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lev.data(), dlev.p, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sig.data(), dsig.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sige.data(), dsige.p, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(perm.data(), g->perm.p, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    buf_release(dsrc, st); buf_release(dlev, st); buf_release(dsig, st); buf_release(dsige, st);
+    if (e != cudaSuccess) return cuda_fail(e, "debug extract");
+    for (size_t r2 = 0; r2 < n; ++r2) {
+        const int v = perm[r2];
+        if (level) level[v] = lev[r2];
+        int ex = 0;
+        double mant = std::frexp((double)sig[r2], &ex);  // representation only: m * 2^e -> [0.5,1) * 2^x
+        if (sigma_mant) sigma_mant[v] = mant;
+        if (sigma_exp) sigma_exp[v] = sig[r2] ? ex + sige[r2] : 0;
+    }
+    return r;
+}
+
+bc_status bc_server_config(int32_t slots, int64_t memory_budget) {
+    if (slots < 1 || slots > 64 || memory_budget < 0)
+        return fail(BC_E_INVALID_ARG, "slots must be in [1, 64] and the budget >= 0");
+    Server& S = server();
+    std::lock_guard<std::mutex> lk(S.mu);
+    if (S.started) return fail(BC_E_INVALID_ARG, "the server is already running; configure before the first submit");
+    S.slots = slots;
+    S.budget = memory_budget;
+    return BC_OK;
+}
+
+bc_status bc_batch_submit(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_job* job) {
+    if (!g || !job) return fail(BC_E_INVALID_ARG, "NULL argument");
+    if (nsrc < 0 || (nsrc > 0 && !sources)) return fail(BC_E_INVALID_ARG, "bad source list");
+    if (!out_bc && g->n > 0) return fail(BC_E_INVALID_ARG, "out_bc is NULL");
+    if (nsrc > 0 && is_device_ptr(sources)) return fail(BC_E_INVALID_ARG, "bc_batch_submit takes host sources");
+    for (int i = 0; i < nsrc; ++i)
+        if (sources[i] < 0 || sources[i] >= g->n)
+            return fail(BC_E_SOURCE, "source %d (entry %d) is outside [0, %d)", sources[i], i, g->n);
+    auto j = std::make_shared<Job>();
+    j->g = g;
+    j->src.assign(sources, sources + nsrc);
+    j->out = out_bc;
+    j->t_submit = std::chrono::steady_clock::now();
+    Server& S = server();
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        server_start_locked(S);
+        j->id = S.next_id++;
+        S.jobs[j->id] = j;
+        if (nsrc == 0 || g->n == 0) {
+            cudaError_t e = g->n ? cudaMemset(out_bc, 0, sizeof(double) * (size_t)g->n) : cudaSuccess;
+            j->result = e == cudaSuccess ? BC_OK : cuda_fail(e, "zero output");
+            j->done = true;
+            j->t_done = std::chrono::steady_clock::now();
+            S.completed++;
+        } else {
+            S.queue.push_back(j);
+        }
+    }
+    S.cv_work.notify_all();
+    *job = j->id;
+    return BC_OK;
+}
+
+static bc_status poll_impl(bc_job job, double* latency_s, int64_t timeout_ms, bool wait) {
+    Server& S = server();
+    std::unique_lock<std::mutex> lk(S.mu);
+    auto it = S.jobs.find(job);
+    if (it == S.jobs.end()) return fail(BC_E_INVALID_ARG, "unknown or already released job %llu", (unsigned long long)job);
+    std::shared_ptr<Job> j = it->second;
+    if (wait && !j->done) {
+        auto pred = [&] { return j->done; };
+        if (timeout_ms < 0) S.cv_done.wait(lk, pred);
+        else S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred);
+    }
+    if (!j->done) return BC_PENDING;
+    if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
+    S.jobs.erase(it);
+    return j->result;
+}
+
+bc_status bc_poll(bc_job job) { return poll_impl(job, nullptr, 0, false); }
+bc_status bc_poll_ex(bc_job job, double* latency_s) { return poll_impl(job, latency_s, 0, false); }
+bc_status bc_wait(bc_job job, int64_t timeout_ms) { return poll_impl(job, nullptr, timeout_ms, true); }
+bc_status bc_wait_ex(bc_job job, int64_t timeout_ms, double* latency_s) {
+    return poll_impl(job, latency_s, timeout_ms, true);
+}
+
+bc_status bc_server_stats(int32_t* peak_concurrency, int64_t* completed) {
+    Server& S = server();
+    std::lock_guard<std::mutex> lk(S.mu);
+    if (peak_concurrency) *peak_concurrency = S.peak;
+    if (completed) *completed = S.completed;
+    return BC_OK;
+}
+
+const char* bc_status_string(bc_status st) {
+    switch (st) {
+        case BC_OK: return "BC_OK";
+        case BC_PENDING: return "BC_PENDING";
+        case BC_W_SIGMA_INEXACT: return "BC_W_SIGMA_INEXACT";
+        case BC_E_INVALID_ARG: return "BC_E_INVALID_ARG";
+        case BC_E_INVALID_GRAPH: return "BC_E_INVALID_GRAPH";
+        case BC_E_SOURCE: return "BC_E_SOURCE";
+        case BC_E_NOMEM: return "BC_E_NOMEM";
+        case BC_E_TIMEOUT: return "BC_E_TIMEOUT";
+        case BC_E_CUDA: return "BC_E_CUDA";
+        case BC_E_SIGMA_RANGE: return "BC_E_SIGMA_RANGE";
+        case BC_E_LIMIT: return "BC_E_LIMIT";
+    }
+    return "BC_UNKNOWN";
+}
+
+const char* bc_last_error(void) { return t_err.c_str(); }
+
+}  // extern "C"

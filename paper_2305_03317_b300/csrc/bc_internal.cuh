@@ -1,0 +1,100 @@
+// Internal types shared by the libbc CUDA sources (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bcx {
+
+constexpr int kChunk = 1024;        // arcs per ordered partial sum (fixed: results depend on it)
+constexpr int kMaxLevel = 65534;    // levels are uint16; 0xFFFF marks "not reached"
+constexpr int kThreads = 256;       // threads per block of the persistent kernels
+constexpr int kWarps = kThreads / 32;
+constexpr int kLevelSlots = kMaxLevel + 3;
+constexpr uint16_t kNoLevel = 0xFFFF;
+
+// Ctl::err bits (fatal for the launch)
+enum : int { ERR_TIMEOUT = 1, ERR_SIGMA_RANGE = 2, ERR_LIMIT = 4, ERR_CAPACITY = 8 };
+// per-batch status bits
+enum : int { BST_DONE = 1, BST_INEXACT = 2, BST_NEED_EXT = 4 };
+
+struct Ctl {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int err;
+    int flags;                 // BST_* bits raised inside the current batch
+    unsigned int wq[8];        // dynamic work counters, two per phase slot
+    int max_levels;            // deepest BFS over the launch
+    int pull_levels;
+    int push_levels;
+    int pad[5];
+};
+
+// Level bookkeeping, indexed by BFS level.
+struct LevelArrays {
+    int* cnt;            // light entries of the level
+    int* hcnt;           // heavy entries of the level
+    int* start;          // first light entry index
+    int* hstart;         // first heavy entry index
+    long long* dsum;     // sum of degrees of the level's entries
+    long long* fulldeg;  // sum of degrees of vertices whose every column was reached at that level
+};
+
+struct KParams {
+    // graph (relabelled: ids sorted by degree descending, heavy rows first, isolated last)
+    int n, n_nz, n_heavy;
+    long long m_nz;
+    const int* off;
+    const int* adj;
+    // sources, relabelled, [nbatch][K]; -1 = unused column
+    const int* src;
+    int nbatch;
+    // per-slot state
+    uint32_t* V;               // [n][W] reached-column masks
+    uint32_t* F[3];            // [n][W] frontier masks of three consecutive levels
+    uint16_t* lvl;             // [n][K]
+    unsigned long long* sig;   // [n][K] path counts (mantissa in the extended form); delta bits after the sweep
+    int* sig_e;                // [n][K] extended-form exponent (may be null when ext == 0)
+    double* rho;               // [n][K] (1 + delta) / sigma (mantissa in the extended form)
+    int* rho_e;                // [n][K]
+    int* ent;                  // light level lists (vertex ids)
+    int* hent;                 // heavy level lists
+    long long cap, hcap;
+    int* stamp;                // [n] push-claim stamps
+    LevelArrays la;
+    Ctl* ctl;
+    int* batch_status;         // [nbatch]
+    double* const* job_bc;     // [njobs] accumulated BC per job (relabelled ids, device pointers)
+    const int* col_job;        // [nbatch][K] job of each column; null = every column is job 0
+    // options
+    int direction;             // 0 auto, 1 push, 2 pull
+    float alpha, beta;
+    long long budget;          // barrier spin budget (cycles)
+    int ext;                   // run the extended path-count form
+    int forward_only;          // debug: stop after the forward sweep (no delta, no BC)
+};
+
+// Host-side launchers (bc_kernels.cu)
+cudaError_t launch_batches(int K, const KParams& p, int blocks, cudaStream_t st);
+int max_coop_blocks(int K, int* per_sm);
+cudaError_t launch_unpermute(const double* bc_rel, const int* inv, double* out, int n, cudaStream_t st);
+cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, int n, int K, int* dst,
+                               int nbatch, int* bad, cudaStream_t st);
+cudaError_t launch_debug_extract(const KParams& p, int K, int* level_rel, unsigned long long* sig_rel,
+                                 int* sige_rel, cudaStream_t st);
+
+// Ingest (ingest.cu)
+struct IngestOut {
+    int* off;       // [n+1] device
+    int* adj;       // [m] device
+    int* perm;      // [n] new -> original
+    int* inv;       // [n] original -> new
+    int max_deg;
+    int n_nz;
+    int reason;     // 0 ok, else 1 offsets, 2 index range, 3 self-loop, 4 duplicate, 5 asymmetric
+};
+typedef void* (*AllocFn)(size_t, cudaStream_t);
+typedef void (*FreeFn)(void*, cudaStream_t);
+cudaError_t ingest(const int* d_off_in, const int* d_adj_in, int n, long long m, bool validate,
+                   cudaStream_t st, AllocFn alloc, FreeFn dfree, IngestOut* out, bool* oom);
+
+}  // namespace bcx

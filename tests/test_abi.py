@@ -1,0 +1,54 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads and exports every
+function that include/bc.h declares (no compute calls: no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(bc_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+def test_header_parses():
+    fns = declared_functions()
+    for must in ("bc_graph_create", "bc_compute", "bc_batch_submit", "bc_poll", "bc_debug_source",
+                 "bc_status_string", "bc_last_error", "bc_set_allocator"):
+        assert must in fns
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_2305_03317_b300 import build
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    import paper_2305_03317_b300 as bc
+    lib = bc.load()
+    assert bc.status_string(bc.BC_OK) == "BC_OK"
+    assert bc.status_string(bc.BC_E_TIMEOUT) == "BC_E_TIMEOUT"
+    # argument validation happens before any device work
+    assert lib.bc_graph_create(None, None, 3, 0, 1, None, ctypes.byref(ctypes.c_void_p())) == bc.BC_E_INVALID_ARG
+    assert "NULL" in bc.last_error()
+    assert lib.bc_server_config(0, 0) == bc.BC_E_INVALID_ARG
+    assert lib.bc_poll(12345) == bc.BC_E_INVALID_ARG
+
+
+def test_product_path_has_no_oracle_import():
+    pkg = os.path.join(ROOT, "paper_2305_03317_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
+                assert "liboracle" not in src and "brandes.c" not in src, f

@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerance (derived for the reading that BC is the raw sum of delta): every
+delta term is non-negative, so no cancellation; double rounding of a sum of
+k positive terms is bounded by ~k * 2^-53 relative.  The GPU forms the sum as
+sigma_v * sum_w (1+delta_w)/sigma_w while the oracle forms per-arc ratios, so
+the two differ by a few ulps per level of the DAG; 1e-9 relative per vertex
+is far above that and exact zeros must stay exact zeros.  Levels and path
+counts below 2^53 are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import bcgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def bc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_03317_b300 as m
+    m.load()
+    return m
+
+
+def assert_bc_close(got, want, rel=REL):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert got.shape == want.shape
+    zero = want == 0
+    assert np.all(got[zero] == 0), "exact zeros must stay zero"
+    err = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    assert np.all(err[~zero] <= rel), f"max rel err {err[~zero].max()}"
+
+
+def gpu_bc(bc, g, src, **kw):
+    G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(np.asarray(src, np.int32), **kw)
+    res = out.cpu().numpy().copy()
+    stats = G.stats()
+    G.close()
+    return res, st, stats
+
+
+# ----------------------------------------------------------------- ingest
+
+@pytest.mark.parametrize("g", [bcgen.rmat(12, 8, 1), bcgen.grid(30, 31, 0.05, 2), bcgen.star(50),
+                               bcgen.disjoint_union(bcgen.path(5), bcgen.empty_graph(4), bcgen.cycle(9)),
+                               bcgen.rmat_n(3000, 11, 5)], ids=lambda g: g.name)
+def test_relabel_matches_oracle(bc, g):
+    G = bc.Graph(g.off, g.adj)
+    perm, off, adj = G.export()
+    operm, _, ooff, oadj = oracle.relabel(g.off, g.adj)
+    assert np.array_equal(perm, operm)
+    assert np.array_equal(off, ooff)
+    assert np.array_equal(adj, oadj)
+    deg = g.degrees()
+    assert G.max_degree == int(deg.max()) and G.n_nonisolated == int((deg > 0).sum())
+
+
+def test_invalid_graphs_rejected(bc):
+    g = bcgen.cycle(6)
+    cases = []
+    off = g.off.copy(); off[2] = off[1] - 1; cases.append((off, g.adj))
+    adj = g.adj.copy(); adj[3] = 6; cases.append((g.off, adj))
+    adj = g.adj.copy(); adj[0] = 0; cases.append((g.off, adj))
+    adj = g.adj.copy(); adj[1] = adj[0]; cases.append((g.off, adj))
+    h = bcgen.path(4)
+    adj = h.adj.copy(); adj[1] = 3; cases.append((h.off, adj))
+    for off, adj in cases:
+        assert oracle.validate(off, adj) != 0
+        with pytest.raises(bc.BCError) as ei:
+            bc.Graph(off, adj)
+        assert ei.value.status == bc.BC_E_INVALID_GRAPH
+
+
+def test_source_out_of_range_and_empty(bc):
+    g = bcgen.path(5)
+    G = bc.Graph(g.off, g.adj)
+    with pytest.raises(bc.BCError) as ei:
+        G.compute(np.array([5], np.int32))
+    assert ei.value.status == bc.BC_E_SOURCE
+    out, st = G.compute(np.zeros(0, np.int32))
+    assert st == bc.BC_OK and np.all(out.cpu().numpy() == 0)
+    # the graph is still usable after a rejected call
+    out, _ = G.compute(np.arange(5, dtype=np.int32))
+    assert_bc_close(out.cpu().numpy(), oracle.bc(g.off, g.adj, np.arange(5)))
+
+
+# ----------------------------------------------------------------- exact small cases
+
+@pytest.mark.parametrize("K", [1, 32, 64, 128])
+def test_golden_fixtures(bc, K):
+    from golden_io import load
+    for rec in load():
+        got, _, _ = gpu_bc(bc, bcgen.CSR(rec["off"], rec["adj"]), rec["src"], batch_width=K)
+        assert_bc_close(got, [float(x) for x in rec["bc"]], rel=1e-12)
+
+
+@pytest.mark.parametrize("g,half", [
+    (bcgen.path(300), lambda n: [i * (n - 1 - i) for i in range(n)]),
+    (bcgen.star(200), lambda n: [(n - 1) * (n - 2) / 2] + [0] * (n - 1)),
+    (bcgen.cycle(101), lambda n: [(n - 1) * (n - 3) / 8] * n),
+    (bcgen.cycle(100), lambda n: [(n - 2) ** 2 / 8] * n),
+    (bcgen.complete(12), lambda n: [0] * n),
+], ids=["path300", "star200", "cycle101", "cycle100", "K12"])
+def test_closed_forms(bc, g, half):
+    got, _, _ = gpu_bc(bc, g, np.arange(g.n))
+    assert_bc_close(got / 2, half(g.n), rel=1e-12)
+
+
+def test_complete_bipartite_and_tree(bc):
+    import math
+    g = bcgen.complete_bipartite(4, 7)
+    got, _, _ = gpu_bc(bc, g, np.arange(g.n))
+    assert_bc_close(got / 2, [math.comb(7, 2) / 4] * 4 + [math.comb(4, 2) / 7] * 7, rel=1e-12)
+    t = bcgen.random_tree(3000, 3)
+    got, _, _ = gpu_bc(bc, t, np.arange(t.n))
+    assert_bc_close(got, oracle.bc(t.off, t.adj, np.arange(t.n)), rel=1e-12)
+
+
+# ----------------------------------------------------------------- R-MAT, all widths
+
+@pytest.fixture(scope="module")
+def rmat12():
+    g = bcgen.rmat(12, 8, 1)
+    return g, oracle.bc(g.off, g.adj, np.arange(g.n))
+
+
+@pytest.mark.parametrize("K", [1, 32, 64, 128])
+def test_rmat12_all_sources(bc, rmat12, K):
+    g, want = rmat12
+    got, st, stats = gpu_bc(bc, g, np.arange(g.n), batch_width=K)
+    assert st == bc.BC_OK
+    assert stats["batch_width"] == K
+    assert_bc_close(got, want)
+
+
+def test_rmat12_bitwise_across_widths_and_directions(bc, rmat12):
+    g, _ = rmat12
+    src = bcgen.sample_sources(g, 300, 4)
+    ref, _, _ = gpu_bc(bc, g, src, batch_width=64)
+    for kw in [dict(batch_width=1), dict(batch_width=32), dict(batch_width=128), dict(batch_width=64, direction=1),
+               dict(batch_width=64, direction=2), dict(batch_width=64, heavy_degree=8),
+               dict(batch_width=32, heavy_degree=40, direction=2)]:
+        got, _, _ = gpu_bc(bc, g, src, **kw)
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
+
+
+def test_duplicate_sources_count_twice(bc):
+    g = bcgen.rmat(10, 6, 3)
+    src = np.array([5, 9, 5, 5, 100, 9], np.int32)
+    got, _, _ = gpu_bc(bc, g, src, batch_width=32)
+    assert_bc_close(got, oracle.bc(g.off, g.adj, src))
+
+
+def test_ragged_batches_and_isolated_sources(bc):
+    g = bcgen.disjoint_union(bcgen.rmat(11, 8, 2), bcgen.empty_graph(3))
+    src = np.concatenate([bcgen.sample_sources(g, 77, 9), np.array([g.n - 1, g.n - 2], np.int32)])
+    for K in (32, 64):
+        got, _, stats = gpu_bc(bc, g, src, batch_width=K)
+        assert stats["batches"] == -(-len(src) // K)
+        assert_bc_close(got, oracle.bc(g.off, g.adj, src))
+
+
+# ----------------------------------------------------------------- levels and path counts
+
+def test_debug_source_levels_and_sigma(bc):
+    g = bcgen.rmat(12, 8, 1)
+    G = bc.Graph(g.off, g.adj)
+    for s in bcgen.sample_sources(g, 5, 2):
+        lev, mant, ex, _ = G.debug_source(int(s))
+        d = oracle.source_detail(g.off, g.adj, int(s))
+        assert np.array_equal(lev, d["level"])
+        sig = np.ldexp(mant, ex)
+        assert np.array_equal(sig, d["sigma"])
+
+
+def test_full_grid_extended_range(bc):
+    """Path counts up to C(298,149) ~ 2^293: beyond 2^64, so the extended form runs."""
+    g = bcgen.grid(150, 150, 0.0)
+    src = np.array([0, 151, 150 * 75 + 75], np.int32)
+    G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(src, batch_width=32)
+    stats = G.stats()
+    assert st == bc.BC_W_SIGMA_INEXACT and stats["ext_batches"] > 0
+    want = oracle.bc_ld(g.off, g.adj, src).astype(np.float64)
+    assert_bc_close(out.cpu().numpy(), want)
+    lev, mant, ex, _ = G.debug_source(0)
+    olev, omant, oex, _ = oracle.source_sigma_split(g.off, g.adj, 0)
+    assert np.array_equal(lev, olev)
+    rel = np.abs(mant * np.ldexp(1.0, ex - oex) - omant) / omant
+    assert rel.max() <= 1e-12
+    # counts below 2^53 stay exact in the extended form
+    small = oex <= 53
+    assert np.array_equal(np.ldexp(mant[small], ex[small]), np.ldexp(omant[small], oex[small]))
+
+
+# ----------------------------------------------------------------- failure handling
+
+def test_barrier_timeout_reports_and_recovers(bc):
+    g = bcgen.rmat(11, 8, 1)
+    G = bc.Graph(g.off, g.adj)
+    src = bcgen.sample_sources(g, 64, 1)
+    with pytest.raises(bc.BCError) as ei:
+        G.compute(src, batch_width=64, barrier_budget=1)
+    assert ei.value.status == bc.BC_E_TIMEOUT
+    out, st = G.compute(src, batch_width=64)
+    assert_bc_close(out.cpu().numpy(), oracle.bc(g.off, g.adj, src))
+
+
+# ----------------------------------------------------------------- serving
+
+def test_serving_alone_equals_mix(bc):
+    import torch
+    graphs = [bcgen.rmat(11, 8, 1), bcgen.rmat(12, 4, 2), bcgen.grid(40, 40, 0.05, 3)]
+    Gs = [bc.Graph(g.off, g.adj) for g in graphs]
+    reqs = [(i % 3, bcgen.sample_sources(graphs[i % 3], k, 10 + i)) for i, k in
+            enumerate([1, 3, 40, 7, 130, 2, 64, 5, 17, 300, 1, 33])]
+
+    def run(batch):
+        outs, jobs = [], []
+        for gi, src in batch:
+            o = torch.empty(graphs[gi].n, dtype=torch.float64, device="cuda")
+            outs.append(o)
+            jobs.append(Gs[gi].submit(src, o))
+        for j in jobs:
+            assert j.wait(120000) is not None
+        return [o.cpu().numpy().copy() for o in outs]
+
+    alone = [run([r])[0] for r in reqs]
+    mixed = run(reqs)
+    for (gi, src), a, b in zip(reqs, alone, mixed):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+        assert_bc_close(b, oracle.bc(graphs[gi].off, graphs[gi].adj, src))
+    peak, done = bc.server_stats()
+    assert done >= 2 * len(reqs)
