@@ -1,0 +1,380 @@
+"""Benchmark: exact Brandes BC throughput on one B300 (traversed source-arcs per second).
+
+Default workload: undirected R-MAT scale 22, edge factor 16 (a=.57 b=.19 c=.19,
+seeded, self-loops and duplicates removed), 4096 sources sampled uniformly
+over non-isolated vertices; one step = one bc_compute over all 4096 sources
+on the resident graph (batched traversal, width chosen by the library).
+
+Metric: BC traversed edges/s = sources x m / time, m = CSR arcs (each
+undirected edge counted twice).  `value` times bc_compute with sources and
+output already on the device; `e2e` times the same call from pinned host
+sources to a pinned host copy of the result.  The roofline object reports the
+persistent traversal kernel against the measured HBM copy bandwidth using the
+algorithmic byte model B_s = 8m/k + m/4 + 16 E_dag(s) + 24 n_s per source.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload rmat22|rmat12|grid|serve] [--sources S] [--batch-width K]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BC traversed edges/s (sources x edges) on 1 B300, % HBM roofline; p50/p99 latency"
+UNIT = "source-arcs/s"
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "rmat12", "grid", "serve", "rmat"])
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--ef", type=float, default=16)
+    ap.add_argument("--sources", type=int, default=0)
+    ap.add_argument("--batch-width", type=int, default=0)
+    ap.add_argument("--direction", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (req/s)")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(a):
+    import bcgen
+    if a.workload in ("rmat22", "rmat"):
+        scale, ef = (22, 16) if a.workload == "rmat22" else (a.scale, a.ef)
+        g = bcgen.rmat(scale, ef, 1)
+        S = a.sources or 4096
+        src = bcgen.sample_sources(g, S, 1)
+        desc = dict(workload=f"rmat{scale}_ef{ef:g}", graph=f"undirected R-MAT scale {scale}, edge factor {ef:g}, "
+                    "a=.57 b=.19 c=.19, seed 1, self-loops/duplicates removed, int32 CSR",
+                    sources=int(len(src)), source_sampling="uniform without replacement over degree>=1, seed 1")
+    elif a.workload == "rmat12":
+        g = bcgen.rmat(12, 8, 1)
+        src = np.arange(g.n, dtype=np.int32)
+        desc = dict(workload="rmat12_ef8_all_sources", graph="undirected R-MAT scale 12, edge factor 8, seed 1",
+                    sources=int(g.n), source_sampling="every vertex")
+    else:  # grid
+        g = bcgen.grid(1024, 1024, 0.05, 1)
+        S = a.sources or 256
+        src = bcgen.sample_sources(g, S, 1)
+        desc = dict(workload="grid1024x1024_rm5pct", graph="1024x1024 4-neighbour grid, 5% of edges removed (seed 1)",
+                    sources=int(len(src)), source_sampling="uniform without replacement over degree>=1, seed 1")
+    desc.update(n=g.n, m=g.m)
+    return g, src, desc
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback 6.4 TB/s (no MEASURED_PEAKS.json)"
+
+
+def committed_traffic(kernel_name, workload):
+    """Per-source DRAM bytes from the committed ncu summary, or None if absent/stale."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        src = open(os.path.join(ROOT, "paper_2305_03317_b300", "csrc", "bc_kernels.cu"), "rb").read()
+        if d.get("kernel_source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        e = d.get("entries", {}).get(f"{kernel_name}|{workload}")
+        return None if e is None else float(e["dram_bytes_per_source"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dag_stats(G, g, src, nsample=4):
+    """Mean E_dag and reached count per source for the byte model, from the
+    library's own levels (bc_debug_source) on a few sources."""
+    deg = np.diff(g.off.astype(np.int64))
+    row = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    ed, ns = [], []
+    for s in src[:: max(1, len(src) // nsample)][:nsample]:
+        lev, _, _, _ = G.debug_source(int(s))
+        lv, lw = lev[row], lev[g.adj]
+        ed.append(int(np.count_nonzero((lv >= 0) & (lw == lv + 1))))
+        ns.append(int(np.count_nonzero(lev >= 0)))
+    return float(np.mean(ed)), float(np.mean(ns))
+
+
+def cpu_baseline(g, src, per_core=1, max_threads=64):
+    import oracle
+    cores = max(1, min(os.cpu_count() or 1, max_threads))
+    sample = src[: max(1, min(len(src), cores * per_core))]
+    t = time.perf_counter()
+    oracle.bc(g.off, g.adj, sample, threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": len(sample) * g.m / dt, "unit": UNIT, "cores": int(min(cores, len(sample))), "kind": "oracle",
+            "sample": f"{len(sample)} of the workload's sources (first {len(sample)}), full graph, "
+                      f"{dt:.1f} s wall on {min(cores, len(sample))} threads"}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g, src, desc = make_workload(a)
+    cores = max(1, min(os.cpu_count() or 1, 64))
+    per_step = src[:cores]
+    for _ in range(a.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated on the CPU
+    import oracle
+    times = []
+    for i in range(a.steps):
+        t = time.perf_counter()
+        oracle.bc(g.off, g.adj, per_step, threads=cores)
+        times.append(time.perf_counter() - t)
+    dt = float(np.mean(times))
+    val = len(per_step) * g.m / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(desc, step=f"oracle over {len(per_step)} sources (one per host thread)"),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": int(min(cores, len(per_step))), "kind": "oracle",
+                             "sample": f"{len(per_step)} sources per step of the same workload"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(a):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2305_03317_b300 as bc
+
+    if a.workload == "serve":
+        return run_serve(a, bc, torch)
+
+    g, src, desc = make_workload(a)
+    if world > 1:  # weak scaling: every rank runs its own sources of the same size
+        import bcgen
+        src = bcgen.sample_sources(g, len(src), 1 + rank)
+    t0 = time.perf_counter()
+    G = bc.Graph(g.off, g.adj)
+    torch.cuda.synchronize()
+    ingest_s = time.perf_counter() - t0
+    d_src = torch.from_numpy(src).cuda()
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    opts = dict(batch_width=a.batch_width, direction=a.direction)
+
+    for _ in range(max(a.warmup, 0)):
+        G.compute(d_src, out=out, **opts)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, kern_ms, launches, statuses = [], [], 0, set()
+    ev0.record(stream)
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = G.compute(d_src, out=out, **opts)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        s = G.stats()
+        kern_ms.append(s["kernel_ms"])
+        launches += s["kernel_launches"]
+        statuses.add(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    stats = G.stats()
+    ms = total_ms / a.steps
+    value = world * len(src) * g.m / (ms / 1e3)
+
+    # end to end: pinned host sources in, pinned host result out, through the public call
+    h_src = torch.from_numpy(src).pin_memory()
+    h_out = torch.empty(g.n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(a.steps, 3))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        G.compute(h_src.numpy(), out=out, **opts)
+        h_out.copy_(out, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    # roofline of the persistent traversal kernel
+    K = stats["batch_width"]
+    ed, ns = dag_stats(G, g, src)
+    nb = stats["batches"]
+    model_bytes = nb * (8.0 * g.m + K * g.m / 4.0) + len(src) * (16.0 * ed + 24.0 * ns)
+    kms = float(np.mean(kern_ms))
+    peak, peak_src = measured_peak()
+    achieved = model_bytes / (kms / 1e3) / 1e9
+    kname = f"bc_persistent<{K}>"
+    tr = committed_traffic(kname, desc["workload"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": dict(desc, step="one bc_compute over all sources on the resident graph",
+                       batch_width=K, batches=nb, levels=stats["max_levels"], pull_levels=stats["pull_levels"],
+                       push_levels=stats["push_levels"], ingest_s=round(ingest_s, 3),
+                       l2="inputs larger than L2 (CSR and per-batch state are GBs, L2 126 MB)",
+                       parallelism=f"dp{world} (sources sharded per rank)" if world > 1 else "single GPU",
+                       statuses=sorted(int(x) for x in statuses)),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "what": "per bc_compute step"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": (tr * len(src)) if tr is not None else None,
+                     "kernel": kname, "kernel_ms": kms, "model_bytes": model_bytes,
+                     "model": f"per source 8m/k + m/4 + 16*E_dag + 24*n_s; E_dag={ed:.0f}, n_s={ns:.0f} "
+                              f"(mean of 4 sources' levels)", "peak_source": peak_src},
+        "e2e": {"value": len(src) * g.m / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(4 * len(src)),
+                "d2h_bytes_per_step": int(8 * g.n), "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, src)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_serve(a, bc, torch):
+    """Serving: open-loop Poisson stream over a resident pool of R-MAT graphs."""
+    import bcgen
+    scales = [14, 16, 18, 20]
+    pool = [bcgen.rmat(s, 16, 1) for s in scales]
+    Gs = [bc.Graph(g.off, g.adj) for g in pool]
+    reqs = bcgen.poisson_requests(a.rate, a.duration, len(pool), seed=1)
+    outs = [torch.empty(pool[gi].n, dtype=torch.float64, device="cuda") for _, gi, _ in reqs]
+    srcs = [bcgen.sample_sources(pool[gi], k, 100 + i) for i, (_, gi, k) in enumerate(reqs)]
+    bc.server_config(4, 0)
+    # warm-up: one request per graph
+    for G, g in zip(Gs, pool):
+        o = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        G.submit(bcgen.sample_sources(g, 4, 5), o).wait()
+    jobs = []
+    t0 = time.perf_counter()
+    for (t, gi, k), o, s in zip(reqs, outs, srcs):
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        jobs.append(Gs[gi].submit(s, o))
+    lat = [j.wait()[1] for j in jobs]
+    wall = time.perf_counter() - t0
+    arcs = sum(len(s) * pool[gi].m for s, (_, gi, _) in zip(srcs, reqs))
+    peak, done = bc.server_stats()
+    line = {"metric": METRIC, "value": arcs / wall, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": len(pool),
+            "ms_per_step": wall * 1e3 / max(len(reqs), 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"serve_poisson{a.rate:g}", "pool": [f"rmat{s}_ef16" for s in scales],
+                       "requests": len(reqs), "k": "round(2^U[0,10]) sources", "duration_s": a.duration},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "what": "submit to completion per request"},
+            "peak_concurrency": peak}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -99,8 +99,9 @@ typedef struct {
     int32_t direction;       /* 0 = auto push/pull switching, 1 = push only, 2 = pull only */
     float alpha;             /* switch to pull when frontier arcs * alpha > unvisited arcs (0 = 14) */
     float beta;              /* back to push when frontier vertices * beta < non-isolated vertices (0 = 24) */
-    int32_t heavy_degree;    /* rows above this degree are processed by a whole thread block (0 = 4096) */
-    int32_t blocks_per_sm;   /* persistent-grid residency (0 = occupancy maximum, capped at 4) */
+    int32_t group_vertices;  /* rows of degree <= 1024 handled per warp task, 1..32 (0 = 32); results do not
+                                depend on it (sums follow fixed 1024-arc chunks of each row) */
+    int32_t blocks_per_sm;   /* persistent-grid residency (0 = occupancy maximum) */
     int64_t barrier_budget;  /* device cycles a grid-barrier wait may spin before BC_E_TIMEOUT
                                 (0 = about 20 s; tests may set 1 to force a timeout) */
 } bc_options;
@@ -127,6 +128,7 @@ typedef struct {
     int32_t ext_batches;     /* batches rerun in the extended-range path-count form */
     int32_t grid_blocks;     /* persistent grid size */
     int32_t kernel_launches; /* kernels launched by the call */
+    float kernel_ms;         /* device time of the persistent traversal launches (CUDA events on the call's stream) */
 } bc_run_stats;
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 

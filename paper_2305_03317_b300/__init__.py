@@ -44,14 +44,15 @@ class BCError(RuntimeError):
 
 class bc_options(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("direction", ctypes.c_int32), ("alpha", ctypes.c_float),
-                ("beta", ctypes.c_float), ("heavy_degree", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("beta", ctypes.c_float), ("group_vertices", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("barrier_budget", ctypes.c_int64)]
 
 
 class bc_run_stats(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("batches", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("pull_levels", ctypes.c_int32), ("push_levels", ctypes.c_int32), ("ext_batches", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("kernel_ms", ctypes.c_float)]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -194,7 +195,7 @@ class Graph:
             pass
 
     def compute(self, sources, out=None, stream=None, batch_width: int = 0, direction: int = 0,
-                alpha: float = 0.0, beta: float = 0.0, heavy_degree: int = 0, blocks_per_sm: int = 0,
+                alpha: float = 0.0, beta: float = 0.0, group_vertices: int = 0, blocks_per_sm: int = 0,
                 barrier_budget: int = 0):
         """BC over ``sources`` (host numpy or device int32 tensor). Returns (out, status)."""
         import torch
@@ -203,7 +204,7 @@ class Graph:
         if isinstance(sources, np.ndarray):
             sources = np.ascontiguousarray(sources, dtype=np.int32)
         nsrc = int(sources.shape[0]) if isinstance(sources, np.ndarray) else int(sources.numel())
-        opt = bc_options(batch_width, direction, alpha, beta, heavy_degree, blocks_per_sm, barrier_budget)
+        opt = bc_options(batch_width, direction, alpha, beta, group_vertices, blocks_per_sm, barrier_budget)
         s = load().bc_compute_ex(self._h, _ptr(sources) if nsrc else None, nsrc, _ptr(out) if self.n else None,
                                  _stream_handle(stream), ctypes.byref(opt))
         _check(s)

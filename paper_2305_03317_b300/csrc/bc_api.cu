@@ -112,35 +112,46 @@ static void buf_release(DevBuf& b, cudaStream_t st) {
 // ------------------------------------------------------------------ graph
 struct Workspace {
     int K = 0;
-    int n_heavy = -1;
-    bool has_ext = false;
-    DevBuf V, F[3], lvl, sig, sig_e, rho, rho_e, ent, hent, stamp;
-    DevBuf cnt, hcnt, start, hstart, dsum, fulldeg, ctl, bstat, bc, src, bad, jobptr, coljob;
+    DevBuf V, F[3], sig, sig_e, rho, rho_e, ent, emask, hent, hmask, hpre, stamp;
+    DevBuf scr_v, scr_e, scr_or, arr;
+    DevBuf cnt, hcnt, start, hstart, dsum, fulldeg, hchunks, ctl, bstat, bc, src, bad, jobptr, coljob;
     long long cap = 0, hcap = 0;
-    void release(cudaStream_t st) {
-        DevBuf* all[] = {&V, &F[0], &F[1], &F[2], &lvl, &sig, &sig_e, &rho, &rho_e, &ent, &hent, &stamp,
-                         &cnt, &hcnt, &start, &hstart, &dsum, &fulldeg, &ctl, &bstat, &bc, &src, &bad,
-                         &jobptr, &coljob};
-        for (DevBuf* b : all) buf_release(*b, st);
+    DevBuf* all_bufs(std::vector<DevBuf*>& v) {
+        DevBuf* a[] = {&V, &F[0], &F[1], &F[2], &sig, &sig_e, &rho, &rho_e, &ent, &emask, &hent, &hmask, &hpre,
+                       &stamp, &scr_v, &scr_e, &scr_or, &arr, &cnt, &hcnt, &start, &hstart, &dsum, &fulldeg,
+                       &hchunks, &ctl, &bstat, &bc, &src, &bad, &jobptr, &coljob};
+        v.assign(a, a + sizeof(a) / sizeof(a[0]));
+        return nullptr;
     }
-    size_t bytes() const {
-        const DevBuf* all[] = {&V, &F[0], &F[1], &F[2], &lvl, &sig, &sig_e, &rho, &rho_e, &ent, &hent, &stamp,
-                               &cnt, &hcnt, &start, &hstart, &dsum, &fulldeg, &ctl, &bstat, &bc, &src, &bad,
-                               &jobptr, &coljob};
+    void release(cudaStream_t st) {
+        std::vector<DevBuf*> v;
+        all_bufs(v);
+        for (DevBuf* b : v) buf_release(*b, st);
+    }
+    size_t bytes() {
+        std::vector<DevBuf*> v;
+        all_bufs(v);
         size_t t = 0;
-        for (const DevBuf* b : all) t += b->bytes;
+        for (DevBuf* b : v) t += b->bytes;
         return t;
     }
 };
 
+// Entry-list capacity per vertex: a vertex enters a level list at most once per
+// distinct level across the batch's columns, so K bounds it; the first try
+// uses a smaller factor and the call reruns with K on overflow.
+static int cap_factor(int K, int sticky) { return sticky > 0 ? sticky : (K < 24 ? K : 24); }
+
 // Bytes a workspace needs for n vertices at width K (plus the extended arrays).
-static size_t ws_need(int n, int K, int n_heavy, bool ext, int nbatch, int njobs) {
+static size_t ws_need(int n, int K, int n_heavy, long long hc, bool ext, int nbatch, int njobs, int capf) {
     const size_t nn = (size_t)(n > 0 ? n : 1);
     const int W = K >= 32 ? K / 32 : 1;
-    size_t b = 4 * sizeof(uint32_t) * nn * W + sizeof(uint16_t) * nn * K + 2 * sizeof(double) * nn * K;
+    size_t b = 4 * sizeof(uint32_t) * nn * W + 2 * sizeof(double) * nn * K + sizeof(int) * nn;
     if (ext) b += 2 * sizeof(int) * nn * K;
-    b += sizeof(int) * nn * K + sizeof(int) * (size_t)(n_heavy > 0 ? n_heavy : 1) * K + sizeof(int) * nn;
-    b += (4 * sizeof(int) + 2 * sizeof(long long)) * kLevelSlots + sizeof(Ctl);
+    b += (sizeof(int) + sizeof(uint32_t) * W) * nn * (size_t)capf;
+    b += (2 * sizeof(int) + sizeof(uint32_t) * W) * (size_t)(n_heavy > 0 ? n_heavy : 1) * K;
+    b += (size_t)(hc > 0 ? hc : 1) * ((8 + (ext ? 4 : 0)) * K + 4 * W) + sizeof(int) * (size_t)(n_heavy + 1);
+    b += (5 * sizeof(int) + 2 * sizeof(long long)) * kLevelSlots + sizeof(Ctl);
     b += sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * (1 + 2 * K) + sizeof(double) * nn;
     b += sizeof(double*) * (size_t)(njobs > 0 ? njobs : 1);
     return b;
@@ -151,11 +162,14 @@ struct bc_graph {
     long long m = 0;
     int max_deg = 0;
     int n_nz = 0;
-    DevBuf off, adj, perm, inv;
+    int n_heavy = -1;      // rows with degree > kChunk (a prefix of the new ids); -1 = not yet counted
+    long long hchunk_total = 0;
+    DevBuf off, adj, perm, inv, hcum;
     AllocHook hook;
     std::mutex mu;
     std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
     bool sticky_ext = false;
+    std::map<int, int> sticky_cap;                 // entry capacity factor that sufficed, by width
     bc_run_stats last{};
     cudaStream_t last_stream = nullptr;
 };
@@ -170,53 +184,72 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static int heavy_count(bc_graph* g, int threshold, cudaStream_t st, bc_status* err) {
-    // degrees are non-increasing in new ids: binary search over the offsets
-    // using a handful of device reads.
-    int lo = 0, hi = g->n_nz;  // first r with deg(r) <= threshold
+// Heavy rows and their chunk prefix, once per graph: degrees are non-increasing
+// in new ids, so the heavy rows are a prefix found by binary search; the
+// prefix of chunk counts is built on the host from their offsets.
+static bc_status ensure_heavy(bc_graph* g, cudaStream_t st) {
+    if (g->n_heavy >= 0) return BC_OK;
+    int lo = 0, hi = g->n_nz;  // first r with deg(r) <= kChunk
     const int* off = (const int*)g->off.p;
     while (lo < hi) {
         int mid = (lo + hi) / 2;
         int two[2];
         cudaError_t e = cudaMemcpyAsync(two, off + mid, sizeof two, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            *err = cuda_fail(e, "heavy-row count");
-            return -1;
-        }
-        if (two[1] - two[0] > threshold) lo = mid + 1;
+        if (e != cudaSuccess) return cuda_fail(e, "heavy-row count");
+        if (two[1] - two[0] > kChunk) lo = mid + 1;
         else hi = mid;
     }
-    return lo;
+    const int nh = lo;
+    std::vector<int> ho((size_t)nh + 1), cum((size_t)nh + 1);
+    cudaError_t e = cudaMemcpyAsync(ho.data(), off, sizeof(int) * ((size_t)nh + 1), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "heavy-row offsets");
+    cum[0] = 0;
+    for (int r = 0; r < nh; ++r) cum[r + 1] = cum[r] + (ho[r + 1] - ho[r] + kChunk - 1) / kChunk;
+    if (!buf_ensure(g->hcum, sizeof(int) * ((size_t)nh + 1), st)) return fail(BC_E_NOMEM, "heavy-row table");
+    e = cudaMemcpyAsync(g->hcum.p, cum.data(), sizeof(int) * ((size_t)nh + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "heavy-row table");
+    g->n_heavy = nh;
+    g->hchunk_total = cum[nh];
+    return BC_OK;
 }
 
-static bool ws_ensure(Workspace* w, int n_vert, int K, int n_heavy, bool ext, int nbatch, int njobs,
-                      cudaStream_t st) {
+static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, int njobs, int capf, cudaStream_t st) {
     w->K = K;
-    const size_t n = (size_t)(n_vert > 0 ? n_vert : 1);
+    const size_t n = (size_t)(g->n > 0 ? g->n : 1);
     const int W = K >= 32 ? K / 32 : 1;
-    const long long cap = (long long)n * K;
-    const long long hcap = (long long)(n_heavy > 0 ? n_heavy : 1) * K;
+    const long long cap = (long long)n * capf;
+    const long long hcap = (long long)(g->n_heavy > 0 ? g->n_heavy : 1) * K;
+    const size_t hc = (size_t)(g->hchunk_total > 0 ? g->hchunk_total : 1);
     const size_t nb = (size_t)(nbatch > 0 ? nbatch : 1);
     bool ok = true;
     ok &= buf_ensure(w->V, sizeof(uint32_t) * n * W, st);
     for (int i = 0; i < 3; ++i) ok &= buf_ensure(w->F[i], sizeof(uint32_t) * n * W, st);
-    ok &= buf_ensure(w->lvl, sizeof(uint16_t) * n * K, st);
     ok &= buf_ensure(w->sig, sizeof(unsigned long long) * n * K, st);
     ok &= buf_ensure(w->rho, sizeof(double) * n * K, st);
     if (ext) {
         ok &= buf_ensure(w->sig_e, sizeof(int) * n * K, st);
         ok &= buf_ensure(w->rho_e, sizeof(int) * n * K, st);
+        ok &= buf_ensure(w->scr_e, sizeof(int) * hc * K, st);
     }
     ok &= buf_ensure(w->ent, sizeof(int) * (size_t)cap, st);
+    ok &= buf_ensure(w->emask, sizeof(uint32_t) * W * (size_t)cap, st);
     ok &= buf_ensure(w->hent, sizeof(int) * (size_t)hcap, st);
+    ok &= buf_ensure(w->hmask, sizeof(uint32_t) * W * (size_t)hcap, st);
+    ok &= buf_ensure(w->hpre, sizeof(int) * (size_t)hcap, st);
     ok &= buf_ensure(w->stamp, sizeof(int) * n, st);
+    ok &= buf_ensure(w->scr_v, sizeof(unsigned long long) * hc * K, st);
+    ok &= buf_ensure(w->scr_or, sizeof(uint32_t) * hc * W, st);
+    ok &= buf_ensure(w->arr, sizeof(int) * (size_t)(g->n_heavy > 0 ? g->n_heavy : 1), st);
     ok &= buf_ensure(w->cnt, sizeof(int) * kLevelSlots, st);
     ok &= buf_ensure(w->hcnt, sizeof(int) * kLevelSlots, st);
     ok &= buf_ensure(w->start, sizeof(int) * kLevelSlots, st);
     ok &= buf_ensure(w->hstart, sizeof(int) * kLevelSlots, st);
     ok &= buf_ensure(w->dsum, sizeof(long long) * kLevelSlots, st);
     ok &= buf_ensure(w->fulldeg, sizeof(long long) * kLevelSlots, st);
+    ok &= buf_ensure(w->hchunks, sizeof(int) * kLevelSlots, st);
     ok &= buf_ensure(w->ctl, sizeof(Ctl), st);
     ok &= buf_ensure(w->bstat, sizeof(int) * nb, st);
     ok &= buf_ensure(w->bc, sizeof(double) * n, st);
@@ -225,22 +258,20 @@ static bool ws_ensure(Workspace* w, int n_vert, int K, int n_heavy, bool ext, in
     ok &= buf_ensure(w->bad, sizeof(int), st);
     ok &= buf_ensure(w->jobptr, sizeof(double*) * (size_t)(njobs > 0 ? njobs : 1), st);
     if (!ok) {
-        fail(BC_E_NOMEM, "device allocation failed for a batch-width-%d workspace (n=%d)", K, n_vert);
+        fail(BC_E_NOMEM, "device allocation failed for a batch-width-%d workspace (n=%d)", K, g->n);
         return false;
     }
     w->cap = cap;
     w->hcap = hcap;
-    w->n_heavy = n_heavy;
-    w->has_ext = w->sig_e.p != nullptr;
     return true;
 }
 
-static KParams make_params(bc_graph* g, Workspace* w, int n_heavy, int nbatch, const bc_options& o, bool ext) {
+static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_options& o, bool ext) {
     KParams p;
     memset(&p, 0, sizeof p);
     p.n = g->n;
     p.n_nz = g->n_nz;
-    p.n_heavy = n_heavy;
+    p.n_heavy = g->n_heavy;
     p.m_nz = g->m;
     p.off = (const int*)g->off.p;
     p.adj = (const int*)g->adj.p;
@@ -248,15 +279,22 @@ static KParams make_params(bc_graph* g, Workspace* w, int n_heavy, int nbatch, c
     p.nbatch = nbatch;
     p.V = (uint32_t*)w->V.p;
     for (int i = 0; i < 3; ++i) p.F[i] = (uint32_t*)w->F[i].p;
-    p.lvl = (uint16_t*)w->lvl.p;
     p.sig = (unsigned long long*)w->sig.p;
     p.sig_e = (int*)w->sig_e.p;
     p.rho = (double*)w->rho.p;
     p.rho_e = (int*)w->rho_e.p;
     p.ent = (int*)w->ent.p;
+    p.emask = (uint32_t*)w->emask.p;
     p.hent = (int*)w->hent.p;
+    p.hmask = (uint32_t*)w->hmask.p;
+    p.hpre = (int*)w->hpre.p;
     p.cap = w->cap;
     p.hcap = w->hcap;
+    p.hcum = (const int*)g->hcum.p;
+    p.scr_v = (unsigned long long*)w->scr_v.p;
+    p.scr_e = (int*)w->scr_e.p;
+    p.scr_or = (uint32_t*)w->scr_or.p;
+    p.arr = (int*)w->arr.p;
     p.stamp = (int*)w->stamp.p;
     p.la.cnt = (int*)w->cnt.p;
     p.la.hcnt = (int*)w->hcnt.p;
@@ -264,6 +302,7 @@ static KParams make_params(bc_graph* g, Workspace* w, int n_heavy, int nbatch, c
     p.la.hstart = (int*)w->hstart.p;
     p.la.dsum = (long long*)w->dsum.p;
     p.la.fulldeg = (long long*)w->fulldeg.p;
+    p.la.hchunks = (int*)w->hchunks.p;
     p.ctl = (Ctl*)w->ctl.p;
     p.batch_status = (int*)w->bstat.p;
     p.job_bc = (double* const*)w->jobptr.p;
@@ -274,6 +313,7 @@ static KParams make_params(bc_graph* g, Workspace* w, int n_heavy, int nbatch, c
     p.budget = o.barrier_budget > 0 ? o.barrier_budget : 40000000000ll;
     p.ext = ext ? 1 : 0;
     p.forward_only = 0;
+    p.group = o.group_vertices > 0 ? o.group_vertices : 32;
     return p;
 }
 
@@ -284,7 +324,7 @@ static int choose_width(int n, int nsrc, int requested) {
     if (nsrc <= 1) return 1;
     if (nsrc <= 32) return 32;
     const double bytes128 = (double)n * 128 * 20;
-    if (nsrc >= 256 && bytes128 < 16e9) return 128;
+    if (nsrc >= 256 && bytes128 < 24e9) return 128;
     return 64;
 }
 
@@ -293,18 +333,19 @@ static bc_status check_opts(const bc_options& o) {
         o.batch_width != 128)
         return fail(BC_E_INVALID_ARG, "batch_width must be 0, 1, 32, 64 or 128 (got %d)", o.batch_width);
     if (o.direction < 0 || o.direction > 2) return fail(BC_E_INVALID_ARG, "direction must be 0, 1 or 2");
-    if (o.heavy_degree < 0 || o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0)
+    if (o.group_vertices < 0 || o.group_vertices > 32) return fail(BC_E_INVALID_ARG, "group_vertices must be in [0, 32]");
+    if (o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0)
         return fail(BC_E_INVALID_ARG, "negative option value");
     return BC_OK;
 }
 
-static int grid_blocks(int K, int blocks_per_sm, int share) {
+static int grid_blocks(int K, bool ext, int blocks_per_sm, int share) {
     int per_sm = 0;
-    const int maxb = max_coop_blocks(K, &per_sm);
+    const int maxb = max_coop_blocks(K, ext, &per_sm);
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int bps = blocks_per_sm > 0 ? blocks_per_sm : (per_sm < 4 ? per_sm : 4);
+    int bps = blocks_per_sm > 0 ? blocks_per_sm : per_sm;
     if (bps > per_sm) bps = per_sm;
     int blocks = bps * sms;
     if (blocks > maxb) blocks = maxb;
@@ -318,10 +359,12 @@ static int grid_blocks(int K, int blocks_per_sm, int share) {
 struct RunOut {
     bool need_ext = false;
     bool inexact = false;
+    bool capacity = false;
+    float kernel_ms = 0.f;
     Ctl ctl{};
 };
 
-static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int nsrc, int K, int n_heavy, int blocks,
+static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int nsrc, int K, int blocks,
                           const bc_options& o, bool ext, const std::vector<double*>& job_bc,
                           const std::vector<int>* col_job, bool forward_only, cudaStream_t st, RunOut* ro) {
     const int nbatch = (nsrc + K - 1) / K;
@@ -343,21 +386,39 @@ static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int 
     if (bad) return fail(BC_E_SOURCE, "a source id is outside [0, %d)", g->n);
     if ((e = cudaMemsetAsync(w->ctl.p, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_fail(e, "memset");
     if ((e = cudaMemsetAsync(w->bstat.p, 0, sizeof(int) * nbatch, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    KParams p = make_params(g, w, n_heavy, nbatch, o, ext);
+    if ((e = cudaMemsetAsync(w->arr.p, 0, w->arr.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    KParams p = make_params(g, w, nbatch, o, ext);
     p.forward_only = forward_only ? 1 : 0;
     if (col_job) p.col_job = (const int*)w->coljob.p;
-    if ((e = launch_batches(K, p, blocks, st)) != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+    cudaEvent_t ev[2];
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    cudaEventRecord(ev[0], st);
+    e = launch_batches(K, p, blocks, st);
+    cudaEventRecord(ev[1], st);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        return cuda_fail(e, "persistent kernel launch");
+    }
     std::vector<int> bst(nbatch);
     if ((e = cudaMemcpyAsync(&ro->ctl, w->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "status read");
     if ((e = cudaMemcpyAsync(bst.data(), w->bstat.p, sizeof(int) * nbatch, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
         return cuda_fail(e, "status read");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "persistent kernel");
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) cudaEventElapsedTime(&ro->kernel_ms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent kernel");
     const Ctl& ctl = ro->ctl;
     if (ctl.err & ERR_TIMEOUT) return fail(BC_E_TIMEOUT, "a grid-barrier wait exceeded its cycle budget");
     if (ctl.err & ERR_LIMIT) return fail(BC_E_LIMIT, "BFS deeper than %d levels", kMaxLevel);
-    if (ctl.err & ERR_CAPACITY) return fail(BC_E_CUDA, "internal: level-list capacity exceeded");
+    if (ctl.err == ERR_CAPACITY) {
+        ro->capacity = true;
+        return BC_OK;
+    }
     if (ctl.err) return fail(BC_E_CUDA, "internal device error 0x%x", ctl.err);
     ro->need_ext = false;
     ro->inexact = false;
@@ -369,37 +430,44 @@ static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int 
     return BC_OK;
 }
 
-// A full call: batches of K, extended-form rerun when a count overflows 64
-// bits, accumulation into job buffers.  `zero` clears each job buffer first.
+// A full call: batches of K, reruns when a count overflows 64 bits (extended
+// form) or the level lists overflow (full capacity), accumulation into job
+// buffers (cleared first).
 static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc, const bc_options& o, int blocks_share,
                           const std::vector<double*>& job_bc, const std::vector<int>* col_job, bool forward_only,
-                          cudaStream_t st, bc_run_stats* stats, int* K_out, int* nheavy_out, bool* ext_out) {
+                          cudaStream_t st, bc_run_stats* stats, int* K_out, bool* ext_out, int* levels_out) {
     const int K = choose_width(g->n, nsrc, o.batch_width);
     const int nbatch = (nsrc + K - 1) / K;
-    const int heavy_thr = o.heavy_degree > 0 ? o.heavy_degree : 4096;
-    bc_status err = BC_OK;
-    const int n_heavy = heavy_count(g, heavy_thr, st, &err);
-    if (n_heavy < 0) return err;
-    const int blocks = grid_blocks(K, o.blocks_per_sm, blocks_share);
-    if (blocks < 1) return fail(BC_E_CUDA, "persistent kernel cannot be resident (occupancy 0)");
+    bc_status err = ensure_heavy(g, st);
+    if (err != BC_OK) return err;
     bool ext = g->sticky_ext;
+    int capf = cap_factor(K, g->sticky_cap.count(K) ? g->sticky_cap[K] : 0);
     bc_run_stats s{};
     s.batch_width = K;
     s.batches = nbatch;
-    s.grid_blocks = blocks;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        if (!ws_ensure(w, g->n, K, n_heavy, ext, nbatch, (int)job_bc.size(), st)) return BC_E_NOMEM;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        const int blocks = grid_blocks(K, ext, o.blocks_per_sm, blocks_share);
+        if (blocks < 1) return fail(BC_E_CUDA, "persistent kernel cannot be resident (occupancy 0)");
+        s.grid_blocks = blocks;
+        if (!ws_ensure(w, g, K, ext, nbatch, (int)job_bc.size(), capf, st)) return BC_E_NOMEM;
         for (double* jb : job_bc) {
             cudaError_t e = cudaMemsetAsync(jb, 0, sizeof(double) * (size_t)(g->n > 0 ? g->n : 1), st);
             if (e != cudaSuccess) return cuda_fail(e, "memset");
         }
         RunOut ro;
-        bc_status r = run_core(g, w, d_src, nsrc, K, n_heavy, blocks, o, ext, job_bc, col_job, forward_only, st, &ro);
+        bc_status r = run_core(g, w, d_src, nsrc, K, blocks, o, ext, job_bc, col_job, forward_only, st, &ro);
         if (r != BC_OK) return r;
         s.kernel_launches += 2;
+        s.kernel_ms += ro.kernel_ms;
         s.max_levels = ro.ctl.max_levels;
         s.pull_levels += ro.ctl.pull_levels;
         s.push_levels += ro.ctl.push_levels;
+        if (ro.capacity) {
+            if (capf >= K) return fail(BC_E_CUDA, "internal: level-list capacity exceeded at the bound");
+            capf = K;
+            g->sticky_cap[K] = K;
+            continue;
+        }
         if (ro.need_ext && !ext) {
             // rerun the whole call in the extended form, so that every source is
             // accumulated in list order exactly as in a single pass
@@ -411,11 +479,11 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
         if (ext) s.ext_batches = nbatch;
         if (stats) *stats = s;
         if (K_out) *K_out = K;
-        if (nheavy_out) *nheavy_out = n_heavy;
         if (ext_out) *ext_out = ext;
+        if (levels_out) *levels_out = ro.ctl.last_levels;
         return ro.inexact ? BC_W_SIGMA_INEXACT : BC_OK;
     }
-    return fail(BC_E_CUDA, "internal: extended rerun did not settle");
+    return fail(BC_E_CUDA, "internal: reruns did not settle");
 }
 
 // ------------------------------------------------------------------ serving
@@ -475,7 +543,8 @@ void worker_main(int slot) {
                     const auto& j = S.queue[i];
                     const int K = choose_width(j->g->n, (int)j->src.size(), 0);
                     const long long need =
-                        (long long)ws_need(j->g->n, K, j->g->n_nz, j->g->sticky_ext, 64, 64) +
+                        (long long)ws_need(j->g->n, K, j->g->n_heavy > 0 ? j->g->n_heavy : 0, j->g->hchunk_total,
+                                           j->g->sticky_ext, 64, 64, cap_factor(K, 0)) +
                         (long long)sizeof(double) * j->g->n * 64;
                     grow = need > my_reserved ? need - my_reserved : 0;
                     if (S.reserved + grow <= S.budget || S.running == 0) { lead = i; break; }
@@ -784,19 +853,19 @@ bc_status bc_debug_source(bc_graph* g, int32_t s, int32_t* level, double* sigma_
     auto& slot = g->ws[32];
     if (!slot) slot.reset(new Workspace());
     Workspace* w = slot.get();
-    int K = 0, n_heavy = 0;
+    int K = 0, levels = 0;
     bool ext = false;
     bc_status r = buf_ensure(w->bc, sizeof(double) * n, st) ? BC_OK : fail(BC_E_NOMEM, "debug buffers");
     if (r == BC_OK) {
         std::vector<double*> jb{(double*)w->bc.p};
-        r = run_jobs(g, w, (const int*)dsrc.p, 1, o, 1, jb, nullptr, true, st, nullptr, &K, &n_heavy, &ext);
+        r = run_jobs(g, w, (const int*)dsrc.p, 1, o, 1, jb, nullptr, true, st, nullptr, &K, &ext, &levels);
     }
-    KParams p = make_params(g, w, n_heavy, 1, o, ext);
+    KParams p = make_params(g, w, 1, o, ext);
     if (r < 0) {
         buf_release(dsrc, st); buf_release(dlev, st); buf_release(dsig, st); buf_release(dsige, st);
         return r;
     }
-    cudaError_t e = launch_debug_extract(p, 32, (int*)dlev.p, (unsigned long long*)dsig.p, (int*)dsige.p, st);
+    cudaError_t e = launch_debug_extract(p, 32, levels, (int*)dlev.p, (unsigned long long*)dsig.p, (int*)dsige.p, st);
     std::vector<int> lev(n), sige(n), perm(n);
     std::vector<unsigned long long> sig(n);
     if (e == cudaSuccess) e = cudaMemcpyAsync(lev.data(), dlev.p, sizeof(int) * n, cudaMemcpyDeviceToHost, st);

@@ -5,7 +5,8 @@
 
 namespace bcx {
 
-constexpr int kChunk = 1024;        // arcs per ordered partial sum (fixed: results depend on it)
+constexpr int kChunk = 1024;        // arcs per ordered partial sum (fixed: results depend on it);
+                                    // rows longer than this are "heavy" and split into chunk tasks
 constexpr int kMaxLevel = 65534;    // levels are uint16; 0xFFFF marks "not reached"
 constexpr int kThreads = 256;       // threads per block of the persistent kernels
 constexpr int kWarps = kThreads / 32;
@@ -26,7 +27,8 @@ struct Ctl {
     int max_levels;            // deepest BFS over the launch
     int pull_levels;
     int push_levels;
-    int pad[5];
+    int last_levels;           // levels of the last batch (debug runs)
+    int pad[4];
 };
 
 // Level bookkeeping, indexed by BFS level.
@@ -37,6 +39,7 @@ struct LevelArrays {
     int* hstart;         // first heavy entry index
     long long* dsum;     // sum of degrees of the level's entries
     long long* fulldeg;  // sum of degrees of vertices whose every column was reached at that level
+    int* hchunks;        // number of 1024-arc chunk tasks of the level's heavy entries
 };
 
 struct KParams {
@@ -51,14 +54,22 @@ struct KParams {
     // per-slot state
     uint32_t* V;               // [n][W] reached-column masks
     uint32_t* F[3];            // [n][W] frontier masks of three consecutive levels
-    uint16_t* lvl;             // [n][K]
     unsigned long long* sig;   // [n][K] path counts (mantissa in the extended form); delta bits after the sweep
     int* sig_e;                // [n][K] extended-form exponent (may be null when ext == 0)
     double* rho;               // [n][K] (1 + delta) / sigma (mantissa in the extended form)
     int* rho_e;                // [n][K]
-    int* ent;                  // light level lists (vertex ids)
+    int* ent;                  // light level lists (vertex ids), level by level
+    uint32_t* emask;           // [cap][W] columns of each light entry at its level
     int* hent;                 // heavy level lists
+    uint32_t* hmask;           // [hcap][W]
+    int* hpre;                 // [hcap] exclusive chunk prefix within the entry's level
     long long cap, hcap;
+    // heavy rows (degree > kChunk): ids [0, n_heavy); chunk slots hcum[r] .. hcum[r+1)
+    const int* hcum;           // [n_heavy + 1]
+    unsigned long long* scr_v; // [hcum[n_heavy]][K] chunk partial sums
+    int* scr_e;                // [hcum[n_heavy]][K] partial exponents (extended form)
+    uint32_t* scr_or;          // [hcum[n_heavy]][W] chunk OR of matched masks
+    int* arr;                  // [n_heavy] chunk arrival counters (zero between phases)
     int* stamp;                // [n] push-claim stamps
     LevelArrays la;
     Ctl* ctl;
@@ -71,15 +82,16 @@ struct KParams {
     long long budget;          // barrier spin budget (cycles)
     int ext;                   // run the extended path-count form
     int forward_only;          // debug: stop after the forward sweep (no delta, no BC)
+    int group;                 // light rows per warp task (1..32)
 };
 
 // Host-side launchers (bc_kernels.cu)
 cudaError_t launch_batches(int K, const KParams& p, int blocks, cudaStream_t st);
-int max_coop_blocks(int K, int* per_sm);
+int max_coop_blocks(int K, bool ext, int* per_sm);
 cudaError_t launch_unpermute(const double* bc_rel, const int* inv, double* out, int n, cudaStream_t st);
 cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, int n, int K, int* dst,
                                int nbatch, int* bad, cudaStream_t st);
-cudaError_t launch_debug_extract(const KParams& p, int K, int* level_rel, unsigned long long* sig_rel,
+cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
                                  int* sige_rel, cudaStream_t st);
 
 // Ingest (ingest.cu)

@@ -12,19 +12,31 @@
 //   * the path-count sum sigma_c(w) = sum of sigma_c(v) over frontier
 //     neighbours v (the BFS body w.sigma += v.sigma of the BC listing), pulled
 //     over each new vertex's row: no atomics.
-// Then the reverse sweep (iterateInReverse) walks the kept level lists from
-// the deepest level up, pulling rho_c(w) = (1 + delta_c(w)) / sigma_c(w) from
-// DAG successors:  delta_c(v) = sigma_c(v) * sum_w rho_c(w).  This equals the
-// listing's per-arc (sigma_v / sigma_w)(1 + delta_w) summed over w, with one
-// division per vertex and column instead of one per arc.  Finally each vertex
-// adds its columns' delta into BC (source columns excluded), in column order.
+// The reverse sweep (iterateInReverse) walks the kept level lists (vertex id
+// and column mask per entry) from the deepest level up, pulling
+// rho_c(w) = (1 + delta_c(w)) / sigma_c(w) from DAG successors:
+//     delta_c(v) = sigma_c(v) * sum_w rho_c(w).
+// This equals the listing's per-arc (sigma_v / sigma_w)(1 + delta_w) summed
+// over w, with one division per vertex and column instead of one per arc.
+// Finally each vertex adds its columns' delta into BC (source columns
+// excluded) in column order.
 //
-// Lanes map to columns (K >= 32: lane l owns columns [W*l, W*l + W), W = K/32)
-// so that a neighbour's per-column values are one coalesced row read; with
-// K == 1 lanes map to neighbours instead.  Every floating-point sum runs in
-// CSR order within fixed 1024-arc chunks, chunks combined in order, so each
-// column's arithmetic is independent of K, of the other columns and of the
-// push/pull choice: results are bitwise reproducible across batch widths.
+// Work decomposition (uniform units, no block-level phases):
+//   * rows of degree <= 1024 ("light") are handled up to 32 vertices per warp
+//     task; the warp enumerates the concatenated arcs of its rows 32 at a time
+//     (load-balanced: every lane holds one arc), then walks the matching arcs
+//     in CSR order with lanes mapped to columns (lane l owns columns
+//     [W*l, W*l+W), W = K/32) so that a neighbour's per-column values are one
+//     coalesced row read.  With K == 1 lanes load their own arc's value and
+//     the values are added in lane order.
+//   * rows of degree > 1024 ("heavy", a prefix of the degree-sorted ids) are
+//     cut into 1024-arc chunk tasks.  Each chunk's partial sum goes to a
+//     scratch slot; the warp that completes the last chunk combines the
+//     partials in chunk order and finishes the vertex.
+// Every floating-point sum therefore runs in CSR order within fixed 1024-arc
+// chunks, chunks combined in order: each column's arithmetic is independent
+// of K, of the other columns, of the grouping and of the push/pull choice, so
+// results are bitwise reproducible across all of them.
 //
 // Grid-wide phases are separated by a software barrier whose wait is bounded
 // by a cycle budget; on expiry it raises ERR_TIMEOUT and every block returns.
@@ -65,7 +77,7 @@ struct GridTeam {
                 while (*genp == g) {
                     if (*errp) { bad = 1; break; }
                     if (clock64() - t0 > budget) { atomicOr(&ctl->err, ERR_TIMEOUT); bad = 1; break; }
-                    __nanosleep(64);
+                    __nanosleep(32);
                 }
             }
             __threadfence();
@@ -76,18 +88,6 @@ struct GridTeam {
         return !s_bad;
     }
 };
-
-// ------------------------------------------------------------------ work distribution
-__device__ __forceinline__ int block_grab(unsigned int* ctr, long long total) {
-    __shared__ int s_item;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int i = atomicAdd(ctr, 1u);
-        s_item = ((long long)i < total) ? (int)i : -1;
-    }
-    __syncthreads();
-    return s_item;
-}
 
 __device__ __forceinline__ long long warp_grab(unsigned int* ctr, long long total, int G, int& cnt) {
     unsigned int i = 0;
@@ -101,13 +101,8 @@ __device__ __forceinline__ long long warp_grab(unsigned int* ctr, long long tota
 
 // ------------------------------------------------------------------ masks
 template <int W>
-struct Mask {
-    uint32_t w[W];
-};
-
-template <int W>
-__device__ __forceinline__ void load_mask(const uint32_t* base, int v, uint32_t (&m)[W]) {
-    const uint32_t* p = base + (size_t)v * W;
+__device__ __forceinline__ void load_mask(const uint32_t* base, long long idx, uint32_t (&m)[W]) {
+    const uint32_t* p = base + (size_t)idx * W;
     if constexpr (W == 1) {
         m[0] = p[0];
     } else if constexpr (W == 2) {
@@ -120,6 +115,18 @@ __device__ __forceinline__ void load_mask(const uint32_t* base, int v, uint32_t 
 }
 
 template <int W>
+__device__ __forceinline__ void store_mask_full(uint32_t* base, long long idx, const uint32_t (&m)[W]) {
+    uint32_t* p = base + (size_t)idx * W;
+    if constexpr (W == 1) {
+        p[0] = m[0];
+    } else if constexpr (W == 2) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(m[0], m[1]);
+    } else {
+        *reinterpret_cast<uint4*>(p) = make_uint4(m[0], m[1], m[2], m[3]);
+    }
+}
+
+template <int W>
 __device__ __forceinline__ bool mask_any(const uint32_t (&m)[W]) {
     uint32_t a = 0;
 #pragma unroll
@@ -127,10 +134,19 @@ __device__ __forceinline__ bool mask_any(const uint32_t (&m)[W]) {
     return a != 0;
 }
 
-// bits of column group [W*lane, W*lane+W) taken from word `word` of the mask
+// bits of column group [W*lane, W*lane+W) from word `word` of a mask
 template <int W>
 __device__ __forceinline__ uint32_t lane_field(uint32_t word, int lane) {
     return (word >> ((W * lane) & 31)) & ((1u << W) - 1u);
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&m)[W], int t) {
+    uint32_t x = m[0];
+#pragma unroll
+    for (int i = 1; i < W; ++i)
+        if (i == t) x = m[i];
+    return x;
 }
 
 // ------------------------------------------------------------------ extended-range arithmetic
@@ -168,422 +184,424 @@ __device__ __forceinline__ void xd_add(double& ar, int& ae, double xr, int xe) {
     }
 }
 
-// ------------------------------------------------------------------ accumulators
-// Per lane, W columns.  FWD: path counts.  BWD: sums of rho.
+// ------------------------------------------------------------------ accumulation
+// A running sum per (owner, column): FWD path counts (u64, or 64-bit mantissa
+// with exponent), BWD sums of rho (double bits, or double with exponent).
 enum { FWD = 0, BWD = 1 };
 
-template <int W, bool EXT, int DIR>
-struct Acc {
-    unsigned long long m[W];  // FWD mantissa
-    double r[W];              // BWD value
-    int e[W];                 // exponent (EXT)
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int t = 0; t < W; ++t) { m[t] = 0ull; r[t] = 0.0; e[t] = 0; }
-    }
-    // add column t of another accumulator / term
-    __device__ __forceinline__ void add1(int t, unsigned long long xm, double xr, int xe, bool& carry) {
-        if constexpr (DIR == FWD) {
-            if constexpr (EXT) {
-                xu_add(m[t], e[t], xm, xe);
-            } else {
-                unsigned long long s = m[t] + xm;
-                carry |= (s < xm);
-                m[t] = s;
-            }
-        } else {
-            if constexpr (EXT) xd_add(r[t], e[t], xr, xe);
-            else r[t] += xr;
-        }
-    }
-    __device__ __forceinline__ void add_acc(const Acc& o, bool& carry) {
-#pragma unroll
-        for (int t = 0; t < W; ++t) add1(t, o.m[t], o.r[t], o.e[t], carry);
-    }
-};
-
-// ------------------------------------------------------------------ gathers
-// Load the per-column term of neighbour v for this lane's columns selected by `my`.
-template <int K, int W, bool EXT, int DIR>
-__device__ __forceinline__ void load_term(const KParams& p, int v, uint32_t my, Acc<W, EXT, DIR>& tm) {
-    tm.zero();
-    if (!my) return;
-    const int lane = lane_id();
-    const size_t base = (size_t)v * K + (K == 1 ? 0 : (size_t)W * lane);
+template <bool EXT, int DIR>
+__device__ __forceinline__ void acc_add(unsigned long long& v, int& e, unsigned long long x, int xe, bool& carry) {
     if constexpr (DIR == FWD) {
-        const unsigned long long* s = p.sig + base;
-        if constexpr (W == 1) {
-            tm.m[0] = s[0];
-        } else if constexpr (W == 2) {
-            ulonglong2 x = *reinterpret_cast<const ulonglong2*>(s);
-            tm.m[0] = x.x; tm.m[1] = x.y;
-        } else {
-            ulonglong2 x = *reinterpret_cast<const ulonglong2*>(s);
-            ulonglong2 y = *reinterpret_cast<const ulonglong2*>(s + 2);
-            tm.m[0] = x.x; tm.m[1] = x.y; tm.m[2] = y.x; tm.m[3] = y.y;
-        }
         if constexpr (EXT) {
-#pragma unroll
-            for (int t = 0; t < W; ++t) tm.e[t] = p.sig_e[base + t];
+            xu_add(v, e, x, xe);
+        } else {
+            const unsigned long long s = v + x;
+            carry |= (s < x);
+            v = s;
         }
     } else {
-        const double* s = p.rho + base;
-        if constexpr (W == 1) {
-            tm.r[0] = s[0];
-        } else if constexpr (W == 2) {
-            double2 x = *reinterpret_cast<const double2*>(s);
-            tm.r[0] = x.x; tm.r[1] = x.y;
-        } else {
-            double2 x = *reinterpret_cast<const double2*>(s);
-            double2 y = *reinterpret_cast<const double2*>(s + 2);
-            tm.r[0] = x.x; tm.r[1] = x.y; tm.r[2] = y.x; tm.r[3] = y.y;
-        }
-        if constexpr (EXT) {
-#pragma unroll
-            for (int t = 0; t < W; ++t) tm.e[t] = p.rho_e[base + t];
-        }
+        double r = __longlong_as_double((long long)v);
+        if constexpr (EXT) xd_add(r, e, __longlong_as_double((long long)x), xe);
+        else r += __longlong_as_double((long long)x);
+        v = (unsigned long long)__double_as_longlong(r);
     }
-#pragma unroll
-    for (int t = 0; t < W; ++t)
-        if (!((my >> t) & 1u)) { tm.m[t] = 0ull; tm.r[t] = 0.0; tm.e[t] = 0; }
 }
 
-// One chunk [cb, ce) of a row, in CSR order, into `part` (zeroed by the caller).
-// Fm: neighbour masks; want: the columns of interest (uniform across the warp);
-// orm: per-lane OR of the matched masks (reduced by the caller).
-template <int K, int W, bool EXT, int DIR>
-__device__ __forceinline__ void gather_chunk(const KParams& p, long long cb, long long ce, const uint32_t* Fm,
-                                             const uint32_t (&want)[W], Acc<W, EXT, DIR>& part,
-                                             uint32_t (&orm)[W], bool& carry) {
+// ------------------------------------------------------------------ per-warp shared state
+template <int K>
+struct Geo {
+    static constexpr int W = K >= 32 ? K / 32 : 1;
+    // owners per light task: the per-owner accumulator rows use G*K <= 512 slots
+    static constexpr int G = K == 1 ? 32 : (K == 32 ? 16 : (K == 64 ? 8 : 4));
+    static constexpr int PCAP = 512;  // (arc, column) pairs buffered per round window
+};
+
+template <int K, bool EXT>
+struct WarpSmem {
+    static constexpr int W = Geo<K>::W, G = Geo<K>::G;
+    int ov[G];                    // owner vertex
+    int obeg[G];                  // first arc index (into adj) of the owner's range
+    int ostart[G];                // exclusive prefix of range lengths
+    int opos[G];                  // entry position of the owner (lists) or -1
+    uint32_t owant[G][W];         // columns of interest of the owner
+    uint32_t onm[G][W];           // OR of the owner's matched columns
+    unsigned long long acc[G * K];  // running sums, owner-major
+    int acce[EXT ? G * K : 1];    // exponents (extended form)
+    int sv[32];                   // neighbour of each arc of the current step
+    int so[32];                   // owner of each arc of the current step
+    uint32_t pr[Geo<K>::PCAP];    // expanded pairs: arc << 16 | column
+    int av[32];                   // append staging (pull): vertex
+    uint32_t am[32][W];           // append staging: mask
+    long long adeg;               // append staging: degree sum
+};
+
+// Fill the owner table (lane i describes owner i < ng) and return the arc total.
+template <int K, bool EXT>
+__device__ __forceinline__ int set_owners(WarpSmem<K, EXT>& ws, int ng, int v, int beg, int len, int pos,
+                                          const uint32_t (&want)[Geo<K>::W]) {
+    constexpr int W = Geo<K>::W;
     const int lane = lane_id();
-    const int myword = (W * lane) >> 5;
-    for (long long base = cb; base < ce; base += 32) {
-        const long long e = base + lane;
-        int v = 0;
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncwarp();
+    if (lane < ng) {
+        ws.ov[lane] = v;
+        ws.obeg[lane] = beg;
+        ws.ostart[lane] = incl - len;
+        ws.opos[lane] = pos;
+#pragma unroll
+        for (int t = 0; t < W; ++t) ws.owant[lane][t] = want[t];
+    }
+    __syncwarp();
+    return __shfl_sync(FULL_MASK, incl, 31);
+}
+
+// ------------------------------------------------------------------ grouped, pair-compacted gather
+// Walks the arcs of ng owners (ranges in the owner table, T arcs in total) 32
+// at a time, in CSR order.  For each arc (owner o, neighbour v) the matched
+// columns f = Fm[v] & want(o) are expanded into (arc, column) pairs, and the
+// pairs are processed 32 per round, one per lane: the term of v at column c is
+// added into acc[o][c].  Exact path counts use shared-memory atomics (integer
+// sums: order-free); every other sum is ordered: lanes hitting the same
+// (owner, column) add in lane order, which is CSR order.
+template <int K, bool EXT, int DIR>
+__device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>& ws, int ng, int T,
+                                             const uint32_t* __restrict__ Fm, bool& carry) {
+    constexpr int W = Geo<K>::W;
+    constexpr int PCAP = Geo<K>::PCAP;
+    constexpr bool ORDERED = EXT || DIR == BWD;
+    const int lane = lane_id();
+    const unsigned int lt = (1u << lane) - 1u;
+    for (int i = lane; i < ng * K; i += 32) {
+        ws.acc[i] = 0ull;
+        if constexpr (EXT) ws.acce[i] = 0;
+    }
+    for (int i = lane; i < ng * W; i += 32) (&ws.onm[0][0])[i] = 0u;
+    __syncwarp();
+    const unsigned long long* termv =
+        DIR == FWD ? p.sig : reinterpret_cast<const unsigned long long*>(p.rho);
+    const int* terme = DIR == FWD ? p.sig_e : p.rho_e;
+    for (int base = 0; base < T; base += 32) {
+        const int a = base + lane;
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1)
+            if (o + step < ng && ws.ostart[o + step] <= a) o += step;
+        int v = 0, n = 0;
         uint32_t f[W];
 #pragma unroll
         for (int t = 0; t < W; ++t) f[t] = 0;
-        if (e < ce) {
-            v = __ldg(p.adj + e);
+        if (a < T) {
+            v = __ldg(p.adj + ws.obeg[o] + (a - ws.ostart[o]));
             load_mask<W>(Fm, v, f);
 #pragma unroll
-            for (int t = 0; t < W; ++t) f[t] &= want[t];
-        }
-#pragma unroll
-        for (int t = 0; t < W; ++t) orm[t] |= f[t];
-        unsigned int bal = __ballot_sync(FULL_MASK, mask_any<W>(f));
-        if constexpr (K == 1) {
-            // lanes own neighbours: each matching lane loads its own term, then the
-            // terms are added in lane (= CSR) order by every lane.
-            Acc<W, EXT, DIR> mine;
-            load_term<K, W, EXT, DIR>(p, v, f[0] & 1u, mine);
-            while (bal) {
-                const int j = __ffs(bal) - 1;
-                bal &= bal - 1;
-                unsigned long long xm = __shfl_sync(FULL_MASK, mine.m[0], j);
-                double xr = __shfl_sync(FULL_MASK, mine.r[0], j);
-                int xe = __shfl_sync(FULL_MASK, mine.e[0], j);
-                part.add1(0, xm, xr, xe, carry);
+            for (int t = 0; t < W; ++t) {
+                f[t] &= ws.owant[o][t];
+                n += __popc(f[t]);
             }
-        } else {
-            while (bal) {
-                int js[4];
-                int nj = 0;
+        }
+        if (!__any_sync(FULL_MASK, n > 0)) continue;
+        if (n > 0) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (bal) { js[q] = __ffs(bal) - 1; bal &= bal - 1; nj = q + 1; }
-                    else js[q] = 0;
-                }
-                Acc<W, EXT, DIR> tm[4];
-                uint32_t my[4];
+            for (int t = 0; t < W; ++t)
+                if (f[t]) atomicOr(&ws.onm[o][t], f[t]);
+        }
+        ws.sv[lane] = v;
+        ws.so[lane] = o;
+        int incl = n;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int vj = __shfl_sync(FULL_MASK, v, js[q]);
-                    uint32_t word = 0;
+        for (int s = 1; s < 32; s <<= 1) {
+            int y = __shfl_up_sync(FULL_MASK, incl, s);
+            if (lane >= s) incl += y;
+        }
+        const int P = incl - n;
+        const int tot = __shfl_sync(FULL_MASK, incl, 31);
+        __syncwarp();
+        int j0 = 0, pb = 0;
+        while (pb < tot) {
+            // window: the arcs from j0 whose pairs fit in the buffer (always >= 1 arc)
+            const unsigned int inwin = __ballot_sync(FULL_MASK, lane >= j0 && incl - pb <= PCAP);
+            const int j1 = 32 - __clz(inwin);
+            const int pe = __shfl_sync(FULL_MASK, incl, j1 - 1);
+            if (lane >= j0 && lane < j1 && n > 0) {
+                int idx = P - pb;
 #pragma unroll
-                    for (int t = 0; t < W; ++t) {
-                        uint32_t x = __shfl_sync(FULL_MASK, f[t], js[q]);
-                        if (t == myword) word = x;
+                for (int t = 0; t < W; ++t) {
+                    uint32_t m = f[t];
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        ws.pr[idx++] = ((uint32_t)lane << 16) | (uint32_t)(t * 32 + b);
                     }
-                    my[q] = (q < nj) ? lane_field<W>(word, lane) : 0u;
-                    load_term<K, W, EXT, DIR>(p, vj, my[q], tm[q]);
                 }
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < nj) part.add_acc(tm[q], carry);
             }
-        }
-    }
-}
-
-// Whole row by one warp: chunks of kChunk arcs, each summed in order from zero,
-// combined in order into `total` (zeroed here).
-template <int K, int W, bool EXT, int DIR>
-__device__ __forceinline__ void warp_row(const KParams& p, long long beg, long long end, const uint32_t* Fm,
-                                         const uint32_t (&want)[W], Acc<W, EXT, DIR>& total, uint32_t (&orm)[W],
-                                         bool& carry) {
-    total.zero();
-    for (long long cb = beg; cb < end; cb += kChunk) {
-        Acc<W, EXT, DIR> part;
-        part.zero();
-        const long long ce = (end < cb + kChunk) ? end : cb + kChunk;
-        gather_chunk<K, W, EXT, DIR>(p, cb, ce, Fm, want, part, orm, carry);
-        total.add_acc(part, carry);
-    }
-}
-
-template <int W>
-__device__ __forceinline__ void warp_or_reduce(uint32_t (&m)[W]) {
-#pragma unroll
-    for (int t = 0; t < W; ++t) m[t] = __reduce_or_sync(FULL_MASK, m[t]);
-}
-
-// Shared scratch for block-level (heavy) rows.
-template <int W>
-struct HeavySmem {
-    unsigned long long m[kWarps][32 * W];
-    double r[kWarps][32 * W];
-    int e[kWarps][32 * W];
-    uint32_t orm[W];
-    int carry;
-};
-
-// Whole row by the block: warp w takes chunks w, w + kWarps, ...; partials are
-// combined in chunk order by warp 0, which returns the total.  The OR of the
-// matched masks is returned to every warp.
-template <int K, int W, bool EXT, int DIR>
-__device__ void block_row(const KParams& p, long long beg, long long end, const uint32_t* Fm,
-                          const uint32_t (&want)[W], Acc<W, EXT, DIR>& total, uint32_t (&orm)[W], bool& carry,
-                          HeavySmem<W>& sh) {
-    const int lane = lane_id(), wid = warp_id();
-    total.zero();
-    if (threadIdx.x < W) sh.orm[threadIdx.x] = 0;
-    if (threadIdx.x == 0) sh.carry = 0;
-    const long long nch = (end - beg + kChunk - 1) / kChunk;
-    for (long long r0 = 0; r0 < nch; r0 += kWarps) {
-        Acc<W, EXT, DIR> part;
-        part.zero();
-        const long long c = r0 + wid;
-        if (c < nch) {
-            const long long cb = beg + c * kChunk;
-            const long long ce = (end < cb + kChunk) ? end : cb + kChunk;
-            gather_chunk<K, W, EXT, DIR>(p, cb, ce, Fm, want, part, orm, carry);
-        }
-        // K == 1: every lane holds the same partial; lane-indexed slots keep the code uniform
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
-            sh.m[wid][lane * W + t] = part.m[t];
-            sh.r[wid][lane * W + t] = part.r[t];
-            sh.e[wid][lane * W + t] = part.e[t];
-        }
-        __syncthreads();
-        if (wid == 0) {
-            const long long lim = (nch - r0 < kWarps) ? (nch - r0) : kWarps;
-            for (int w2 = 0; w2 < lim; ++w2) {
-#pragma unroll
-                for (int t = 0; t < W; ++t)
-                    total.add1(t, sh.m[w2][lane * W + t], sh.r[w2][lane * W + t], sh.e[w2][lane * W + t], carry);
+            __syncwarp();
+            const int cnt = pe - pb;
+            for (int r = 0; r < cnt; r += 32) {
+                const int q = r + lane;
+                const bool valid = q < cnt;
+                int slot = 0;
+                unsigned long long x = 0ull;
+                int xe = 0;
+                if (valid) {
+                    const uint32_t e = ws.pr[q];
+                    const int j = (int)(e >> 16), c = (int)(e & 0xFFFFu);
+                    const size_t idx = (size_t)ws.sv[j] * K + c;
+                    slot = ws.so[j] * K + c;
+                    x = termv[idx];
+                    if constexpr (EXT) xe = terme[idx];
+                }
+                if constexpr (!ORDERED) {
+                    if (valid) {
+                        const unsigned long long old = atomicAdd(&ws.acc[slot], x);
+                        carry |= (old + x < old);
+                    }
+                } else {
+                    const int key = valid ? slot : -(lane + 1);
+                    const unsigned int peers = __match_any_sync(FULL_MASK, key);
+                    const int rank = __popc(peers & lt);
+                    const int maxr = __reduce_max_sync(FULL_MASK, valid ? rank : 0);
+                    for (int k = 0; k <= maxr; ++k) {
+                        if (valid && rank == k) {
+                            unsigned long long av = ws.acc[slot];
+                            int ae = EXT ? ws.acce[slot] : 0;
+                            acc_add<EXT, DIR>(av, ae, x, xe, carry);
+                            ws.acc[slot] = av;
+                            if constexpr (EXT) ws.acce[slot] = ae;
+                        }
+                        __syncwarp();
+                    }
+                }
             }
+            __syncwarp();
+            j0 = j1;
+            pb = pe;
         }
-        __syncthreads();
+        __syncwarp();
     }
-    warp_or_reduce<W>(orm);
-    if (lane == 0) {
-#pragma unroll
-        for (int t = 0; t < W; ++t) atomicOr(&sh.orm[t], orm[t]);
-        if (carry) atomicOr(&sh.carry, 1);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < W; ++t) orm[t] = sh.orm[t];
-    carry = sh.carry != 0;
-    __syncthreads();
+    __syncwarp();
 }
 
-// ------------------------------------------------------------------ appends
-// Per-warp staging of discovered vertices; flushed 32 at a time.
-struct AppendBuf {
-    int v[kWarps][32];
-    long long dsum[kWarps];
-};
+// ------------------------------------------------------------------ finishing a vertex
+// Forward: write path counts (from the owner's accumulator row) of the newly
+// reached columns nm of w and mark them reached.
+template <int K, bool EXT>
+__device__ __forceinline__ void fwd_write(const KParams& p, int w, const uint32_t (&nm)[Geo<K>::W], int lev,
+                                          const uint32_t (&act)[Geo<K>::W], const unsigned long long* accrow,
+                                          const int* accerow) {
+    constexpr int W = Geo<K>::W;
+    const int lane = lane_id();
+    uint32_t my;
+    if constexpr (K == 1) my = (lane == 0) ? (nm[0] & 1u) : 0u;
+    else my = lane_field<W>(pick<W>(nm, (W * lane) >> 5), lane);
+    bool inexact = false;
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        if ((my >> t) & 1u) {
+            const int c = K == 1 ? 0 : W * lane + t;
+            const size_t idx = (size_t)w * K + c;
+            const unsigned long long x = accrow[c];
+            p.sig[idx] = x;
+            int xe = 0;
+            if constexpr (EXT) {
+                xe = accerow[c];
+                p.sig_e[idx] = xe;
+            }
+            inexact |= (xe > 0 || x >= (1ull << 53));
+        }
+    }
+    if (__any_sync(FULL_MASK, inexact) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
+    bool full = true;
+    if (lane < W) {
+        const uint32_t nv = p.V[(size_t)w * W + lane] | pick<W>(nm, lane);
+        p.V[(size_t)w * W + lane] = nv;
+        const uint32_t a = pick<W>(act, lane);
+        full = (nv & a) == a;
+    }
+    if (__all_sync(FULL_MASK, full) && lane == 0)
+        atomicAdd((unsigned long long*)&p.la.fulldeg[lev], (unsigned long long)(p.off[w + 1] - p.off[w]));
+}
 
-__device__ __forceinline__ void flush_append(const KParams& p, int lev, AppendBuf& ab, int& cnt) {
-    const int lane = lane_id(), wid = warp_id();
+// Backward: delta and rho of v for its columns mk from the rho sums.
+template <int K, bool EXT>
+__device__ __forceinline__ void bwd_write(const KParams& p, int v, const uint32_t (&mk)[Geo<K>::W],
+                                          const unsigned long long* accrow, const int* accerow) {
+    constexpr int W = Geo<K>::W;
+    const int lane = lane_id();
+    uint32_t my;
+    if constexpr (K == 1) my = (lane == 0) ? (mk[0] & 1u) : 0u;
+    else my = lane_field<W>(pick<W>(mk, (W * lane) >> 5), lane);
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        if ((my >> t) & 1u) {
+            const int c = K == 1 ? 0 : W * lane + t;
+            const size_t idx = (size_t)v * K + c;
+            const double sd = (double)p.sig[idx];  // rounds only when the count is >= 2^53
+            const double sr = __longlong_as_double((long long)accrow[c]);
+            double delta, rho;
+            if constexpr (EXT) {
+                const int se = p.sig_e[idx];
+                delta = scalbn(sd * sr, se + accerow[c]);
+                rho = (1.0 + delta) / sd;
+                p.rho_e[idx] = -se;
+            } else {
+                delta = sd * sr;
+                rho = (1.0 + delta) / sd;
+            }
+            p.sig[idx] = (unsigned long long)__double_as_longlong(delta);
+            p.rho[idx] = rho;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ list appends
+template <int K, bool EXT>
+__device__ __forceinline__ void flush_append(const KParams& p, int lev, WarpSmem<K, EXT>& ws, int& cnt) {
+    constexpr int W = Geo<K>::W;
+    const int lane = lane_id();
     if (cnt == 0) return;
     __syncwarp();
     int base = 0;
     if (lane == 0) {
         base = atomicAdd(&p.la.cnt[lev], cnt);
-        atomicAdd((unsigned long long*)&p.la.dsum[lev], (unsigned long long)ab.dsum[wid]);
-        ab.dsum[wid] = 0;
+        atomicAdd((unsigned long long*)&p.la.dsum[lev], (unsigned long long)ws.adeg);
+        ws.adeg = 0;
     }
     base = __shfl_sync(FULL_MASK, base, 0);
     const long long pos = (long long)p.la.start[lev] + base + lane;
     if (lane < cnt) {
-        if (pos < p.cap) p.ent[pos] = ab.v[wid][lane];
-        else atomicOr(&p.ctl->err, ERR_CAPACITY);
+        if (pos < p.cap) {
+            p.ent[pos] = ws.av[lane];
+            uint32_t m[W];
+#pragma unroll
+            for (int t = 0; t < W; ++t) m[t] = ws.am[lane][t];
+            store_mask_full<W>(p.emask, pos, m);
+        } else {
+            atomicOr(&p.ctl->err, ERR_CAPACITY);
+        }
     }
     __syncwarp();
     cnt = 0;
 }
 
-// append one vertex (called by the whole warp, uniform)
-__device__ __forceinline__ void warp_append(const KParams& p, int lev, int w, long long deg, AppendBuf& ab, int& cnt) {
-    const int lane = lane_id(), wid = warp_id();
-    if (lane == 0) { ab.v[wid][cnt] = w; ab.dsum[wid] += deg; }
-    __syncwarp();
-    ++cnt;
-    if (cnt == 32) flush_append(p, lev, ab, cnt);
-}
-
-__device__ __forceinline__ void heavy_append(const KParams& p, int lev, int w, long long deg) {
-    int i = atomicAdd(&p.la.hcnt[lev], 1);
+template <int W>
+__device__ __forceinline__ void heavy_append(const KParams& p, int lev, int w, long long deg, const uint32_t (&m)[W]) {
+    const int i = atomicAdd(&p.la.hcnt[lev], 1);
     atomicAdd((unsigned long long*)&p.la.dsum[lev], (unsigned long long)deg);
-    long long pos = (long long)p.la.hstart[lev] + i;
-    if (pos < p.hcap) p.hent[pos] = w;
-    else atomicOr(&p.ctl->err, ERR_CAPACITY);
-}
-
-// ------------------------------------------------------------------ vertex finalisation
-// Forward: write path counts and levels of the newly reached columns `nm` of w.
-template <int K, int W, bool EXT>
-__device__ __forceinline__ void fwd_finish(const KParams& p, int w, const uint32_t (&nm)[W], int lev,
-                                           const uint32_t (&active)[W], const Acc<W, EXT, FWD>& tot) {
-    const int lane = lane_id();
-    if constexpr (K == 1) {
-        if (lane == 0) {
-            p.sig[w] = tot.m[0];
-            if constexpr (EXT) p.sig_e[w] = tot.e[0];
-            p.lvl[w] = (uint16_t)lev;
-            p.V[w] |= nm[0];
-            bool inexact = EXT ? (tot.e[0] > 0 || tot.m[0] >= (1ull << 53)) : (tot.m[0] >= (1ull << 53));
-            if (inexact) atomicOr(&p.ctl->flags, BST_INEXACT);
-            if ((p.V[w] & active[0]) == active[0])
-                atomicAdd((unsigned long long*)&p.la.fulldeg[lev], (unsigned long long)(p.off[w + 1] - p.off[w]));
-        }
+    const long long pos = (long long)p.la.hstart[lev] + i;
+    if (pos < p.hcap) {
+        p.hent[pos] = w;
+        store_mask_full<W>(p.hmask, pos, m);
     } else {
-        const int myword = (W * lane) >> 5;
-        uint32_t word = 0;
-#pragma unroll
-        for (int t = 0; t < W; ++t)
-            if (t == myword) word = nm[t];
-        const uint32_t my = lane_field<W>(word, lane);
-        bool inexact = false;
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
-            if ((my >> t) & 1u) {
-                const size_t idx = (size_t)w * K + W * lane + t;
-                p.sig[idx] = tot.m[t];
-                if constexpr (EXT) p.sig_e[idx] = tot.e[t];
-                p.lvl[idx] = (uint16_t)lev;
-                inexact |= EXT ? (tot.e[t] > 0 || tot.m[t] >= (1ull << 53)) : (tot.m[t] >= (1ull << 53));
-            }
-        }
-        if (__any_sync(FULL_MASK, inexact) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
-        bool full = true;
-        if (lane < W) {
-            uint32_t nv = p.V[(size_t)w * W + lane] | nm[0];
-            // select nm[lane] without dynamic register indexing
-#pragma unroll
-            for (int t = 0; t < W; ++t)
-                if (t == lane) nv = p.V[(size_t)w * W + lane] | nm[t];
-            p.V[(size_t)w * W + lane] = nv;
-            uint32_t act = active[0];
-#pragma unroll
-            for (int t = 0; t < W; ++t)
-                if (t == lane) act = active[t];
-            full = (nv & act) == act;
-        }
-        full = __all_sync(FULL_MASK, full);
-        if (full && lane == 0)
-            atomicAdd((unsigned long long*)&p.la.fulldeg[lev], (unsigned long long)(p.off[w + 1] - p.off[w]));
+        atomicOr(&p.ctl->err, ERR_CAPACITY);
     }
 }
 
-// Backward: from the rho sums, delta and rho of v for its columns `mk` at level l.
-template <int K, int W, bool EXT>
-__device__ __forceinline__ void bwd_finish(const KParams& p, int v, const uint32_t (&mk)[W],
-                                           const Acc<W, EXT, BWD>& tot) {
+// ------------------------------------------------------------------ heavy chunk tasks
+__device__ __forceinline__ int nchunks(int deg) { return (deg + kChunk - 1) / kChunk; }
+
+// Task t of a heavy list level -> (entry position, chunk), by binary search of
+// the level's chunk prefix.
+__device__ __forceinline__ void heavy_list_task(const KParams& p, int lev, int t, int& pos, int& chunk) {
+    int lo = p.la.hstart[lev], hi = lo + p.la.hcnt[lev] - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.hpre[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    pos = lo;
+    chunk = t - p.hpre[lo];
+}
+
+// Static heavy task t -> (vertex r, chunk) for the pull phase.
+__device__ __forceinline__ void heavy_static_task(const KParams& p, int t, int& r, int& chunk) {
+    int lo = 0, hi = p.n_heavy - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.hcum[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    r = lo;
+    chunk = t - p.hcum[lo];
+}
+
+// Exclusive chunk prefix of the heavy entries of a level (block 0, warp 0).
+__device__ void heavy_prefix(const KParams& p, int lev) {
+    if (blockIdx.x != 0 || warp_id() != 0) return;
     const int lane = lane_id();
-    uint32_t my;
-    if constexpr (K == 1) {
-        my = (lane == 0) ? (mk[0] & 1u) : 0u;
-    } else {
-        const int myword = (W * lane) >> 5;
-        uint32_t word = 0;
+    const int hs = p.la.hstart[lev], hc = p.la.hcnt[lev];
+    int carry = 0;
+    for (int i = 0; i < hc; i += 32) {
+        int c = 0;
+        if (i + lane < hc) {
+            const int v = p.hent[hs + i + lane];
+            c = nchunks(p.off[v + 1] - p.off[v]);
+        }
+        int incl = c;
 #pragma unroll
-        for (int t = 0; t < W; ++t)
-            if (t == myword) word = mk[t];
-        my = lane_field<W>(word, lane);
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (i + lane < hc) p.hpre[hs + i + lane] = carry + incl - c;
+        carry += __shfl_sync(FULL_MASK, incl, 31);
+    }
+    if (lane == 0) p.la.hchunks[lev] = carry;
+}
+
+// Store the chunk partial held in accumulator row 0; returns true (warp-
+// uniform) for the warp that completes the vertex, after combining every
+// partial, in chunk order, back into row 0 (and their masks into nm).
+template <int K, bool EXT, int DIR>
+__device__ __forceinline__ bool heavy_partial(const KParams& p, WarpSmem<K, EXT>& ws, int r, int chunk, int nch,
+                                              uint32_t (&nm)[Geo<K>::W]) {
+    constexpr int W = Geo<K>::W;
+    const int lane = lane_id();
+    const size_t slot = (size_t)(p.hcum[r] + chunk);
+    for (int c = lane; c < K; c += 32) {
+        p.scr_v[slot * K + c] = ws.acc[c];
+        if constexpr (EXT) p.scr_e[slot * K + c] = ws.acce[c];
+    }
+    if (lane < W) p.scr_or[slot * W + lane] = ws.onm[0][lane];
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = (atomicAdd(&p.arr[r], 1) == nch - 1);
+    last = __shfl_sync(FULL_MASK, last, 0);
+    if (!last) return false;
+    __threadfence();
+    bool carry = false;
+    const size_t s0 = (size_t)p.hcum[r];
+    for (int c = lane; c < K; c += 32) {
+        unsigned long long v = 0ull;
+        int e = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+            const unsigned long long x = *(volatile unsigned long long*)&p.scr_v[(s0 + ch) * K + c];
+            const int xe = EXT ? *(volatile int*)&p.scr_e[(s0 + ch) * K + c] : 0;
+            acc_add<EXT, DIR>(v, e, x, xe, carry);
+        }
+        ws.acc[c] = v;
+        if constexpr (EXT) ws.acce[c] = e;
     }
 #pragma unroll
     for (int t = 0; t < W; ++t) {
-        if ((my >> t) & 1u) {
-            const size_t idx = (size_t)v * K + (K == 1 ? 0 : W * lane + t);
-            const unsigned long long sm = p.sig[idx];
-            const double sd = (double)sm;  // rounds only when the count is >= 2^53
-            double delta, rho;
-            int rho_e = 0;
-            if constexpr (EXT) {
-                const int se = p.sig_e[idx];
-                delta = scalbn(sd * tot.r[t], se + tot.e[t]);
-                rho = (1.0 + delta) / sd;
-                rho_e = -se;
-            } else {
-                delta = sd * tot.r[t];
-                rho = (1.0 + delta) / sd;
-            }
-            p.sig[idx] = (unsigned long long)__double_as_longlong(delta);
-            p.rho[idx] = rho;
-            if constexpr (EXT) p.rho_e[idx] = rho_e;
-        }
+        uint32_t m = 0;
+        for (int ch = 0; ch < nch; ++ch) m |= *(volatile uint32_t*)&p.scr_or[(s0 + ch) * W + t];
+        nm[t] = m;
     }
+    __syncwarp();
+    if (lane == 0) p.arr[r] = 0;
+    return true;
 }
 
 // ------------------------------------------------------------------ phases
-template <int K>
-struct Cfg {
-    static constexpr int W = K >= 32 ? K / 32 : 1;
-};
-
-// Level-`lev` column mask of v from the stored levels (K >= 32: every lane
-// tests its W columns; the words are assembled with OR reductions).
-template <int K, int W>
-__device__ __forceinline__ void level_mask(const KParams& p, int v, int lev, uint32_t (&mk)[W]) {
-    const int lane = lane_id();
-    uint32_t vm[W];
-    load_mask<W>(p.V, v, vm);
-    if constexpr (K == 1) {
-        mk[0] = (vm[0] & 1u) && p.lvl[v] == (uint16_t)lev ? 1u : 0u;
-    } else {
-        uint32_t field = 0;
-#pragma unroll
-        for (int t = 0; t < W; ++t)
-            if (p.lvl[(size_t)v * K + W * lane + t] == (uint16_t)lev) field |= 1u << t;
-        const int myword = (W * lane) >> 5;
-#pragma unroll
-        for (int t = 0; t < W; ++t) {
-            uint32_t contrib = (t == myword) ? (field << ((W * lane) & 31)) : 0u;
-            mk[t] = __reduce_or_sync(FULL_MASK, contrib) & vm[t];
-        }
-    }
+__device__ __forceinline__ unsigned int* wq(const KParams& p, int ph, int which) {
+    return &p.ctl->wq[(ph & 3) * 2 + which];
 }
-
-template <int W>
-__device__ __forceinline__ void store_mask(uint32_t* base, int v, const uint32_t (&m)[W]) {
-    const int lane = lane_id();
-    if (lane < W) {
-        uint32_t x = m[0];
-#pragma unroll
-        for (int t = 0; t < W; ++t)
-            if (t == lane) x = m[t];
-        base[(size_t)v * W + lane] = x;
-    }
-}
-
-// Per-phase counters: slot = ph & 3; the slot two phases ahead is cleared here.
-__device__ __forceinline__ unsigned int* wq_heavy(const KParams& p, int ph) { return &p.ctl->wq[(ph & 3) * 2]; }
-__device__ __forceinline__ unsigned int* wq_light(const KParams& p, int ph) { return &p.ctl->wq[(ph & 3) * 2 + 1]; }
 __device__ __forceinline__ void phase_prologue(const KParams& p, int ph) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         p.ctl->wq[((ph + 2) & 3) * 2] = 0;
@@ -598,111 +616,140 @@ __device__ void clear_level_masks(const KParams& p, uint32_t* F, int lev) {
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (long long i = tid; i < (c + hc) * W; i += nthr) {
-        long long j = i / W;
-        int t = (int)(i % W);
-        int v = j < c ? p.ent[s + j] : p.hent[hs + (j - c)];
+        const long long j = i / W;
+        const int t = (int)(i % W);
+        const int v = j < c ? p.ent[s + j] : p.hent[hs + (j - c)];
         F[(size_t)v * W + t] = 0;
     }
 }
 
 template <int K>
-__device__ void active_mask(const KParams& p, int b, uint32_t (&act)[Cfg<K>::W]) {
-    constexpr int W = Cfg<K>::W;
+__device__ void active_mask(const KParams& p, int b, uint32_t (&act)[Geo<K>::W]) {
+    constexpr int W = Geo<K>::W;
 #pragma unroll
     for (int t = 0; t < W; ++t) act[t] = 0;
     for (int c = 0; c < K; ++c)
         if (p.src[(size_t)b * K + c] >= 0) act[c >> 5] |= 1u << (c & 31);
 }
 
+template <int W>
+__device__ __forceinline__ void read_mask_s(const uint32_t (&src)[W], uint32_t (&m)[W]) {
+#pragma unroll
+    for (int t = 0; t < W; ++t) m[t] = src[t];
+}
+
 // Pull (bottom-up) discovery fused with the path-count sum, iteration `it`
 // (frontier = level it, new vertices get level it + 1).
 template <int K, bool EXT>
-__device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&act)[Cfg<K>::W], AppendBuf& ab,
-                           HeavySmem<Cfg<K>::W>& hs) {
-    constexpr int W = Cfg<K>::W;
+__device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&act)[Geo<K>::W], WarpSmem<K, EXT>& ws,
+                           int group) {
+    constexpr int W = Geo<K>::W;
     const int lane = lane_id();
     const uint32_t* Fc = p.F[it % 3];
     uint32_t* Fn = p.F[(it + 1) % 3];
     const int lev = it + 1;
     bool carry = false;
     phase_prologue(p, ph);
-    // heavy rows: whole blocks
+    // heavy rows: chunk tasks over the static prefix of heavy ids
+    const int HC = p.n_heavy > 0 ? p.hcum[p.n_heavy] : 0;
     for (;;) {
-        int w = block_grab(wq_heavy(p, ph), p.n_heavy);
-        if (w < 0) break;
+        int cnt;
+        const long long t0 = warp_grab(wq(p, ph, 0), HC, 1, cnt);
+        if (t0 < 0) break;
+        int r, chunk;
+        heavy_static_task(p, (int)t0, r, chunk);
         uint32_t vm[W], um[W];
-        load_mask<W>(p.V, w, vm);
+        load_mask<W>(p.V, r, vm);
 #pragma unroll
         for (int t = 0; t < W; ++t) um[t] = act[t] & ~vm[t];
         if (!mask_any<W>(um)) continue;
-        Acc<W, EXT, FWD> tot;
+        const int rb = p.off[r], deg = p.off[r + 1] - rb, nch = nchunks(deg);
+        const int cb = chunk * kChunk, len = min(kChunk, deg - cb);
+        const int T = set_owners<K, EXT>(ws, 1, r, rb + cb, lane == 0 ? len : 0, -1, um);
+        group_gather<K, EXT, FWD>(p, ws, 1, T, Fc, carry);
         uint32_t nm[W];
-#pragma unroll
-        for (int t = 0; t < W; ++t) nm[t] = 0;
-        block_row<K, W, EXT, FWD>(p, p.off[w], p.off[w + 1], Fc, um, tot, nm, carry, hs);
-        if (mask_any<W>(nm) && warp_id() == 0) {
-            store_mask<W>(Fn, w, nm);
-            fwd_finish<K, W, EXT>(p, w, nm, lev, act, tot);
-            if (lane == 0) heavy_append(p, lev, w, p.off[w + 1] - p.off[w]);
+        if (heavy_partial<K, EXT, FWD>(p, ws, r, chunk, nch, nm) && mask_any<W>(nm)) {
+            if (lane == 0) store_mask_full<W>(Fn, r, nm);
+            fwd_write<K, EXT>(p, r, nm, lev, act, ws.acc, ws.acce);
+            if (lane == 0) heavy_append<W>(p, lev, r, deg, nm);
         }
     }
-    // light rows: one warp each
+    // light rows: groups of consecutive ids
     int acnt = 0;
+    if (lane == 0) ws.adeg = 0;
     const long long nlight = (long long)p.n_nz - p.n_heavy;
+    const long long ngroups = (nlight + group - 1) / group;
     for (;;) {
         int cnt;
-        long long i0 = warp_grab(wq_light(p, ph), nlight, 32, cnt);
-        if (i0 < 0) break;
-        for (int q = 0; q < cnt; ++q) {
-            const int w = p.n_heavy + (int)(i0 + q);
-            uint32_t vm[W], um[W];
-            load_mask<W>(p.V, w, vm);
+        const long long g0 = warp_grab(wq(p, ph, 1), ngroups, 1, cnt);
+        if (g0 < 0) break;
+        const long long first = p.n_heavy + g0 * group;
+        const int ng = (int)min((long long)group, (long long)p.n_nz - first);
+        int v = 0, beg = 0, len = 0;
+        uint32_t um[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) um[t] = 0;
+        if (lane < ng) {
+            v = (int)(first + lane);
+            uint32_t vm[W];
+            load_mask<W>(p.V, v, vm);
 #pragma unroll
             for (int t = 0; t < W; ++t) um[t] = act[t] & ~vm[t];
-            if (!mask_any<W>(um)) continue;
-            Acc<W, EXT, FWD> tot;
+            beg = p.off[v];
+            len = mask_any<W>(um) ? p.off[v + 1] - beg : 0;
+        }
+        if (!__any_sync(FULL_MASK, len > 0)) continue;
+        const int T = set_owners<K, EXT>(ws, ng, v, beg, len, -1, um);
+        group_gather<K, EXT, FWD>(p, ws, ng, T, Fc, carry);
+        for (int o = 0; o < ng; ++o) {
             uint32_t nm[W];
+            read_mask_s<W>(ws.onm[o], nm);
+            if (!mask_any<W>(nm)) continue;
+            const int w = ws.ov[o];
+            if (lane == 0) store_mask_full<W>(Fn, w, nm);
+            fwd_write<K, EXT>(p, w, nm, lev, act, ws.acc + o * K, ws.acce + (EXT ? o * K : 0));
+            if (lane == 0) {
+                ws.av[acnt] = w;
 #pragma unroll
-            for (int t = 0; t < W; ++t) nm[t] = 0;
-            warp_row<K, W, EXT, FWD>(p, p.off[w], p.off[w + 1], Fc, um, tot, nm, carry);
-            warp_or_reduce<W>(nm);
-            if (mask_any<W>(nm)) {
-                store_mask<W>(Fn, w, nm);
-                fwd_finish<K, W, EXT>(p, w, nm, lev, act, tot);
-                warp_append(p, lev, w, p.off[w + 1] - p.off[w], ab, acnt);
+                for (int t = 0; t < W; ++t) ws.am[acnt][t] = nm[t];
+                ws.adeg += p.off[w + 1] - p.off[w];
             }
+            __syncwarp();
+            if (++acnt == 32) flush_append<K, EXT>(p, lev, ws, acnt);
         }
     }
-    flush_append(p, lev, ab, acnt);
-    if (__any_sync(FULL_MASK, carry) && lane_id() == 0) atomicOr(&p.ctl->flags, BST_NEED_EXT);
+    flush_append<K, EXT>(p, lev, ws, acnt);
+    if (__any_sync(FULL_MASK, carry) && lane == 0) atomicOr(&p.ctl->flags, BST_NEED_EXT);
     if (it >= 1) clear_level_masks<W>(p, p.F[(it + 2) % 3], it - 1);
 }
 
 // Push (top-down) discovery over the frontier entries of level `it`.
-template <int K>
-__device__ void phase_push(const KParams& p, int it, int ph, const uint32_t (&act)[Cfg<K>::W]) {
-    constexpr int W = Cfg<K>::W;
+template <int K, bool EXT>
+__device__ void phase_push(const KParams& p, int it, int ph, WarpSmem<K, EXT>& ws, int group) {
+    constexpr int W = Geo<K>::W;
     const int lane = lane_id();
-    const uint32_t* Fc = p.F[it % 3];
     uint32_t* Fn = p.F[(it + 1) % 3];
     const int lev = it + 1;
     const int stampv = lev;
     phase_prologue(p, ph);
-    auto visit = [&](int v, long long e0, long long e1, long long step) {
-        uint32_t fm[W];
-        load_mask<W>(Fc, v, fm);
-        for (long long base = e0; base < e1; base += step) {
-            const long long e = base + lane;
+    // claim unseen columns of the neighbours of the owner table's arcs
+    auto visit = [&](int ng, int T) {
+        for (int base = 0; base < T; base += 32) {
+            const int a = base + lane;
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1)
+                if (o + step < ng && ws.ostart[o + step] <= a) o += step;
             bool light_claim = false, heavy_claim = false;
             int w = 0;
             long long deg = 0;
-            if (e < e1) {
-                w = __ldg(p.adj + e);
+            if (a < T) {
+                w = __ldg(p.adj + ws.obeg[o] + (a - ws.ostart[o]));
                 uint32_t vw[W], nb[W];
                 load_mask<W>(p.V, w, vw);
                 bool any = false;
 #pragma unroll
-                for (int t = 0; t < W; ++t) { nb[t] = fm[t] & ~vw[t]; any |= nb[t] != 0; }
+                for (int t = 0; t < W; ++t) { nb[t] = ws.owant[o][t] & ~vw[t]; any |= nb[t] != 0; }
                 if (any) {
 #pragma unroll
                     for (int t = 0; t < W; ++t)
@@ -718,7 +765,7 @@ __device__ void phase_push(const KParams& p, int it, int ph, const uint32_t (&ac
             if (lb) {
                 long long ds = light_claim ? deg : 0;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(FULL_MASK, ds, o);
+                for (int s = 16; s > 0; s >>= 1) ds += __shfl_xor_sync(FULL_MASK, ds, s);
                 int base0 = 0;
                 const int leader = __ffs(lb) - 1;
                 if (lane == leader) {
@@ -732,112 +779,176 @@ __device__ void phase_push(const KParams& p, int it, int ph, const uint32_t (&ac
                     else atomicOr(&p.ctl->err, ERR_CAPACITY);
                 }
             }
-            if (heavy_claim) heavy_append(p, lev, w, deg);
+            if (heavy_claim) {
+                const int i = atomicAdd(&p.la.hcnt[lev], 1);
+                atomicAdd((unsigned long long*)&p.la.dsum[lev], (unsigned long long)deg);
+                const long long pos = (long long)p.la.hstart[lev] + i;
+                if (pos < p.hcap) p.hent[pos] = w;
+                else atomicOr(&p.ctl->err, ERR_CAPACITY);
+            }
         }
     };
-    // heavy frontier rows: whole blocks, warps interleaved over the row
-    const int hs = p.la.hstart[it], hc = p.la.hcnt[it];
-    for (;;) {
-        int i = block_grab(wq_heavy(p, ph), hc);
-        if (i < 0) break;
-        const int v = p.hent[hs + i];
-        visit(v, (long long)p.off[v] + warp_id() * 32, p.off[v + 1], (long long)kThreads);
-    }
-    const int ls = p.la.start[it], lc = p.la.cnt[it];
+    // heavy frontier rows: chunk tasks
+    const int HT = p.la.hcnt[it] > 0 ? p.la.hchunks[it] : 0;
     for (;;) {
         int cnt;
-        long long i0 = warp_grab(wq_light(p, ph), lc, 4, cnt);
-        if (i0 < 0) break;
-        for (int q = 0; q < cnt; ++q) {
-            const int v = p.ent[ls + i0 + q];
-            visit(v, p.off[v], p.off[v + 1], 32);
-        }
+        const long long t0 = warp_grab(wq(p, ph, 0), HT, 1, cnt);
+        if (t0 < 0) break;
+        int pos, chunk;
+        heavy_list_task(p, it, (int)t0, pos, chunk);
+        const int v = p.hent[pos];
+        uint32_t fm[W];
+        load_mask<W>(p.hmask, pos, fm);
+        const int rb = p.off[v], deg = p.off[v + 1] - rb;
+        const int cb = chunk * kChunk, len = min(kChunk, deg - cb);
+        const int T = set_owners<K, EXT>(ws, 1, v, rb + cb, lane == 0 ? len : 0, pos, fm);
+        visit(1, T);
+        __syncwarp();
     }
-    (void)act;
+    // light frontier entries: groups
+    constexpr int G = Geo<K>::G;
+    const int grp = group < G ? group : G;
+    const int ls = p.la.start[it], lc = p.la.cnt[it];
+    const long long ngroups = (lc + grp - 1) / grp;
+    for (;;) {
+        int cnt;
+        const long long g0 = warp_grab(wq(p, ph, 1), ngroups, 1, cnt);
+        if (g0 < 0) break;
+        const int first = (int)(g0 * grp);
+        const int ng = min(grp, lc - first);
+        int v = 0, beg = 0, len = 0;
+        uint32_t fm[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) fm[t] = 0;
+        if (lane < ng) {
+            v = p.ent[ls + first + lane];
+            load_mask<W>(p.emask, ls + first + lane, fm);
+            beg = p.off[v];
+            len = p.off[v + 1] - beg;
+        }
+        const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, fm);
+        visit(ng, T);
+        __syncwarp();
+    }
 }
 
 // Path counts of the vertices claimed by the push phase (entries of level it+1).
 template <int K, bool EXT>
-__device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&act)[Cfg<K>::W],
-                            HeavySmem<Cfg<K>::W>& hs) {
-    constexpr int W = Cfg<K>::W;
+__device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&act)[Geo<K>::W],
+                            WarpSmem<K, EXT>& ws, int group) {
+    constexpr int W = Geo<K>::W;
+    const int lane = lane_id();
     const uint32_t* Fc = p.F[it % 3];
     const uint32_t* Fn = p.F[(it + 1) % 3];
     const int lev = it + 1;
     bool carry = false;
     phase_prologue(p, ph);
-    const int hst = p.la.hstart[lev], hc = p.la.hcnt[lev];
-    for (;;) {
-        int i = block_grab(wq_heavy(p, ph), hc);
-        if (i < 0) break;
-        const int w = p.hent[hst + i];
-        uint32_t nm[W], orm[W];
-        load_mask<W>(Fn, w, nm);
-#pragma unroll
-        for (int t = 0; t < W; ++t) orm[t] = 0;
-        Acc<W, EXT, FWD> tot;
-        block_row<K, W, EXT, FWD>(p, p.off[w], p.off[w + 1], Fc, nm, tot, orm, carry, hs);
-        if (warp_id() == 0) fwd_finish<K, W, EXT>(p, w, nm, lev, act, tot);
-    }
-    const int ls = p.la.start[lev], lc = p.la.cnt[lev];
+    const int HT = p.la.hcnt[lev] > 0 ? p.la.hchunks[lev] : 0;
     for (;;) {
         int cnt;
-        long long i0 = warp_grab(wq_light(p, ph), lc, 4, cnt);
-        if (i0 < 0) break;
-        for (int q = 0; q < cnt; ++q) {
-            const int w = p.ent[ls + i0 + q];
-            uint32_t nm[W], orm[W];
-            load_mask<W>(Fn, w, nm);
-#pragma unroll
-            for (int t = 0; t < W; ++t) orm[t] = 0;
-            Acc<W, EXT, FWD> tot;
-            warp_row<K, W, EXT, FWD>(p, p.off[w], p.off[w + 1], Fc, nm, tot, orm, carry);
-            fwd_finish<K, W, EXT>(p, w, nm, lev, act, tot);
+        const long long t0 = warp_grab(wq(p, ph, 0), HT, 1, cnt);
+        if (t0 < 0) break;
+        int pos, chunk;
+        heavy_list_task(p, lev, (int)t0, pos, chunk);
+        const int w = p.hent[pos];
+        uint32_t nm[W];
+        load_mask<W>(Fn, w, nm);
+        const int rb = p.off[w], deg = p.off[w + 1] - rb, nch = nchunks(deg);
+        const int cb = chunk * kChunk, len = min(kChunk, deg - cb);
+        const int T = set_owners<K, EXT>(ws, 1, w, rb + cb, lane == 0 ? len : 0, pos, nm);
+        group_gather<K, EXT, FWD>(p, ws, 1, T, Fc, carry);
+        uint32_t om[W];
+        if (heavy_partial<K, EXT, FWD>(p, ws, w, chunk, nch, om)) {
+            fwd_write<K, EXT>(p, w, nm, lev, act, ws.acc, ws.acce);
+            if (lane == 0) store_mask_full<W>(p.hmask, pos, nm);
         }
     }
-    if (__any_sync(FULL_MASK, carry) && lane_id() == 0) atomicOr(&p.ctl->flags, BST_NEED_EXT);
+    const int ls = p.la.start[lev], lc = p.la.cnt[lev];
+    const long long ngroups = (lc + group - 1) / group;
+    for (;;) {
+        int cnt;
+        const long long g0 = warp_grab(wq(p, ph, 1), ngroups, 1, cnt);
+        if (g0 < 0) break;
+        const int first = (int)(g0 * group);
+        const int ng = min(group, lc - first);
+        int v = 0, beg = 0, len = 0;
+        uint32_t nm[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) nm[t] = 0;
+        if (lane < ng) {
+            v = p.ent[ls + first + lane];
+            load_mask<W>(Fn, v, nm);
+            beg = p.off[v];
+            len = p.off[v + 1] - beg;
+        }
+        const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, nm);
+        group_gather<K, EXT, FWD>(p, ws, ng, T, Fc, carry);
+        for (int o = 0; o < ng; ++o) {
+            uint32_t want[W];
+            read_mask_s<W>(ws.owant[o], want);
+            fwd_write<K, EXT>(p, ws.ov[o], want, lev, act, ws.acc + o * K, ws.acce + (EXT ? o * K : 0));
+            if (lane == 0) store_mask_full<W>(p.emask, ws.opos[o], want);
+        }
+    }
+    if (__any_sync(FULL_MASK, carry) && lane == 0) atomicOr(&p.ctl->flags, BST_NEED_EXT);
     if (it >= 1) clear_level_masks<W>(p, p.F[(it + 2) % 3], it - 1);
 }
 
 // Reverse sweep over level l: delta and rho of its entries from level l+1.
 template <int K, bool EXT>
-__device__ void phase_back(const KParams& p, int l, int ph, HeavySmem<Cfg<K>::W>& hs) {
-    constexpr int W = Cfg<K>::W;
+__device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws, int group) {
+    constexpr int W = Geo<K>::W;
+    const int lane = lane_id();
     const uint32_t* Fd = p.F[(l + 1) % 3];  // level l+1 masks
-    uint32_t* Fl = p.F[l % 3];              // level l masks (written for level l-1)
+    uint32_t* Fl = p.F[l % 3];              // level l masks (read by level l-1)
     bool carry = false;
     phase_prologue(p, ph);
-    const int hst = p.la.hstart[l], hc = p.la.hcnt[l];
+    const int HT = p.la.hcnt[l] > 0 ? p.la.hchunks[l] : 0;
     for (;;) {
-        int i = block_grab(wq_heavy(p, ph), hc);
-        if (i < 0) break;
-        const int v = p.hent[hst + i];
-        uint32_t mk[W], orm[W];
-        level_mask<K, W>(p, v, l, mk);
-#pragma unroll
-        for (int t = 0; t < W; ++t) orm[t] = 0;
-        Acc<W, EXT, BWD> tot;
-        block_row<K, W, EXT, BWD>(p, p.off[v], p.off[v + 1], Fd, mk, tot, orm, carry, hs);
-        if (warp_id() == 0) {
-            bwd_finish<K, W, EXT>(p, v, mk, tot);
-            store_mask<W>(Fl, v, mk);
+        int cnt;
+        const long long t0 = warp_grab(wq(p, ph, 0), HT, 1, cnt);
+        if (t0 < 0) break;
+        int pos, chunk;
+        heavy_list_task(p, l, (int)t0, pos, chunk);
+        const int v = p.hent[pos];
+        uint32_t mk[W];
+        load_mask<W>(p.hmask, pos, mk);
+        const int rb = p.off[v], deg = p.off[v + 1] - rb, nch = nchunks(deg);
+        const int cb = chunk * kChunk, len = min(kChunk, deg - cb);
+        const int T = set_owners<K, EXT>(ws, 1, v, rb + cb, lane == 0 ? len : 0, pos, mk);
+        group_gather<K, EXT, BWD>(p, ws, 1, T, Fd, carry);
+        uint32_t om[W];
+        if (heavy_partial<K, EXT, BWD>(p, ws, v, chunk, nch, om)) {
+            bwd_write<K, EXT>(p, v, mk, ws.acc, ws.acce);
+            if (lane == 0) store_mask_full<W>(Fl, v, mk);
         }
     }
     const int ls = p.la.start[l], lc = p.la.cnt[l];
+    const long long ngroups = (lc + group - 1) / group;
     for (;;) {
         int cnt;
-        long long i0 = warp_grab(wq_light(p, ph), lc, 4, cnt);
-        if (i0 < 0) break;
-        for (int q = 0; q < cnt; ++q) {
-            const int v = p.ent[ls + i0 + q];
-            uint32_t mk[W], orm[W];
-            level_mask<K, W>(p, v, l, mk);
+        const long long g0 = warp_grab(wq(p, ph, 1), ngroups, 1, cnt);
+        if (g0 < 0) break;
+        const int first = (int)(g0 * group);
+        const int ng = min(group, lc - first);
+        int v = 0, beg = 0, len = 0;
+        uint32_t mk[W];
 #pragma unroll
-            for (int t = 0; t < W; ++t) orm[t] = 0;
-            Acc<W, EXT, BWD> tot;
-            warp_row<K, W, EXT, BWD>(p, p.off[v], p.off[v + 1], Fd, mk, tot, orm, carry);
-            bwd_finish<K, W, EXT>(p, v, mk, tot);
-            store_mask<W>(Fl, v, mk);
+        for (int t = 0; t < W; ++t) mk[t] = 0;
+        if (lane < ng) {
+            v = p.ent[ls + first + lane];
+            load_mask<W>(p.emask, ls + first + lane, mk);
+            beg = p.off[v];
+            len = p.off[v + 1] - beg;
+        }
+        const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, mk);
+        group_gather<K, EXT, BWD>(p, ws, ng, T, Fd, carry);
+        for (int o = 0; o < ng; ++o) {
+            uint32_t want[W];
+            read_mask_s<W>(ws.owant[o], want);
+            const int u = ws.ov[o];
+            bwd_write<K, EXT>(p, u, want, ws.acc + o * K, ws.acce + (EXT ? o * K : 0));
+            if (lane == 0) store_mask_full<W>(Fl, u, want);
         }
     }
     clear_level_masks<W>(p, p.F[(l + 2) % 3], l + 2);
@@ -850,13 +961,13 @@ __device__ void phase_back(const KParams& p, int l, int ph, HeavySmem<Cfg<K>::W>
 // else shares the batch.
 template <int K>
 __device__ void phase_bc(const KParams& p, int b) {
-    constexpr int W = Cfg<K>::W;
+    constexpr int W = Geo<K>::W;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const int* src = p.src + (size_t)b * K;
     const int* cj = p.col_job ? p.col_job + (size_t)b * K : nullptr;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < p.n_nz; v += nthr) {
         uint32_t vm[W];
-        load_mask<W>(p.V, (int)v, vm);
+        load_mask<W>(p.V, v, vm);
         if (!mask_any<W>(vm)) continue;
         int cur = -1;
         double acc = 0.0;
@@ -878,11 +989,12 @@ __device__ void phase_bc(const KParams& p, int b) {
 
 // ------------------------------------------------------------------ one batch
 template <int K, bool EXT>
-__device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, AppendBuf& ab,
-                          HeavySmem<Cfg<K>::W>& hs) {
-    constexpr int W = Cfg<K>::W;
+__device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, WarpSmem<K, EXT>& ws) {
+    constexpr int W = Geo<K>::W;
+    constexpr int G = Geo<K>::G;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int group = p.group < G ? p.group : G;
     uint32_t act[W];
     active_mask<K>(p, b, act);
 
@@ -896,7 +1008,7 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Appe
     }
     if (tid == 0) { p.ctl->flags = 0; p.la.start[0] = 0; p.la.hstart[0] = 0; }
     if (!team.sync()) return false;
-    // init B: sources (block 0): level 0 entries, unique vertices
+    // init B: sources (block 0): level-0 entries, one per distinct source vertex
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int* src = p.src + (size_t)b * K;
         for (int c = 0; c < K; ++c) {
@@ -907,14 +1019,26 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Appe
             p.F[0][(size_t)s * W + (c >> 5)] |= bit;
             p.sig[(size_t)s * K + c] = 1ull;
             if (EXT) p.sig_e[(size_t)s * K + c] = 0;
-            p.lvl[(size_t)s * K + c] = 0;
+        }
+        for (int c = 0; c < K; ++c) {
+            const int s = src[c];
+            if (s < 0) continue;
             bool first = true;
             for (int c2 = 0; c2 < c; ++c2)
                 if (src[c2] == s) { first = false; break; }
             if (!first) continue;
+            uint32_t m[W];
+            load_mask<W>(p.F[0], s, m);
             const long long deg = p.off[s + 1] - p.off[s];
-            if (s < p.n_heavy) { p.hent[p.la.hcnt[0]++] = s; }
-            else { p.ent[p.la.cnt[0]++] = s; }
+            if (s < p.n_heavy) {
+                const int i = p.la.hcnt[0]++;
+                p.hent[i] = s;
+                store_mask_full<W>(p.hmask, i, m);
+            } else {
+                const int i = p.la.cnt[0]++;
+                p.ent[i] = s;
+                store_mask_full<W>(p.emask, i, m);
+            }
             p.la.dsum[0] += deg;
         }
     }
@@ -927,6 +1051,12 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Appe
     for (;; ++it) {
         const int nf = p.la.cnt[it] + p.la.hcnt[it];
         if (nf == 0) break;
+        if ((long long)p.la.start[it] + p.la.cnt[it] > p.cap || (long long)p.la.hstart[it] + p.la.hcnt[it] > p.hcap) {
+            // the level lists overflowed their capacity: every block sees the same
+            // counts and leaves; the host reruns the call with full capacity
+            if (tid == 0) atomicOr(&p.ctl->err, ERR_CAPACITY);
+            return false;
+        }
         if (it + 1 > kMaxLevel) {
             if (tid == 0) atomicOr(&p.ctl->err, ERR_LIMIT);
             return false;
@@ -938,9 +1068,8 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Appe
         else if (p.direction == 2) pull = true;
         else if (!pull) pull = (double)mf * p.alpha > (double)mu;
         else pull = !((double)nf * p.beta < (double)p.n_nz && (double)mf * p.alpha < (double)mu);
-        // next level's start offsets: every block writes the same values itself, so
-        // its own warps (ordered by the phase's first __syncthreads) read them
-        // without a grid barrier; counters two levels ahead are cleared here.
+        // next level's start offsets: every block writes the same values itself,
+        // so its own warps read them after the block-wide barrier below
         if (threadIdx.x == 0) {
             p.la.start[it + 1] = p.la.start[it] + p.la.cnt[it];
             p.la.hstart[it + 1] = p.la.hstart[it] + p.la.hcnt[it];
@@ -952,12 +1081,21 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Appe
         if (tid == 1 && it + 2 < kLevelSlots) {
             p.la.cnt[it + 2] = 0; p.la.hcnt[it + 2] = 0; p.la.dsum[it + 2] = 0; p.la.fulldeg[it + 2] = 0;
         }
+        __syncthreads();
         if (pull) {
-            phase_pull<K, EXT>(p, it, ph++, act, ab, hs);
+            phase_pull<K, EXT>(p, it, ph++, act, ws, group);
         } else {
-            phase_push<K>(p, it, ph++, act);
+            if (p.la.hcnt[it] > 0) {  // chunk prefix of the heavy frontier entries
+                heavy_prefix(p, it);
+                if (!team.sync()) return false;
+            }
+            phase_push<K, EXT>(p, it, ph++, ws, group);
             if (!team.sync()) return false;
-            phase_sigma<K, EXT>(p, it, ph++, act, hs);
+            if (p.la.hcnt[it + 1] > 0) {
+                heavy_prefix(p, it + 1);
+                if (!team.sync()) return false;
+            }
+            phase_sigma<K, EXT>(p, it, ph++, act, ws, group);
         }
         if (!team.sync()) return false;
         if (*(volatile int*)&p.ctl->flags & BST_NEED_EXT) break;
@@ -969,12 +1107,19 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Appe
     }
     if (tid == 0 && L + 1 > p.ctl->max_levels) p.ctl->max_levels = L + 1;
     if (p.forward_only) {
-        if (tid == 0) p.batch_status[b] = BST_DONE | (p.ctl->flags & BST_INEXACT);
+        if (tid == 0) {
+            p.batch_status[b] = BST_DONE | (p.ctl->flags & BST_INEXACT);
+            p.ctl->last_levels = L + 1;
+        }
         return team.sync();
     }
     // the forward sweep leaves buffer L%3 = level L masks, the others zero
     for (int l = L; l >= 1; --l) {
-        phase_back<K, EXT>(p, l, ph++, hs);
+        if (p.la.hcnt[l] > 0) {
+            heavy_prefix(p, l);
+            if (!team.sync()) return false;
+        }
+        phase_back<K, EXT>(p, l, ph++, ws, group);
         if (!team.sync()) return false;
     }
     phase_bc<K>(p, b);
@@ -982,18 +1127,15 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Appe
     return team.sync();
 }
 
-template <int K>
-__global__ void __launch_bounds__(kThreads) bc_persistent(KParams p) {
-    __shared__ AppendBuf ab;
-    __shared__ HeavySmem<Cfg<K>::W> hs;
-    if (threadIdx.x < kWarps) ab.dsum[threadIdx.x] = 0;
-    __syncthreads();
+template <int K, bool EXT>
+__global__ void __launch_bounds__(kThreads, 3) bc_persistent(KParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem<K, EXT>* wsm = reinterpret_cast<WarpSmem<K, EXT>*>(smem_raw);
     GridTeam team{p.ctl, p.budget};
     int ph = 0;
-    for (int b = 0; b < p.nbatch; ++b) {
-        bool ok = p.ext ? run_batch<K, true>(p, b, team, ph, ab, hs) : run_batch<K, false>(p, b, team, ph, ab, hs);
-        if (!ok) return;
-    }
+    WarpSmem<K, EXT>& ws = wsm[warp_id()];
+    for (int b = 0; b < p.nbatch; ++b)
+        if (!run_batch<K, EXT>(p, b, team, ph, ws)) return;
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -1015,51 +1157,85 @@ __global__ void k_map_sources(const int* __restrict__ src, int nsrc, const int* 
     }
 }
 
-__global__ void k_debug_extract(KParams p, int K, int* level_rel, unsigned long long* sig_rel, int* sige_rel) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= p.n) return;
+// Levels and path counts of column 0 after a forward-only run (one block):
+// every entry of level l (light then heavy lists) with bit 0 set.
+__global__ void k_debug_extract(KParams p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
+                                int* sige_rel) {
     const int W = K >= 32 ? K / 32 : 1;
-    bool reached = (p.V[(size_t)v * W] & 1u) != 0;
-    level_rel[v] = reached ? (int)p.lvl[(size_t)v * K] : -1;
-    sig_rel[v] = reached ? p.sig[(size_t)v * K] : 0ull;
-    sige_rel[v] = (reached && p.ext) ? p.sig_e[(size_t)v * K] : 0;
+    for (long long v = threadIdx.x; v < p.n; v += blockDim.x) {
+        level_rel[v] = -1;
+        sig_rel[v] = 0;
+        sige_rel[v] = 0;
+    }
+    __syncthreads();
+    for (int l = 0; l < levels; ++l) {
+        const int s = p.la.start[l], c = p.la.cnt[l], hs = p.la.hstart[l], hc = p.la.hcnt[l];
+        for (long long i = threadIdx.x; i < c + hc; i += blockDim.x) {
+            const int v = i < c ? p.ent[s + i] : p.hent[hs + (i - c)];
+            const uint32_t w0 = i < c ? p.emask[(size_t)(s + i) * W] : p.hmask[(size_t)(hs + i - c) * W];
+            if (w0 & 1u) {
+                level_rel[v] = l;
+                sig_rel[v] = p.sig[(size_t)v * K];
+                sige_rel[v] = p.ext ? p.sig_e[(size_t)v * K] : 0;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ host launchers
-template <int K>
+template <int K, bool EXT>
+static size_t smem_bytes() { return sizeof(WarpSmem<K, EXT>) * kWarps; }
+
+template <int K, bool EXT>
+static cudaError_t prepare() {
+    static bool done = false;  // attribute set once per process (single device)
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(bc_persistent<K, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes<K, EXT>());
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int K, bool EXT>
 static cudaError_t launch_k(const KParams& p, int blocks, cudaStream_t st) {
+    cudaError_t e = prepare<K, EXT>();
+    if (e != cudaSuccess) return e;
     KParams q = p;
     void* args[] = {&q};
-    return cudaLaunchCooperativeKernel((const void*)bc_persistent<K>, dim3(blocks), dim3(kThreads), args, 0, st);
+    return cudaLaunchCooperativeKernel((const void*)bc_persistent<K, EXT>, dim3(blocks), dim3(kThreads), args,
+                                       smem_bytes<K, EXT>(), st);
 }
 
 cudaError_t launch_batches(int K, const KParams& p, int blocks, cudaStream_t st) {
+    const bool ext = p.ext != 0;
     switch (K) {
-        case 1: return launch_k<1>(p, blocks, st);
-        case 32: return launch_k<32>(p, blocks, st);
-        case 64: return launch_k<64>(p, blocks, st);
-        case 128: return launch_k<128>(p, blocks, st);
+        case 1: return ext ? launch_k<1, true>(p, blocks, st) : launch_k<1, false>(p, blocks, st);
+        case 32: return ext ? launch_k<32, true>(p, blocks, st) : launch_k<32, false>(p, blocks, st);
+        case 64: return ext ? launch_k<64, true>(p, blocks, st) : launch_k<64, false>(p, blocks, st);
+        case 128: return ext ? launch_k<128, true>(p, blocks, st) : launch_k<128, false>(p, blocks, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int K>
+template <int K, bool EXT>
 static int occ() {
+    if (prepare<K, EXT>() != cudaSuccess) return 0;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bc_persistent<K>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bc_persistent<K, EXT>, kThreads, smem_bytes<K, EXT>());
     return nb;
 }
 
-int max_coop_blocks(int K, int* per_sm) {
+int max_coop_blocks(int K, bool ext, int* per_sm) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int nb = 0;
     switch (K) {
-        case 1: nb = occ<1>(); break;
-        case 32: nb = occ<32>(); break;
-        case 64: nb = occ<64>(); break;
-        case 128: nb = occ<128>(); break;
+        case 1: nb = ext ? occ<1, true>() : occ<1, false>(); break;
+        case 32: nb = ext ? occ<32, true>() : occ<32, false>(); break;
+        case 64: nb = ext ? occ<64, true>() : occ<64, false>(); break;
+        case 128: nb = ext ? occ<128, true>() : occ<128, false>(); break;
     }
     if (per_sm) *per_sm = nb;
     return nb * sms;
@@ -1079,10 +1255,10 @@ cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_debug_extract(const KParams& p, int K, int* level_rel, unsigned long long* sig_rel, int* sige_rel,
-                                 cudaStream_t st) {
+cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
+                                 int* sige_rel, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
-    k_debug_extract<<<(p.n + 255) / 256, 256, 0, st>>>(p, K, level_rel, sig_rel, sige_rel);
+    k_debug_extract<<<1, 1024, 0, st>>>(p, K, levels, level_rel, sig_rel, sige_rel);
     return cudaGetLastError();
 }
 

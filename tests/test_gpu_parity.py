@@ -147,8 +147,8 @@ def test_rmat12_bitwise_across_widths_and_directions(bc, rmat12):
     src = bcgen.sample_sources(g, 300, 4)
     ref, _, _ = gpu_bc(bc, g, src, batch_width=64)
     for kw in [dict(batch_width=1), dict(batch_width=32), dict(batch_width=128), dict(batch_width=64, direction=1),
-               dict(batch_width=64, direction=2), dict(batch_width=64, heavy_degree=8),
-               dict(batch_width=32, heavy_degree=40, direction=2)]:
+               dict(batch_width=64, direction=2), dict(batch_width=64, group_vertices=1),
+               dict(batch_width=32, group_vertices=7, direction=2), dict(batch_width=1, group_vertices=3)]:
         got, _, _ = gpu_bc(bc, g, src, **kw)
         assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
 
