@@ -104,6 +104,7 @@ typedef struct {
     int32_t blocks_per_sm;   /* persistent-grid residency (0 = occupancy maximum) */
     int64_t barrier_budget;  /* device cycles a grid-barrier wait may spin before BC_E_TIMEOUT
                                 (0 = about 20 s; tests may set 1 to force a timeout) */
+    int32_t trace;           /* 1 = record a device timestamp at the end of every grid-wide phase */
 } bc_options;
 
 /*
@@ -131,6 +132,15 @@ typedef struct {
     float kernel_ms;         /* device time of the persistent traversal launches (CUDA events on the call's stream) */
 } bc_run_stats;
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
+
+/*
+ * Phase trace of the last call made with bc_options.trace = 1: up to `cap`
+ * records of (tag, t_ns) as int64 pairs in `out` (host), *count = records.
+ * tag = kind << 24 | level, kind 1 init, 2 pull level, 3 push discovery,
+ * 4 path-count sum after push, 5 reverse level, 6 BC accumulation, 7 chunk
+ * prefix; t_ns = device global timer at the end of the phase.
+ */
+bc_status bc_last_trace(const bc_graph* g, int64_t* out, int32_t cap, int32_t* count);
 
 /*
  * Serving: continuous batching over resident graphs.  bc_batch_submit queues a

@@ -45,7 +45,7 @@ class BCError(RuntimeError):
 class bc_options(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("direction", ctypes.c_int32), ("alpha", ctypes.c_float),
                 ("beta", ctypes.c_float), ("group_vertices", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("barrier_budget", ctypes.c_int64)]
+                ("barrier_budget", ctypes.c_int64), ("trace", ctypes.c_int32)]
 
 
 class bc_run_stats(ctypes.Structure):
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_server_stats": [P, P],
         "bc_server_config": [i32, i64],
         "bc_debug_source": [P, i32, P, P, P],
+        "bc_last_trace": [P, P, i32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -196,7 +197,7 @@ class Graph:
 
     def compute(self, sources, out=None, stream=None, batch_width: int = 0, direction: int = 0,
                 alpha: float = 0.0, beta: float = 0.0, group_vertices: int = 0, blocks_per_sm: int = 0,
-                barrier_budget: int = 0):
+                barrier_budget: int = 0, trace: bool = False):
         """BC over ``sources`` (host numpy or device int32 tensor). Returns (out, status)."""
         import torch
         if out is None:
@@ -204,7 +205,8 @@ class Graph:
         if isinstance(sources, np.ndarray):
             sources = np.ascontiguousarray(sources, dtype=np.int32)
         nsrc = int(sources.shape[0]) if isinstance(sources, np.ndarray) else int(sources.numel())
-        opt = bc_options(batch_width, direction, alpha, beta, group_vertices, blocks_per_sm, barrier_budget)
+        opt = bc_options(batch_width, direction, alpha, beta, group_vertices, blocks_per_sm, barrier_budget,
+                         1 if trace else 0)
         s = load().bc_compute_ex(self._h, _ptr(sources) if nsrc else None, nsrc, _ptr(out) if self.n else None,
                                  _stream_handle(stream), ctypes.byref(opt))
         _check(s)
@@ -214,6 +216,20 @@ class Graph:
         st = bc_run_stats()
         _check(load().bc_last_run_stats(self._h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in st._fields_}
+
+    TRACE_KINDS = {1: "init", 2: "pull", 3: "push", 4: "sigma", 5: "back", 6: "bc", 7: "prefix"}
+
+    def trace(self):
+        """Phase trace of the last compute(trace=True): list of (kind, level, t_ns)."""
+        cap = 1 << 16
+        buf = np.empty(2 * cap, np.int64)
+        cnt = ctypes.c_int32()
+        _check(load().bc_last_trace(self._h, buf.ctypes.data, cap, ctypes.byref(cnt)))
+        out = []
+        for i in range(cnt.value):
+            tag, t = int(buf[2 * i]), int(buf[2 * i + 1])
+            out.append((self.TRACE_KINDS.get(tag >> 24, str(tag >> 24)), tag & 0xFFFFFF, t))
+        return out
 
     def export(self):
         perm = np.empty(max(self.n, 1), np.int32)

@@ -114,12 +114,12 @@ struct Workspace {
     int K = 0;
     DevBuf V, F[3], sig, sig_e, rho, rho_e, ent, emask, hent, hmask, hpre, stamp;
     DevBuf scr_v, scr_e, scr_or, arr;
-    DevBuf cnt, hcnt, start, hstart, dsum, fulldeg, hchunks, ctl, bstat, bc, src, bad, jobptr, coljob;
+    DevBuf cnt, hcnt, start, hstart, dsum, fulldeg, hchunks, ctl, bstat, bc, src, bad, jobptr, coljob, trace;
     long long cap = 0, hcap = 0;
     DevBuf* all_bufs(std::vector<DevBuf*>& v) {
         DevBuf* a[] = {&V, &F[0], &F[1], &F[2], &sig, &sig_e, &rho, &rho_e, &ent, &emask, &hent, &hmask, &hpre,
                        &stamp, &scr_v, &scr_e, &scr_or, &arr, &cnt, &hcnt, &start, &hstart, &dsum, &fulldeg,
-                       &hchunks, &ctl, &bstat, &bc, &src, &bad, &jobptr, &coljob};
+                       &hchunks, &ctl, &bstat, &bc, &src, &bad, &jobptr, &coljob, &trace};
         v.assign(a, a + sizeof(a) / sizeof(a[0]));
         return nullptr;
     }
@@ -171,6 +171,7 @@ struct bc_graph {
     bool sticky_ext = false;
     std::map<int, int> sticky_cap;                 // entry capacity factor that sufficed, by width
     bc_run_stats last{};
+    std::vector<long long> last_trace;             // (tag, t_ns) pairs of the last traced call
     cudaStream_t last_stream = nullptr;
 };
 
@@ -314,6 +315,8 @@ static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_optio
     p.ext = ext ? 1 : 0;
     p.forward_only = 0;
     p.group = o.group_vertices > 0 ? o.group_vertices : 32;
+    p.trace = nullptr;
+    p.trace_cap = 0;
     return p;
 }
 
@@ -390,6 +393,12 @@ static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int 
     KParams p = make_params(g, w, nbatch, o, ext);
     p.forward_only = forward_only ? 1 : 0;
     if (col_job) p.col_job = (const int*)w->coljob.p;
+    const int kTraceCap = 1 << 16;
+    if (o.trace) {
+        if (!buf_ensure(w->trace, sizeof(long long) * 2 * kTraceCap, st)) return fail(BC_E_NOMEM, "trace buffer");
+        p.trace = (long long*)w->trace.p;
+        p.trace_cap = kTraceCap;
+    }
     cudaEvent_t ev[2];
     cudaEventCreate(&ev[0]);
     cudaEventCreate(&ev[1]);
@@ -413,6 +422,13 @@ static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int 
     cudaEventDestroy(ev[1]);
     if (e != cudaSuccess) return cuda_fail(e, "persistent kernel");
     const Ctl& ctl = ro->ctl;
+    if (o.trace) {
+        const int nrec = ctl.trace_n < kTraceCap ? ctl.trace_n : kTraceCap;
+        g->last_trace.assign((size_t)2 * nrec, 0);
+        if (nrec > 0 && (e = cudaMemcpy(g->last_trace.data(), w->trace.p, sizeof(long long) * 2 * nrec,
+                                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "trace read");
+    }
     if (ctl.err & ERR_TIMEOUT) return fail(BC_E_TIMEOUT, "a grid-barrier wait exceeded its cycle budget");
     if (ctl.err & ERR_LIMIT) return fail(BC_E_LIMIT, "BFS deeper than %d levels", kMaxLevel);
     if (ctl.err == ERR_CAPACITY) {
@@ -825,6 +841,15 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
 
 bc_status bc_compute(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream) {
     return bc_compute_ex(g, sources, nsrc, out_bc, stream, nullptr);
+}
+
+bc_status bc_last_trace(const bc_graph* g, int64_t* out, int32_t cap, int32_t* count) {
+    if (!g || !count || (cap > 0 && !out) || cap < 0) return fail(BC_E_INVALID_ARG, "bad argument");
+    const int nrec = (int)(g->last_trace.size() / 2);
+    const int k = nrec < cap ? nrec : cap;
+    for (int i = 0; i < 2 * k; ++i) out[i] = g->last_trace[i];
+    *count = k;
+    return BC_OK;
 }
 
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st) {

@@ -14,9 +14,11 @@ constexpr int kLevelSlots = kMaxLevel + 3;
 constexpr uint16_t kNoLevel = 0xFFFF;
 
 // Ctl::err bits (fatal for the launch)
-enum : int { ERR_TIMEOUT = 1, ERR_SIGMA_RANGE = 2, ERR_LIMIT = 4, ERR_CAPACITY = 8 };
+enum : int { ERR_TIMEOUT = 1, ERR_SIGMA_RANGE = 2, ERR_LIMIT = 4, ERR_CAPACITY = 8, ERR_INTERNAL = 16 };
 // per-batch status bits
 enum : int { BST_DONE = 1, BST_INEXACT = 2, BST_NEED_EXT = 4 };
+// trace tags: kind << 24 | level (kinds below)
+enum : int { TR_INIT = 1, TR_PULL = 2, TR_PUSH = 3, TR_SIGMA = 4, TR_BACK = 5, TR_BC = 6, TR_PREFIX = 7 };
 
 struct Ctl {
     unsigned int bar_count;
@@ -28,7 +30,8 @@ struct Ctl {
     int pull_levels;
     int push_levels;
     int last_levels;           // levels of the last batch (debug runs)
-    int pad[4];
+    int trace_n;               // pairs written to the trace
+    int pad[3];
 };
 
 // Level bookkeeping, indexed by BFS level.
@@ -82,6 +85,8 @@ struct KParams {
     long long budget;          // barrier spin budget (cycles)
     int ext;                   // run the extended path-count form
     int forward_only;          // debug: stop after the forward sweep (no delta, no BC)
+    long long* trace;          // optional phase trace: (tag, globaltimer ns) pairs; null = off
+    int trace_cap;             // pairs the trace buffer holds
     int group;                 // light rows per warp task (1..32)
 };
 

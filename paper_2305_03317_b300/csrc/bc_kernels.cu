@@ -89,14 +89,35 @@ struct GridTeam {
     }
 };
 
-__device__ __forceinline__ long long warp_grab(unsigned int* ctr, long long total, int G, int& cnt) {
-    unsigned int i = 0;
-    if (lane_id() == 0) i = atomicAdd(ctr, (unsigned int)G);
-    i = __shfl_sync(FULL_MASK, i, 0);
-    if ((long long)i >= total) { cnt = 0; return -1; }
-    long long rem = total - (long long)i;
-    cnt = rem < G ? (int)rem : G;
-    return (long long)i;
+// Phase trace: block 0 stamps the end of every grid-wide phase (after its barrier).
+__device__ __forceinline__ void trace_mark(const KParams& p, int kind, int level) {
+    if (p.trace == nullptr || blockIdx.x != 0 || threadIdx.x != 0) return;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    const int i = p.ctl->trace_n;
+    if (i < p.trace_cap) {
+        p.trace[2 * i] = ((long long)kind << 24) | (long long)(level & 0xFFFFFF);
+        p.trace[2 * i + 1] = (long long)t;
+        p.ctl->trace_n = i + 1;
+    }
+}
+
+// Work distribution inside a phase: a warp's first task is its global warp
+// index (no atomics while tasks are fewer than warps); later tasks come from a
+// per-phase counter.  Returns -1 when the phase has no task left for the warp.
+__device__ __forceinline__ long long next_task(unsigned int* ctr, long long total, bool& first) {
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    long long t;
+    if (first) {
+        first = false;
+        t = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5;
+    } else {
+        if (total <= nw) return -1;
+        unsigned int i = 0;
+        if (lane_id() == 0) i = atomicAdd(ctr, 1u);
+        t = nw + (long long)__shfl_sync(FULL_MASK, i, 0);
+    }
+    return t < total ? t : -1;
 }
 
 // ------------------------------------------------------------------ masks
@@ -341,39 +362,51 @@ __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>&
             }
             __syncwarp();
             const int cnt = pe - pb;
-            for (int r = 0; r < cnt; r += 32) {
-                const int q = r + lane;
-                const bool valid = q < cnt;
-                int slot = 0;
-                unsigned long long x = 0ull;
-                int xe = 0;
-                if (valid) {
-                    const uint32_t e = ws.pr[q];
-                    const int j = (int)(e >> 16), c = (int)(e & 0xFFFFu);
-                    const size_t idx = (size_t)ws.sv[j] * K + c;
-                    slot = ws.so[j] * K + c;
-                    x = termv[idx];
-                    if constexpr (EXT) xe = terme[idx];
-                }
-                if constexpr (!ORDERED) {
-                    if (valid) {
-                        const unsigned long long old = atomicAdd(&ws.acc[slot], x);
-                        carry |= (old + x < old);
+            constexpr int R = 4;  // rounds whose loads are in flight together
+            for (int r0 = 0; r0 < cnt; r0 += 32 * R) {
+                int slot[R];
+                unsigned long long x[R];
+                int xe[R];
+                bool valid[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int q = r0 + 32 * i + lane;
+                    valid[i] = q < cnt;
+                    slot[i] = 0;
+                    x[i] = 0ull;
+                    xe[i] = 0;
+                    if (valid[i]) {
+                        const uint32_t e = ws.pr[q];
+                        const int j = (int)(e >> 16), c = (int)(e & 0xFFFFu);
+                        const size_t idx = (size_t)ws.sv[j] * K + c;
+                        slot[i] = ws.so[j] * K + c;
+                        x[i] = termv[idx];
+                        if constexpr (EXT) xe[i] = terme[idx];
                     }
-                } else {
-                    const int key = valid ? slot : -(lane + 1);
-                    const unsigned int peers = __match_any_sync(FULL_MASK, key);
-                    const int rank = __popc(peers & lt);
-                    const int maxr = __reduce_max_sync(FULL_MASK, valid ? rank : 0);
-                    for (int k = 0; k <= maxr; ++k) {
-                        if (valid && rank == k) {
-                            unsigned long long av = ws.acc[slot];
-                            int ae = EXT ? ws.acce[slot] : 0;
-                            acc_add<EXT, DIR>(av, ae, x, xe, carry);
-                            ws.acc[slot] = av;
-                            if constexpr (EXT) ws.acce[slot] = ae;
+                }
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    if (r0 + 32 * i >= cnt) break;
+                    if constexpr (!ORDERED) {
+                        if (valid[i]) {
+                            const unsigned long long old = atomicAdd(&ws.acc[slot[i]], x[i]);
+                            carry |= (old + x[i] < old);
                         }
-                        __syncwarp();
+                    } else {
+                        const int key = valid[i] ? slot[i] : -(lane + 1);
+                        const unsigned int peers = __match_any_sync(FULL_MASK, key);
+                        const int rank = __popc(peers & lt);
+                        const int maxr = __reduce_max_sync(FULL_MASK, valid[i] ? rank : 0);
+                        for (int k = 0; k <= maxr; ++k) {
+                            if (valid[i] && rank == k) {
+                                unsigned long long av = ws.acc[slot[i]];
+                                int ae = EXT ? ws.acce[slot[i]] : 0;
+                                acc_add<EXT, DIR>(av, ae, x[i], xe[i], carry);
+                                ws.acc[slot[i]] = av;
+                                if constexpr (EXT) ws.acce[slot[i]] = ae;
+                            }
+                            __syncwarp();
+                        }
                     }
                 }
             }
@@ -386,77 +419,126 @@ __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>&
     __syncwarp();
 }
 
-// ------------------------------------------------------------------ finishing a vertex
-// Forward: write path counts (from the owner's accumulator row) of the newly
-// reached columns nm of w and mark them reached.
-template <int K, bool EXT>
-__device__ __forceinline__ void fwd_write(const KParams& p, int w, const uint32_t (&nm)[Geo<K>::W], int lev,
-                                          const uint32_t (&act)[Geo<K>::W], const unsigned long long* accrow,
-                                          const int* accerow) {
-    constexpr int W = Geo<K>::W;
-    const int lane = lane_id();
-    uint32_t my;
-    if constexpr (K == 1) my = (lane == 0) ? (nm[0] & 1u) : 0u;
-    else my = lane_field<W>(pick<W>(nm, (W * lane) >> 5), lane);
-    bool inexact = false;
+// ------------------------------------------------------------------ finishing vertices
+// Position of the k-th (0-based) set bit of x (x has more than k set bits).
+__device__ __forceinline__ int select_bit(uint32_t x, int k) {
+    int pos = 0;
 #pragma unroll
-    for (int t = 0; t < W; ++t) {
-        if ((my >> t) & 1u) {
-            const int c = K == 1 ? 0 : W * lane + t;
-            const size_t idx = (size_t)w * K + c;
-            const unsigned long long x = accrow[c];
-            p.sig[idx] = x;
-            int xe = 0;
-            if constexpr (EXT) {
-                xe = accerow[c];
-                p.sig_e[idx] = xe;
-            }
-            inexact |= (xe > 0 || x >= (1ull << 53));
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const uint32_t low = x & ((1u << sh) - 1u);
+        const int c = __popc(low);
+        if (k >= c) {
+            k -= c;
+            x >>= sh;
+            pos += sh;
+        } else {
+            x = low;
         }
     }
-    if (__any_sync(FULL_MASK, inexact) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
-    bool full = true;
-    if (lane < W) {
-        const uint32_t nv = p.V[(size_t)w * W + lane] | pick<W>(nm, lane);
-        p.V[(size_t)w * W + lane] = nv;
-        const uint32_t a = pick<W>(act, lane);
-        full = (nv & a) == a;
-    }
-    if (__all_sync(FULL_MASK, full) && lane == 0)
-        atomicAdd((unsigned long long*)&p.la.fulldeg[lev], (unsigned long long)(p.off[w + 1] - p.off[w]));
+    return pos;
 }
 
-// Backward: delta and rho of v for its columns mk from the rho sums.
-template <int K, bool EXT>
-__device__ __forceinline__ void bwd_write(const KParams& p, int v, const uint32_t (&mk)[Geo<K>::W],
-                                          const unsigned long long* accrow, const int* accerow) {
-    constexpr int W = Geo<K>::W;
-    const int lane = lane_id();
-    uint32_t my;
-    if constexpr (K == 1) my = (lane == 0) ? (mk[0] & 1u) : 0u;
-    else my = lane_field<W>(pick<W>(mk, (W * lane) >> 5), lane);
+// Column of the k-th set bit of a W-word mask.
+template <int W>
+__device__ __forceinline__ int select_col(const uint32_t* m, int k) {
+    int base = 0;
 #pragma unroll
-    for (int t = 0; t < W; ++t) {
-        if ((my >> t) & 1u) {
-            const int c = K == 1 ? 0 : W * lane + t;
-            const size_t idx = (size_t)v * K + c;
-            const double sd = (double)p.sig[idx];  // rounds only when the count is >= 2^53
-            const double sr = __longlong_as_double((long long)accrow[c]);
-            double delta, rho;
-            if constexpr (EXT) {
-                const int se = p.sig_e[idx];
-                delta = scalbn(sd * sr, se + accerow[c]);
-                rho = (1.0 + delta) / sd;
-                p.rho_e[idx] = -se;
-            } else {
-                delta = sd * sr;
-                rho = (1.0 + delta) / sd;
-            }
-            p.sig[idx] = (unsigned long long)__double_as_longlong(delta);
-            p.rho[idx] = rho;
+    for (int t = 0; t < W - 1; ++t) {
+        const int c = __popc(m[t]);
+        if (k >= c && base == t * 32) {
+            k -= c;
+            base = (t + 1) * 32;
         }
     }
+    return base + select_bit(m[base >> 5], k);
 }
+
+// Finish the columns of the group's owners, one (owner, column) pair per lane:
+// masks[o] selects the columns of owner o (row o of the accumulator).
+// FWD writes the path counts; BWD turns rho sums into delta and rho.
+template <int K, bool EXT, int DIR>
+__device__ __forceinline__ void write_columns(const KParams& p, const WarpSmem<K, EXT>& ws, int ng,
+                                              const uint32_t (*masks)[Geo<K>::W]) {
+    constexpr int W = Geo<K>::W;
+    const int lane = lane_id();
+    int cnt = 0;
+    if (lane < ng) {
+#pragma unroll
+        for (int t = 0; t < W; ++t) cnt += __popc(masks[lane][t]);
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        int y = __shfl_up_sync(FULL_MASK, incl, s);
+        if (lane >= s) incl += y;
+    }
+    const int Q = __shfl_sync(FULL_MASK, incl, 31);
+    const int ex = incl - cnt;  // exclusive prefix of owner `lane`
+    bool inexact = false;
+    for (int r = 0; r < Q; r += 32) {
+        const int q = r + lane;
+        // owner: the largest o < ng with exclusive prefix <= q
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = o + step;
+            const int sc = __shfl_sync(FULL_MASK, ex, cand < 32 ? cand : 31);
+            if (cand < ng && sc <= q) o = cand;
+        }
+        const int so = __shfl_sync(FULL_MASK, ex, o);
+        if (q < Q) {
+            const int c = (K == 1) ? 0 : select_col<W>(masks[o], q - so);
+            const int v = ws.ov[o];
+            const size_t idx = (size_t)v * K + c;
+            const int slot = o * K + c;
+            if constexpr (DIR == FWD) {
+                const unsigned long long x = ws.acc[slot];
+                p.sig[idx] = x;
+                int xe = 0;
+                if constexpr (EXT) {
+                    xe = ws.acce[slot];
+                    p.sig_e[idx] = xe;
+                }
+                inexact |= (xe > 0 || x >= (1ull << 53));
+            } else {
+                const double sd = (double)p.sig[idx];  // rounds only when the count is >= 2^53
+                const double sr = __longlong_as_double((long long)ws.acc[slot]);
+                double delta, rho;
+                if constexpr (EXT) {
+                    const int se = p.sig_e[idx];
+                    delta = scalbn(sd * sr, se + ws.acce[slot]);
+                    rho = (1.0 + delta) / sd;
+                    p.rho_e[idx] = -se;
+                } else {
+                    delta = sd * sr;
+                    rho = (1.0 + delta) / sd;
+                }
+                p.sig[idx] = (unsigned long long)__double_as_longlong(delta);
+                p.rho[idx] = rho;
+            }
+        }
+    }
+    if (DIR == FWD && __any_sync(FULL_MASK, inexact) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
+}
+
+// Owner-level forward bookkeeping (lane o handles owner o): mark the newly
+// reached columns nm in V and account vertices whose every column is reached.
+template <int W>
+__device__ __forceinline__ void mark_reached(const KParams& p, int w, const uint32_t (&nm)[W], int lev,
+                                             const uint32_t (&act)[W]) {
+    uint32_t vm[W];
+    load_mask<W>(p.V, w, vm);
+    bool full = true;
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        vm[t] |= nm[t];
+        full &= (vm[t] & act[t]) == act[t];
+    }
+    store_mask_full<W>(p.V, w, vm);
+    if (full) atomicAdd((unsigned long long*)&p.la.fulldeg[lev], (unsigned long long)(p.off[w + 1] - p.off[w]));
+}
+
+__device__ __forceinline__ int nchunks(int deg) { return (deg + kChunk - 1) / kChunk; }
 
 // ------------------------------------------------------------------ list appends
 template <int K, bool EXT>
@@ -502,7 +584,6 @@ __device__ __forceinline__ void heavy_append(const KParams& p, int lev, int w, l
 }
 
 // ------------------------------------------------------------------ heavy chunk tasks
-__device__ __forceinline__ int nchunks(int deg) { return (deg + kChunk - 1) / kChunk; }
 
 // Task t of a heavy list level -> (entry position, chunk), by binary search of
 // the level's chunk prefix.
@@ -529,16 +610,21 @@ __device__ __forceinline__ void heavy_static_task(const KParams& p, int t, int& 
     chunk = t - p.hcum[lo];
 }
 
-// Exclusive chunk prefix of the heavy entries of a level (block 0, warp 0).
+// Exclusive chunk prefix of the heavy entries of a level (recomputed from the
+// row lengths, so it may run more than once per level).  Block 0 scans in tiles.
 __device__ void heavy_prefix(const KParams& p, int lev) {
-    if (blockIdx.x != 0 || warp_id() != 0) return;
-    const int lane = lane_id();
+    if (blockIdx.x != 0) return;
+    __shared__ int wsum[kWarps];
+    __shared__ int carry_s;
+    const int lane = lane_id(), wid = warp_id();
     const int hs = p.la.hstart[lev], hc = p.la.hcnt[lev];
-    int carry = 0;
-    for (int i = 0; i < hc; i += 32) {
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int i0 = 0; i0 < hc; i0 += kThreads) {
+        const int i = i0 + threadIdx.x;
         int c = 0;
-        if (i + lane < hc) {
-            const int v = p.hent[hs + i + lane];
+        if (i < hc) {
+            const int v = p.hent[hs + i];
             c = nchunks(p.off[v + 1] - p.off[v]);
         }
         int incl = c;
@@ -547,10 +633,24 @@ __device__ void heavy_prefix(const KParams& p, int lev) {
             int y = __shfl_up_sync(FULL_MASK, incl, o);
             if (lane >= o) incl += y;
         }
-        if (i + lane < hc) p.hpre[hs + i + lane] = carry + incl - c;
-        carry += __shfl_sync(FULL_MASK, incl, 31);
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        int before = carry_s;
+        for (int w2 = 0; w2 < wid; ++w2) before += wsum[w2];
+        if (i < hc) p.hpre[hs + i] = before + incl - c;
+        __syncthreads();
+        if (threadIdx.x == kThreads - 1) carry_s = before + incl;
+        __syncthreads();
     }
-    if (lane == 0) p.la.hchunks[lev] = carry;
+    if (threadIdx.x == 0) {
+        const int total = p.n_heavy > 0 ? p.hcum[p.n_heavy] : 0;
+        if (carry_s > total) {  // impossible for consistent lists: refuse to schedule
+            atomicOr(&p.ctl->err, ERR_INTERNAL);
+            p.la.hchunks[lev] = 0;
+        } else {
+            p.la.hchunks[lev] = carry_s;
+        }
+    }
 }
 
 // Store the chunk partial held in accumulator row 0; returns true (warp-
@@ -652,9 +752,8 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
     phase_prologue(p, ph);
     // heavy rows: chunk tasks over the static prefix of heavy ids
     const int HC = p.n_heavy > 0 ? p.hcum[p.n_heavy] : 0;
-    for (;;) {
-        int cnt;
-        const long long t0 = warp_grab(wq(p, ph, 0), HC, 1, cnt);
+    for (bool fst = true;;) {
+        const long long t0 = next_task(wq(p, ph, 0), HC, fst);
         if (t0 < 0) break;
         int r, chunk;
         heavy_static_task(p, (int)t0, r, chunk);
@@ -669,9 +768,17 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
         group_gather<K, EXT, FWD>(p, ws, 1, T, Fc, carry);
         uint32_t nm[W];
         if (heavy_partial<K, EXT, FWD>(p, ws, r, chunk, nch, nm) && mask_any<W>(nm)) {
-            if (lane == 0) store_mask_full<W>(Fn, r, nm);
-            fwd_write<K, EXT>(p, r, nm, lev, act, ws.acc, ws.acce);
-            if (lane == 0) heavy_append<W>(p, lev, r, deg, nm);
+            if (lane == 0) {
+#pragma unroll
+                for (int t = 0; t < W; ++t) ws.onm[0][t] = nm[t];
+            }
+            __syncwarp();
+            write_columns<K, EXT, FWD>(p, ws, 1, ws.onm);
+            if (lane == 0) {
+                store_mask_full<W>(Fn, r, nm);
+                mark_reached<W>(p, r, nm, lev, act);
+                heavy_append<W>(p, lev, r, deg, nm);
+            }
         }
     }
     // light rows: groups of consecutive ids
@@ -679,9 +786,8 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
     if (lane == 0) ws.adeg = 0;
     const long long nlight = (long long)p.n_nz - p.n_heavy;
     const long long ngroups = (nlight + group - 1) / group;
-    for (;;) {
-        int cnt;
-        const long long g0 = warp_grab(wq(p, ph, 1), ngroups, 1, cnt);
+    for (bool fst = true;;) {
+        const long long g0 = next_task(wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const long long first = p.n_heavy + g0 * group;
         const int ng = (int)min((long long)group, (long long)p.n_nz - first);
@@ -701,21 +807,37 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
         if (!__any_sync(FULL_MASK, len > 0)) continue;
         const int T = set_owners<K, EXT>(ws, ng, v, beg, len, -1, um);
         group_gather<K, EXT, FWD>(p, ws, ng, T, Fc, carry);
-        for (int o = 0; o < ng; ++o) {
-            uint32_t nm[W];
-            read_mask_s<W>(ws.onm[o], nm);
-            if (!mask_any<W>(nm)) continue;
-            const int w = ws.ov[o];
-            if (lane == 0) store_mask_full<W>(Fn, w, nm);
-            fwd_write<K, EXT>(p, w, nm, lev, act, ws.acc + o * K, ws.acce + (EXT ? o * K : 0));
-            if (lane == 0) {
-                ws.av[acnt] = w;
-#pragma unroll
-                for (int t = 0; t < W; ++t) ws.am[acnt][t] = nm[t];
-                ws.adeg += p.off[w + 1] - p.off[w];
+        write_columns<K, EXT, FWD>(p, ws, ng, ws.onm);
+        // owners reached in this level (lane o = owner o): masks, V, staged appends
+        uint32_t nm[W];
+        bool found = false;
+        int w = 0;
+        if (lane < ng) {
+            read_mask_s<W>(ws.onm[lane], nm);
+            found = mask_any<W>(nm);
+            w = ws.ov[lane];
+            if (found) {
+                store_mask_full<W>(Fn, w, nm);
+                mark_reached<W>(p, w, nm, lev, act);
             }
+        }
+        const unsigned int fb = __ballot_sync(FULL_MASK, found);
+        const int nf = __popc(fb);
+        if (nf) {
+            if (acnt + nf > 32) flush_append<K, EXT>(p, lev, ws, acnt);
+            long long dg = found ? (long long)(p.off[w + 1] - p.off[w]) : 0;
+#pragma unroll
+            for (int s2 = 16; s2 > 0; s2 >>= 1) dg += __shfl_xor_sync(FULL_MASK, dg, s2);
+            if (found) {
+                const int slot = acnt + __popc(fb & ((1u << lane) - 1u));
+                ws.av[slot] = w;
+#pragma unroll
+                for (int t = 0; t < W; ++t) ws.am[slot][t] = nm[t];
+            }
+            if (lane == 0) ws.adeg += dg;
             __syncwarp();
-            if (++acnt == 32) flush_append<K, EXT>(p, lev, ws, acnt);
+            acnt += nf;
+            if (acnt == 32) flush_append<K, EXT>(p, lev, ws, acnt);
         }
     }
     flush_append<K, EXT>(p, lev, ws, acnt);
@@ -790,9 +912,8 @@ __device__ void phase_push(const KParams& p, int it, int ph, WarpSmem<K, EXT>& w
     };
     // heavy frontier rows: chunk tasks
     const int HT = p.la.hcnt[it] > 0 ? p.la.hchunks[it] : 0;
-    for (;;) {
-        int cnt;
-        const long long t0 = warp_grab(wq(p, ph, 0), HT, 1, cnt);
+    for (bool fst = true;;) {
+        const long long t0 = next_task(wq(p, ph, 0), HT, fst);
         if (t0 < 0) break;
         int pos, chunk;
         heavy_list_task(p, it, (int)t0, pos, chunk);
@@ -810,9 +931,8 @@ __device__ void phase_push(const KParams& p, int it, int ph, WarpSmem<K, EXT>& w
     const int grp = group < G ? group : G;
     const int ls = p.la.start[it], lc = p.la.cnt[it];
     const long long ngroups = (lc + grp - 1) / grp;
-    for (;;) {
-        int cnt;
-        const long long g0 = warp_grab(wq(p, ph, 1), ngroups, 1, cnt);
+    for (bool fst = true;;) {
+        const long long g0 = next_task(wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const int first = (int)(g0 * grp);
         const int ng = min(grp, lc - first);
@@ -844,9 +964,8 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
     bool carry = false;
     phase_prologue(p, ph);
     const int HT = p.la.hcnt[lev] > 0 ? p.la.hchunks[lev] : 0;
-    for (;;) {
-        int cnt;
-        const long long t0 = warp_grab(wq(p, ph, 0), HT, 1, cnt);
+    for (bool fst = true;;) {
+        const long long t0 = next_task(wq(p, ph, 0), HT, fst);
         if (t0 < 0) break;
         int pos, chunk;
         heavy_list_task(p, lev, (int)t0, pos, chunk);
@@ -859,15 +978,17 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
         group_gather<K, EXT, FWD>(p, ws, 1, T, Fc, carry);
         uint32_t om[W];
         if (heavy_partial<K, EXT, FWD>(p, ws, w, chunk, nch, om)) {
-            fwd_write<K, EXT>(p, w, nm, lev, act, ws.acc, ws.acce);
-            if (lane == 0) store_mask_full<W>(p.hmask, pos, nm);
+            write_columns<K, EXT, FWD>(p, ws, 1, ws.owant);
+            if (lane == 0) {
+                mark_reached<W>(p, w, nm, lev, act);
+                store_mask_full<W>(p.hmask, pos, nm);
+            }
         }
     }
     const int ls = p.la.start[lev], lc = p.la.cnt[lev];
     const long long ngroups = (lc + group - 1) / group;
-    for (;;) {
-        int cnt;
-        const long long g0 = warp_grab(wq(p, ph, 1), ngroups, 1, cnt);
+    for (bool fst = true;;) {
+        const long long g0 = next_task(wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const int first = (int)(g0 * group);
         const int ng = min(group, lc - first);
@@ -883,11 +1004,12 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
         }
         const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, nm);
         group_gather<K, EXT, FWD>(p, ws, ng, T, Fc, carry);
-        for (int o = 0; o < ng; ++o) {
+        write_columns<K, EXT, FWD>(p, ws, ng, ws.owant);
+        if (lane < ng) {
             uint32_t want[W];
-            read_mask_s<W>(ws.owant[o], want);
-            fwd_write<K, EXT>(p, ws.ov[o], want, lev, act, ws.acc + o * K, ws.acce + (EXT ? o * K : 0));
-            if (lane == 0) store_mask_full<W>(p.emask, ws.opos[o], want);
+            read_mask_s<W>(ws.owant[lane], want);
+            mark_reached<W>(p, ws.ov[lane], want, lev, act);
+            store_mask_full<W>(p.emask, ws.opos[lane], want);
         }
     }
     if (__any_sync(FULL_MASK, carry) && lane == 0) atomicOr(&p.ctl->flags, BST_NEED_EXT);
@@ -904,9 +1026,8 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
     bool carry = false;
     phase_prologue(p, ph);
     const int HT = p.la.hcnt[l] > 0 ? p.la.hchunks[l] : 0;
-    for (;;) {
-        int cnt;
-        const long long t0 = warp_grab(wq(p, ph, 0), HT, 1, cnt);
+    for (bool fst = true;;) {
+        const long long t0 = next_task(wq(p, ph, 0), HT, fst);
         if (t0 < 0) break;
         int pos, chunk;
         heavy_list_task(p, l, (int)t0, pos, chunk);
@@ -919,15 +1040,14 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
         group_gather<K, EXT, BWD>(p, ws, 1, T, Fd, carry);
         uint32_t om[W];
         if (heavy_partial<K, EXT, BWD>(p, ws, v, chunk, nch, om)) {
-            bwd_write<K, EXT>(p, v, mk, ws.acc, ws.acce);
+            write_columns<K, EXT, BWD>(p, ws, 1, ws.owant);
             if (lane == 0) store_mask_full<W>(Fl, v, mk);
         }
     }
     const int ls = p.la.start[l], lc = p.la.cnt[l];
     const long long ngroups = (lc + group - 1) / group;
-    for (;;) {
-        int cnt;
-        const long long g0 = warp_grab(wq(p, ph, 1), ngroups, 1, cnt);
+    for (bool fst = true;;) {
+        const long long g0 = next_task(wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const int first = (int)(g0 * group);
         const int ng = min(group, lc - first);
@@ -943,12 +1063,11 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
         }
         const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, mk);
         group_gather<K, EXT, BWD>(p, ws, ng, T, Fd, carry);
-        for (int o = 0; o < ng; ++o) {
+        write_columns<K, EXT, BWD>(p, ws, ng, ws.owant);
+        if (lane < ng) {
             uint32_t want[W];
-            read_mask_s<W>(ws.owant[o], want);
-            const int u = ws.ov[o];
-            bwd_write<K, EXT>(p, u, want, ws.acc + o * K, ws.acce + (EXT ? o * K : 0));
-            if (lane == 0) store_mask_full<W>(Fl, u, want);
+            read_mask_s<W>(ws.owant[lane], want);
+            store_mask_full<W>(Fl, ws.ov[lane], want);
         }
     }
     clear_level_masks<W>(p, p.F[(l + 2) % 3], l + 2);
@@ -1008,6 +1127,7 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
     }
     if (tid == 0) { p.ctl->flags = 0; p.la.start[0] = 0; p.la.hstart[0] = 0; }
     if (!team.sync()) return false;
+    trace_mark(p, TR_INIT, b);
     // init B: sources (block 0): level-0 entries, one per distinct source vertex
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int* src = p.src + (size_t)b * K;
@@ -1043,6 +1163,7 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
         }
     }
     if (!team.sync()) return false;
+    trace_mark(p, TR_INIT, b);
 
     // forward sweep
     long long full_arcs = 0;
@@ -1088,16 +1209,20 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
             if (p.la.hcnt[it] > 0) {  // chunk prefix of the heavy frontier entries
                 heavy_prefix(p, it);
                 if (!team.sync()) return false;
+                trace_mark(p, TR_PREFIX, it);
             }
             phase_push<K, EXT>(p, it, ph++, ws, group);
             if (!team.sync()) return false;
+            trace_mark(p, TR_PUSH, it);
             if (p.la.hcnt[it + 1] > 0) {
                 heavy_prefix(p, it + 1);
                 if (!team.sync()) return false;
+                trace_mark(p, TR_PREFIX, it + 1);
             }
             phase_sigma<K, EXT>(p, it, ph++, act, ws, group);
         }
         if (!team.sync()) return false;
+        trace_mark(p, pull ? TR_PULL : TR_SIGMA, it);
         if (*(volatile int*)&p.ctl->flags & BST_NEED_EXT) break;
     }
     const int L = it - 1;  // deepest nonempty level
@@ -1118,13 +1243,17 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
         if (p.la.hcnt[l] > 0) {
             heavy_prefix(p, l);
             if (!team.sync()) return false;
+            trace_mark(p, TR_PREFIX, l);
         }
         phase_back<K, EXT>(p, l, ph++, ws, group);
         if (!team.sync()) return false;
+        trace_mark(p, TR_BACK, l);
     }
     phase_bc<K>(p, b);
     if (tid == 0) p.batch_status[b] = BST_DONE | (p.ctl->flags & BST_INEXACT);
-    return team.sync();
+    const bool ok = team.sync();
+    trace_mark(p, TR_BC, b);
+    return ok;
 }
 
 template <int K, bool EXT>

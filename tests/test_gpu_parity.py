@@ -241,3 +241,43 @@ def test_serving_alone_equals_mix(bc):
         assert_bc_close(b, oracle.bc(graphs[gi].off, graphs[gi].adj, src))
     peak, done = bc.server_stats()
     assert done >= 2 * len(reqs)
+
+
+# ----------------------------------------------------------------- rows above 1024 arcs (chunk tasks)
+
+@pytest.fixture(scope="module")
+def heavy_graph():
+    g = bcgen.rmat(14, 64, 3)  # 106 rows above 1024 arcs, the largest ~6.9K arcs (7 chunks)
+    assert int(g.degrees().max()) > 4 * 1024
+    src = bcgen.sample_sources(g, 160, 7)
+    return g, src, oracle.bc(g.off, g.adj, src)
+
+
+@pytest.mark.parametrize("kw", [dict(batch_width=1), dict(batch_width=32), dict(batch_width=64),
+                                dict(batch_width=128), dict(batch_width=64, direction=1),
+                                dict(batch_width=64, direction=2), dict(batch_width=32, group_vertices=5)],
+                         ids=lambda kw: "-".join(f"{k}{v}" for k, v in kw.items()))
+def test_heavy_rows_parity(bc, heavy_graph, kw):
+    g, src, want = heavy_graph
+    got, st, stats = gpu_bc(bc, g, src, **kw)
+    assert_bc_close(got, want)
+
+
+def test_heavy_rows_bitwise_across_forms(bc, heavy_graph):
+    g, src, _ = heavy_graph
+    ref, _, _ = gpu_bc(bc, g, src, batch_width=64)
+    for kw in [dict(batch_width=1), dict(batch_width=128), dict(batch_width=32, direction=1),
+               dict(batch_width=128, direction=2)]:
+        got, _, _ = gpu_bc(bc, g, src, **kw)
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
+
+
+def test_star_hub_all_sources(bc):
+    """A hub of degree 3000 (3 chunks) reached at level 0 and level 1, all sources."""
+    g = bcgen.disjoint_union(bcgen.star(3001), bcgen.path(3))
+    for K in (1, 64):
+        got, _, _ = gpu_bc(bc, g, np.arange(g.n), batch_width=K)
+        half = np.zeros(g.n)
+        half[0] = 3000 * 2999 / 2
+        half[3002] = 1
+        assert_bc_close(got / 2, half, rel=1e-12)
