@@ -9,7 +9,7 @@ Contents:
   * ``bc`` / ``bc_ld`` / ``source_detail`` -- plain single-threaded Brandes in
     double or long double (``brandes.c``), following the paper's computeBC
     (Appendix A, BC listing) with iterateInBFS / iterateInReverse semantics
-    (Section 2.2): sigma summed over BFS-DAG predecessors, delta pulled from
+    (Section 2.3.2): sigma summed over BFS-DAG predecessors, delta pulled from
     DAG successors in reverse BFS order as (sigma_v/sigma_w)(1+delta_w), and
     BC the raw sum of delta over the listed sources (source excluded).
   * ``brute_force_bc`` -- exact rational BC from explicit enumeration of every

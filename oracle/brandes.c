@@ -5,7 +5,7 @@
  * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
  * call it.  It shares no code, header, table or helper with the CUDA library.
  *
- * What it computes (the paper's computeBC, Appendix A, BC listing; Section 2,
+ * What it computes (the paper's computeBC, Appendix A, BC listing; Section 2.3.2,
  * iterateInBFS / iterateInReverse):
  *   for every source s in the given list (duplicates counted once per entry):
  *     sigma = 0, delta = 0, sigma[s] = 1, level[s] = 0

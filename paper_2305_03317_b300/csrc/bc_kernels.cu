@@ -3,7 +3,7 @@
 // One cooperative launch runs every batch of a bc_compute call.  A batch is
 // K sources (K = 1, 32, 64 or 128) traversed together: column c of every
 // per-vertex array belongs to source c of the batch, and all columns advance
-// one BFS level per iteration (the paper's iterateInBFS, Section 2.2, run for
+// one BFS level per iteration (the paper's iterateInBFS, Section 2.3.2, run for
 // K roots at once).  Per iteration:
 //   * discovery, either top-down (push: frontier rows claim unseen neighbours
 //     with atomicOr on their column masks, warp-aggregated list appends) or

@@ -2,7 +2,7 @@
 // the relabelled CSR with sorted rows.
 //
 // The paper's backend copies the CSR to the GPU once and keeps it there
-// (Section 3.1; Section 4 on transfer minimisation).  Here the copy is also
+// (Section 3.1; Section 4.3 on keeping transfers few).  Here the copy is also
 // relabelled: new id r is the r-th vertex in (degree descending, original id
 // ascending) order, so heavy rows form a prefix [0, n_heavy) and isolated
 // vertices a suffix [n_nz, n).  Both sorts are one stable LSD radix sort of
