@@ -173,6 +173,29 @@ bc_status bc_server_config(int32_t slots, int64_t memory_budget);
  */
 bc_status bc_debug_source(bc_graph* g, int32_t s, int32_t* level, double* sigma_mant, int32_t* sigma_exp);
 
+/*
+ * BC for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is an addition of this library).  Some host code may not
+ * call cudaMalloc: a framework that owns the whole device through its own pool
+ * and forbids other allocations (to hold a hard memory cap), or a
+ * latency-critical path that must never enter the CUDA allocator.  Such a
+ * caller passes everything on the device: offsets[n+1] and indices[m] (int32
+ * undirected CSR, used as given: offsets and index range are checked, symmetry,
+ * self-loops and duplicates are not), sources[nsrc] (original ids), and
+ * out_bc[n] (overwritten with the same raw BC as bc_compute, within 1e-9
+ * relative).  All working state lives in one static device array of about
+ * 37 MB that every GPU loading the library holds until exit; hence
+ * n <= 32768 vertices (BC_E_LIMIT beyond), batches of 32 sources.  The call
+ * allocates nothing and returns when the result is final.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress with
+ * that device current): make that first call before any stream capture.
+ * Every call shares the array and it keeps the last call's contents (each call
+ * clears what must start at zero): calls that overlap on the GPU, from
+ * several streams or threads, race and must not be issued.
+ */
+bc_status bc_compute_noalloc(const int32_t* offsets, const int32_t* indices, int32_t n, int64_t m,
+                             const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream);
+
 const char* bc_status_string(bc_status st);
 const char* bc_last_error(void);
 

@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_server_config": [i32, i64],
         "bc_debug_source": [P, i32, P, P, P],
         "bc_last_trace": [P, P, i32, P],
+        "bc_compute_noalloc": [P, P, i32, i64, P, i32, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

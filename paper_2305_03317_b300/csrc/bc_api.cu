@@ -39,6 +39,8 @@ static bc_status fail(bc_status st, const char* fmt, ...) {
     return st;
 }
 
+void bcx::set_last_error(const char* msg) { t_err = msg; }
+
 static bc_status cuda_fail(cudaError_t e, const char* what) {
     return fail(BC_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }

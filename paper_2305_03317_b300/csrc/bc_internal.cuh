@@ -99,6 +99,9 @@ cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, in
 cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
                                  int* sige_rel, cudaStream_t st);
 
+// Thread-local detail returned by bc_last_error() (bc_api.cu)
+void set_last_error(const char* msg);
+
 // Ingest (ingest.cu)
 struct IngestOut {
     int* off;       // [n+1] device
