@@ -143,6 +143,32 @@ bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 bc_status bc_last_trace(const bc_graph* g, int64_t* out, int32_t cap, int32_t* count);
 
 /*
+ * Many graphs in one recorded sequence: for each item, BC over its sources
+ * (host array, original ids, copied at create) on its graph into its output
+ * (device, n doubles).  bc_many_create groups the items by batch width,
+ * allocates one workspace per width, and records every item's work (source
+ * mapping, one persistent launch over all of its batches, a status word, the
+ * unpermute) into a CUDA graph; bc_many_run replays it on `stream`, then
+ * redoes alone any item that needed the extended path-count form or larger
+ * level lists, and returns the worst status (per item in item_status[nitems],
+ * may be NULL).  Outputs must stay alive while the plan is run.  Results are
+ * bitwise those of bc_compute on each item.
+ */
+typedef struct bc_many_plan bc_many_plan;
+typedef struct {
+    bc_graph* graph;
+    const int32_t* sources;
+    int32_t nsrc;
+    double* out_bc;
+} bc_item;
+bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options* opt, bc_stream_t stream,
+                         bc_many_plan** out);
+bc_status bc_many_run(bc_many_plan* plan, bc_stream_t stream, bc_status* item_status);
+bc_status bc_many_destroy(bc_many_plan* plan);
+/* Items in the plan and kernel launches recorded in its graph. */
+bc_status bc_many_info(const bc_many_plan* plan, int32_t* items, int32_t* kernel_launches);
+
+/*
  * Serving: continuous batching over resident graphs.  bc_batch_submit queues a
  * job (sources copied from host memory at submit time; out_bc is a device
  * array of n doubles that must stay alive until bc_poll returns a final

@@ -55,6 +55,11 @@ class bc_run_stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_float)]
 
 
+class bc_item(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("sources", ctypes.c_void_p), ("nsrc", ctypes.c_int32),
+                ("out_bc", ctypes.c_void_p)]
+
+
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
     """Load libbc.so and declare its signatures (raises if the file is missing)."""
     global _lib
@@ -84,6 +89,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_debug_source": [P, i32, P, P, P],
         "bc_last_trace": [P, P, i32, P],
         "bc_compute_noalloc": [P, P, i32, i64, P, i32, P, P],
+        "bc_many_create": [ctypes.POINTER(bc_item), i32, ctypes.POINTER(bc_options), P, ctypes.POINTER(P)],
+        "bc_many_run": [P, P, P],
+        "bc_many_destroy": [P],
+        "bc_many_info": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -257,6 +266,44 @@ class Graph:
         return Job(int(jid.value), self, out, src)
 
 
+class ManyPlan:
+    """Many (graph, sources, output) items recorded once into a CUDA graph (bc_many_create)."""
+
+    def __init__(self, items, stream=None, **opts):
+        """items: list of (Graph, host int32 sources, device float64 output tensor)."""
+        lib = load()
+        self._keep = [(g, np.ascontiguousarray(s, dtype=np.int32), o) for g, s, o in items]
+        arr = (bc_item * max(len(items), 1))()
+        for i, (g, s, o) in enumerate(self._keep):
+            arr[i] = bc_item(g._h, s.ctypes.data if s.size else None, int(s.size), _ptr(o) if g.n else None)
+        opt = bc_options(opts.get("batch_width", 0), opts.get("direction", 0), 0.0, 0.0, 0, opts.get("blocks_per_sm", 0),
+                         0, 0)
+        self._h = ctypes.c_void_p()
+        _check(lib.bc_many_create(arr, len(items), ctypes.byref(opt), _stream_handle(stream), ctypes.byref(self._h)))
+
+    def run(self, stream=None):
+        """Replay; returns the per-item statuses."""
+        st = np.zeros(max(len(self._keep), 1), np.int32)
+        _check(load().bc_many_run(self._h, _stream_handle(stream), st.ctypes.data))
+        return st[: len(self._keep)]
+
+    def info(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().bc_many_info(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return {"items": a.value, "kernel_launches": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().bc_many_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _has_cuda() -> bool:
     try:
         import torch
@@ -265,4 +312,4 @@ def _has_cuda() -> bool:
         return False
 
 
-__all__ = ["Graph", "Job", "BCError", "load", "status_string", "last_error", "server_config", "server_stats"]
+__all__ = ["Graph", "Job", "ManyPlan", "BCError", "load", "status_string", "last_error", "server_config", "server_stats"]

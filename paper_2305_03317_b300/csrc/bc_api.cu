@@ -6,6 +6,7 @@
 // method happens on the host: it only marshals sizes, pointers and statuses.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -219,13 +220,16 @@ static bc_status ensure_heavy(bc_graph* g, cudaStream_t st) {
     return BC_OK;
 }
 
-static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, int njobs, int capf, cudaStream_t st) {
+// Workspace sized for graphs of at most n_vert vertices, n_heavy heavy rows and
+// hchunks heavy chunks.
+static bool ws_ensure_dims(Workspace* w, int n_vert, int n_heavy, long long hchunks, int K, bool ext, int nbatch,
+                           int njobs, int capf, cudaStream_t st) {
     w->K = K;
-    const size_t n = (size_t)(g->n > 0 ? g->n : 1);
+    const size_t n = (size_t)(n_vert > 0 ? n_vert : 1);
     const int W = K >= 32 ? K / 32 : 1;
     const long long cap = (long long)n * capf;
-    const long long hcap = (long long)(g->n_heavy > 0 ? g->n_heavy : 1) * K;
-    const size_t hc = (size_t)(g->hchunk_total > 0 ? g->hchunk_total : 1);
+    const long long hcap = (long long)(n_heavy > 0 ? n_heavy : 1) * K;
+    const size_t hc = (size_t)(hchunks > 0 ? hchunks : 1);
     const size_t nb = (size_t)(nbatch > 0 ? nbatch : 1);
     bool ok = true;
     ok &= buf_ensure(w->V, sizeof(uint32_t) * n * W, st);
@@ -245,7 +249,7 @@ static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, in
     ok &= buf_ensure(w->stamp, sizeof(int) * n, st);
     ok &= buf_ensure(w->scr_v, sizeof(unsigned long long) * hc * K, st);
     ok &= buf_ensure(w->scr_or, sizeof(uint32_t) * hc * W, st);
-    ok &= buf_ensure(w->arr, sizeof(int) * (size_t)(g->n_heavy > 0 ? g->n_heavy : 1), st);
+    ok &= buf_ensure(w->arr, sizeof(int) * (size_t)(n_heavy > 0 ? n_heavy : 1), st);
     ok &= buf_ensure(w->cnt, sizeof(int) * kLevelSlots, st);
     ok &= buf_ensure(w->hcnt, sizeof(int) * kLevelSlots, st);
     ok &= buf_ensure(w->start, sizeof(int) * kLevelSlots, st);
@@ -261,12 +265,16 @@ static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, in
     ok &= buf_ensure(w->bad, sizeof(int), st);
     ok &= buf_ensure(w->jobptr, sizeof(double*) * (size_t)(njobs > 0 ? njobs : 1), st);
     if (!ok) {
-        fail(BC_E_NOMEM, "device allocation failed for a batch-width-%d workspace (n=%d)", K, g->n);
+        fail(BC_E_NOMEM, "device allocation failed for a batch-width-%d workspace (n=%d)", K, n_vert);
         return false;
     }
     w->cap = cap;
     w->hcap = hcap;
     return true;
+}
+
+static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, int njobs, int capf, cudaStream_t st) {
+    return ws_ensure_dims(w, g->n, g->n_heavy, g->hchunk_total, K, ext, nbatch, njobs, capf, st);
 }
 
 static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_options& o, bool ext) {
@@ -667,6 +675,89 @@ void server_start_locked(Server& S) {
 
 }  // namespace
 
+// ------------------------------------------------------------------ many graphs, one captured sequence
+// Every item (graph, sources, output) gets: source mapping, one persistent
+// cooperative launch over all its batches, a status word, the unpermute into
+// its output.  Items are grouped by batch width; one workspace per width,
+// sized for the largest graph of the group, serves its items in stream order.
+// The whole sequence is recorded once into a CUDA graph and replayed by
+// bc_many_run; items whose status asks for the extended path-count form or
+// larger level lists are redone afterwards through bc_compute_ex.
+struct ManyItem {
+    bc_graph* g = nullptr;
+    std::vector<int> src;      // original ids (host copy)
+    long long src_off = 0;     // into the plan's device source buffer
+    double* out = nullptr;
+    int K = 0, nbatch = 0;
+};
+
+struct bc_many_plan {
+    std::vector<ManyItem> items;
+    std::map<int, std::unique_ptr<Workspace>> ws;  // by width
+    DevBuf dsrc, dstatus;
+    bc_options opt{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+};
+
+static void many_release(bc_many_plan* pl) {
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    cudaStream_t st = pl->cap_stream;
+    if (st) cudaStreamSynchronize(st);
+    for (auto& kv : pl->ws) kv.second->release(st);
+    buf_release(pl->dsrc, st);
+    buf_release(pl->dstatus, st);
+    if (st) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+}
+
+// Record the per-item sequence on the plan's capture stream.
+static bc_status many_record(bc_many_plan* pl) {
+    cudaStream_t st = pl->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    bc_status r = BC_OK;
+    int launches = 0;
+    for (size_t i = 0; i < pl->items.size() && r == BC_OK; ++i) {
+        ManyItem& it = pl->items[i];
+        bc_graph* g = it.g;
+        Workspace* w = pl->ws[it.K].get();
+        const int blocks = grid_blocks(it.K, false, pl->opt.blocks_per_sm, 1);
+        KParams p = make_params(g, w, it.nbatch, pl->opt, false);
+        int* status = (int*)pl->dstatus.p + i;
+        if ((e = cudaMemsetAsync(w->ctl.p, 0, sizeof(Ctl), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(w->bstat.p, 0, sizeof(int) * it.nbatch, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(w->arr.p, 0, w->arr.bytes, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(w->bc.p, 0, sizeof(double) * (size_t)(g->n > 0 ? g->n : 1), st)) != cudaSuccess ||
+            (e = launch_map_sources((const int*)pl->dsrc.p + it.src_off, (int)it.src.size(), (const int*)g->inv.p,
+                                    g->n, it.K, (int*)w->src.p, it.nbatch, (int*)w->bad.p, st)) != cudaSuccess ||
+            (e = launch_batches(it.K, p, blocks, st)) != cudaSuccess ||
+            (e = launch_collect_status((const Ctl*)w->ctl.p, (const int*)w->bstat.p, it.nbatch, status, st)) !=
+                cudaSuccess ||
+            (e = launch_unpermute((const double*)w->bc.p, (const int*)g->inv.p, it.out, g->n, st)) != cudaSuccess) {
+            r = cuda_fail(e, "recording the many-graph sequence");
+        }
+        launches += 4;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (r != BC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    pl->graph = graph;
+    e = cudaGraphInstantiate(&pl->exec, graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    pl->launches = launches;
+    return BC_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -911,6 +1002,129 @@ bc_status bc_debug_source(bc_graph* g, int32_t s, int32_t* level, double* sigma_
         if (sigma_exp) sigma_exp[v] = sig[r2] ? ex + sige[r2] : 0;
     }
     return r;
+}
+
+bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options* opt, bc_stream_t stream,
+                         bc_many_plan** out) {
+    if (!out || nitems < 0 || (nitems > 0 && !items)) return fail(BC_E_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    bc_options o;
+    memset(&o, 0, sizeof o);
+    if (opt) o = *opt;
+    bc_status cs = check_opts(o);
+    if (cs != BC_OK) return cs;
+    cudaStream_t ust = (cudaStream_t)stream;
+    std::unique_ptr<bc_many_plan> pl(new bc_many_plan());
+    pl->opt = o;
+    long long total_src = 0;
+    // items, validated on the host; per-width dimensions
+    struct Dims { int n = 0, nh = 0, nb = 0; long long hc = 0; };
+    std::map<int, Dims> dims;
+    for (int i = 0; i < nitems; ++i) {
+        const bc_item& x = items[i];
+        if (!x.graph || x.nsrc < 0 || (x.nsrc > 0 && !x.sources) || (!x.out_bc && x.graph->n > 0))
+            return fail(BC_E_INVALID_ARG, "item %d: bad graph, sources or output", i);
+        bc_graph* g = x.graph;
+        for (int k = 0; k < x.nsrc; ++k)
+            if (x.sources[k] < 0 || x.sources[k] >= g->n)
+                return fail(BC_E_SOURCE, "item %d: source %d outside [0, %d)", i, x.sources[k], g->n);
+        bc_status r = ensure_heavy(g, ust);
+        if (r != BC_OK) return r;
+        ManyItem it;
+        it.g = g;
+        it.src.assign(x.sources, x.sources + x.nsrc);
+        it.out = x.out_bc;
+        it.K = choose_width(g->n, x.nsrc, o.batch_width);
+        it.nbatch = (x.nsrc + it.K - 1) / it.K;
+        it.src_off = total_src;
+        total_src += x.nsrc;
+        Dims& d = dims[it.K];
+        d.n = std::max(d.n, g->n);
+        d.nh = std::max(d.nh, g->n_heavy);
+        d.hc = std::max(d.hc, g->hchunk_total);
+        d.nb = std::max(d.nb, it.nbatch);
+        pl->items.push_back(std::move(it));
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "stream");
+    cudaStream_t st = pl->cap_stream;
+    auto bail = [&](bc_status r) {
+        many_release(pl.get());
+        return r;
+    };
+    for (auto& kv : dims) {
+        std::unique_ptr<Workspace> w(new Workspace());
+        if (!ws_ensure_dims(w.get(), kv.second.n, kv.second.nh, kv.second.hc, kv.first, false, kv.second.nb, 1,
+                            cap_factor(kv.first, 0), st))
+            return bail(BC_E_NOMEM);
+        double* jb = (double*)w->bc.p;
+        if ((e = cudaMemcpyAsync(w->jobptr.p, &jb, sizeof(double*), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return bail(cuda_fail(e, "job table"));
+        pl->ws[kv.first] = std::move(w);
+    }
+    if (!buf_ensure(pl->dsrc, sizeof(int) * (size_t)(total_src > 0 ? total_src : 1), st) ||
+        !buf_ensure(pl->dstatus, sizeof(int) * (size_t)(nitems > 0 ? nitems : 1), st))
+        return bail(fail(BC_E_NOMEM, "plan buffers"));
+    std::vector<int> all;
+    all.reserve((size_t)total_src);
+    for (auto& it : pl->items) all.insert(all.end(), it.src.begin(), it.src.end());
+    if (total_src > 0 &&
+        (e = cudaMemcpyAsync(pl->dsrc.p, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+        return bail(cuda_fail(e, "source copy"));
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(e, "plan set-up"));
+    bc_status r = many_record(pl.get());
+    if (r != BC_OK) return bail(r);
+    *out = pl.release();
+    return BC_OK;
+}
+
+bc_status bc_many_run(bc_many_plan* pl, bc_stream_t stream, bc_status* item_status) {
+    if (!pl) return fail(BC_E_INVALID_ARG, "plan is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ni = pl->items.size();
+    if (ni == 0) return BC_OK;
+    cudaError_t e = cudaGraphLaunch(pl->exec, st);
+    std::vector<int> status(ni);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(status.data(), pl->dstatus.p, sizeof(int) * ni, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "many-graph run");
+    bc_status overall = BC_OK;
+    for (size_t i = 0; i < ni; ++i) {
+        const int w = status[i];
+        bc_status r;
+        if ((w >> 8) & ERR_TIMEOUT) {
+            r = fail(BC_E_TIMEOUT, "item %zu: a grid-barrier wait exceeded its cycle budget", i);
+        } else if ((w >> 8) & ERR_LIMIT) {
+            r = fail(BC_E_LIMIT, "item %zu: BFS deeper than %d levels", i, kMaxLevel);
+        } else if ((w >> 8) || (w & (BST_NEED_EXT | 0x80))) {
+            // extended path-count form or larger level lists: redo this item alone
+            ManyItem& it = pl->items[i];
+            r = bc_compute_ex(it.g, it.src.data(), (int)it.src.size(), it.out, stream, &pl->opt);
+        } else {
+            r = (w & BST_INEXACT) ? BC_W_SIGMA_INEXACT : BC_OK;
+        }
+        if (item_status) item_status[i] = r;
+        if (r < 0 && overall >= 0) overall = r;
+        else if (r == BC_W_SIGMA_INEXACT && overall == BC_OK) overall = r;
+    }
+    return overall;
+}
+
+bc_status bc_many_destroy(bc_many_plan* pl) {
+    if (!pl) return fail(BC_E_INVALID_ARG, "plan is NULL");
+    many_release(pl);
+    delete pl;
+    return BC_OK;
+}
+
+bc_status bc_many_info(const bc_many_plan* pl, int32_t* items, int32_t* kernel_launches) {
+    if (!pl) return fail(BC_E_INVALID_ARG, "plan is NULL");
+    if (items) *items = (int32_t)pl->items.size();
+    if (kernel_launches) *kernel_launches = pl->launches;
+    return BC_OK;
 }
 
 bc_status bc_server_config(int32_t slots, int64_t memory_budget) {

@@ -94,6 +94,7 @@ struct KParams {
 cudaError_t launch_batches(int K, const KParams& p, int blocks, cudaStream_t st);
 int max_coop_blocks(int K, bool ext, int* per_sm);
 cudaError_t launch_unpermute(const double* bc_rel, const int* inv, double* out, int n, cudaStream_t st);
+cudaError_t launch_collect_status(const Ctl* ctl, const int* bstat, int nbatch, int* out, cudaStream_t st);
 cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, int n, int K, int* dst,
                                int nbatch, int* bad, cudaStream_t st);
 cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,

@@ -1312,6 +1312,19 @@ __global__ void k_debug_extract(KParams p, int K, int levels, int* level_rel, un
     }
 }
 
+// One status word per launch: Ctl error bits << 8 | OR of the batch status
+// bits | 0x80 when a batch neither finished nor asked for the extended form.
+__global__ void k_collect_status(const Ctl* ctl, const int* bstat, int nbatch, int* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int flags = 0;
+    for (int b = 0; b < nbatch; ++b) {
+        const int x = bstat[b];
+        flags |= x;
+        if (!(x & (BST_DONE | BST_NEED_EXT))) flags |= 0x80;
+    }
+    *out = (ctl->err << 8) | flags;
+}
+
 // ------------------------------------------------------------------ host launchers
 template <int K, bool EXT>
 static size_t smem_bytes() { return sizeof(WarpSmem<K, EXT>) * kWarps; }
@@ -1330,10 +1343,19 @@ template <int K, bool EXT>
 static cudaError_t launch_k(const KParams& p, int blocks, cudaStream_t st) {
     cudaError_t e = prepare<K, EXT>();
     if (e != cudaSuccess) return e;
-    KParams q = p;
-    void* args[] = {&q};
-    return cudaLaunchCooperativeKernel((const void*)bc_persistent<K, EXT>, dim3(blocks), dim3(kThreads), args,
-                                       smem_bytes<K, EXT>(), st);
+    // cooperative launch (all blocks co-resident) through the attribute form,
+    // which stream capture records into a CUDA graph
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem_bytes<K, EXT>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bc_persistent<K, EXT>, p);
 }
 
 cudaError_t launch_batches(int K, const KParams& p, int blocks, cudaStream_t st) {
@@ -1368,6 +1390,11 @@ int max_coop_blocks(int K, bool ext, int* per_sm) {
     }
     if (per_sm) *per_sm = nb;
     return nb * sms;
+}
+
+cudaError_t launch_collect_status(const Ctl* ctl, const int* bstat, int nbatch, int* out, cudaStream_t st) {
+    k_collect_status<<<1, 32, 0, st>>>(ctl, bstat, nbatch, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_unpermute(const double* bc_rel, const int* inv, double* out, int n, cudaStream_t st) {

@@ -281,3 +281,33 @@ def test_star_hub_all_sources(bc):
         half[0] = 3000 * 2999 / 2
         half[3002] = 1
         assert_bc_close(got / 2, half, rel=1e-12)
+
+
+# ----------------------------------------------------------------- many graphs, one recorded sequence
+
+def test_many_graphs_plan_matches_single_calls(bc):
+    import torch
+    sizes = [(300, 6, 11), (1000, 12, 12), (2500, 20, 13), (4000, 8, 14), (700, 31, 15), (5000, 16, 16)]
+    graphs = [bcgen.rmat_n(n, ef, seed) for n, ef, seed in sizes] + [bcgen.grid(70, 70, 0.0),
+                                                                      bcgen.star(2500)]
+    items, refs, oracles = [], [], []
+    for i, g in enumerate(graphs):
+        src = np.arange(g.n, dtype=np.int32) if g.n <= 1200 else bcgen.sample_sources(g, 100, 30 + i)
+        G = bc.Graph(g.off, g.adj)
+        out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        items.append((G, src, out))
+        ref, _ = bc.Graph(g.off, g.adj).compute(src)
+        refs.append(ref.cpu().numpy().copy())
+        want = oracle.bc_ld(g.off, g.adj, src).astype(np.float64) if g.n == 4900 else oracle.bc(g.off, g.adj, src)
+        oracles.append(want)
+    plan = bc.ManyPlan(items)
+    assert plan.info()["items"] == len(items)
+    for rep in range(2):  # replay twice
+        st = plan.run()
+        assert all(int(x) in (bc.BC_OK, bc.BC_W_SIGMA_INEXACT) for x in st)
+        for (G, src, out), ref, want in zip(items, refs, oracles):
+            got = out.cpu().numpy()
+            assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+            assert_bc_close(got, want)
+    # the 70x70 full grid needs the extended form: its item is redone alone
+    assert int(st[len(sizes)]) == bc.BC_W_SIGMA_INEXACT
