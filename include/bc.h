@@ -105,6 +105,8 @@ typedef struct {
     int64_t barrier_budget;  /* device cycles a grid-barrier wait may spin before BC_E_TIMEOUT
                                 (0 = about 20 s; tests may set 1 to force a timeout) */
     int32_t trace;           /* 1 = record a device timestamp at the end of every grid-wide phase */
+    int32_t teams;           /* independent groups of blocks, each running its own batches (0 = auto:
+                                one block per ~2^19 arcs per team, at most one team per batch) */
 } bc_options;
 
 /*
@@ -130,6 +132,7 @@ typedef struct {
     int32_t grid_blocks;     /* persistent grid size */
     int32_t kernel_launches; /* kernels launched by the call */
     float kernel_ms;         /* device time of the persistent traversal launches (CUDA events on the call's stream) */
+    int32_t teams;           /* teams of the last launch */
 } bc_run_stats;
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 

@@ -113,31 +113,85 @@ static void buf_release(DevBuf& b, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ graph
+// Per-team arrays live in one arena: team t's slice starts at t * team_bytes and
+// every slice has the same layout (offsets below).  Launch-wide arrays are
+// separate buffers.
+struct TeamLayout {
+    size_t V = 0, F0 = 0, F1 = 0, F2 = 0, sig = 0, rho = 0, sig_e = 0, rho_e = 0, ent = 0, emask = 0;
+    size_t hent = 0, hmask = 0, hpre = 0, stamp = 0, scr_v = 0, scr_e = 0, scr_or = 0, arr = 0;
+    size_t cnt = 0, hcnt = 0, start = 0, hstart = 0, hchunks = 0, dsum = 0, fulldeg = 0, ctl = 0;
+    size_t bytes = 0;
+    long long cap = 0, hcap = 0;
+    int arr_ints = 0, level_slots = 0;
+};
+
+static TeamLayout team_layout(int n_vert, int n_heavy, long long hchunks, int K, bool ext, int capf) {
+    TeamLayout L;
+    const size_t n = (size_t)(n_vert > 0 ? n_vert : 1);
+    const size_t W = K >= 32 ? (size_t)K / 32 : 1;
+    const size_t nh = (size_t)(n_heavy > 0 ? n_heavy : 1);
+    const size_t hc = (size_t)(hchunks > 0 ? hchunks : 1);
+    L.cap = (long long)n * capf;
+    L.hcap = (long long)nh * K;
+    L.arr_ints = (int)nh;
+    L.level_slots = (int)std::min<long long>(kLevelSlots, (long long)n + 3);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 255) / 256 * 256;
+        return at;
+    };
+    L.V = take(4 * n * W);
+    L.F0 = take(4 * n * W);
+    L.F1 = take(4 * n * W);
+    L.F2 = take(4 * n * W);
+    L.sig = take(8 * n * K);
+    L.rho = take(8 * n * K);
+    if (ext) {
+        L.sig_e = take(4 * n * K);
+        L.rho_e = take(4 * n * K);
+    }
+    L.ent = take(4 * (size_t)L.cap);
+    L.emask = take(4 * W * (size_t)L.cap);
+    L.hent = take(4 * (size_t)L.hcap);
+    L.hmask = take(4 * W * (size_t)L.hcap);
+    L.hpre = take(4 * (size_t)L.hcap);
+    L.stamp = take(4 * n);
+    L.scr_v = take(8 * hc * K);
+    if (ext) L.scr_e = take(4 * hc * K);
+    L.scr_or = take(4 * hc * W);
+    L.arr = take(4 * nh);
+    const size_t ls = (size_t)L.level_slots;
+    L.cnt = take(4 * ls);
+    L.hcnt = take(4 * ls);
+    L.start = take(4 * ls);
+    L.hstart = take(4 * ls);
+    L.hchunks = take(4 * ls);
+    L.dsum = take(8 * ls);
+    L.fulldeg = take(8 * ls);
+    L.ctl = take(sizeof(Ctl));
+    L.bytes = o;
+    return L;
+}
+
 struct Workspace {
     int K = 0;
-    DevBuf V, F[3], sig, sig_e, rho, rho_e, ent, emask, hent, hmask, hpre, stamp;
-    DevBuf scr_v, scr_e, scr_or, arr;
-    DevBuf cnt, hcnt, start, hstart, dsum, fulldeg, hchunks, ctl, bstat, bc, src, bad, jobptr, coljob, trace;
-    long long cap = 0, hcap = 0;
-    DevBuf* all_bufs(std::vector<DevBuf*>& v) {
-        DevBuf* a[] = {&V, &F[0], &F[1], &F[2], &sig, &sig_e, &rho, &rho_e, &ent, &emask, &hent, &hmask, &hpre,
-                       &stamp, &scr_v, &scr_e, &scr_or, &arr, &cnt, &hcnt, &start, &hstart, &dsum, &fulldeg,
-                       &hchunks, &ctl, &bstat, &bc, &src, &bad, &jobptr, &coljob, &trace};
-        v.assign(a, a + sizeof(a) / sizeof(a[0]));
-        return nullptr;
-    }
+    bool ext = false;
+    int nteams = 0;
+    TeamLayout lay;
+    DevBuf arena;  // nteams * lay.bytes
+    DevBuf gctl, bstat, bc, src, bad, jobptr, coljob, trace;
     void release(cudaStream_t st) {
-        std::vector<DevBuf*> v;
-        all_bufs(v);
-        for (DevBuf* b : v) buf_release(*b, st);
+        DevBuf* all[] = {&arena, &gctl, &bstat, &bc, &src, &bad, &jobptr, &coljob, &trace};
+        for (DevBuf* b : all) buf_release(*b, st);
     }
-    size_t bytes() {
-        std::vector<DevBuf*> v;
-        all_bufs(v);
+    size_t bytes() const {
+        const DevBuf* all[] = {&arena, &gctl, &bstat, &bc, &src, &bad, &jobptr, &coljob, &trace};
         size_t t = 0;
-        for (DevBuf* b : v) t += b->bytes;
+        for (const DevBuf* b : all) t += b->bytes;
         return t;
     }
+    char* at(size_t off) const { return (char*)arena.p + off; }
 };
 
 // Entry-list capacity per vertex: a vertex enters a level list at most once per
@@ -145,19 +199,11 @@ struct Workspace {
 // uses a smaller factor and the call reruns with K on overflow.
 static int cap_factor(int K, int sticky) { return sticky > 0 ? sticky : (K < 24 ? K : 24); }
 
-// Bytes a workspace needs for n vertices at width K (plus the extended arrays).
+// Bytes a single-team workspace needs (admission estimate for serving).
 static size_t ws_need(int n, int K, int n_heavy, long long hc, bool ext, int nbatch, int njobs, int capf) {
-    const size_t nn = (size_t)(n > 0 ? n : 1);
-    const int W = K >= 32 ? K / 32 : 1;
-    size_t b = 4 * sizeof(uint32_t) * nn * W + 2 * sizeof(double) * nn * K + sizeof(int) * nn;
-    if (ext) b += 2 * sizeof(int) * nn * K;
-    b += (sizeof(int) + sizeof(uint32_t) * W) * nn * (size_t)capf;
-    b += (2 * sizeof(int) + sizeof(uint32_t) * W) * (size_t)(n_heavy > 0 ? n_heavy : 1) * K;
-    b += (size_t)(hc > 0 ? hc : 1) * ((8 + (ext ? 4 : 0)) * K + 4 * W) + sizeof(int) * (size_t)(n_heavy + 1);
-    b += (5 * sizeof(int) + 2 * sizeof(long long)) * kLevelSlots + sizeof(Ctl);
-    b += sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * (1 + 2 * K) + sizeof(double) * nn;
-    b += sizeof(double*) * (size_t)(njobs > 0 ? njobs : 1);
-    return b;
+    const TeamLayout L = team_layout(n, n_heavy, hc, K, ext, capf);
+    return L.bytes + sizeof(Ctl) + sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * (1 + 2 * K) +
+           sizeof(double) * (size_t)(n > 0 ? n : 1) + sizeof(double*) * (size_t)(njobs > 0 ? njobs : 1);
 }
 
 struct bc_graph {
@@ -220,44 +266,17 @@ static bc_status ensure_heavy(bc_graph* g, cudaStream_t st) {
     return BC_OK;
 }
 
-// Workspace sized for graphs of at most n_vert vertices, n_heavy heavy rows and
-// hchunks heavy chunks.
+// Workspace for `nteams` teams, each sized for graphs of at most n_vert
+// vertices, n_heavy heavy rows and hchunks heavy chunks.
 static bool ws_ensure_dims(Workspace* w, int n_vert, int n_heavy, long long hchunks, int K, bool ext, int nbatch,
-                           int njobs, int capf, cudaStream_t st) {
-    w->K = K;
+                           int njobs, int capf, int nteams, cudaStream_t st) {
+    const TeamLayout L = team_layout(n_vert, n_heavy, hchunks, K, ext, capf);
     const size_t n = (size_t)(n_vert > 0 ? n_vert : 1);
-    const int W = K >= 32 ? K / 32 : 1;
-    const long long cap = (long long)n * capf;
-    const long long hcap = (long long)(n_heavy > 0 ? n_heavy : 1) * K;
-    const size_t hc = (size_t)(hchunks > 0 ? hchunks : 1);
     const size_t nb = (size_t)(nbatch > 0 ? nbatch : 1);
-    bool ok = true;
-    ok &= buf_ensure(w->V, sizeof(uint32_t) * n * W, st);
-    for (int i = 0; i < 3; ++i) ok &= buf_ensure(w->F[i], sizeof(uint32_t) * n * W, st);
-    ok &= buf_ensure(w->sig, sizeof(unsigned long long) * n * K, st);
-    ok &= buf_ensure(w->rho, sizeof(double) * n * K, st);
-    if (ext) {
-        ok &= buf_ensure(w->sig_e, sizeof(int) * n * K, st);
-        ok &= buf_ensure(w->rho_e, sizeof(int) * n * K, st);
-        ok &= buf_ensure(w->scr_e, sizeof(int) * hc * K, st);
-    }
-    ok &= buf_ensure(w->ent, sizeof(int) * (size_t)cap, st);
-    ok &= buf_ensure(w->emask, sizeof(uint32_t) * W * (size_t)cap, st);
-    ok &= buf_ensure(w->hent, sizeof(int) * (size_t)hcap, st);
-    ok &= buf_ensure(w->hmask, sizeof(uint32_t) * W * (size_t)hcap, st);
-    ok &= buf_ensure(w->hpre, sizeof(int) * (size_t)hcap, st);
-    ok &= buf_ensure(w->stamp, sizeof(int) * n, st);
-    ok &= buf_ensure(w->scr_v, sizeof(unsigned long long) * hc * K, st);
-    ok &= buf_ensure(w->scr_or, sizeof(uint32_t) * hc * W, st);
-    ok &= buf_ensure(w->arr, sizeof(int) * (size_t)(n_heavy > 0 ? n_heavy : 1), st);
-    ok &= buf_ensure(w->cnt, sizeof(int) * kLevelSlots, st);
-    ok &= buf_ensure(w->hcnt, sizeof(int) * kLevelSlots, st);
-    ok &= buf_ensure(w->start, sizeof(int) * kLevelSlots, st);
-    ok &= buf_ensure(w->hstart, sizeof(int) * kLevelSlots, st);
-    ok &= buf_ensure(w->dsum, sizeof(long long) * kLevelSlots, st);
-    ok &= buf_ensure(w->fulldeg, sizeof(long long) * kLevelSlots, st);
-    ok &= buf_ensure(w->hchunks, sizeof(int) * kLevelSlots, st);
-    ok &= buf_ensure(w->ctl, sizeof(Ctl), st);
+    // keep a larger arena when it already fits the new layout's total
+    const size_t need = L.bytes * (size_t)(nteams > 0 ? nteams : 1);
+    bool ok = buf_ensure(w->arena, need, st);
+    ok &= buf_ensure(w->gctl, sizeof(Ctl), st);
     ok &= buf_ensure(w->bstat, sizeof(int) * nb, st);
     ok &= buf_ensure(w->bc, sizeof(double) * n, st);
     ok &= buf_ensure(w->src, sizeof(int) * nb * K, st);
@@ -265,21 +284,25 @@ static bool ws_ensure_dims(Workspace* w, int n_vert, int n_heavy, long long hchu
     ok &= buf_ensure(w->bad, sizeof(int), st);
     ok &= buf_ensure(w->jobptr, sizeof(double*) * (size_t)(njobs > 0 ? njobs : 1), st);
     if (!ok) {
-        fail(BC_E_NOMEM, "device allocation failed for a batch-width-%d workspace (n=%d)", K, n_vert);
+        fail(BC_E_NOMEM, "device allocation failed for a batch-width-%d workspace (n=%d, %d teams)", K, n_vert, nteams);
         return false;
     }
-    w->cap = cap;
-    w->hcap = hcap;
+    w->K = K;
+    w->ext = ext;
+    w->nteams = nteams;
+    w->lay = L;
     return true;
 }
 
-static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, int njobs, int capf, cudaStream_t st) {
-    return ws_ensure_dims(w, g->n, g->n_heavy, g->hchunk_total, K, ext, nbatch, njobs, capf, st);
+static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, int njobs, int capf, int nteams,
+                      cudaStream_t st) {
+    return ws_ensure_dims(w, g->n, g->n_heavy, g->hchunk_total, K, ext, nbatch, njobs, capf, nteams, st);
 }
 
-static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_options& o, bool ext) {
+static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_options& o, bool ext, int team_blocks) {
     KParams p;
     memset(&p, 0, sizeof p);
+    const TeamLayout& L = w->lay;
     p.n = g->n;
     p.n_nz = g->n_nz;
     p.n_heavy = g->n_heavy;
@@ -288,33 +311,36 @@ static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_optio
     p.adj = (const int*)g->adj.p;
     p.src = (const int*)w->src.p;
     p.nbatch = nbatch;
-    p.V = (uint32_t*)w->V.p;
-    for (int i = 0; i < 3; ++i) p.F[i] = (uint32_t*)w->F[i].p;
-    p.sig = (unsigned long long*)w->sig.p;
-    p.sig_e = (int*)w->sig_e.p;
-    p.rho = (double*)w->rho.p;
-    p.rho_e = (int*)w->rho_e.p;
-    p.ent = (int*)w->ent.p;
-    p.emask = (uint32_t*)w->emask.p;
-    p.hent = (int*)w->hent.p;
-    p.hmask = (uint32_t*)w->hmask.p;
-    p.hpre = (int*)w->hpre.p;
-    p.cap = w->cap;
-    p.hcap = w->hcap;
+    p.V = (uint32_t*)w->at(L.V);
+    p.F[0] = (uint32_t*)w->at(L.F0);
+    p.F[1] = (uint32_t*)w->at(L.F1);
+    p.F[2] = (uint32_t*)w->at(L.F2);
+    p.sig = (unsigned long long*)w->at(L.sig);
+    p.rho = (double*)w->at(L.rho);
+    p.sig_e = ext ? (int*)w->at(L.sig_e) : nullptr;
+    p.rho_e = ext ? (int*)w->at(L.rho_e) : nullptr;
+    p.ent = (int*)w->at(L.ent);
+    p.emask = (uint32_t*)w->at(L.emask);
+    p.hent = (int*)w->at(L.hent);
+    p.hmask = (uint32_t*)w->at(L.hmask);
+    p.hpre = (int*)w->at(L.hpre);
+    p.cap = L.cap;
+    p.hcap = L.hcap;
     p.hcum = (const int*)g->hcum.p;
-    p.scr_v = (unsigned long long*)w->scr_v.p;
-    p.scr_e = (int*)w->scr_e.p;
-    p.scr_or = (uint32_t*)w->scr_or.p;
-    p.arr = (int*)w->arr.p;
-    p.stamp = (int*)w->stamp.p;
-    p.la.cnt = (int*)w->cnt.p;
-    p.la.hcnt = (int*)w->hcnt.p;
-    p.la.start = (int*)w->start.p;
-    p.la.hstart = (int*)w->hstart.p;
-    p.la.dsum = (long long*)w->dsum.p;
-    p.la.fulldeg = (long long*)w->fulldeg.p;
-    p.la.hchunks = (int*)w->hchunks.p;
-    p.ctl = (Ctl*)w->ctl.p;
+    p.scr_v = (unsigned long long*)w->at(L.scr_v);
+    p.scr_e = ext ? (int*)w->at(L.scr_e) : nullptr;
+    p.scr_or = (uint32_t*)w->at(L.scr_or);
+    p.arr = (int*)w->at(L.arr);
+    p.stamp = (int*)w->at(L.stamp);
+    p.la.cnt = (int*)w->at(L.cnt);
+    p.la.hcnt = (int*)w->at(L.hcnt);
+    p.la.start = (int*)w->at(L.start);
+    p.la.hstart = (int*)w->at(L.hstart);
+    p.la.dsum = (long long*)w->at(L.dsum);
+    p.la.fulldeg = (long long*)w->at(L.fulldeg);
+    p.la.hchunks = (int*)w->at(L.hchunks);
+    p.ctl = (Ctl*)w->at(L.ctl);
+    p.gctl = (Ctl*)w->gctl.p;
     p.batch_status = (int*)w->bstat.p;
     p.job_bc = (double* const*)w->jobptr.p;
     p.col_job = nullptr;
@@ -327,7 +353,21 @@ static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_optio
     p.group = o.group_vertices > 0 ? o.group_vertices : 32;
     p.trace = nullptr;
     p.trace_cap = 0;
+    p.team_blocks = team_blocks;
+    p.nteams = w->nteams;
+    p.team_bytes = (long long)L.bytes;
+    p.level_slots = L.level_slots;
     return p;
+}
+
+// Reset the launch-wide and per-team control blocks before a launch.
+static cudaError_t reset_controls(Workspace* w, int nbatch, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(w->gctl.p, 0, sizeof(Ctl), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->bstat.p, 0, sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1), st);
+    if (e == cudaSuccess)
+        e = launch_team_reset((Ctl*)w->at(w->lay.ctl), (int*)w->at(w->lay.arr), (long long)w->lay.bytes, w->nteams,
+                              w->lay.arr_ints, st);
+    return e;
 }
 
 static int choose_width(int n, int nsrc, int requested) {
@@ -347,7 +387,7 @@ static bc_status check_opts(const bc_options& o) {
         return fail(BC_E_INVALID_ARG, "batch_width must be 0, 1, 32, 64 or 128 (got %d)", o.batch_width);
     if (o.direction < 0 || o.direction > 2) return fail(BC_E_INVALID_ARG, "direction must be 0, 1 or 2");
     if (o.group_vertices < 0 || o.group_vertices > 32) return fail(BC_E_INVALID_ARG, "group_vertices must be in [0, 32]");
-    if (o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0)
+    if (o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0 || o.teams < 0)
         return fail(BC_E_INVALID_ARG, "negative option value");
     return BC_OK;
 }
@@ -366,6 +406,33 @@ static int grid_blocks(int K, bool ext, int blocks_per_sm, int share) {
     return blocks;
 }
 
+// Teams for a launch: blocks per team grow with the graph's arcs (about one
+// block per 2^19 arcs, so small graphs run one team per SM-sized group and the
+// largest graphs one team over the whole grid); no more teams than batches,
+// and the per-team arenas within a memory budget.
+static void choose_teams(long long m, int nbatch, int blocks, size_t team_bytes, int forced, int* nteams,
+                         int* team_blocks) {
+    int T;
+    if (forced > 0) {
+        T = forced;
+    } else {
+        long long per = (m >> 19) + 1;
+        if (per < 1) per = 1;
+        T = (int)std::max<long long>(1, blocks / std::min<long long>(per, blocks));
+    }
+    T = std::min(T, std::max(1, nbatch));
+    T = std::min(T, blocks);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        fr = (size_t)16 << 30;
+    }
+    const double budget = std::min(0.3 * (double)fr, 24e9);
+    while (T > 1 && (double)T * (double)team_bytes > budget) --T;
+    *nteams = T;
+    *team_blocks = blocks / T;
+}
+
 // One traversal run of a source list (original ids, device) on workspace w:
 // map sources, launch the persistent kernel over all batches, read the status.
 // job_bc buffers (relabelled, one per job) are accumulated, not cleared.
@@ -377,7 +444,7 @@ struct RunOut {
     Ctl ctl{};
 };
 
-static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int nsrc, int K, int blocks,
+static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int nsrc, int K, int team_blocks,
                           const bc_options& o, bool ext, const std::vector<double*>& job_bc,
                           const std::vector<int>* col_job, bool forward_only, cudaStream_t st, RunOut* ro) {
     const int nbatch = (nsrc + K - 1) / K;
@@ -397,10 +464,8 @@ static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int 
         return cuda_fail(e, "source check");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "source check");
     if (bad) return fail(BC_E_SOURCE, "a source id is outside [0, %d)", g->n);
-    if ((e = cudaMemsetAsync(w->ctl.p, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = cudaMemsetAsync(w->bstat.p, 0, sizeof(int) * nbatch, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = cudaMemsetAsync(w->arr.p, 0, w->arr.bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
-    KParams p = make_params(g, w, nbatch, o, ext);
+    if ((e = reset_controls(w, nbatch, st)) != cudaSuccess) return cuda_fail(e, "reset");
+    KParams p = make_params(g, w, nbatch, o, ext, team_blocks);
     p.forward_only = forward_only ? 1 : 0;
     if (col_job) p.col_job = (const int*)w->coljob.p;
     const int kTraceCap = 1 << 16;
@@ -413,7 +478,7 @@ static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int 
     cudaEventCreate(&ev[0]);
     cudaEventCreate(&ev[1]);
     cudaEventRecord(ev[0], st);
-    e = launch_batches(K, p, blocks, st);
+    e = launch_batches(K, p, team_blocks * w->nteams, st);
     cudaEventRecord(ev[1], st);
     if (e != cudaSuccess) {
         cudaEventDestroy(ev[0]);
@@ -421,7 +486,7 @@ static bc_status run_core(bc_graph* g, Workspace* w, const int* d_src_orig, int 
         return cuda_fail(e, "persistent kernel launch");
     }
     std::vector<int> bst(nbatch);
-    if ((e = cudaMemcpyAsync(&ro->ctl, w->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(&ro->ctl, w->gctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "status read");
     if ((e = cudaMemcpyAsync(bst.data(), w->bstat.p, sizeof(int) * nbatch, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
@@ -474,14 +539,18 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
     for (int attempt = 0; attempt < 4; ++attempt) {
         const int blocks = grid_blocks(K, ext, o.blocks_per_sm, blocks_share);
         if (blocks < 1) return fail(BC_E_CUDA, "persistent kernel cannot be resident (occupancy 0)");
-        s.grid_blocks = blocks;
-        if (!ws_ensure(w, g, K, ext, nbatch, (int)job_bc.size(), capf, st)) return BC_E_NOMEM;
+        int nteams = 1, team_blocks = blocks;
+        const TeamLayout L = team_layout(g->n, g->n_heavy, g->hchunk_total, K, ext, capf);
+        choose_teams(g->m, nbatch, blocks, L.bytes, o.teams, &nteams, &team_blocks);
+        s.grid_blocks = nteams * team_blocks;
+        s.teams = nteams;
+        if (!ws_ensure(w, g, K, ext, nbatch, (int)job_bc.size(), capf, nteams, st)) return BC_E_NOMEM;
         for (double* jb : job_bc) {
             cudaError_t e = cudaMemsetAsync(jb, 0, sizeof(double) * (size_t)(g->n > 0 ? g->n : 1), st);
             if (e != cudaSuccess) return cuda_fail(e, "memset");
         }
         RunOut ro;
-        bc_status r = run_core(g, w, d_src, nsrc, K, blocks, o, ext, job_bc, col_job, forward_only, st, &ro);
+        bc_status r = run_core(g, w, d_src, nsrc, K, team_blocks, o, ext, job_bc, col_job, forward_only, st, &ro);
         if (r != BC_OK) return r;
         s.kernel_launches += 2;
         s.kernel_ms += ro.kernel_ms;
@@ -728,16 +797,23 @@ static bc_status many_record(bc_many_plan* pl) {
         bc_graph* g = it.g;
         Workspace* w = pl->ws[it.K].get();
         const int blocks = grid_blocks(it.K, false, pl->opt.blocks_per_sm, 1);
-        KParams p = make_params(g, w, it.nbatch, pl->opt, false);
+        // this item's teams: as many as its batches and the workspace's slices allow
+        int nteams = 1, team_blocks = blocks;
+        choose_teams(g->m, it.nbatch, blocks, w->lay.bytes, pl->opt.teams, &nteams, &team_blocks);
+        nteams = std::min(nteams, w->nteams);
+        team_blocks = blocks / nteams;
+        const int saved = w->nteams;
+        w->nteams = nteams;
+        KParams p = make_params(g, w, it.nbatch, pl->opt, false, team_blocks);
         int* status = (int*)pl->dstatus.p + i;
-        if ((e = cudaMemsetAsync(w->ctl.p, 0, sizeof(Ctl), st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(w->bstat.p, 0, sizeof(int) * it.nbatch, st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(w->arr.p, 0, w->arr.bytes, st)) != cudaSuccess ||
+        e = reset_controls(w, it.nbatch, st);
+        w->nteams = saved;
+        if (e != cudaSuccess ||
             (e = cudaMemsetAsync(w->bc.p, 0, sizeof(double) * (size_t)(g->n > 0 ? g->n : 1), st)) != cudaSuccess ||
             (e = launch_map_sources((const int*)pl->dsrc.p + it.src_off, (int)it.src.size(), (const int*)g->inv.p,
                                     g->n, it.K, (int*)w->src.p, it.nbatch, (int*)w->bad.p, st)) != cudaSuccess ||
-            (e = launch_batches(it.K, p, blocks, st)) != cudaSuccess ||
-            (e = launch_collect_status((const Ctl*)w->ctl.p, (const int*)w->bstat.p, it.nbatch, status, st)) !=
+            (e = launch_batches(it.K, p, team_blocks * nteams, st)) != cudaSuccess ||
+            (e = launch_collect_status((const Ctl*)w->gctl.p, (const int*)w->bstat.p, it.nbatch, status, st)) !=
                 cudaSuccess ||
             (e = launch_unpermute((const double*)w->bc.p, (const int*)g->inv.p, it.out, g->n, st)) != cudaSuccess) {
             r = cuda_fail(e, "recording the many-graph sequence");
@@ -978,7 +1054,7 @@ bc_status bc_debug_source(bc_graph* g, int32_t s, int32_t* level, double* sigma_
         std::vector<double*> jb{(double*)w->bc.p};
         r = run_jobs(g, w, (const int*)dsrc.p, 1, o, 1, jb, nullptr, true, st, nullptr, &K, &ext, &levels);
     }
-    KParams p = make_params(g, w, 1, o, ext);
+    KParams p = make_params(g, w, 1, o, ext, 1);
     if (r < 0) {
         buf_release(dsrc, st); buf_release(dlev, st); buf_release(dsig, st); buf_release(dsige, st);
         return r;
@@ -1018,7 +1094,7 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
     pl->opt = o;
     long long total_src = 0;
     // items, validated on the host; per-width dimensions
-    struct Dims { int n = 0, nh = 0, nb = 0; long long hc = 0; };
+    struct Dims { int n = 0, nh = 0, nb = 0, teams = 1; long long hc = 0; };
     std::map<int, Dims> dims;
     for (int i = 0; i < nitems; ++i) {
         const bc_item& x = items[i];
@@ -1043,6 +1119,13 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
         d.nh = std::max(d.nh, g->n_heavy);
         d.hc = std::max(d.hc, g->hchunk_total);
         d.nb = std::max(d.nb, it.nbatch);
+        {
+            const int blocks = grid_blocks(it.K, false, o.blocks_per_sm, 1);
+            int T = 1, B = blocks;
+            const TeamLayout L = team_layout(g->n, g->n_heavy, g->hchunk_total, it.K, false, cap_factor(it.K, 0));
+            choose_teams(g->m, it.nbatch, blocks, L.bytes, o.teams, &T, &B);
+            d.teams = std::max(d.teams, T);
+        }
         pl->items.push_back(std::move(it));
     }
     cudaError_t e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
@@ -1054,8 +1137,15 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
     };
     for (auto& kv : dims) {
         std::unique_ptr<Workspace> w(new Workspace());
+        // slices for the most teams any item of this width uses, each sized for the
+        // largest graph of the width (capped by the same memory budget)
+        const TeamLayout L = team_layout(kv.second.n, kv.second.nh, kv.second.hc, kv.first, false, cap_factor(kv.first, 0));
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        int T = kv.second.teams;
+        while (T > 1 && (double)T * (double)L.bytes > std::min(0.3 * (double)fr, 24e9)) --T;
         if (!ws_ensure_dims(w.get(), kv.second.n, kv.second.nh, kv.second.hc, kv.first, false, kv.second.nb, 1,
-                            cap_factor(kv.first, 0), st))
+                            cap_factor(kv.first, 0), T, st))
             return bail(BC_E_NOMEM);
         double* jb = (double*)w->bc.p;
         if ((e = cudaMemcpyAsync(w->jobptr.p, &jb, sizeof(double*), cudaMemcpyHostToDevice, st)) != cudaSuccess ||

@@ -31,7 +31,8 @@ struct Ctl {
     int push_levels;
     int last_levels;           // levels of the last batch (debug runs)
     int trace_n;               // pairs written to the trace
-    int pad[3];
+    unsigned int bc_next;      // global control: the next batch allowed to add into BC
+    int pad[2];
 };
 
 // Level bookkeeping, indexed by BFS level.
@@ -75,7 +76,8 @@ struct KParams {
     int* arr;                  // [n_heavy] chunk arrival counters (zero between phases)
     int* stamp;                // [n] push-claim stamps
     LevelArrays la;
-    Ctl* ctl;
+    Ctl* ctl;                  // this team's control block (barrier, work counters, batch flags)
+    Ctl* gctl;                 // launch-wide control block (errors, statistics, BC order, trace)
     int* batch_status;         // [nbatch]
     double* const* job_bc;     // [njobs] accumulated BC per job (relabelled ids, device pointers)
     const int* col_job;        // [nbatch][K] job of each column; null = every column is job 0
@@ -88,6 +90,14 @@ struct KParams {
     long long* trace;          // optional phase trace: (tag, globaltimer ns) pairs; null = off
     int trace_cap;             // pairs the trace buffer holds
     int group;                 // light rows per warp task (1..32)
+    // teams: gridDim.x = nteams * team_blocks; team t owns blocks [t*team_blocks, (t+1)*team_blocks)
+    // and the workspace slice at +t*team_bytes of every per-team array; batches go round-robin
+    int team_blocks;
+    int nteams;
+    int team;                  // set in the kernel's team view
+    int rank;                  // block index inside the team (team view)
+    long long team_bytes;
+    int level_slots;           // entries of each level array (>= levels + 3)
 };
 
 // Host-side launchers (bc_kernels.cu)
@@ -95,6 +105,7 @@ cudaError_t launch_batches(int K, const KParams& p, int blocks, cudaStream_t st)
 int max_coop_blocks(int K, bool ext, int* per_sm);
 cudaError_t launch_unpermute(const double* bc_rel, const int* inv, double* out, int n, cudaStream_t st);
 cudaError_t launch_collect_status(const Ctl* ctl, const int* bstat, int nbatch, int* out, cudaStream_t st);
+cudaError_t launch_team_reset(Ctl* ctl0, int* arr0, long long team_bytes, int nteams, int arr_ints, cudaStream_t st);
 cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, int n, int K, int* dst,
                                int nbatch, int* bad, cudaStream_t st);
 cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,

@@ -53,22 +53,31 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 
 // ------------------------------------------------------------------ barrier
+// Barrier over the blocks of one team (a plain block barrier for one-block
+// teams); errors are read from the launch-wide control block.
 struct GridTeam {
     Ctl* ctl;
+    Ctl* gctl;
+    int nblocks;
     long long budget;
 
     // Returns false when the launch has failed (timeout or a fatal error).
     __device__ bool sync() {
         __shared__ int s_bad;
         __syncthreads();
+        if (nblocks == 1) {
+            if (threadIdx.x == 0) s_bad = *(volatile int*)&gctl->err != 0;
+            __syncthreads();
+            return !s_bad;
+        }
         if (threadIdx.x == 0) {
             int bad = 0;
             volatile unsigned int* genp = &ctl->bar_gen;
-            volatile int* errp = &ctl->err;
+            volatile int* errp = &gctl->err;
             unsigned int g = *genp;
             __threadfence();
             unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-            if (arrived == gridDim.x - 1) {
+            if (arrived == (unsigned int)nblocks - 1) {
                 atomicExch(&ctl->bar_count, 0u);
                 __threadfence();
                 atomicAdd(&ctl->bar_gen, 1u);
@@ -76,7 +85,7 @@ struct GridTeam {
                 long long t0 = clock64();
                 while (*genp == g) {
                     if (*errp) { bad = 1; break; }
-                    if (clock64() - t0 > budget) { atomicOr(&ctl->err, ERR_TIMEOUT); bad = 1; break; }
+                    if (clock64() - t0 > budget) { atomicOr(&gctl->err, ERR_TIMEOUT); bad = 1; break; }
                     __nanosleep(32);
                 }
             }
@@ -91,26 +100,26 @@ struct GridTeam {
 
 // Phase trace: block 0 stamps the end of every grid-wide phase (after its barrier).
 __device__ __forceinline__ void trace_mark(const KParams& p, int kind, int level) {
-    if (p.trace == nullptr || blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (p.trace == nullptr || p.team != 0 || p.rank != 0 || threadIdx.x != 0) return;
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    const int i = p.ctl->trace_n;
+    const int i = p.gctl->trace_n;
     if (i < p.trace_cap) {
         p.trace[2 * i] = ((long long)kind << 24) | (long long)(level & 0xFFFFFF);
         p.trace[2 * i + 1] = (long long)t;
-        p.ctl->trace_n = i + 1;
+        p.gctl->trace_n = i + 1;
     }
 }
 
 // Work distribution inside a phase: a warp's first task is its global warp
 // index (no atomics while tasks are fewer than warps); later tasks come from a
 // per-phase counter.  Returns -1 when the phase has no task left for the warp.
-__device__ __forceinline__ long long next_task(unsigned int* ctr, long long total, bool& first) {
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+__device__ __forceinline__ long long next_task(const KParams& p, unsigned int* ctr, long long total, bool& first) {
+    const long long nw = ((long long)p.team_blocks * blockDim.x) >> 5;
     long long t;
     if (first) {
         first = false;
-        t = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5;
+        t = (((long long)p.rank * blockDim.x) + threadIdx.x) >> 5;
     } else {
         if (total <= nw) return -1;
         unsigned int i = 0;
@@ -563,7 +572,7 @@ __device__ __forceinline__ void flush_append(const KParams& p, int lev, WarpSmem
             for (int t = 0; t < W; ++t) m[t] = ws.am[lane][t];
             store_mask_full<W>(p.emask, pos, m);
         } else {
-            atomicOr(&p.ctl->err, ERR_CAPACITY);
+            atomicOr(&p.gctl->err, ERR_CAPACITY);
         }
     }
     __syncwarp();
@@ -579,7 +588,7 @@ __device__ __forceinline__ void heavy_append(const KParams& p, int lev, int w, l
         p.hent[pos] = w;
         store_mask_full<W>(p.hmask, pos, m);
     } else {
-        atomicOr(&p.ctl->err, ERR_CAPACITY);
+        atomicOr(&p.gctl->err, ERR_CAPACITY);
     }
 }
 
@@ -613,7 +622,7 @@ __device__ __forceinline__ void heavy_static_task(const KParams& p, int t, int& 
 // Exclusive chunk prefix of the heavy entries of a level (recomputed from the
 // row lengths, so it may run more than once per level).  Block 0 scans in tiles.
 __device__ void heavy_prefix(const KParams& p, int lev) {
-    if (blockIdx.x != 0) return;
+    if (p.rank != 0) return;
     __shared__ int wsum[kWarps];
     __shared__ int carry_s;
     const int lane = lane_id(), wid = warp_id();
@@ -645,7 +654,7 @@ __device__ void heavy_prefix(const KParams& p, int lev) {
     if (threadIdx.x == 0) {
         const int total = p.n_heavy > 0 ? p.hcum[p.n_heavy] : 0;
         if (carry_s > total) {  // impossible for consistent lists: refuse to schedule
-            atomicOr(&p.ctl->err, ERR_INTERNAL);
+            atomicOr(&p.gctl->err, ERR_INTERNAL);
             p.la.hchunks[lev] = 0;
         } else {
             p.la.hchunks[lev] = carry_s;
@@ -703,7 +712,7 @@ __device__ __forceinline__ unsigned int* wq(const KParams& p, int ph, int which)
     return &p.ctl->wq[(ph & 3) * 2 + which];
 }
 __device__ __forceinline__ void phase_prologue(const KParams& p, int ph) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (p.rank == 0 && threadIdx.x == 0) {
         p.ctl->wq[((ph + 2) & 3) * 2] = 0;
         p.ctl->wq[((ph + 2) & 3) * 2 + 1] = 0;
     }
@@ -713,8 +722,8 @@ __device__ __forceinline__ void phase_prologue(const KParams& p, int ph) {
 template <int W>
 __device__ void clear_level_masks(const KParams& p, uint32_t* F, int lev) {
     const long long s = p.la.start[lev], c = p.la.cnt[lev], hs = p.la.hstart[lev], hc = p.la.hcnt[lev];
-    const long long nthr = (long long)gridDim.x * blockDim.x;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)p.team_blocks * blockDim.x;
+    const long long tid = (long long)p.rank * blockDim.x + threadIdx.x;
     for (long long i = tid; i < (c + hc) * W; i += nthr) {
         const long long j = i / W;
         const int t = (int)(i % W);
@@ -753,7 +762,7 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
     // heavy rows: chunk tasks over the static prefix of heavy ids
     const int HC = p.n_heavy > 0 ? p.hcum[p.n_heavy] : 0;
     for (bool fst = true;;) {
-        const long long t0 = next_task(wq(p, ph, 0), HC, fst);
+        const long long t0 = next_task(p, wq(p, ph, 0), HC, fst);
         if (t0 < 0) break;
         int r, chunk;
         heavy_static_task(p, (int)t0, r, chunk);
@@ -787,7 +796,7 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
     const long long nlight = (long long)p.n_nz - p.n_heavy;
     const long long ngroups = (nlight + group - 1) / group;
     for (bool fst = true;;) {
-        const long long g0 = next_task(wq(p, ph, 1), ngroups, fst);
+        const long long g0 = next_task(p, wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const long long first = p.n_heavy + g0 * group;
         const int ng = (int)min((long long)group, (long long)p.n_nz - first);
@@ -898,7 +907,7 @@ __device__ void phase_push(const KParams& p, int it, int ph, WarpSmem<K, EXT>& w
                 if (light_claim) {
                     const long long pos = (long long)p.la.start[lev] + base0 + __popc(lb & ((1u << lane) - 1u));
                     if (pos < p.cap) p.ent[pos] = w;
-                    else atomicOr(&p.ctl->err, ERR_CAPACITY);
+                    else atomicOr(&p.gctl->err, ERR_CAPACITY);
                 }
             }
             if (heavy_claim) {
@@ -906,14 +915,14 @@ __device__ void phase_push(const KParams& p, int it, int ph, WarpSmem<K, EXT>& w
                 atomicAdd((unsigned long long*)&p.la.dsum[lev], (unsigned long long)deg);
                 const long long pos = (long long)p.la.hstart[lev] + i;
                 if (pos < p.hcap) p.hent[pos] = w;
-                else atomicOr(&p.ctl->err, ERR_CAPACITY);
+                else atomicOr(&p.gctl->err, ERR_CAPACITY);
             }
         }
     };
     // heavy frontier rows: chunk tasks
     const int HT = p.la.hcnt[it] > 0 ? p.la.hchunks[it] : 0;
     for (bool fst = true;;) {
-        const long long t0 = next_task(wq(p, ph, 0), HT, fst);
+        const long long t0 = next_task(p, wq(p, ph, 0), HT, fst);
         if (t0 < 0) break;
         int pos, chunk;
         heavy_list_task(p, it, (int)t0, pos, chunk);
@@ -932,7 +941,7 @@ __device__ void phase_push(const KParams& p, int it, int ph, WarpSmem<K, EXT>& w
     const int ls = p.la.start[it], lc = p.la.cnt[it];
     const long long ngroups = (lc + grp - 1) / grp;
     for (bool fst = true;;) {
-        const long long g0 = next_task(wq(p, ph, 1), ngroups, fst);
+        const long long g0 = next_task(p, wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const int first = (int)(g0 * grp);
         const int ng = min(grp, lc - first);
@@ -965,7 +974,7 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
     phase_prologue(p, ph);
     const int HT = p.la.hcnt[lev] > 0 ? p.la.hchunks[lev] : 0;
     for (bool fst = true;;) {
-        const long long t0 = next_task(wq(p, ph, 0), HT, fst);
+        const long long t0 = next_task(p, wq(p, ph, 0), HT, fst);
         if (t0 < 0) break;
         int pos, chunk;
         heavy_list_task(p, lev, (int)t0, pos, chunk);
@@ -988,7 +997,7 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
     const int ls = p.la.start[lev], lc = p.la.cnt[lev];
     const long long ngroups = (lc + group - 1) / group;
     for (bool fst = true;;) {
-        const long long g0 = next_task(wq(p, ph, 1), ngroups, fst);
+        const long long g0 = next_task(p, wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const int first = (int)(g0 * group);
         const int ng = min(group, lc - first);
@@ -1027,7 +1036,7 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
     phase_prologue(p, ph);
     const int HT = p.la.hcnt[l] > 0 ? p.la.hchunks[l] : 0;
     for (bool fst = true;;) {
-        const long long t0 = next_task(wq(p, ph, 0), HT, fst);
+        const long long t0 = next_task(p, wq(p, ph, 0), HT, fst);
         if (t0 < 0) break;
         int pos, chunk;
         heavy_list_task(p, l, (int)t0, pos, chunk);
@@ -1047,7 +1056,7 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
     const int ls = p.la.start[l], lc = p.la.cnt[l];
     const long long ngroups = (lc + group - 1) / group;
     for (bool fst = true;;) {
-        const long long g0 = next_task(wq(p, ph, 1), ngroups, fst);
+        const long long g0 = next_task(p, wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const int first = (int)(g0 * group);
         const int ng = min(group, lc - first);
@@ -1081,10 +1090,10 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
 template <int K>
 __device__ void phase_bc(const KParams& p, int b) {
     constexpr int W = Geo<K>::W;
-    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long nthr = (long long)p.team_blocks * blockDim.x;
     const int* src = p.src + (size_t)b * K;
     const int* cj = p.col_job ? p.col_job + (size_t)b * K : nullptr;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < p.n_nz; v += nthr) {
+    for (long long v = (long long)p.rank * blockDim.x + threadIdx.x; v < p.n_nz; v += nthr) {
         uint32_t vm[W];
         load_mask<W>(p.V, v, vm);
         if (!mask_any<W>(vm)) continue;
@@ -1106,13 +1115,42 @@ __device__ void phase_bc(const KParams& p, int b) {
     }
 }
 
+// ------------------------------------------------------------------ BC order across teams
+// Batch b may add into BC only after batch b-1 has: the team's first thread
+// waits (bounded) for the launch-wide turn counter, then the team proceeds.
+__device__ bool bc_turn_wait(const KParams& p, GridTeam& team, int b) {
+    if (p.nteams > 1 && p.rank == 0 && threadIdx.x == 0) {
+        volatile unsigned int* turn = &p.gctl->bc_next;
+        volatile int* errp = &p.gctl->err;
+        const long long t0 = clock64();
+        while (*turn != (unsigned int)b) {
+            if (*errp) break;
+            if (clock64() - t0 > p.budget) {
+                atomicOr(&p.gctl->err, ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    return team.sync();
+}
+
+// After the team barrier that follows its BC phase: hand the turn to batch b+1.
+__device__ __forceinline__ void bc_turn_pass(const KParams& p, int b) {
+    if (p.nteams > 1 && p.rank == 0 && threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&p.gctl->bc_next, (unsigned int)(b + 1));
+    }
+}
+
 // ------------------------------------------------------------------ one batch
 template <int K, bool EXT>
 __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, WarpSmem<K, EXT>& ws) {
     constexpr int W = Geo<K>::W;
     constexpr int G = Geo<K>::G;
-    const long long nthr = (long long)gridDim.x * blockDim.x;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)p.team_blocks * blockDim.x;
+    const long long tid = (long long)p.rank * blockDim.x + threadIdx.x;
     const int group = p.group < G ? p.group : G;
     uint32_t act[W];
     active_mask<K>(p, b, act);
@@ -1129,7 +1167,7 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
     if (!team.sync()) return false;
     trace_mark(p, TR_INIT, b);
     // init B: sources (block 0): level-0 entries, one per distinct source vertex
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (p.rank == 0 && threadIdx.x == 0) {
         const int* src = p.src + (size_t)b * K;
         for (int c = 0; c < K; ++c) {
             const int s = src[c];
@@ -1175,11 +1213,11 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
         if ((long long)p.la.start[it] + p.la.cnt[it] > p.cap || (long long)p.la.hstart[it] + p.la.hcnt[it] > p.hcap) {
             // the level lists overflowed their capacity: every block sees the same
             // counts and leaves; the host reruns the call with full capacity
-            if (tid == 0) atomicOr(&p.ctl->err, ERR_CAPACITY);
+            if (tid == 0) atomicOr(&p.gctl->err, ERR_CAPACITY);
             return false;
         }
-        if (it + 1 > kMaxLevel) {
-            if (tid == 0) atomicOr(&p.ctl->err, ERR_LIMIT);
+        if (it + 1 > kMaxLevel || it + 3 > p.level_slots) {
+            if (tid == 0) atomicOr(&p.gctl->err, ERR_LIMIT);
             return false;
         }
         full_arcs += p.la.fulldeg[it];
@@ -1196,10 +1234,10 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
             p.la.hstart[it + 1] = p.la.hstart[it] + p.la.hcnt[it];
         }
         if (tid == 0) {
-            if (pull) p.ctl->pull_levels++;
-            else p.ctl->push_levels++;
+            if (pull) atomicAdd(&p.gctl->pull_levels, 1);
+            else atomicAdd(&p.gctl->push_levels, 1);
         }
-        if (tid == 1 && it + 2 < kLevelSlots) {
+        if (tid == 1 && it + 2 < p.level_slots) {
             p.la.cnt[it + 2] = 0; p.la.hcnt[it + 2] = 0; p.la.dsum[it + 2] = 0; p.la.fulldeg[it + 2] = 0;
         }
         __syncthreads();
@@ -1228,14 +1266,18 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
     const int L = it - 1;  // deepest nonempty level
     if (!EXT && (*(volatile int*)&p.ctl->flags & BST_NEED_EXT)) {
         if (tid == 0) p.batch_status[b] = BST_NEED_EXT;
+        if (!bc_turn_wait(p, team, b)) return false;
+        bc_turn_pass(p, b);
         return team.sync();
     }
-    if (tid == 0 && L + 1 > p.ctl->max_levels) p.ctl->max_levels = L + 1;
+    if (tid == 0) atomicMax(&p.gctl->max_levels, L + 1);
     if (p.forward_only) {
         if (tid == 0) {
             p.batch_status[b] = BST_DONE | (p.ctl->flags & BST_INEXACT);
-            p.ctl->last_levels = L + 1;
+            p.gctl->last_levels = L + 1;
         }
+        if (!bc_turn_wait(p, team, b)) return false;
+        bc_turn_pass(p, b);
         return team.sync();
     }
     // the forward sweep leaves buffer L%3 = level L masks, the others zero
@@ -1249,22 +1291,67 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
         if (!team.sync()) return false;
         trace_mark(p, TR_BACK, l);
     }
+    // batches add into BC in batch order, whichever team ran them
+    if (!bc_turn_wait(p, team, b)) return false;
     phase_bc<K>(p, b);
     if (tid == 0) p.batch_status[b] = BST_DONE | (p.ctl->flags & BST_INEXACT);
     const bool ok = team.sync();
+    bc_turn_pass(p, b);
     trace_mark(p, TR_BC, b);
     return ok;
+}
+
+template <typename T>
+__device__ __forceinline__ void shift_ptr(T*& ptr, long long d) {
+    if (ptr) ptr = reinterpret_cast<T*>(reinterpret_cast<char*>(ptr) + d);
+}
+
+// The team view of the parameters: every per-team array moved to this team's slice.
+__device__ void make_team_view(KParams& t, const KParams& p) {
+    t = p;
+    t.team = blockIdx.x / p.team_blocks;
+    t.rank = blockIdx.x % p.team_blocks;
+    const long long d = (long long)t.team * p.team_bytes;
+    shift_ptr(t.V, d);
+    shift_ptr(t.F[0], d);
+    shift_ptr(t.F[1], d);
+    shift_ptr(t.F[2], d);
+    shift_ptr(t.sig, d);
+    shift_ptr(t.sig_e, d);
+    shift_ptr(t.rho, d);
+    shift_ptr(t.rho_e, d);
+    shift_ptr(t.ent, d);
+    shift_ptr(t.emask, d);
+    shift_ptr(t.hent, d);
+    shift_ptr(t.hmask, d);
+    shift_ptr(t.hpre, d);
+    shift_ptr(t.scr_v, d);
+    shift_ptr(t.scr_e, d);
+    shift_ptr(t.scr_or, d);
+    shift_ptr(t.arr, d);
+    shift_ptr(t.stamp, d);
+    shift_ptr(t.la.cnt, d);
+    shift_ptr(t.la.hcnt, d);
+    shift_ptr(t.la.start, d);
+    shift_ptr(t.la.hstart, d);
+    shift_ptr(t.la.dsum, d);
+    shift_ptr(t.la.fulldeg, d);
+    shift_ptr(t.la.hchunks, d);
+    shift_ptr(t.ctl, d);
 }
 
 template <int K, bool EXT>
 __global__ void __launch_bounds__(kThreads, 3) bc_persistent(KParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ KParams tv;
     WarpSmem<K, EXT>* wsm = reinterpret_cast<WarpSmem<K, EXT>*>(smem_raw);
-    GridTeam team{p.ctl, p.budget};
+    if (threadIdx.x == 0) make_team_view(tv, p);
+    __syncthreads();
+    GridTeam team{tv.ctl, tv.gctl, tv.team_blocks, tv.budget};
     int ph = 0;
     WarpSmem<K, EXT>& ws = wsm[warp_id()];
-    for (int b = 0; b < p.nbatch; ++b)
-        if (!run_batch<K, EXT>(p, b, team, ph, ws)) return;
+    for (int b = tv.team; b < tv.nbatch; b += tv.nteams)
+        if (!run_batch<K, EXT>(tv, b, team, ph, ws)) return;
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -1390,6 +1477,23 @@ int max_coop_blocks(int K, bool ext, int* per_sm) {
     }
     if (per_sm) *per_sm = nb;
     return nb * sms;
+}
+
+// Zero every team's control block and chunk arrival counters.
+__global__ void k_team_reset(char* ctl0, char* arr0, long long team_bytes, int nteams, int arr_ints) {
+    const int t = blockIdx.x;
+    if (t >= nteams) return;
+    int* c = reinterpret_cast<int*>(ctl0 + (long long)t * team_bytes);
+    for (int i = threadIdx.x; i < (int)(sizeof(Ctl) / sizeof(int)); i += blockDim.x) c[i] = 0;
+    int* a = reinterpret_cast<int*>(arr0 + (long long)t * team_bytes);
+    for (int i = threadIdx.x; i < arr_ints; i += blockDim.x) a[i] = 0;
+}
+
+cudaError_t launch_team_reset(Ctl* ctl0, int* arr0, long long team_bytes, int nteams, int arr_ints, cudaStream_t st) {
+    if (nteams <= 0) return cudaSuccess;
+    k_team_reset<<<nteams, 256, 0, st>>>(reinterpret_cast<char*>(ctl0), reinterpret_cast<char*>(arr0), team_bytes,
+                                         nteams, arr_ints);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_collect_status(const Ctl* ctl, const int* bstat, int nbatch, int* out, cudaStream_t st) {

@@ -210,6 +210,10 @@ extern "C" bc_status bc_compute_noalloc(const int32_t* offsets, const int32_t* i
     p.la.dsum = (long long*)(base + oDsum);
     p.la.fulldeg = (long long*)(base + oFull);
     p.ctl = (Ctl*)(base + oCtl);
+    p.gctl = p.ctl;  // one team: its control block is the launch-wide one
+    p.nteams = 1;
+    p.team_bytes = 0;
+    p.level_slots = kLevelSlots;
     p.batch_status = (int*)(base + oBst);
     p.job_bc = (double* const*)(base + oJob);
     p.col_job = nullptr;
@@ -231,6 +235,7 @@ extern "C" bc_status bc_compute_noalloc(const int32_t* offsets, const int32_t* i
         int per_sm = 0;
         const int blocks = max_coop_blocks(kNaK, ext != 0, &per_sm);
         if (blocks < 1) return na_fail(BC_E_CUDA, "persistent kernel cannot be resident");
+        p.team_blocks = blocks;
         bool need_ext = false;
         inexact = false;
         for (long long s0 = 0; s0 < nsrc; s0 += kNaMaxBatches * kNaK) {

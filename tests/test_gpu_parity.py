@@ -148,7 +148,8 @@ def test_rmat12_bitwise_across_widths_and_directions(bc, rmat12):
     ref, _, _ = gpu_bc(bc, g, src, batch_width=64)
     for kw in [dict(batch_width=1), dict(batch_width=32), dict(batch_width=128), dict(batch_width=64, direction=1),
                dict(batch_width=64, direction=2), dict(batch_width=64, group_vertices=1),
-               dict(batch_width=32, group_vertices=7, direction=2), dict(batch_width=1, group_vertices=3)]:
+               dict(batch_width=32, group_vertices=7, direction=2), dict(batch_width=1, group_vertices=3),
+               dict(batch_width=64, teams=1), dict(batch_width=32, teams=3), dict(batch_width=1, teams=7)]:
         got, _, _ = gpu_bc(bc, g, src, **kw)
         assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
 
@@ -187,6 +188,9 @@ def test_full_grid_extended_range(bc):
     g = bcgen.grid(150, 150, 0.0)
     src = np.array([0, 151, 150 * 75 + 75], np.int32)
     G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(np.concatenate([src] * 11), batch_width=1, teams=4)  # 33 batches over 4 teams
+    assert st == bc.BC_W_SIGMA_INEXACT
+    assert_bc_close(out.cpu().numpy(), 11 * oracle.bc_ld(g.off, g.adj, src).astype(np.float64))
     out, st = G.compute(src, batch_width=32)
     stats = G.stats()
     assert st == bc.BC_W_SIGMA_INEXACT and stats["ext_batches"] > 0
@@ -267,7 +271,7 @@ def test_heavy_rows_bitwise_across_forms(bc, heavy_graph):
     g, src, _ = heavy_graph
     ref, _, _ = gpu_bc(bc, g, src, batch_width=64)
     for kw in [dict(batch_width=1), dict(batch_width=128), dict(batch_width=32, direction=1),
-               dict(batch_width=128, direction=2)]:
+               dict(batch_width=128, direction=2), dict(batch_width=32, teams=5), dict(batch_width=64, teams=1)]:
         got, _, _ = gpu_bc(bc, g, src, **kw)
         assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
 
