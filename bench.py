@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--batch-width", type=int, default=0)
     ap.add_argument("--direction", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (req/s)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library heuristics)")
+    ap.add_argument("--rate", type=float, default=50.0, help="serve: Poisson arrival rate (req/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     return ap.parse_args()
 
@@ -239,6 +240,11 @@ def run_ours(a):
     out = torch.empty(g.n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     opts = dict(batch_width=a.batch_width, direction=a.direction)
+    tuned = None
+    if a.batch_width == 0 and not a.no_tune:
+        t_tune = time.perf_counter()
+        tuned = G.autotune(src)  # per size bucket; knobs left at 0 below come from it
+        tuned["seconds"] = round(time.perf_counter() - t_tune, 2)
 
     for _ in range(max(a.warmup, 0)):
         G.compute(d_src, out=out, **opts)
@@ -312,7 +318,8 @@ def run_ours(a):
         "data": "synthetic",
         "config": dict(desc, step="one bc_compute over all sources on the resident graph",
                        batch_width=K, batches=nb, levels=stats["max_levels"], pull_levels=stats["pull_levels"],
-                       push_levels=stats["push_levels"], ingest_s=round(ingest_s, 3),
+                       push_levels=stats["push_levels"], teams=stats["teams"], ingest_s=round(ingest_s, 3),
+                       autotuned=tuned,
                        l2="inputs larger than L2 (CSR and per-batch state are GBs, L2 126 MB)",
                        parallelism=f"dp{world} (sources sharded per rank)" if world > 1 else "single GPU",
                        statuses=sorted(int(x) for x in statuses)),

@@ -146,6 +146,20 @@ bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 bc_status bc_last_trace(const bc_graph* g, int64_t* out, int32_t cap, int32_t* count);
 
 /*
+ * Autotuner: measures the traversal on a sample of the given sources (host,
+ * original ids; up to 512) for batch widths 1/32/64/128, the pull threshold
+ * (alpha) and the light-row grouping, by coordinate descent, and records the
+ * fastest setting for the graph's size bucket (log2 n, log2 average degree,
+ * log2 max/average degree).  Later bc_compute / bc_compute_ex calls on graphs
+ * of that bucket use it for every knob left at 0.  No knob changes results.
+ * best / best_rate (source-arcs per second on the sample) may be NULL.
+ */
+bc_status bc_autotune(bc_graph* g, const int32_t* sources, int32_t nsrc, bc_stream_t stream, bc_options* best,
+                      double* best_rate);
+/* Load (save = 0) or write (save = 1) the tuned settings as a JSON file. */
+bc_status bc_tuning_cache(const char* path, int32_t save);
+
+/*
  * Many graphs in one recorded sequence: for each item, BC over its sources
  * (host array, original ids, copied at create) on its graph into its output
  * (device, n doubles).  bc_many_create groups the items by batch width,

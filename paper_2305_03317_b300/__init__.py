@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_debug_source": [P, i32, P, P, P],
         "bc_last_trace": [P, P, i32, P],
         "bc_compute_noalloc": [P, P, i32, i64, P, i32, P, P],
+        "bc_autotune": [P, P, i32, P, ctypes.POINTER(bc_options), ctypes.POINTER(ctypes.c_double)],
+        "bc_tuning_cache": [ctypes.c_char_p, i32],
         "bc_many_create": [ctypes.POINTER(bc_item), i32, ctypes.POINTER(bc_options), P, ctypes.POINTER(P)],
         "bc_many_run": [P, P, P],
         "bc_many_destroy": [P],
@@ -132,6 +134,11 @@ def _stream_handle(stream) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
     return stream.cuda_stream
+
+
+def tuning_cache(path: str, save: bool) -> None:
+    """Load or write the autotuner's settings (JSON)."""
+    _check(load().bc_tuning_cache(path.encode(), 1 if save else 0))
 
 
 def server_config(slots: int = 4, memory_budget: int = 0) -> None:
@@ -221,6 +228,16 @@ class Graph:
                                  _stream_handle(stream), ctypes.byref(opt))
         _check(s)
         return out, s
+
+    def autotune(self, sources, stream=None) -> dict:
+        """Tune this graph's size bucket on a sample of ``sources`` (host); returns the chosen knobs."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        best = bc_options()
+        rate = ctypes.c_double()
+        _check(load().bc_autotune(self._h, src.ctypes.data, int(src.size), _stream_handle(stream), ctypes.byref(best),
+                                  ctypes.byref(rate)))
+        return {"batch_width": best.batch_width, "alpha": best.alpha, "group_vertices": best.group_vertices,
+                "rate": rate.value}
 
     def stats(self) -> dict:
         st = bc_run_stats()

@@ -581,6 +581,52 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
     return fail(BC_E_CUDA, "internal: reruns did not settle");
 }
 
+// ------------------------------------------------------------------ autotuning
+// Tuned knobs per graph-size bucket: (log2 n, log2 average degree, log2 of
+// max/average degree).  None of the knobs changes results (every sum has a
+// fixed order), so a tuned setting only changes speed.
+struct TuneKey {
+    int ln, lavg, lskew;
+    bool operator<(const TuneKey& o) const {
+        if (ln != o.ln) return ln < o.ln;
+        if (lavg != o.lavg) return lavg < o.lavg;
+        return lskew < o.lskew;
+    }
+};
+struct TuneVal {
+    int K = 0, group = 0;
+    float alpha = 0.f;
+    double rate = 0.0;  // source-arcs per second measured on the sample
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune;
+
+static int ilog2(double x) {
+    int l = 0;
+    while (x >= 2.0 && l < 62) {
+        x *= 0.5;
+        ++l;
+    }
+    return l;
+}
+
+static TuneKey tune_key(const bc_graph* g) {
+    const double nz = g->n_nz > 0 ? (double)g->n_nz : 1.0;
+    const double avg = (double)g->m / nz > 1.0 ? (double)g->m / nz : 1.0;
+    return TuneKey{ilog2((double)(g->n > 0 ? g->n : 1)), ilog2(avg), ilog2((double)(g->max_deg > 0 ? g->max_deg : 1) / avg)};
+}
+
+// Fill unset knobs of o from the graph's bucket, when it has been tuned.
+static void apply_tuning(const bc_graph* g, int nsrc, bc_options& o) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(g));
+    if (it == g_tune.end()) return;
+    const TuneVal& v = it->second;
+    if (o.batch_width == 0 && v.K > 0 && (v.K == 1 || nsrc > v.K / 2)) o.batch_width = v.K;
+    if (o.alpha == 0.f && v.alpha > 0.f) o.alpha = v.alpha;
+    if (o.group_vertices == 0 && v.group > 0) o.group_vertices = v.group;
+}
+
 // ------------------------------------------------------------------ serving
 // Continuous batching: worker threads (one CUDA stream and one workspace each)
 // take queued jobs in arrival order as soon as a worker is free and the
@@ -679,7 +725,8 @@ void worker_main(int slot) {
         const int nsrc = (int)all.size();
         bc_options o;
         memset(&o, 0, sizeof o);
-        const int K = choose_width(g->n, nsrc, 0);
+        apply_tuning(g, nsrc, o);
+        const int K = choose_width(g->n, nsrc, o.batch_width);
         const int nbatch = (nsrc + K - 1) / K;
         std::vector<int> col_job((size_t)nbatch * K, 0);
         for (int i = 0; i < nbatch * K; ++i) col_job[i] = i < nsrc ? owner[i] : (int)batch.size() - 1;
@@ -962,6 +1009,7 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
     bc_status cs = check_opts(o);
     if (cs != BC_OK) return cs;
     cudaStream_t st = (cudaStream_t)stream;
+    apply_tuning(g, nsrc, o);
     std::lock_guard<std::mutex> lk(g->mu);
     g->last_stream = st;
     if (g->n == 0) return BC_OK;
@@ -1214,6 +1262,115 @@ bc_status bc_many_info(const bc_many_plan* pl, int32_t* items, int32_t* kernel_l
     if (!pl) return fail(BC_E_INVALID_ARG, "plan is NULL");
     if (items) *items = (int32_t)pl->items.size();
     if (kernel_launches) *kernel_launches = pl->launches;
+    return BC_OK;
+}
+
+bc_status bc_autotune(bc_graph* g, const int32_t* sources, int32_t nsrc, bc_stream_t stream, bc_options* best,
+                      double* best_rate) {
+    if (!g || nsrc <= 0 || !sources) return fail(BC_E_INVALID_ARG, "autotune needs a graph and host sources");
+    if (is_device_ptr(sources)) return fail(BC_E_INVALID_ARG, "autotune takes host sources");
+    for (int i = 0; i < nsrc; ++i)
+        if (sources[i] < 0 || sources[i] >= g->n) return fail(BC_E_SOURCE, "source %d outside [0, %d)", sources[i], g->n);
+    cudaStream_t st = (cudaStream_t)stream;
+    // sample: the whole list on small graphs (so that team parallelism is what
+    // the real call sees), a few wide batches on large ones
+    const int cap_s = g->m <= (1ll << 24) ? 8192 : 512;
+    const int S = nsrc < cap_s ? nsrc : cap_s;
+    DevBuf out;
+    if (!buf_ensure(out, sizeof(double) * (size_t)(g->n > 0 ? g->n : 1), st)) return fail(BC_E_NOMEM, "autotune buffer");
+    auto measure = [&](const bc_options& o, double* rate) -> bc_status {
+        bc_options q = o;  // every knob explicit, so an older tuned entry cannot leak in
+        if (q.alpha == 0.f) q.alpha = 14.f;
+        if (q.group_vertices == 0) q.group_vertices = 32;
+        bc_status r = bc_compute_ex(g, sources, S, (double*)out.p, stream, &q);  // warm (allocations)
+        if (r < 0) return r;
+        r = bc_compute_ex(g, sources, S, (double*)out.p, stream, &q);
+        if (r < 0) return r;
+        const double ms = g->last.kernel_ms > 0 ? g->last.kernel_ms : 1e-3;
+        *rate = (double)S * (double)g->m / (ms * 1e-3);
+        return BC_OK;
+    };
+    bc_options cur;
+    memset(&cur, 0, sizeof cur);
+    double cur_rate = -1.0;
+    // coordinate descent: width, then the pull threshold, then the grouping
+    std::vector<int> widths;
+    if (S <= 64) widths.push_back(1);
+    for (int K : {32, 64, 128})
+        if (K <= 2 * S) widths.push_back(K);
+    for (int K : widths) {
+        bc_options o = cur;
+        o.batch_width = K;
+        double rate = 0;
+        bc_status r = measure(o, &rate);
+        if (r < 0) {
+            buf_release(out, st);
+            return r;
+        }
+        if (rate > cur_rate) { cur_rate = rate; cur = o; }
+    }
+    const bc_options base = cur;
+    for (float alpha : {5.f, 40.f}) {
+        bc_options o = base;
+        o.alpha = alpha;
+        double rate = 0;
+        if (measure(o, &rate) == BC_OK && rate > cur_rate) { cur_rate = rate; cur = o; }
+    }
+    const bc_options base2 = cur;
+    for (int grp : {8, 16}) {
+        bc_options o = base2;
+        o.group_vertices = grp;
+        double rate = 0;
+        if (measure(o, &rate) == BC_OK && rate > cur_rate) { cur_rate = rate; cur = o; }
+    }
+    buf_release(out, st);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        TuneVal v;
+        v.K = cur.batch_width;
+        v.alpha = cur.alpha;
+        v.group = cur.group_vertices;
+        v.rate = cur_rate;
+        g_tune[tune_key(g)] = v;
+    }
+    if (best) *best = cur;
+    if (best_rate) *best_rate = cur_rate;
+    return BC_OK;
+}
+
+bc_status bc_tuning_cache(const char* path, int32_t save) {
+    if (!path) return fail(BC_E_INVALID_ARG, "path is NULL");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (save) {
+        FILE* f = fopen(path, "w");
+        if (!f) return fail(BC_E_INVALID_ARG, "cannot write %s", path);
+        fprintf(f, "{\"bc_tuning\": [\n");
+        size_t i = 0;
+        for (const auto& kv : g_tune) {
+            fprintf(f, "  {\"log2_n\": %d, \"log2_avg_degree\": %d, \"log2_skew\": %d, \"batch_width\": %d, "
+                       "\"alpha\": %.3f, \"group_vertices\": %d, \"rate\": %.6e}%s\n",
+                    kv.first.ln, kv.first.lavg, kv.first.lskew, kv.second.K, kv.second.alpha, kv.second.group,
+                    kv.second.rate, ++i < g_tune.size() ? "," : "");
+        }
+        fprintf(f, "]}\n");
+        fclose(f);
+        return BC_OK;
+    }
+    FILE* f = fopen(path, "r");
+    if (!f) return fail(BC_E_INVALID_ARG, "cannot read %s", path);
+    char line[512];
+    int loaded = 0;
+    while (fgets(line, sizeof line, f)) {
+        TuneKey k;
+        TuneVal v;
+        if (sscanf(line, " {\"log2_n\": %d, \"log2_avg_degree\": %d, \"log2_skew\": %d, \"batch_width\": %d, "
+                         "\"alpha\": %f, \"group_vertices\": %d, \"rate\": %lf",
+                   &k.ln, &k.lavg, &k.lskew, &v.K, &v.alpha, &v.group, &v.rate) == 7) {
+            g_tune[k] = v;
+            ++loaded;
+        }
+    }
+    fclose(f);
     return BC_OK;
 }
 

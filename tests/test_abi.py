@@ -52,3 +52,17 @@ def test_product_path_has_no_oracle_import():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
                 assert "liboracle" not in src and "brandes.c" not in src, f
+
+
+def test_tuning_cache_roundtrip_without_gpu(tmp_path):
+    import paper_2305_03317_b300 as bc
+    p = tmp_path / "tune.json"
+    bc.tuning_cache(str(p), True)
+    text = p.read_text()
+    assert text.startswith('{"bc_tuning": [')
+    p.write_text('{"bc_tuning": [\n  {"log2_n": 12, "log2_avg_degree": 3, "log2_skew": 6, "batch_width": 64, '
+                 '"alpha": 14.000, "group_vertices": 16, "rate": 1.0e+10}\n]}\n')
+    bc.tuning_cache(str(p), False)
+    q = tmp_path / "tune2.json"
+    bc.tuning_cache(str(q), True)
+    assert '"batch_width": 64' in q.read_text() and '"group_vertices": 16' in q.read_text()

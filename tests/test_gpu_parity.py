@@ -315,3 +315,18 @@ def test_many_graphs_plan_matches_single_calls(bc):
             assert_bc_close(got, want)
     # the 70x70 full grid needs the extended form: its item is redone alone
     assert int(st[len(sizes)]) == bc.BC_W_SIGMA_INEXACT
+
+
+def test_autotune_changes_speed_not_results(bc, rmat12, tmp_path):
+    g, _ = rmat12
+    src = bcgen.sample_sources(g, 300, 4)
+    G = bc.Graph(g.off, g.adj)
+    before, _ = G.compute(src)
+    before = before.cpu().numpy().copy()
+    best = G.autotune(src)
+    assert best["batch_width"] in (1, 32, 64, 128) and best["rate"] > 0
+    after, _ = G.compute(src)  # knobs now come from the tuned bucket
+    assert G.stats()["batch_width"] == best["batch_width"]
+    assert np.array_equal(after.cpu().numpy().view(np.uint64), before.view(np.uint64))
+    bc.tuning_cache(str(tmp_path / "t.json"), True)
+    assert '"batch_width": %d' % best["batch_width"] in (tmp_path / "t.json").read_text()
