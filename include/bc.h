@@ -107,6 +107,9 @@ typedef struct {
     int32_t trace;           /* 1 = record a device timestamp at the end of every grid-wide phase */
     int32_t teams;           /* independent groups of blocks, each running its own batches (0 = auto:
                                 one block per ~2^19 arcs per team, at most one team per batch) */
+    int32_t dense_min;       /* batch widths >= 32: an arc matching at least this many columns of its row's
+                                batch is summed by the whole warp, one lane per column group, instead of one
+                                (arc, column) pair per lane (0 = auto); results do not depend on it */
 } bc_options;
 
 /*

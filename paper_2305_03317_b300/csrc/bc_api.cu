@@ -299,6 +299,11 @@ static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, in
     return ws_ensure_dims(w, g->n, g->n_heavy, g->hchunk_total, K, ext, nbatch, njobs, capf, nteams, st);
 }
 
+// Matched columns from which an arc is cheaper summed column-mapped (one warp
+// step per arc) than as compacted pairs; measured on R-MAT scale 22 (one
+// batch per width): 48 of 128 and 32 of 64; at 32 columns the two forms tie.
+static int default_dense_min(int K) { return K >= 128 ? 48 : 32; }
+
 static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_options& o, bool ext, int team_blocks) {
     KParams p;
     memset(&p, 0, sizeof p);
@@ -351,6 +356,7 @@ static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_optio
     p.ext = ext ? 1 : 0;
     p.forward_only = 0;
     p.group = o.group_vertices > 0 ? o.group_vertices : 32;
+    p.dense_min = o.dense_min > 0 ? o.dense_min : default_dense_min(w->K);
     p.trace = nullptr;
     p.trace_cap = 0;
     p.team_blocks = team_blocks;
@@ -387,7 +393,7 @@ static bc_status check_opts(const bc_options& o) {
         return fail(BC_E_INVALID_ARG, "batch_width must be 0, 1, 32, 64 or 128 (got %d)", o.batch_width);
     if (o.direction < 0 || o.direction > 2) return fail(BC_E_INVALID_ARG, "direction must be 0, 1 or 2");
     if (o.group_vertices < 0 || o.group_vertices > 32) return fail(BC_E_INVALID_ARG, "group_vertices must be in [0, 32]");
-    if (o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0 || o.teams < 0)
+    if (o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0 || o.teams < 0 || o.dense_min < 0)
         return fail(BC_E_INVALID_ARG, "negative option value");
     return BC_OK;
 }

@@ -90,6 +90,7 @@ struct KParams {
     long long* trace;          // optional phase trace: (tag, globaltimer ns) pairs; null = off
     int trace_cap;             // pairs the trace buffer holds
     int group;                 // light rows per warp task (1..32)
+    int dense_min;             // matched columns from which an arc is summed column-mapped (K >= 32)
     // teams: gridDim.x = nteams * team_blocks; team t owns blocks [t*team_blocks, (t+1)*team_blocks)
     // and the workspace slice at +t*team_bytes of every per-team array; batches go round-robin
     int team_blocks;

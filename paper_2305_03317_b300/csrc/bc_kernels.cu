@@ -40,6 +40,7 @@
 //
 // Grid-wide phases are separated by a software barrier whose wait is bounded
 // by a cycle budget; on expiry it raises ERR_TIMEOUT and every block returns.
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -170,6 +171,31 @@ __device__ __forceinline__ uint32_t lane_field(uint32_t word, int lane) {
     return (word >> ((W * lane) & 31)) & ((1u << W) - 1u);
 }
 
+// W consecutive 8-byte terms (16-byte aligned when W >= 2)
+template <int W>
+__device__ __forceinline__ void load_terms(const unsigned long long* p, unsigned long long (&x)[W]) {
+    if constexpr (W == 1) {
+        x[0] = p[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2) {
+            const ulonglong2 y = *reinterpret_cast<const ulonglong2*>(p + i);
+            x[i] = y.x;
+            x[i + 1] = y.y;
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void store_terms(unsigned long long* p, const unsigned long long (&x)[W]) {
+    if constexpr (W == 1) {
+        p[0] = x[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2) *reinterpret_cast<ulonglong2*>(p + i) = make_ulonglong2(x[i], x[i + 1]);
+    }
+}
+
 template <int W>
 __device__ __forceinline__ uint32_t pick(const uint32_t (&m)[W], int t) {
     uint32_t x = m[0];
@@ -243,11 +269,13 @@ struct Geo {
     static constexpr int W = K >= 32 ? K / 32 : 1;
     // owners per light task: the per-owner accumulator rows use G*K <= 512 slots
     static constexpr int G = K == 1 ? 32 : (K == 32 ? 16 : (K == 64 ? 8 : 4));
-    static constexpr int PCAP = 512;  // (arc, column) pairs buffered per round window
+    static constexpr int PCAP = 512;  // (arc, column) pairs expanded per window
 };
 
+// 16-byte aligned so that every warp's copy (consecutive in dynamic shared
+// memory) keeps its accumulator rows aligned for 16-byte vector accesses.
 template <int K, bool EXT>
-struct WarpSmem {
+struct __align__(16) WarpSmem {
     static constexpr int W = Geo<K>::W, G = Geo<K>::G;
     int ov[G];                    // owner vertex
     int obeg[G];                  // first arc index (into adj) of the owner's range
@@ -259,11 +287,19 @@ struct WarpSmem {
     int acce[EXT ? G * K : 1];    // exponents (extended form)
     int sv[32];                   // neighbour of each arc of the current step
     int so[32];                   // owner of each arc of the current step
+    uint32_t fw[32][W];           // matched columns of each arc of the current step
     uint32_t pr[Geo<K>::PCAP];    // expanded pairs: arc << 16 | column
     int av[32];                   // append staging (pull): vertex
     uint32_t am[32][W];           // append staging: mask
     long long adeg;               // append staging: degree sum
 };
+
+using WS128 = WarpSmem<128, false>;
+using WS64 = WarpSmem<64, false>;
+using WS32 = WarpSmem<32, false>;
+static_assert(sizeof(WS128) % 16 == 0 && offsetof(WS128, acc) % 16 == 0 && sizeof(WS64) % 16 == 0 &&
+              offsetof(WS64, acc) % 16 == 0 && sizeof(WS32) % 16 == 0 && offsetof(WS32, acc) % 16 == 0,
+              "column-mapped accumulator rows need 16-byte alignment");
 
 // Fill the owner table (lane i describes owner i < ng) and return the arc total.
 template <int K, bool EXT>
@@ -290,6 +326,39 @@ __device__ __forceinline__ int set_owners(WarpSmem<K, EXT>& ws, int ng, int v, i
     return __shfl_sync(FULL_MASK, incl, 31);
 }
 
+// ------------------------------------------------------------------ column-mapped arcs
+// The arcs of bit set `db` (indices into the current step, taken in increasing
+// order, i.e. CSR order) are summed with lanes mapped to columns: lane l adds
+// the terms of its columns [W*l, W*l+W) that the arc matches, reading them as
+// one vector load, into its own accumulator slots.  No two lanes share a slot,
+// so no atomics and no ordering rounds are needed.  Each lane's slots take
+// the arcs in order, so ordered (floating-point) sums stay in CSR order.
+template <int K, bool EXT, int DIR>
+__device__ __forceinline__ void dense_arcs(WarpSmem<K, EXT>& ws, unsigned int db,
+                                           const unsigned long long* __restrict__ termv, bool& carry) {
+    constexpr int W = Geo<K>::W;
+    static_assert(K >= 32 && !EXT, "column-mapped arcs need K >= 32 and the plain form");
+    const int lane = lane_id();
+    const int word = (W * lane) >> 5;
+    while (db) {
+        const int j = __ffs(db) - 1;
+        db &= db - 1;
+        const uint32_t b = lane_field<W>(ws.fw[j][word], lane);
+        if (b) {
+            unsigned long long x[W], r[W];
+            load_terms<W>(termv + (size_t)ws.sv[j] * K + W * lane, x);
+            unsigned long long* a = &ws.acc[ws.so[j] * K + W * lane];
+            load_terms<W>(a, r);
+            int e = 0;
+#pragma unroll
+            for (int i = 0; i < W; ++i)
+                if ((b >> i) & 1u) acc_add<false, DIR>(r[i], e, x[i], 0, carry);
+            store_terms<W>(a, r);
+        }
+    }
+    __syncwarp();
+}
+
 // ------------------------------------------------------------------ grouped, pair-compacted gather
 // Walks the arcs of ng owners (ranges in the owner table, T arcs in total) 32
 // at a time, in CSR order.  For each arc (owner o, neighbour v) the matched
@@ -305,7 +374,6 @@ __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>&
     constexpr int PCAP = Geo<K>::PCAP;
     constexpr bool ORDERED = EXT || DIR == BWD;
     const int lane = lane_id();
-    const unsigned int lt = (1u << lane) - 1u;
     for (int i = lane; i < ng * K; i += 32) {
         ws.acc[i] = 0ull;
         if constexpr (EXT) ws.acce[i] = 0;
@@ -342,6 +410,30 @@ __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>&
         }
         ws.sv[lane] = v;
         ws.so[lane] = o;
+        if constexpr (K >= 32 && !EXT) {
+            // arcs matching many columns go column-mapped.  Integer path counts
+            // split per arc; ordered sums take the whole step one way (every
+            // slot then still adds in CSR order).
+            bool dn;
+            if constexpr (DIR == FWD) {
+                dn = n >= p.dense_min;
+            } else {
+                int tot = n;
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) tot += __shfl_xor_sync(FULL_MASK, tot, s);
+                const int arcs = __popc(__ballot_sync(FULL_MASK, n > 0));
+                dn = n > 0 && tot >= arcs * p.dense_min;
+            }
+            const unsigned int db = __ballot_sync(FULL_MASK, dn);
+            if (db) {
+#pragma unroll
+                for (int t = 0; t < W; ++t) ws.fw[lane][t] = f[t];
+                __syncwarp();
+                dense_arcs<K, EXT, DIR>(ws, db, termv, carry);
+                if (dn) n = 0;
+                if (!__any_sync(FULL_MASK, n > 0)) continue;
+            }
+        }
         int incl = n;
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
@@ -397,14 +489,23 @@ __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>&
                 for (int i = 0; i < R; ++i) {
                     if (r0 + 32 * i >= cnt) break;
                     if constexpr (!ORDERED) {
+                        // integer path counts, order-free: two 32-bit shared atomics (the
+                        // low word's carry goes into the high word).  A term below 2^54
+                        // in sums of at most kChunk terms cannot carry out of 64 bits; a
+                        // larger term sends the batch to the extended form.
                         if (valid[i]) {
-                            const unsigned long long old = atomicAdd(&ws.acc[slot[i]], x[i]);
-                            carry |= (old + x[i] < old);
+                            unsigned int* a32 = reinterpret_cast<unsigned int*>(&ws.acc[slot[i]]);
+                            const unsigned int xl = (unsigned int)x[i], xh = (unsigned int)(x[i] >> 32);
+                            const unsigned int old = atomicAdd(a32, xl);
+                            const unsigned int cy = (old + xl < old) ? 1u : 0u;
+                            if (xh | cy) atomicAdd(a32 + 1, xh + cy);
+                            carry |= (x[i] >> 54) != 0ull;
                         }
                     } else {
+                        // ordered: lanes that share a slot add in lane (CSR) order
                         const int key = valid[i] ? slot[i] : -(lane + 1);
                         const unsigned int peers = __match_any_sync(FULL_MASK, key);
-                        const int rank = __popc(peers & lt);
+                        const int rank = __popc(peers & ((1u << lane) - 1u));
                         const int maxr = __reduce_max_sync(FULL_MASK, valid[i] ? rank : 0);
                         for (int k = 0; k <= maxr; ++k) {
                             if (valid[i] && rank == k) {
@@ -507,20 +608,23 @@ __device__ __forceinline__ void write_columns(const KParams& p, const WarpSmem<K
                 if constexpr (EXT) {
                     xe = ws.acce[slot];
                     p.sig_e[idx] = xe;
+                } else {
+                    p.rho[idx] = __drcp_rn((double)x);  // 1 / sigma, used by the reverse sweep
                 }
                 inexact |= (xe > 0 || x >= (1ull << 53));
             } else {
+                // rho = (1 + delta) / sigma = 1 / sigma + sum, with delta = sigma * sum
                 const double sd = (double)p.sig[idx];  // rounds only when the count is >= 2^53
                 const double sr = __longlong_as_double((long long)ws.acc[slot]);
                 double delta, rho;
                 if constexpr (EXT) {
                     const int se = p.sig_e[idx];
                     delta = scalbn(sd * sr, se + ws.acce[slot]);
-                    rho = (1.0 + delta) / sd;
+                    rho = __drcp_rn(sd) + scalbn(sr, se + ws.acce[slot]);
                     p.rho_e[idx] = -se;
                 } else {
                     delta = sd * sr;
-                    rho = (1.0 + delta) / sd;
+                    rho = p.rho[idx] + sr;
                 }
                 p.sig[idx] = (unsigned long long)__double_as_longlong(delta);
                 p.rho[idx] = rho;
