@@ -287,7 +287,7 @@ struct __align__(16) WarpSmem {
     int acce[EXT ? G * K : 1];    // exponents (extended form)
     int sv[32];                   // neighbour of each arc of the current step
     int so[32];                   // owner of each arc of the current step
-    uint32_t fw[32][W];           // matched columns of each arc of the current step
+    uint32_t fw[32][W];           // matched columns of each arc of the step; slot tags in the rounds
     uint32_t pr[Geo<K>::PCAP];    // expanded pairs: arc << 16 | column
     int av[32];                   // append staging (pull): vertex
     uint32_t am[32][W];           // append staging: mask
@@ -359,6 +359,154 @@ __device__ __forceinline__ void dense_arcs(WarpSmem<K, EXT>& ws, unsigned int db
     __syncwarp();
 }
 
+// One 32-arc step of group_gather: arc `lane` of the step has owner o,
+// neighbour v and matched columns f (n of them).
+template <int K, bool EXT, int DIR>
+__device__ __forceinline__ void gather_step(const KParams& p, WarpSmem<K, EXT>& ws, int o, int v, int n,
+                                            uint32_t (&f)[Geo<K>::W], const unsigned long long* termv,
+                                            const int* terme, bool& carry) {
+    constexpr int W = Geo<K>::W;
+    constexpr int PCAP = Geo<K>::PCAP;
+    constexpr bool ORDERED = EXT || DIR == BWD;
+    const int lane = lane_id();
+    if (!__any_sync(FULL_MASK, n > 0)) return;
+
+    if (n > 0) {
+#pragma unroll
+        for (int t = 0; t < W; ++t)
+            if (f[t]) atomicOr(&ws.onm[o][t], f[t]);
+    }
+    ws.sv[lane] = v;
+    ws.so[lane] = o;
+    if constexpr (K >= 32 && !EXT) {
+        // arcs matching many columns go column-mapped.  Integer path counts
+        // split per arc; ordered sums take the whole step one way (every
+        // slot then still adds in CSR order).
+        bool dn;
+        if constexpr (DIR == FWD) {
+            dn = n >= p.dense_min;
+        } else {
+            int tot = n;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) tot += __shfl_xor_sync(FULL_MASK, tot, s);
+            const int arcs = __popc(__ballot_sync(FULL_MASK, n > 0));
+            dn = n > 0 && tot >= arcs * p.dense_min;
+        }
+        const unsigned int db = __ballot_sync(FULL_MASK, dn);
+        if (db) {
+#pragma unroll
+            for (int t = 0; t < W; ++t) ws.fw[lane][t] = f[t];
+            __syncwarp();
+            dense_arcs<K, EXT, DIR>(ws, db, termv, carry);
+            if (dn) n = 0;
+            if (!__any_sync(FULL_MASK, n > 0)) return;
+        }
+    }
+    int incl = n;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        int y = __shfl_up_sync(FULL_MASK, incl, s);
+        if (lane >= s) incl += y;
+    }
+    const int P = incl - n;
+    const int tot = __shfl_sync(FULL_MASK, incl, 31);
+    __syncwarp();
+    int j0 = 0, pb = 0;
+    while (pb < tot) {
+        // window: the arcs from j0 whose pairs fit in the buffer (always >= 1 arc)
+        const unsigned int inwin = __ballot_sync(FULL_MASK, lane >= j0 && incl - pb <= PCAP);
+        const int j1 = 32 - __clz(inwin);
+        const int pe = __shfl_sync(FULL_MASK, incl, j1 - 1);
+        if (lane >= j0 && lane < j1 && n > 0) {
+            int idx = P - pb;
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                uint32_t m = f[t];
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    ws.pr[idx++] = ((uint32_t)lane << 16) | (uint32_t)(t * 32 + b);
+                }
+            }
+        }
+        __syncwarp();
+        const int cnt = pe - pb;
+        constexpr int R = 4;  // rounds whose loads are in flight together
+        for (int r0 = 0; r0 < cnt; r0 += 32 * R) {
+            int slot[R];
+            unsigned long long x[R];
+            int xe[R];
+            bool valid[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int q = r0 + 32 * i + lane;
+                valid[i] = q < cnt;
+                slot[i] = 0;
+                x[i] = 0ull;
+                xe[i] = 0;
+                if (valid[i]) {
+                    const uint32_t e = ws.pr[q];
+                    const int j = (int)(e >> 16), c = (int)(e & 0xFFFFu);
+                    const size_t idx = (size_t)ws.sv[j] * K + c;
+                    slot[i] = ws.so[j] * K + c;
+                    x[i] = termv[idx];
+                    if constexpr (EXT) xe[i] = terme[idx];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (r0 + 32 * i >= cnt) break;
+                if constexpr (!ORDERED) {
+                    // integer path counts, order-free: two 32-bit shared atomics (the
+                    // low word's carry goes into the high word).  A term below 2^54
+                    // in sums of at most kChunk terms cannot carry out of 64 bits; a
+                    // larger term sends the batch to the extended form.
+                    if (valid[i]) {
+                        unsigned int* a32 = reinterpret_cast<unsigned int*>(&ws.acc[slot[i]]);
+                        const unsigned int xl = (unsigned int)x[i], xh = (unsigned int)(x[i] >> 32);
+                        const unsigned int old = atomicAdd(a32, xl);
+                        const unsigned int cy = (old + xl < old) ? 1u : 0u;
+                        if (xh | cy) atomicAdd(a32 + 1, xh + cy);
+                        carry |= (x[i] >> 54) != 0ull;
+                    }
+                } else {
+                    // ordered: lanes that share a slot add in lane (CSR) order.  A
+                    // cheap test first: every lane writes its id to a hashed tag of
+                    // its slot (the step's mask words are free during the rounds); if
+                    // each reads its own id back, no two lanes share a slot.
+                    constexpr int MK = 32 * W;
+                    uint32_t* tagv = &ws.fw[0][0];
+                    if (valid[i]) tagv[slot[i] & (MK - 1)] = (uint32_t)lane;
+                    __syncwarp();
+                    const bool clash = valid[i] && tagv[slot[i] & (MK - 1)] != (uint32_t)lane;
+                    __syncwarp();
+                    int rank = 0, maxr = 0;
+                    if (__any_sync(FULL_MASK, clash)) {
+                        const int key = valid[i] ? slot[i] : -(lane + 1);
+                        const unsigned int peers = __match_any_sync(FULL_MASK, key);
+                        rank = __popc(peers & ((1u << lane) - 1u));
+                        maxr = __reduce_max_sync(FULL_MASK, valid[i] ? rank : 0);
+                    }
+                    for (int k = 0; k <= maxr; ++k) {
+                        if (valid[i] && rank == k) {
+                            unsigned long long av = ws.acc[slot[i]];
+                            int ae = EXT ? ws.acce[slot[i]] : 0;
+                            acc_add<EXT, DIR>(av, ae, x[i], xe[i], carry);
+                            ws.acc[slot[i]] = av;
+                            if constexpr (EXT) ws.acce[slot[i]] = ae;
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        j0 = j1;
+        pb = pe;
+    }
+    __syncwarp();
+}
+
 // ------------------------------------------------------------------ grouped, pair-compacted gather
 // Walks the arcs of ng owners (ranges in the owner table, T arcs in total) 32
 // at a time, in CSR order.  For each arc (owner o, neighbour v) the matched
@@ -371,8 +519,6 @@ template <int K, bool EXT, int DIR>
 __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>& ws, int ng, int T,
                                              const uint32_t* __restrict__ Fm, bool& carry) {
     constexpr int W = Geo<K>::W;
-    constexpr int PCAP = Geo<K>::PCAP;
-    constexpr bool ORDERED = EXT || DIR == BWD;
     const int lane = lane_id();
     for (int i = lane; i < ng * K; i += 32) {
         ws.acc[i] = 0ull;
@@ -383,148 +529,43 @@ __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>&
     const unsigned long long* termv =
         DIR == FWD ? p.sig : reinterpret_cast<const unsigned long long*>(p.rho);
     const int* terme = DIR == FWD ? p.sig_e : p.rho_e;
-    for (int base = 0; base < T; base += 32) {
-        const int a = base + lane;
+    // Step pipeline (lane = arc): the neighbour ids are loaded two steps ahead
+    // and the frontier masks one step ahead, so a step's own loads are in
+    // flight while the previous steps are processed.
+    auto owner_of = [&](int a) {
         int o = 0;
 #pragma unroll
         for (int step = 16; step >= 1; step >>= 1)
             if (o + step < ng && ws.ostart[o + step] <= a) o += step;
-        int v = 0, n = 0;
+        return o;
+    };
+    auto nbr_of = [&](int a, int o) { return a < T ? __ldg(p.adj + ws.obeg[o] + (a - ws.ostart[o])) : 0; };
+    int o = owner_of(lane);
+    int v = nbr_of(lane, o);
+    uint32_t fr[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t) fr[t] = 0;
+    if (lane < T) load_mask<W>(Fm, v, fr);
+    int o1 = owner_of(lane + 32);
+    int v1 = nbr_of(lane + 32, o1);
+    for (int base = 0; base < T; base += 32) {
+        const int a = base + lane;
+        int n = 0;
         uint32_t f[W];
 #pragma unroll
-        for (int t = 0; t < W; ++t) f[t] = 0;
-        if (a < T) {
-            v = __ldg(p.adj + ws.obeg[o] + (a - ws.ostart[o]));
-            load_mask<W>(Fm, v, f);
-#pragma unroll
-            for (int t = 0; t < W; ++t) {
-                f[t] &= ws.owant[o][t];
-                n += __popc(f[t]);
-            }
+        for (int t = 0; t < W; ++t) {
+            f[t] = a < T ? fr[t] & ws.owant[o][t] : 0u;
+            n += __popc(f[t]);
         }
-        if (!__any_sync(FULL_MASK, n > 0)) continue;
-        if (n > 0) {
+        // next step's masks, the step after's neighbour ids
 #pragma unroll
-            for (int t = 0; t < W; ++t)
-                if (f[t]) atomicOr(&ws.onm[o][t], f[t]);
-        }
-        ws.sv[lane] = v;
-        ws.so[lane] = o;
-        if constexpr (K >= 32 && !EXT) {
-            // arcs matching many columns go column-mapped.  Integer path counts
-            // split per arc; ordered sums take the whole step one way (every
-            // slot then still adds in CSR order).
-            bool dn;
-            if constexpr (DIR == FWD) {
-                dn = n >= p.dense_min;
-            } else {
-                int tot = n;
-#pragma unroll
-                for (int s = 16; s > 0; s >>= 1) tot += __shfl_xor_sync(FULL_MASK, tot, s);
-                const int arcs = __popc(__ballot_sync(FULL_MASK, n > 0));
-                dn = n > 0 && tot >= arcs * p.dense_min;
-            }
-            const unsigned int db = __ballot_sync(FULL_MASK, dn);
-            if (db) {
-#pragma unroll
-                for (int t = 0; t < W; ++t) ws.fw[lane][t] = f[t];
-                __syncwarp();
-                dense_arcs<K, EXT, DIR>(ws, db, termv, carry);
-                if (dn) n = 0;
-                if (!__any_sync(FULL_MASK, n > 0)) continue;
-            }
-        }
-        int incl = n;
-#pragma unroll
-        for (int s = 1; s < 32; s <<= 1) {
-            int y = __shfl_up_sync(FULL_MASK, incl, s);
-            if (lane >= s) incl += y;
-        }
-        const int P = incl - n;
-        const int tot = __shfl_sync(FULL_MASK, incl, 31);
-        __syncwarp();
-        int j0 = 0, pb = 0;
-        while (pb < tot) {
-            // window: the arcs from j0 whose pairs fit in the buffer (always >= 1 arc)
-            const unsigned int inwin = __ballot_sync(FULL_MASK, lane >= j0 && incl - pb <= PCAP);
-            const int j1 = 32 - __clz(inwin);
-            const int pe = __shfl_sync(FULL_MASK, incl, j1 - 1);
-            if (lane >= j0 && lane < j1 && n > 0) {
-                int idx = P - pb;
-#pragma unroll
-                for (int t = 0; t < W; ++t) {
-                    uint32_t m = f[t];
-                    while (m) {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1;
-                        ws.pr[idx++] = ((uint32_t)lane << 16) | (uint32_t)(t * 32 + b);
-                    }
-                }
-            }
-            __syncwarp();
-            const int cnt = pe - pb;
-            constexpr int R = 4;  // rounds whose loads are in flight together
-            for (int r0 = 0; r0 < cnt; r0 += 32 * R) {
-                int slot[R];
-                unsigned long long x[R];
-                int xe[R];
-                bool valid[R];
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const int q = r0 + 32 * i + lane;
-                    valid[i] = q < cnt;
-                    slot[i] = 0;
-                    x[i] = 0ull;
-                    xe[i] = 0;
-                    if (valid[i]) {
-                        const uint32_t e = ws.pr[q];
-                        const int j = (int)(e >> 16), c = (int)(e & 0xFFFFu);
-                        const size_t idx = (size_t)ws.sv[j] * K + c;
-                        slot[i] = ws.so[j] * K + c;
-                        x[i] = termv[idx];
-                        if constexpr (EXT) xe[i] = terme[idx];
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    if (r0 + 32 * i >= cnt) break;
-                    if constexpr (!ORDERED) {
-                        // integer path counts, order-free: two 32-bit shared atomics (the
-                        // low word's carry goes into the high word).  A term below 2^54
-                        // in sums of at most kChunk terms cannot carry out of 64 bits; a
-                        // larger term sends the batch to the extended form.
-                        if (valid[i]) {
-                            unsigned int* a32 = reinterpret_cast<unsigned int*>(&ws.acc[slot[i]]);
-                            const unsigned int xl = (unsigned int)x[i], xh = (unsigned int)(x[i] >> 32);
-                            const unsigned int old = atomicAdd(a32, xl);
-                            const unsigned int cy = (old + xl < old) ? 1u : 0u;
-                            if (xh | cy) atomicAdd(a32 + 1, xh + cy);
-                            carry |= (x[i] >> 54) != 0ull;
-                        }
-                    } else {
-                        // ordered: lanes that share a slot add in lane (CSR) order
-                        const int key = valid[i] ? slot[i] : -(lane + 1);
-                        const unsigned int peers = __match_any_sync(FULL_MASK, key);
-                        const int rank = __popc(peers & ((1u << lane) - 1u));
-                        const int maxr = __reduce_max_sync(FULL_MASK, valid[i] ? rank : 0);
-                        for (int k = 0; k <= maxr; ++k) {
-                            if (valid[i] && rank == k) {
-                                unsigned long long av = ws.acc[slot[i]];
-                                int ae = EXT ? ws.acce[slot[i]] : 0;
-                                acc_add<EXT, DIR>(av, ae, x[i], xe[i], carry);
-                                ws.acc[slot[i]] = av;
-                                if constexpr (EXT) ws.acce[slot[i]] = ae;
-                            }
-                            __syncwarp();
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-            j0 = j1;
-            pb = pe;
-        }
-        __syncwarp();
+        for (int t = 0; t < W; ++t) fr[t] = 0;
+        if (a + 32 < T) load_mask<W>(Fm, v1, fr);
+        const int o2 = owner_of(a + 64);
+        const int v2 = nbr_of(a + 64, o2);
+        const int ocur = o, vcur = v;
+        o = o1; v = v1; o1 = o2; v1 = v2;
+        gather_step<K, EXT, DIR>(p, ws, ocur, vcur, n, f, termv, terme, carry);
     }
     __syncwarp();
 }
