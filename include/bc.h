@@ -208,7 +208,10 @@ bc_status bc_wait(bc_job job, int64_t timeout_ms);
 bc_status bc_wait_ex(bc_job job, int64_t timeout_ms, double* latency_s);
 /* Serving facts: jobs admitted concurrently at peak, total completed. */
 bc_status bc_server_stats(int32_t* peak_concurrency, int64_t* completed);
-/* Slots (concurrent jobs) and device-memory budget for admission (bytes; 0 = 80% of free). */
+/* Slots (traversals run concurrently, each on 1/slots of the GPU; default 1, which measured
+ * best: jobs queued on the same graph are still packed into one traversal) and the device-memory
+ * budget for admission (bytes; 0 = 80% of free).  While the server runs the slot count may only
+ * grow; the call then waits until the traversals in flight have finished. */
 bc_status bc_server_config(int32_t slots, int64_t memory_budget);
 
 /*

@@ -142,7 +142,7 @@ def tuning_cache(path: str, save: bool) -> None:
     _check(load().bc_tuning_cache(path.encode(), 1 if save else 0))
 
 
-def server_config(slots: int = 4, memory_budget: int = 0) -> None:
+def server_config(slots: int = 1, memory_budget: int = 0) -> None:
     _check(load().bc_server_config(slots, memory_budget))
 
 

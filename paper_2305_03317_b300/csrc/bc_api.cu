@@ -215,8 +215,9 @@ struct bc_graph {
     long long hchunk_total = 0;
     DevBuf off, adj, perm, inv, hcum;
     AllocHook hook;
-    std::mutex mu;
+    std::mutex mu;                                 // bc_compute / plans: the per-width workspaces below
     std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
+    std::mutex state_mu;                           // the lazily set facts below (concurrent serving runs)
     bool sticky_ext = false;
     std::map<int, int> sticky_cap;                 // entry capacity factor that sufficed, by width
     bc_run_stats last{};
@@ -238,6 +239,7 @@ static bool is_device_ptr(const void* p) {
 // in new ids, so the heavy rows are a prefix found by binary search; the
 // prefix of chunk counts is built on the host from their offsets.
 static bc_status ensure_heavy(bc_graph* g, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g->state_mu);
     if (g->n_heavy >= 0) return BC_OK;
     int lo = 0, hi = g->n_nz;  // first r with deg(r) <= kChunk
     const int* off = (const int*)g->off.p;
@@ -537,8 +539,13 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
     const int nbatch = (nsrc + K - 1) / K;
     bc_status err = ensure_heavy(g, st);
     if (err != BC_OK) return err;
-    bool ext = g->sticky_ext;
-    int capf = cap_factor(K, g->sticky_cap.count(K) ? g->sticky_cap[K] : 0);
+    bool ext;
+    int capf;
+    {
+        std::lock_guard<std::mutex> lk(g->state_mu);
+        ext = g->sticky_ext;
+        capf = cap_factor(K, g->sticky_cap.count(K) ? g->sticky_cap[K] : 0);
+    }
     bc_run_stats s{};
     s.batch_width = K;
     s.batches = nbatch;
@@ -566,14 +573,20 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
         if (ro.capacity) {
             if (capf >= K) return fail(BC_E_CUDA, "internal: level-list capacity exceeded at the bound");
             capf = K;
-            g->sticky_cap[K] = K;
+            {
+                std::lock_guard<std::mutex> lk(g->state_mu);
+                g->sticky_cap[K] = K;
+            }
             continue;
         }
         if (ro.need_ext && !ext) {
             // rerun the whole call in the extended form, so that every source is
             // accumulated in list order exactly as in a single pass
             ext = true;
-            g->sticky_ext = true;
+            {
+                std::lock_guard<std::mutex> lk(g->state_mu);
+                g->sticky_ext = true;
+            }
             continue;
         }
         if (ro.need_ext) return fail(BC_E_SIGMA_RANGE, "path count beyond the extended range");
@@ -656,7 +669,8 @@ struct Server {
     std::deque<std::shared_ptr<Job>> queue;
     std::map<bc_job, std::shared_ptr<Job>> jobs;
     std::vector<std::thread> workers;
-    int slots = 4;
+    int slots = 1;        // one full-GPU traversal at a time measured best (packing still mixes jobs)
+    bool paused = false;  // set while the slot count changes
     long long budget = 0;  // bytes; 0 = decided at start
     long long reserved = 0;
     int running = 0, peak = 0;
@@ -681,18 +695,30 @@ void worker_main(int slot) {
     for (;;) {
         std::vector<std::shared_ptr<Job>> batch;
         long long grow = 0;
+        int share = 1;  // this run takes 1/share of the GPU's persistent blocks
         {
             std::unique_lock<std::mutex> lk(S.mu);
             for (;;) {
+                if (S.paused || slot >= S.slots) {
+                    S.cv_work.wait(lk);
+                    continue;
+                }
                 // first admissible job in arrival order
                 size_t lead = S.queue.size();
                 for (size_t i = 0; i < S.queue.size(); ++i) {
                     const auto& j = S.queue[i];
                     const int K = choose_width(j->g->n, (int)j->src.size(), 0);
-                    const long long need =
-                        (long long)ws_need(j->g->n, K, j->g->n_heavy > 0 ? j->g->n_heavy : 0, j->g->hchunk_total,
-                                           j->g->sticky_ext, 64, 64, cap_factor(K, 0)) +
-                        (long long)sizeof(double) * j->g->n * 64;
+                    int nh;
+                    long long hc;
+                    bool sext;
+                    {
+                        std::lock_guard<std::mutex> glk(j->g->state_mu);
+                        nh = j->g->n_heavy > 0 ? j->g->n_heavy : 0;
+                        hc = j->g->hchunk_total;
+                        sext = j->g->sticky_ext;
+                    }
+                    const long long need = (long long)ws_need(j->g->n, K, nh, hc, sext, 64, 64, cap_factor(K, 0)) +
+                                           (long long)sizeof(double) * j->g->n * 64;
                     grow = need > my_reserved ? need - my_reserved : 0;
                     if (S.reserved + grow <= S.budget || S.running == 0) { lead = i; break; }
                 }
@@ -713,6 +739,7 @@ void worker_main(int slot) {
                     }
                     S.reserved += grow;
                     my_reserved += grow;
+                    share = S.slots;
                     S.running++;
                     if (S.running > S.peak) S.peak = S.running;
                     break;
@@ -748,9 +775,8 @@ void worker_main(int slot) {
         }
         std::vector<double*> jb;
         for (size_t j = 0; j < batch.size(); ++j) jb.push_back((double*)jobbufs.p + nn * j);
-        if (r == BC_OK) {
-            std::lock_guard<std::mutex> glk(g->mu);
-            r = run_jobs(g, &ws, (const int*)dsrc.p, nsrc, o, S.slots, jb, &col_job, false, st, nullptr, nullptr,
+        if (r == BC_OK) {  // runs on the same graph proceed concurrently (own workspace and stream)
+            r = run_jobs(g, &ws, (const int*)dsrc.p, nsrc, o, share, jb, &col_job, false, st, nullptr, nullptr,
                          nullptr, nullptr);
         }
         if (r >= 0) {
@@ -777,7 +803,6 @@ void worker_main(int slot) {
         }
         S.cv_done.notify_all();
         S.cv_work.notify_all();
-        (void)slot;
     }
 }
 
@@ -1384,10 +1409,27 @@ bc_status bc_server_config(int32_t slots, int64_t memory_budget) {
     if (slots < 1 || slots > 64 || memory_budget < 0)
         return fail(BC_E_INVALID_ARG, "slots must be in [1, 64] and the budget >= 0");
     Server& S = server();
-    std::lock_guard<std::mutex> lk(S.mu);
-    if (S.started) return fail(BC_E_INVALID_ARG, "the server is already running; configure before the first submit");
+    std::unique_lock<std::mutex> lk(S.mu);
+    if (!S.started) {
+        S.slots = slots;
+        S.budget = memory_budget;
+        return BC_OK;
+    }
+    // running: the slot count may grow.  New jobs wait until every traversal
+    // in flight has finished, so runs sized for different shares of the GPU
+    // never have to be co-resident.
+    if (slots < S.slots) return fail(BC_E_INVALID_ARG, "the slot count can only grow while the server runs");
+    if (memory_budget > 0) S.budget = memory_budget;
+    if (slots == S.slots) return BC_OK;
+    S.paused = true;
+    S.cv_done.wait(lk, [&] { return S.running == 0; });
+    for (int i = S.slots; i < slots; ++i) {
+        S.workers.emplace_back(worker_main, i);
+        S.workers.back().detach();
+    }
     S.slots = slots;
-    S.budget = memory_budget;
+    S.paused = false;
+    S.cv_work.notify_all();
     return BC_OK;
 }
 

@@ -196,6 +196,11 @@ def test_full_grid_extended_range(bc):
     assert st == bc.BC_W_SIGMA_INEXACT and stats["ext_batches"] > 0
     want = oracle.bc_ld(g.off, g.adj, src).astype(np.float64)
     assert_bc_close(out.cpu().numpy(), want)
+    # the extended form keeps every column's sums in CSR order too: the plain
+    # per-source form and both batch widths agree bit for bit
+    for kw in (dict(batch_width=1), dict(batch_width=64), dict(batch_width=32, direction=1)):
+        other, _ = G.compute(src, **kw)
+        assert np.array_equal(other.cpu().numpy().view(np.uint64), out.cpu().numpy().view(np.uint64)), kw
     lev, mant, ex, _ = G.debug_source(0)
     olev, omant, oex, _ = oracle.source_sigma_split(g.off, g.adj, 0)
     assert np.array_equal(lev, olev)
@@ -239,12 +244,16 @@ def test_serving_alone_equals_mix(bc):
         return [o.cpu().numpy().copy() for o in outs]
 
     alone = [run([r])[0] for r in reqs]
-    mixed = run(reqs)
+    mixed = run(reqs)  # one slot: jobs of a graph packed into shared batches
     for (gi, src), a, b in zip(reqs, alone, mixed):
         assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
         assert_bc_close(b, oracle.bc(graphs[gi].off, graphs[gi].adj, src))
+    bc.server_config(3)  # three concurrent traversals, several on the same graph
+    mixed3 = run(reqs + reqs)
+    for a, b in zip(alone + alone, mixed3):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
     peak, done = bc.server_stats()
-    assert done >= 2 * len(reqs)
+    assert done >= 4 * len(reqs)
 
 
 # ----------------------------------------------------------------- rows above 1024 arcs (chunk tasks)
