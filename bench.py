@@ -212,6 +212,29 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ sharding (N GPUs, one rank each)
+def shard_sources(g, count, rank, world):
+    """Weak scaling: every rank traverses its own `count` sources (seed 1 + rank);
+    rank 0 of a 1-GPU run gets the single-GPU workload's list."""
+    import bcgen
+    return bcgen.sample_sources(g, count, 1 + (rank if world > 1 else 0))
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: the job finishes when its last rank does."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, nsrc_per_rank, m, ms):
+    """Whole-job throughput: every rank's sources times arcs over the slowest time."""
+    return world * nsrc_per_rank * m / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(a):
     import torch
@@ -232,8 +255,7 @@ def run_ours(a):
 
     g, src, desc = make_workload(a)
     if world > 1:  # weak scaling: every rank runs its own sources of the same size
-        import bcgen
-        src = bcgen.sample_sources(g, len(src), 1 + rank)
+        src = shard_sources(g, len(src), rank, world)
     t0 = time.perf_counter()
     G = bc.Graph(g.off, g.adj)
     torch.cuda.synchronize()
@@ -276,14 +298,10 @@ def run_ours(a):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     stats = G.stats()
     ms = total_ms / a.steps
-    value = world * len(src) * g.m / (ms / 1e3)
+    value = aggregate_rate(world, len(src), g.m, ms)
 
     # end to end: pinned host sources in, pinned host result out, through the public call
     h_src = torch.from_numpy(src).pin_memory()
