@@ -418,7 +418,6 @@ __device__ __forceinline__ void gather_step(const KParams& p, WarpSmem<K, EXT>& 
     constexpr bool ORDERED = EXT || DIR == BWD;
     const int lane = lane_id();
     if (!__any_sync(FULL_MASK, n > 0)) return;
-
     if (n > 0) {
 #pragma unroll
         for (int t = 0; t < W; ++t)
@@ -465,7 +464,27 @@ __device__ __forceinline__ void gather_step(const KParams& p, WarpSmem<K, EXT>& 
         const unsigned int inwin = __ballot_sync(FULL_MASK, lane >= j0 && incl - pb <= PCAP);
         const int j1 = 32 - __clz(inwin);
         const int pe = __shfl_sync(FULL_MASK, incl, j1 - 1);
-        if (lane >= j0 && lane < j1 && n > 0) {
+        // expansion: arcs with few pairs write their own (one lane, serially:
+        // cost = the largest such count); arcs with many can be written by the
+        // whole warp, lanes mapped to the bits of each mask word (cost = W per
+        // arc).  The split threshold is the cheapest of a few candidates.
+        const bool inw = lane >= j0 && lane < j1;
+        const int nw = inw ? n : 0;
+        int coop = 1 << 30;
+        if constexpr (K >= 32) {
+            int best = __reduce_max_sync(FULL_MASK, nw);
+#pragma unroll
+            for (int th = 64; th >= 8; th >>= 1) {
+                if (th > K) continue;
+                const int cost = __reduce_max_sync(FULL_MASK, nw < th ? nw : 0) +
+                                 W * __popc(__ballot_sync(FULL_MASK, nw >= th));
+                if (cost < best) {
+                    best = cost;
+                    coop = th;
+                }
+            }
+        }
+        if (inw && n > 0 && n < coop) {
             int idx = P - pb;
 #pragma unroll
             for (int t = 0; t < W; ++t) {
@@ -474,6 +493,21 @@ __device__ __forceinline__ void gather_step(const KParams& p, WarpSmem<K, EXT>& 
                     const int b = __ffs(m) - 1;
                     m &= m - 1;
                     ws.pr[idx++] = ((uint32_t)lane << 16) | (uint32_t)(t * 32 + b);
+                }
+            }
+        }
+        if constexpr (K >= 32) {
+            unsigned int bm = __ballot_sync(FULL_MASK, inw && n >= coop);
+            while (bm) {
+                const int j = __ffs(bm) - 1;
+                bm &= bm - 1;
+                int idx = __shfl_sync(FULL_MASK, P, j) - pb;
+#pragma unroll
+                for (int t = 0; t < W; ++t) {
+                    const uint32_t ft = __shfl_sync(FULL_MASK, f[t], j);
+                    if ((ft >> lane) & 1u)
+                        ws.pr[idx + __popc(ft & ((1u << lane) - 1u))] = ((uint32_t)j << 16) | (uint32_t)(t * 32 + lane);
+                    idx += __popc(ft);
                 }
             }
         }
