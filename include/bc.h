@@ -124,7 +124,24 @@ bc_status bc_compute(bc_graph* g, const int32_t* sources, int32_t nsrc, double* 
 bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc,
                         bc_stream_t stream, const bc_options* opt);
 
-/* Per-call facts of the last bc_compute / bc_compute_ex on this graph. */
+/*
+ * Multi-source BFS: the forward sweep of bc_compute alone (Section 2.3.2,
+ * iterateInBFS: levels and shortest-path counts) for each listed source, the
+ * same kernels and batching.  sources: nsrc original ids (host or device).
+ * level: device int32[nsrc][n], row i = distance from sources[i] (-1 when
+ * unreachable), original vertex ids; required when n > 0 and nsrc > 0.
+ * sigma: device double[nsrc][n] or NULL = number of shortest paths (exact below
+ * 2^53, rounded above and the call returns BC_W_SIGMA_INEXACT; +inf beyond the
+ * double range unless sigma_exp is given).  sigma_exp: device int32[nsrc][n] or
+ * NULL; when given, sigma holds a mantissa in [0.5, 1) and the count is
+ * sigma * 2^sigma_exp (0 and 0 when unreachable).  Overwrites the outputs; the
+ * call returns after they are final.  Counterpart of the paper's BFS
+ * construct as a standalone operation (no backward sweep, no BC).
+ */
+bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* level, double* sigma,
+                 int32_t* sigma_exp, bc_stream_t stream);
+
+/* Per-call facts of the last bc_compute / bc_compute_ex / bc_bfs on this graph. */
 typedef struct {
     int32_t batch_width;     /* width used */
     int32_t batches;         /* traversals run */

@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_graph_export": [P, P, P, P],
         "bc_compute": [P, P, i32, P, P],
         "bc_compute_ex": [P, P, i32, P, P, ctypes.POINTER(bc_options)],
+        "bc_bfs": [P, P, i32, P, P, P, P],
         "bc_last_run_stats": [P, ctypes.POINTER(bc_run_stats)],
         "bc_batch_submit": [P, P, i32, P, ctypes.POINTER(u64)],
         "bc_poll": [u64],
@@ -265,6 +266,23 @@ class Graph:
         adj = np.empty(max(self.m, 1), np.int32)
         _check(load().bc_graph_export(self._h, perm.ctypes.data, off.ctypes.data, adj.ctypes.data))
         return perm[: self.n], off, adj[: self.m]
+
+    def bfs(self, sources, sigma: bool = True, exponent: bool = False, stream=None):
+        """Multi-source BFS (bc_bfs): level int32[nsrc][n] (-1 unreachable) and, when asked,
+        path counts float64[nsrc][n] (with ``exponent``: mantissas and int32 exponents)."""
+        import torch
+        if isinstance(sources, np.ndarray):
+            sources = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc = int(sources.shape[0]) if isinstance(sources, np.ndarray) else int(sources.numel())
+        shape = (nsrc, self.n)
+        lev = torch.empty(shape, dtype=torch.int32, device="cuda")
+        sg = torch.empty(shape, dtype=torch.float64, device="cuda") if sigma else None
+        ex = torch.empty(shape, dtype=torch.int32, device="cuda") if (sigma and exponent) else None
+        s = load().bc_bfs(self._h, _ptr(sources) if nsrc else None, nsrc, _ptr(lev) if lev.numel() else None,
+                          _ptr(sg) if sg is not None and sg.numel() else None,
+                          _ptr(ex) if ex is not None and ex.numel() else None, _stream_handle(stream))
+        _check(s)
+        return lev, sg, ex, s
 
     def debug_source(self, s: int):
         """(level int32[n], sigma_mant float64[n], sigma_exp int32[n]) for one source."""

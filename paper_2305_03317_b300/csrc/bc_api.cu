@@ -1087,6 +1087,83 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
     return r;
 }
 
+bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* level, double* sigma, int32_t* sigma_exp,
+                 bc_stream_t stream) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    if (nsrc < 0) return fail(BC_E_INVALID_ARG, "nsrc < 0");
+    if (nsrc > 0 && !sources) return fail(BC_E_INVALID_ARG, "sources is NULL");
+    if (nsrc > 0 && g->n > 0 && !level) return fail(BC_E_INVALID_ARG, "level is NULL");
+    if (sigma_exp && !sigma) return fail(BC_E_INVALID_ARG, "sigma_exp needs sigma");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->last_stream = st;
+    if (g->n == 0 || nsrc == 0) return BC_OK;
+    const size_t n = (size_t)g->n, cells = n * (size_t)nsrc;
+    cudaError_t e = cudaMemsetAsync(level, 0xFF, sizeof(int32_t) * cells, st);  // -1: unreachable
+    if (e == cudaSuccess && sigma) e = cudaMemsetAsync(sigma, 0, sizeof(double) * cells, st);
+    if (e == cudaSuccess && sigma_exp) e = cudaMemsetAsync(sigma_exp, 0, sizeof(int32_t) * cells, st);
+    if (e != cudaSuccess) return cuda_fail(e, "clear outputs");
+    const int* d_src = sources;
+    DevBuf tmp;
+    if (!is_device_ptr(sources)) {
+        for (int i = 0; i < nsrc; ++i)
+            if (sources[i] < 0 || sources[i] >= g->n)
+                return fail(BC_E_SOURCE, "source %d (entry %d) is outside [0, %d)", sources[i], i, g->n);
+        if (!buf_ensure(tmp, sizeof(int) * (size_t)nsrc, st)) return fail(BC_E_NOMEM, "source buffer");
+        e = cudaMemcpyAsync(tmp.p, sources, sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            buf_release(tmp, st);
+            return cuda_fail(e, "source copy");
+        }
+        d_src = (const int*)tmp.p;
+    }
+    bc_options o;
+    memset(&o, 0, sizeof o);
+    apply_tuning(g, nsrc, o);
+    const int K = choose_width(g->n, nsrc, o.batch_width);
+    o.batch_width = K;
+    auto& slot = g->ws[K];
+    if (!slot) slot.reset(new Workspace());
+    Workspace* w = slot.get();
+    bc_status r = buf_ensure(w->bc, sizeof(double) * n, st) ? BC_OK : fail(BC_E_NOMEM, "buffers");
+    bool inexact = false;
+    bc_run_stats total{};
+    for (int b0 = 0; r >= 0 && b0 < nsrc; b0 += K) {
+        // one forward-only traversal per batch, then its rows of the output
+        const int cnt = nsrc - b0 < K ? nsrc - b0 : K;
+        std::vector<double*> jb{(double*)w->bc.p};
+        bc_run_stats stats{};
+        int kused = 0, levels = 0;
+        bool ext = false;
+        r = run_jobs(g, w, d_src + b0, cnt, o, 1, jb, nullptr, true, st, &stats, &kused, &ext, &levels);
+        if (r < 0) break;
+        inexact |= r == BC_W_SIGMA_INEXACT;
+        total.batch_width = kused;
+        total.batches += 1;
+        total.kernel_launches += stats.kernel_launches + 1;
+        total.kernel_ms += stats.kernel_ms;
+        total.max_levels = std::max(total.max_levels, levels);
+        total.pull_levels += stats.pull_levels;
+        total.push_levels += stats.push_levels;
+        total.ext_batches += ext ? 1 : 0;
+        total.grid_blocks = stats.grid_blocks;
+        total.teams = stats.teams;
+        KParams p = make_params(g, w, 1, o, ext, 1);
+        const size_t row0 = (size_t)b0 * n;
+        e = launch_bfs_extract(p, kused, levels, cnt, (const int*)g->perm.p, (long long)n, level + row0,
+                               sigma ? sigma + row0 : nullptr, sigma_exp ? sigma_exp + row0 : nullptr, st);
+        if (e != cudaSuccess) r = cuda_fail(e, "bfs extract");
+    }
+    if (r >= 0) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "bfs");
+        g->last = total;
+    }
+    buf_release(tmp, st);
+    if (r >= 0 && inexact) r = BC_W_SIGMA_INEXACT;
+    return r;
+}
+
 bc_status bc_compute(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream) {
     return bc_compute_ex(g, sources, nsrc, out_bc, stream, nullptr);
 }

@@ -1626,6 +1626,46 @@ __global__ void k_debug_extract(KParams p, int K, int levels, int* level_rel, un
     }
 }
 
+// Multi-source BFS output of one batch (after a forward-only traversal): for
+// every level list entry (vertex v, columns at that level) and each of its
+// columns c < ncols, row c gets level[c][perm[v]] = l and the path count
+// (a double, or a mantissa in [0.5, 1) with a separate exponent).
+__global__ void k_bfs_extract(KParams p, int K, int levels, int ncols, const int* __restrict__ perm, long long n,
+                              int* level_out, double* sig_out, int* exp_out) {
+    const int W = K >= 32 ? K / 32 : 1;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int l = 0; l < levels; ++l) {
+        const long long s = p.la.start[l], c = p.la.cnt[l], hs = p.la.hstart[l], hc = p.la.hcnt[l];
+        for (long long i = tid; i < c + hc; i += nthr) {
+            const int v = i < c ? p.ent[s + i] : p.hent[hs + (i - c)];
+            const uint32_t* m = i < c ? p.emask + (size_t)(s + i) * W : p.hmask + (size_t)(hs + (i - c)) * W;
+            const long long vo = perm[v];
+            for (int t = 0; t < W; ++t) {
+                uint32_t bits = m[t];
+                while (bits) {
+                    const int col = t * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (col >= ncols) continue;
+                    const size_t o = (size_t)col * (size_t)n + (size_t)vo;
+                    level_out[o] = l;
+                    if (sig_out) {
+                        const unsigned long long x = p.sig[(size_t)v * K + col];
+                        const int xe = p.ext ? p.sig_e[(size_t)v * K + col] : 0;
+                        if (exp_out) {
+                            int e = 0;
+                            sig_out[o] = frexp((double)x, &e);
+                            exp_out[o] = x ? e + xe : 0;
+                        } else {
+                            sig_out[o] = ldexp((double)x, xe);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 // One status word per launch: Ctl error bits << 8 | OR of the batch status
 // bits | 0x80 when a batch neither finished nor asked for the extended form.
 __global__ void k_collect_status(const Ctl* ctl, const int* bstat, int nbatch, int* out) {
@@ -1739,6 +1779,16 @@ cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, in
     int total = nbatch * K;
     if (total <= 0) return cudaSuccess;
     k_map_sources<<<(total + 255) / 256, 256, 0, st>>>(src_orig, nsrc, inv, n, K, dst, total, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, const int* perm, long long n,
+                               int* level_out, double* sig_out, int* exp_out, cudaStream_t st) {
+    if (n <= 0 || levels <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_bfs_extract<<<4 * (sms > 0 ? sms : 1), 256, 0, st>>>(p, K, levels, ncols, perm, n, level_out, sig_out, exp_out);
     return cudaGetLastError();
 }
 

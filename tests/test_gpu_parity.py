@@ -339,3 +339,37 @@ def test_autotune_changes_speed_not_results(bc, rmat12, tmp_path):
     assert np.array_equal(after.cpu().numpy().view(np.uint64), before.view(np.uint64))
     bc.tuning_cache(str(tmp_path / "t.json"), True)
     assert '"batch_width": %d' % best["batch_width"] in (tmp_path / "t.json").read_text()
+
+
+# ----------------------------------------------------------------- multi-source BFS (bc_bfs)
+
+def test_bfs_levels_and_sigma_match_oracle(bc):
+    g = bcgen.disjoint_union(bcgen.rmat(12, 8, 1), bcgen.path(5))  # unreachable parts and isolated vertices
+    G = bc.Graph(g.off, g.adj)
+    src = bcgen.sample_sources(g, 70, 3)  # a 64-wide batch and a ragged 6-source one
+    src = np.concatenate([src, src[:2]])  # repeated sources get their own rows
+    lev, sig, _, st = G.bfs(src)
+    assert st == bc.BC_OK
+    lev, sig = lev.cpu().numpy(), sig.cpu().numpy()
+    for i, s in enumerate(src):
+        d = oracle.source_detail(g.off, g.adj, int(s))
+        assert np.array_equal(lev[i], d["level"]), i
+        assert np.array_equal(sig[i], np.where(d["level"] >= 0, d["sigma"], 0.0)), i
+
+
+def test_bfs_extended_range_and_errors(bc):
+    g = bcgen.grid(150, 150, 0.0)
+    G = bc.Graph(g.off, g.adj)
+    src = np.array([0, 150 * 75 + 75], np.int32)
+    lev, mant, ex, st = G.bfs(src, exponent=True)
+    assert st == bc.BC_W_SIGMA_INEXACT
+    lev, mant, ex = lev.cpu().numpy(), mant.cpu().numpy(), ex.cpu().numpy()
+    for i, s in enumerate(src):
+        olev, omant, oex, _ = oracle.source_sigma_split(g.off, g.adj, int(s))
+        assert np.array_equal(lev[i], olev)
+        rel = np.abs(mant[i] * np.ldexp(1.0, ex[i] - oex) - omant) / omant
+        assert rel.max() <= 1e-12
+    with pytest.raises(bc.BCError):
+        G.bfs(np.array([g.n], np.int32))
+    lev0, _, _, st0 = G.bfs(np.zeros(0, np.int32))
+    assert st0 == bc.BC_OK and lev0.numel() == 0
