@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "rmat12", "grid", "serve", "rmat", "many"])
+    ap.add_argument("--workload", default="rmat22", choices=["rmat22", "rmat12", "grid", "serve", "rmat", "many", "bfs"])
     ap.add_argument("--graphs", type=int, default=200, help="many: graphs in the pool (the full config has 2000)")
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--ef", type=float, default=16)
@@ -252,6 +252,8 @@ def run_ours(a):
         return run_serve(a, bc, torch)
     if a.workload == "many":
         return run_many(a, bc, torch)
+    if a.workload == "bfs":
+        return run_bfs(a, bc, torch)
 
     g, src, desc = make_workload(a)
     if world > 1:  # weak scaling: every rank runs its own sources of the same size
@@ -411,6 +413,45 @@ def run_many(a, bc, torch):
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "what": "per replay of the whole pool"},
             "gpu_launches": info["kernel_launches"] * a.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_bfs(a, bc, torch):
+    """Multi-source BFS (bc_bfs: the forward sweep alone, levels and path counts per source)."""
+    import bcgen
+    g = bcgen.rmat(a.scale, a.ef, 1)
+    S = a.sources or 256
+    src = bcgen.sample_sources(g, S, 1)
+    G = bc.Graph(g.off, g.adj)
+    d_src = torch.from_numpy(src).cuda()
+    for _ in range(max(a.warmup, 0)):
+        G.bfs(d_src)
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lev, sig, _, st = G.bfs(d_src)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        del lev, sig
+    clk = clocks.stop()
+    s = G.stats()
+    t = float(np.mean(ms))
+    line = {"metric": METRIC, "value": len(src) * g.m / (t / 1e3), "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64 counts, int32 levels", "data": "synthetic",
+            "config": {"workload": f"msbfs_rmat{a.scale}_ef{a.ef:g}", "sources": int(len(src)), "n": g.n, "m": g.m,
+                       "step": "one bc_bfs: levels and path counts of every source into [sources][n] device rows",
+                       "batch_width": s["batch_width"], "batches": s["batches"], "kernel_ms": s["kernel_ms"],
+                       "output_bytes": int(len(src) * g.n * 12)},
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                           "what": "per bc_bfs call"},
+            "gpu_launches": s["kernel_launches"] * a.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
