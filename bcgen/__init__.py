@@ -56,6 +56,8 @@ def _L():
             lib.bcg_draw.argtypes = [u64, u64, u64]
             lib.bcg_unit.restype = f64
             lib.bcg_unit.argtypes = [u64, u64, u64]
+            lib.bcg_units.restype = None
+            lib.bcg_units.argtypes = [u64, u64, i64, i64, P]
             lib.bcg_rmat_edges.restype = None
             lib.bcg_rmat_edges.argtypes = [ctypes.c_int, i64, f64, f64, f64, u64, P, P]
             lib.bcg_random_perm.restype = None
@@ -82,7 +84,8 @@ def _p(a: np.ndarray):
 
 @dataclass
 class CSR:
-    """Undirected simple graph in CSR form: ``off`` (n+1) and ``adj`` (m), int32."""
+    """Simple graph in CSR form: ``off`` (n+1) and ``adj`` (m), int32.  Undirected
+    (symmetric) unless built by ``directed_csr`` / ``orient`` (then out-adjacency)."""
     off: np.ndarray
     adj: np.ndarray
     name: str = ""
@@ -105,6 +108,43 @@ def draw(seed: int, stream: int, t: int) -> int:
 
 def unit(seed: int, stream: int, t: int) -> float:
     return float(_L().bcg_unit(seed, stream, t))
+
+
+def units(seed: int, stream: int, t0: int, count: int) -> np.ndarray:
+    """unit(seed, stream, t0 + i) for i < count."""
+    out = np.empty(max(count, 1), np.float64)
+    _L().bcg_units(seed, stream, t0, count, _p(out))
+    return out[:count]
+
+
+def directed_csr(n: int, src, dst, name: str = "") -> CSR:
+    """Out-adjacency CSR of the arcs (src[i] -> dst[i]): rows sorted, duplicates and
+    self-loops dropped, no symmetrisation."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    keep = src != dst
+    key = np.unique(src[keep] * n + dst[keep])
+    s, d = key // n, key % n
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(off, s + 1, 1)
+    return CSR(np.cumsum(off).astype(np.int32), d.astype(np.int32), name)
+
+
+def orient(g: CSR, seed: int = 1, p_both: float = 0.25) -> CSR:
+    """A directed graph from an undirected one: each edge {u, v} (u < v, k-th in CSR
+    order) keeps both arcs when r < p_both, else u -> v when r < (1 + p_both) / 2,
+    else v -> u, with r = unit(seed, 9, k)."""
+    deg = np.diff(g.off.astype(np.int64))
+    row = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    col = g.adj.astype(np.int64)
+    sel = row < col
+    u, v = row[sel], col[sel]
+    r = units(seed, 9, 0, int(u.shape[0]))
+    both = r < p_both
+    uv = both | (r < (1.0 + p_both) / 2.0)
+    vu = both | ~uv
+    return directed_csr(g.n, np.concatenate([u[uv], v[vu]]), np.concatenate([v[uv], u[vu]]),
+                        f"orient({g.name}, {seed}, {p_both})")
 
 
 def edges_to_csr(n: int, u, v, name: str = "") -> CSR:

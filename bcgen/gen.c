@@ -47,6 +47,12 @@ static inline uint64_t below_k(uint64_t key, uint64_t t, uint64_t bound) {
 
 double bcg_unit(uint64_t seed, uint64_t stream, uint64_t t) { return unit_k(stream_key(seed, stream), t); }
 
+/* out[i] = unit(seed, stream, t0 + i) for i < count */
+void bcg_units(uint64_t seed, uint64_t stream, int64_t t0, int64_t count, double* out) {
+    const uint64_t key = stream_key(seed, stream);
+    for (int64_t i = 0; i < count; ++i) out[i] = unit_k(key, (uint64_t)(t0 + i));
+}
+
 /* R-MAT edge endpoints (raw: may contain self-loops and duplicates). */
 void bcg_rmat_edges(int scale, int64_t nedges, double a, double b, double c, uint64_t seed,
                     int32_t* u, int32_t* v) {

@@ -56,7 +56,8 @@ typedef enum {
 } bc_status;
 
 /* bc_graph_create flags */
-#define BC_UNDIRECTED 1u        /* required: the CSR must be symmetric */
+#define BC_UNDIRECTED 1u        /* the CSR is symmetric (checked); without it the CSR is the
+                                   out-adjacency of a directed graph (arc v -> w listed in row v) */
 #define BC_INPUT_ON_DEVICE 2u   /* offsets/indices are device pointers (else host pointers) */
 #define BC_SKIP_VALIDATION 4u   /* trust the input (self-loops/duplicates/asymmetry unchecked) */
 
@@ -77,6 +78,9 @@ bc_status bc_set_allocator(bc_alloc_fn alloc, bc_free_fn free_fn, void* ctx);
  * caller keeps ownership.  On the device the graph is validated, relabelled
  * by degree (descending, ties by original id) and stored with every row
  * sorted ascending.  Blocks until the graph is ready.  n may be 0.
+ * Directed graphs (no BC_UNDIRECTED): shortest paths follow arcs; the device
+ * also keeps the in-adjacency (the transpose), which the forward pull steps
+ * read; BC is the raw sum over the listed sources, as for undirected graphs.
  */
 bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_t n, int64_t m,
                           uint32_t flags, bc_stream_t stream, bc_graph** out);

@@ -13,7 +13,8 @@ Contents:
     DAG successors in reverse BFS order as (sigma_v/sigma_w)(1+delta_w), and
     BC the raw sum of delta over the listed sources (source excluded).
   * ``brute_force_bc`` -- exact rational BC from explicit enumeration of every
-    shortest path (tiny graphs only); the definition
+    shortest path (tiny graphs only; undirected or directed, paths follow arcs);
+    the definition
     BC(v) = sum_s sum_{t != s, v} sigma_st(v) / sigma_st written out.
   * ``relabel`` / ``validate`` -- the ingest rules (degree-descending stable
     relabelling; CSR validity) in their plain definitions.
@@ -191,14 +192,30 @@ def _bfs_dist(off, adj, s):
     return d
 
 
+def _reverse(off, adj):
+    """CSR of the reversed arcs (the same graph when it is undirected)."""
+    n = len(off) - 1
+    rows = [[] for _ in range(n)]
+    for v in range(n):
+        for e in range(off[v], off[v + 1]):
+            rows[adj[e]].append(v)
+    roff, radj = [0], []
+    for r in rows:
+        radj.extend(sorted(r))
+        roff.append(len(radj))
+    return roff, radj
+
+
 def shortest_paths(off, adj, s, t):
-    """Every shortest s-t path as a tuple of vertices (DFS over distance layers)."""
+    """Every shortest s-t path (following arcs) as a tuple of vertices: DFS over
+    the vertices w with d(s, w) + d(w, t) = d(s, t)."""
     off = [int(x) for x in off]
     adj = [int(x) for x in adj]
     ds = _bfs_dist(off, adj, s)
     if ds[t] < 0:
         return []
-    dt = _bfs_dist(off, adj, t)
+    roff, radj = _reverse(off, adj)
+    dt = _bfs_dist(roff, radj, t)  # distance to t: BFS from t over reversed arcs
     out = []
 
     def walk(path):

@@ -182,10 +182,10 @@ class Job:
 class Graph:
     """A graph resident on the device (relabelled CSR; see bc_graph_create)."""
 
-    def __init__(self, off, adj, validate: bool = True, stream=None):
+    def __init__(self, off, adj, validate: bool = True, stream=None, directed: bool = False):
         lib = load()
         self._h = ctypes.c_void_p()
-        flags = BC_UNDIRECTED | (0 if validate else BC_SKIP_VALIDATION)
+        flags = (0 if directed else BC_UNDIRECTED) | (0 if validate else BC_SKIP_VALIDATION)
         if isinstance(off, np.ndarray):
             off = np.ascontiguousarray(off, dtype=np.int32)
             adj = np.ascontiguousarray(adj, dtype=np.int32)

@@ -213,7 +213,9 @@ struct bc_graph {
     int n_nz = 0;
     int n_heavy = -1;      // rows with degree > kChunk (a prefix of the new ids); -1 = not yet counted
     long long hchunk_total = 0;
+    bool directed = false;
     DevBuf off, adj, perm, inv, hcum;
+    DevBuf ioff, iadj;  // directed: in-CSR for the pull steps
     AllocHook hook;
     std::mutex mu;                                 // bc_compute / plans: the per-width workspaces below
     std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
@@ -316,6 +318,8 @@ static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_optio
     p.m_nz = g->m;
     p.off = (const int*)g->off.p;
     p.adj = (const int*)g->adj.p;
+    p.ioff = g->directed ? (const int*)g->ioff.p : nullptr;
+    p.iadj = g->directed ? (const int*)g->iadj.p : nullptr;
     p.src = (const int*)w->src.p;
     p.nbatch = nbatch;
     p.V = (uint32_t*)w->at(L.V);
@@ -933,13 +937,13 @@ bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_
     if (!offsets || (m > 0 && !indices)) return fail(BC_E_INVALID_ARG, "offsets/indices NULL");
     if (flags & ~(BC_UNDIRECTED | BC_INPUT_ON_DEVICE | BC_SKIP_VALIDATION))
         return fail(BC_E_INVALID_ARG, "unknown flag bits 0x%x", flags);
-    if (!(flags & BC_UNDIRECTED))
-        return fail(BC_E_INVALID_ARG, "only undirected graphs are supported (set BC_UNDIRECTED)");
+    const bool directed = !(flags & BC_UNDIRECTED);
     if (m >= (1ll << 31) - 1 || n >= (1 << 30)) return fail(BC_E_LIMIT, "graph beyond int32 CSR limits");
     cudaStream_t st = (cudaStream_t)stream;
     std::unique_ptr<bc_graph> g(new bc_graph());
     g->n = n;
     g->m = m;
+    g->directed = directed;
     const int* d_off = offsets;
     const int* d_adj = indices;
     DevBuf in_off, in_adj;
@@ -967,7 +971,8 @@ bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_
         std::lock_guard<std::mutex> lk(g_alloc_mu);
         g->hook = g_hook;
     }
-    cudaError_t e = ingest(d_off, d_adj, n, m, !(flags & BC_SKIP_VALIDATION), st, ingest_alloc, ingest_free, &io, &oom);
+    cudaError_t e = ingest(d_off, d_adj, n, m, !(flags & BC_SKIP_VALIDATION), directed, st, ingest_alloc, ingest_free,
+                           &io, &oom);
     buf_release(in_off, st);
     buf_release(in_adj, st);
     auto adopt = [&](DevBuf& b, void* p, size_t bytes) { b.p = p; b.bytes = bytes; b.hook = g->hook; };
@@ -975,8 +980,11 @@ bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_
     adopt(g->adj, io.adj, sizeof(int) * (size_t)(m > 0 ? m : 1));
     adopt(g->perm, io.perm, sizeof(int) * (size_t)(n > 0 ? n : 1));
     adopt(g->inv, io.inv, sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (io.ioff) adopt(g->ioff, io.ioff, sizeof(int) * ((size_t)n + 1));
+    if (io.iadj) adopt(g->iadj, io.iadj, sizeof(int) * (size_t)(m > 0 ? m : 1));
     auto drop = [&]() {
         buf_release(g->off, st); buf_release(g->adj, st); buf_release(g->perm, st); buf_release(g->inv, st);
+        buf_release(g->ioff, st); buf_release(g->iadj, st);
     };
     if (oom) { drop(); return fail(BC_E_NOMEM, "device allocation failed during ingest"); }
     if (e != cudaSuccess) { drop(); return cuda_fail(e, "ingest"); }
@@ -988,7 +996,9 @@ bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_
         return fail(BC_E_INVALID_GRAPH, "invalid CSR: %s", why[io.reason]);
     }
     g->max_deg = io.max_deg;
-    g->n_nz = io.n_nz;
+    // rows are sorted by out-degree; in a directed graph a vertex without out-arcs
+    // can still be reached, so every vertex takes part in the pull steps
+    g->n_nz = directed ? n : io.n_nz;
     *out = g.release();
     return BC_OK;
 }
@@ -1001,6 +1011,8 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->off, st);
     buf_release(g->adj, st);
     buf_release(g->perm, st);
+    buf_release(g->ioff, st);
+    buf_release(g->iadj, st);
     buf_release(g->inv, st);
     cudaStreamSynchronize(st);
     delete g;

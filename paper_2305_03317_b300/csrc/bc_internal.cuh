@@ -52,6 +52,8 @@ struct KParams {
     long long m_nz;
     const int* off;
     const int* adj;
+    const int* ioff;           // directed graphs: in-CSR (transpose) for the pull steps; null = undirected
+    const int* iadj;
     // sources, relabelled, [nbatch][K]; -1 = unused column
     const int* src;
     int nbatch;
@@ -123,13 +125,15 @@ struct IngestOut {
     int* adj;       // [m] device
     int* perm;      // [n] new -> original
     int* inv;       // [n] original -> new
+    int* ioff;      // directed: [n+1] in-CSR (transpose of the relabelled CSR), else null
+    int* iadj;      // directed: [m]
     int max_deg;
     int n_nz;
     int reason;     // 0 ok, else 1 offsets, 2 index range, 3 self-loop, 4 duplicate, 5 asymmetric
 };
 typedef void* (*AllocFn)(size_t, cudaStream_t);
 typedef void (*FreeFn)(void*, cudaStream_t);
-cudaError_t ingest(const int* d_off_in, const int* d_adj_in, int n, long long m, bool validate,
+cudaError_t ingest(const int* d_off_in, const int* d_adj_in, int n, long long m, bool validate, bool directed,
                    cudaStream_t st, AllocFn alloc, FreeFn dfree, IngestOut* out, bool* oom);
 
 }  // namespace bcx

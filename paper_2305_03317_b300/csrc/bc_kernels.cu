@@ -599,7 +599,8 @@ __device__ __forceinline__ void gather_step(const KParams& p, WarpSmem<K, EXT>& 
 // (owner, column) add in lane order, which is CSR order.
 template <int K, bool EXT, int DIR>
 __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>& ws, int ng, int T,
-                                             const uint32_t* __restrict__ Fm, bool& carry) {
+                                             const uint32_t* __restrict__ Fm, const int* __restrict__ adjv,
+                                             bool& carry) {
     constexpr int W = Geo<K>::W;
     const int lane = lane_id();
     for (int i = lane; i < ng * K; i += 32) {
@@ -621,7 +622,7 @@ __device__ __forceinline__ void group_gather(const KParams& p, WarpSmem<K, EXT>&
             if (o + step < ng && ws.ostart[o + step] <= a) o += step;
         return o;
     };
-    auto nbr_of = [&](int a, int o) { return a < T ? __ldg(p.adj + ws.obeg[o] + (a - ws.ostart[o])) : 0; };
+    auto nbr_of = [&](int a, int o) { return a < T ? __ldg(adjv + ws.obeg[o] + (a - ws.ostart[o])) : 0; };
     int o = owner_of(lane);
     int v = nbr_of(lane, o);
     uint32_t fr[W];
@@ -986,8 +987,12 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
     const int lev = it + 1;
     bool carry = false;
     phase_prologue(p, ph);
+    // directed graphs pull over in-rows (the transpose), whole rows: no chunk tasks
+    const bool directed = p.ioff != nullptr;
+    const int* roff = directed ? p.ioff : p.off;
+    const int* radj = directed ? p.iadj : p.adj;
     // heavy rows: chunk tasks over the static prefix of heavy ids
-    const int HC = p.n_heavy > 0 ? p.hcum[p.n_heavy] : 0;
+    const int HC = (!directed && p.n_heavy > 0) ? p.hcum[p.n_heavy] : 0;
     for (bool fst = true;;) {
         const long long t0 = next_task(p, wq(p, ph, 0), HC, fst);
         if (t0 < 0) break;
@@ -1001,7 +1006,7 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
         const int rb = p.off[r], deg = p.off[r + 1] - rb, nch = nchunks(deg);
         const int cb = chunk * kChunk, len = min(kChunk, deg - cb);
         const int T = set_owners<K, EXT>(ws, 1, r, rb + cb, lane == 0 ? len : 0, -1, um);
-        group_gather<K, EXT, FWD>(p, ws, 1, T, Fc, carry);
+        group_gather<K, EXT, FWD>(p, ws, 1, T, Fc, p.adj, carry);
         uint32_t nm[W];
         if (heavy_partial<K, EXT, FWD>(p, ws, r, chunk, nch, nm) && mask_any<W>(nm)) {
             if (lane == 0) {
@@ -1020,12 +1025,13 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
     // light rows: groups of consecutive ids
     int acnt = 0;
     if (lane == 0) ws.adeg = 0;
-    const long long nlight = (long long)p.n_nz - p.n_heavy;
+    const long long lbase = directed ? 0 : p.n_heavy;  // first row of the grouped path
+    const long long nlight = (long long)p.n_nz - lbase;
     const long long ngroups = (nlight + group - 1) / group;
     for (bool fst = true;;) {
         const long long g0 = next_task(p, wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
-        const long long first = p.n_heavy + g0 * group;
+        const long long first = lbase + g0 * group;
         const int ng = (int)min((long long)group, (long long)p.n_nz - first);
         int v = 0, beg = 0, len = 0;
         uint32_t um[W];
@@ -1037,12 +1043,12 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
             load_mask<W>(p.V, v, vm);
 #pragma unroll
             for (int t = 0; t < W; ++t) um[t] = act[t] & ~vm[t];
-            beg = p.off[v];
-            len = mask_any<W>(um) ? p.off[v + 1] - beg : 0;
+            beg = roff[v];
+            len = mask_any<W>(um) ? roff[v + 1] - beg : 0;
         }
         if (!__any_sync(FULL_MASK, len > 0)) continue;
         const int T = set_owners<K, EXT>(ws, ng, v, beg, len, -1, um);
-        group_gather<K, EXT, FWD>(p, ws, ng, T, Fc, carry);
+        group_gather<K, EXT, FWD>(p, ws, ng, T, Fc, radj, carry);
         write_columns<K, EXT, FWD>(p, ws, ng, ws.onm);
         // owners reached in this level (lane o = owner o): masks, V, staged appends
         uint32_t nm[W];
@@ -1055,6 +1061,12 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
             if (found) {
                 store_mask_full<W>(Fn, w, nm);
                 mark_reached<W>(p, w, nm, lev, act);
+                // directed graphs pull every row here: rows heavy by out-degree still
+                // go to the heavy list (chunked push and reverse steps)
+                if (w < p.n_heavy) {
+                    heavy_append<W>(p, lev, w, p.off[w + 1] - p.off[w], nm);
+                    found = false;
+                }
             }
         }
         const unsigned int fb = __ballot_sync(FULL_MASK, found);
@@ -1199,7 +1211,12 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
     const int lev = it + 1;
     bool carry = false;
     phase_prologue(p, ph);
-    const int HT = p.la.hcnt[lev] > 0 ? p.la.hchunks[lev] : 0;
+    // directed graphs sum over in-rows (the transpose), whole rows: heavy entries
+    // (heavy by out-degree) join the grouped path below
+    const bool directed = p.ioff != nullptr;
+    const int* roff = directed ? p.ioff : p.off;
+    const int* radj = directed ? p.iadj : p.adj;
+    const int HT = (!directed && p.la.hcnt[lev] > 0) ? p.la.hchunks[lev] : 0;
     for (bool fst = true;;) {
         const long long t0 = next_task(p, wq(p, ph, 0), HT, fst);
         if (t0 < 0) break;
@@ -1211,7 +1228,7 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
         const int rb = p.off[w], deg = p.off[w + 1] - rb, nch = nchunks(deg);
         const int cb = chunk * kChunk, len = min(kChunk, deg - cb);
         const int T = set_owners<K, EXT>(ws, 1, w, rb + cb, lane == 0 ? len : 0, pos, nm);
-        group_gather<K, EXT, FWD>(p, ws, 1, T, Fc, carry);
+        group_gather<K, EXT, FWD>(p, ws, 1, T, Fc, p.adj, carry);
         uint32_t om[W];
         if (heavy_partial<K, EXT, FWD>(p, ws, w, chunk, nch, om)) {
             write_columns<K, EXT, FWD>(p, ws, 1, ws.owant);
@@ -1221,31 +1238,36 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
             }
         }
     }
-    const int ls = p.la.start[lev], lc = p.la.cnt[lev];
-    const long long ngroups = (lc + group - 1) / group;
+    const int ls = p.la.start[lev], lc = p.la.cnt[lev], hs = p.la.hstart[lev];
+    const int ltot = lc + (directed ? p.la.hcnt[lev] : 0);  // light entries, then (directed) heavy ones
+    const long long ngroups = (ltot + group - 1) / group;
     for (bool fst = true;;) {
         const long long g0 = next_task(p, wq(p, ph, 1), ngroups, fst);
         if (g0 < 0) break;
         const int first = (int)(g0 * group);
-        const int ng = min(group, lc - first);
-        int v = 0, beg = 0, len = 0;
+        const int ng = min(group, ltot - first);
+        int v = 0, beg = 0, len = 0, pos = 0;
         uint32_t nm[W];
 #pragma unroll
         for (int t = 0; t < W; ++t) nm[t] = 0;
         if (lane < ng) {
-            v = p.ent[ls + first + lane];
+            const int i = first + lane;
+            pos = i < lc ? ls + i : -(hs + (i - lc)) - 1;  // >= 0: light list, < 0: heavy list
+            v = i < lc ? p.ent[ls + i] : p.hent[hs + (i - lc)];
             load_mask<W>(Fn, v, nm);
-            beg = p.off[v];
-            len = p.off[v + 1] - beg;
+            beg = roff[v];
+            len = roff[v + 1] - beg;
         }
-        const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, nm);
-        group_gather<K, EXT, FWD>(p, ws, ng, T, Fc, carry);
+        const int T = set_owners<K, EXT>(ws, ng, v, beg, len, pos, nm);
+        group_gather<K, EXT, FWD>(p, ws, ng, T, Fc, radj, carry);
         write_columns<K, EXT, FWD>(p, ws, ng, ws.owant);
         if (lane < ng) {
             uint32_t want[W];
             read_mask_s<W>(ws.owant[lane], want);
             mark_reached<W>(p, ws.ov[lane], want, lev, act);
-            store_mask_full<W>(p.emask, ws.opos[lane], want);
+            const int q = ws.opos[lane];
+            if (q >= 0) store_mask_full<W>(p.emask, q, want);
+            else store_mask_full<W>(p.hmask, -q - 1, want);
         }
     }
     if (__any_sync(FULL_MASK, carry) && lane == 0) atomicOr(&p.ctl->flags, BST_NEED_EXT);
@@ -1273,7 +1295,7 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
         const int rb = p.off[v], deg = p.off[v + 1] - rb, nch = nchunks(deg);
         const int cb = chunk * kChunk, len = min(kChunk, deg - cb);
         const int T = set_owners<K, EXT>(ws, 1, v, rb + cb, lane == 0 ? len : 0, pos, mk);
-        group_gather<K, EXT, BWD>(p, ws, 1, T, Fd, carry);
+        group_gather<K, EXT, BWD>(p, ws, 1, T, Fd, p.adj, carry);
         uint32_t om[W];
         if (heavy_partial<K, EXT, BWD>(p, ws, v, chunk, nch, om)) {
             write_columns<K, EXT, BWD>(p, ws, 1, ws.owant);
@@ -1298,7 +1320,7 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
             len = p.off[v + 1] - beg;
         }
         const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, mk);
-        group_gather<K, EXT, BWD>(p, ws, ng, T, Fd, carry);
+        group_gather<K, EXT, BWD>(p, ws, ng, T, Fd, p.adj, carry);
         write_columns<K, EXT, BWD>(p, ws, ng, ws.owant);
         if (lane < ng) {
             uint32_t want[W];

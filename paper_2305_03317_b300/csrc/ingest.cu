@@ -84,6 +84,16 @@ __global__ void k_csr_from_keys(const unsigned long long* keys, long long m, int
     }
 }
 
+// one warp per relabelled row: reversed arc keys (col << 32 | row) for the in-CSR
+__global__ void k_rev_keys(const int* noff, const int* nadj, int n, unsigned long long* keys) {
+    const int lane = threadIdx.x & 31;
+    const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r = wg; r < n; r += nw)
+        for (long long e = noff[r] + lane; e < noff[r + 1]; e += 32)
+            keys[e] = ((unsigned long long)(unsigned int)nadj[e] << 32) | (unsigned int)r;
+}
+
 __global__ void k_fill_empty_offsets(int* noff, int n) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r <= n) noff[r] = 0;
@@ -301,17 +311,18 @@ int bits_for(unsigned long long x) {
 
 }  // namespace
 
-cudaError_t ingest(const int* d_off, const int* d_adj, int n, long long m, bool validate, cudaStream_t st,
-                   AllocFn alloc, FreeFn dfree, IngestOut* out, bool* oom) {
+cudaError_t ingest(const int* d_off, const int* d_adj, int n, long long m, bool validate, bool directed,
+                   cudaStream_t st, AllocFn alloc, FreeFn dfree, IngestOut* out, bool* oom) {
     Pool pool{alloc, dfree, st};
     out->reason = 0;
     out->off = nullptr; out->adj = nullptr; out->perm = nullptr; out->inv = nullptr;
+    out->ioff = nullptr; out->iadj = nullptr;
     out->max_deg = 0; out->n_nz = 0;
     *oom = false;
-    int* d_err = (int*)pool.get(sizeof(int) * 4);
+    int* d_err = (int*)pool.get(sizeof(int) * 5);
     if (pool.oom) { *oom = true; return cudaErrorMemoryAllocation; }
     int h_err[4] = {0, 0, 0, 0};
-    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int) * 4, st);
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int) * 5, st);
     auto fail = [&](cudaError_t ee) { *oom = pool.oom; return ee; };
 
     // 1. offsets and index range (always: later kernels index with these values)
@@ -368,9 +379,27 @@ cudaError_t ingest(const int* d_off, const int* d_adj, int n, long long m, bool 
         for (int s = 0; s < b; s += 8) shifts[np++] = 32 + s;
         if ((e = radix_sort(pool, &ka, &kb, m, shifts, np)) != cudaSuccess) { cleanup_tmp(); return fail(e); }
         k_csr_from_keys<<<1184, 256, 0, st>>>(ka, m, n, out->off, out->adj, d_err);
-        if (validate) k_check_symmetry<<<1184, 256, 0, st>>>(out->off, out->adj, n, d_err);
+        if (validate && !directed) k_check_symmetry<<<1184, 256, 0, st>>>(out->off, out->adj, n, d_err);
     } else {
         k_fill_empty_offsets<<<(n + 1 + 255) / 256, 256, 0, st>>>(out->off, n);
+    }
+    if (directed) {
+        // in-CSR (the transpose, rows sorted) for the pull steps of directed graphs;
+        // its duplicate/self-loop flags go to a slot nobody reads (the out-CSR's count)
+        out->ioff = (int*)pool.get(sizeof(int) * ((size_t)n + 1));
+        out->iadj = (int*)pool.get(sizeof(int) * (size_t)(m > 0 ? m : 1));
+        if (pool.oom) { cleanup_tmp(); *oom = true; return cudaErrorMemoryAllocation; }
+        if (m > 0) {
+            k_rev_keys<<<1184, 256, 0, st>>>(out->off, out->adj, n, ka);
+            const int b = bits_for((unsigned long long)(n - 1));
+            int shifts[16], np = 0;
+            for (int s = 0; s < b; s += 8) shifts[np++] = s;
+            for (int s = 0; s < b; s += 8) shifts[np++] = 32 + s;
+            if ((e = radix_sort(pool, &ka, &kb, m, shifts, np)) != cudaSuccess) { cleanup_tmp(); return fail(e); }
+            k_csr_from_keys<<<1184, 256, 0, st>>>(ka, m, n, out->ioff, out->iadj, d_err + 4);
+        } else {
+            k_fill_empty_offsets<<<(n + 1 + 255) / 256, 256, 0, st>>>(out->ioff, n);
+        }
     }
     cudaMemsetAsync(d_err + 3, 0, sizeof(int), st);
     k_count_nz<<<(n + 255) / 256, 256, 0, st>>>(out->off, n, d_err + 3);

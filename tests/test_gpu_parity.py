@@ -373,3 +373,77 @@ def test_bfs_extended_range_and_errors(bc):
         G.bfs(np.array([g.n], np.int32))
     lev0, _, _, st0 = G.bfs(np.zeros(0, np.int32))
     assert st0 == bc.BC_OK and lev0.numel() == 0
+
+
+# ----------------------------------------------------------------- directed graphs
+
+@pytest.fixture(scope="module")
+def directed_rmat():
+    g = bcgen.orient(bcgen.rmat(11, 8, 1), 5, 0.3)
+    return g, oracle.bc(g.off, g.adj, np.arange(g.n))
+
+
+def test_directed_relabel_matches_oracle(bc, directed_rmat):
+    g, _ = directed_rmat
+    G = bc.Graph(g.off, g.adj, directed=True)
+    perm, off, adj = G.export()
+    operm, _, ooff, oadj = oracle.relabel(g.off, g.adj)
+    assert np.array_equal(perm, operm) and np.array_equal(off, ooff) and np.array_equal(adj, oadj)
+
+
+@pytest.mark.parametrize("kw", [dict(batch_width=1), dict(batch_width=32), dict(batch_width=64),
+                                dict(batch_width=128), dict(batch_width=64, direction=1),
+                                dict(batch_width=64, direction=2)],
+                         ids=lambda kw: "-".join(f"{k}{v}" for k, v in kw.items()))
+def test_directed_all_sources(bc, directed_rmat, kw):
+    g, want = directed_rmat
+    G = bc.Graph(g.off, g.adj, directed=True)
+    got, st = G.compute(np.arange(g.n, dtype=np.int32), **kw)
+    assert st == bc.BC_OK
+    assert_bc_close(got.cpu().numpy(), want)
+
+
+def test_directed_bitwise_across_forms_and_heavy_rows(bc):
+    g = bcgen.orient(bcgen.rmat(14, 64, 3), 2, 0.5)  # rows above 1024 out-arcs and in-arcs
+    assert int(np.diff(g.off).max()) > 2 * 1024
+    src = bcgen.sample_sources(g, 96, 4)
+    want = oracle.bc(g.off, g.adj, src)
+    G = bc.Graph(g.off, g.adj, directed=True)
+    ref = None
+    for kw in (dict(batch_width=64), dict(batch_width=32, direction=1), dict(batch_width=128, direction=2),
+               dict(batch_width=1), dict(batch_width=64, teams=3)):
+        got, st = G.compute(src, **kw)
+        got = got.cpu().numpy()
+        assert_bc_close(got, want)
+        if ref is None:
+            ref = got
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
+
+
+def test_directed_closed_forms_and_bfs(bc):
+    n = 200
+    dpath = bcgen.directed_csr(n, np.arange(n - 1), np.arange(1, n))
+    got, _ = bc.Graph(dpath.off, dpath.adj, directed=True).compute(np.arange(n, dtype=np.int32))
+    assert_bc_close(got.cpu().numpy(), [i * (n - 1 - i) for i in range(n)], rel=1e-12)
+    dcyc = bcgen.directed_csr(n, np.arange(n), (np.arange(n) + 1) % n)
+    got, _ = bc.Graph(dcyc.off, dcyc.adj, directed=True).compute(np.arange(n, dtype=np.int32))
+    assert_bc_close(got.cpu().numpy(), [(n - 1) * (n - 2) / 2] * n, rel=1e-12)
+    g = bcgen.orient(bcgen.disjoint_union(bcgen.rmat(10, 8, 2), bcgen.path(4)), 3, 0.2)
+    src = bcgen.sample_sources(g, 40, 6)
+    lev, sig, _, _ = bc.Graph(g.off, g.adj, directed=True).bfs(src)
+    lev, sig = lev.cpu().numpy(), sig.cpu().numpy()
+    for i, s in enumerate(src):
+        d = oracle.source_detail(g.off, g.adj, int(s))
+        assert np.array_equal(lev[i], d["level"]) and np.array_equal(sig[i], np.where(d["level"] >= 0, d["sigma"], 0))
+
+
+def test_directed_invalid_inputs(bc):
+    g = bcgen.directed_csr(4, [0, 1, 2], [1, 2, 3])
+    with pytest.raises(bc.BCError):  # a directed CSR is not symmetric
+        bc.Graph(g.off, g.adj)
+    dup = (np.array([0, 2, 2, 2, 2], np.int32), np.array([1, 1], np.int32))
+    with pytest.raises(bc.BCError):
+        bc.Graph(*dup, directed=True)
+    loop = (np.array([0, 1, 1], np.int32), np.array([0], np.int32))
+    with pytest.raises(bc.BCError):
+        bc.Graph(*loop, directed=True)

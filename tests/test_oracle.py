@@ -294,3 +294,36 @@ def test_golden_small_graphs():
     for rec in load():
         got = oracle.bc(rec["off"], rec["adj"], rec["src"])
         assert close(got, [float(x) for x in rec["bc"]]), rec["name"]
+
+
+# ----------------------------------------------------------------- directed graphs (arcs followed one way)
+
+def test_directed_brute_force_matches_oracle():
+    """Shortest paths follow arcs; brute force counts s -> t paths through v."""
+    from fractions import Fraction
+    for seed in range(6):
+        g = bcgen.orient(bcgen.gnp(8, 0.45, seed + 20), seed, 0.3)
+        want = oracle.brute_force_bc(g.off, g.adj, range(g.n))
+        got = oracle.bc(g.off, g.adj, np.arange(g.n))
+        for v in range(g.n):
+            assert abs(got[v] - float(want[v])) <= 1e-12 * max(1.0, float(want[v])), (seed, v)
+        for s in range(g.n):
+            lev, sig = oracle.brute_force_sigma(g.off, g.adj, s)
+            d = oracle.source_detail(g.off, g.adj, s)
+            assert np.array_equal(d["level"], np.array(lev)) and np.array_equal(d["sigma"], np.array(sig, float))
+
+
+def test_directed_closed_forms():
+    n = 11
+    dpath = bcgen.directed_csr(n, np.arange(n - 1), np.arange(1, n))
+    # ordered pairs s < i < t: i * (n - 1 - i); no halving for directed graphs
+    assert np.array_equal(oracle.bc(dpath.off, dpath.adj, np.arange(n)), [i * (n - 1 - i) for i in range(n)])
+    dcyc = bcgen.directed_csr(n, np.arange(n), (np.arange(n) + 1) % n)
+    # every ordered pair has one path of length (t - s) mod n: each vertex is interior (n-1)(n-2)/2 times
+    assert np.all(oracle.bc(dcyc.off, dcyc.adj, np.arange(n)) == (n - 1) * (n - 2) / 2)
+    out_star = bcgen.directed_csr(n, np.zeros(n - 1, int), np.arange(1, n))
+    assert np.all(oracle.bc(out_star.off, out_star.adj, np.arange(n)) == 0)
+    # orienting with p_both = 1 keeps every arc: the undirected graph itself
+    g = bcgen.rmat(8, 4, 2)
+    both = bcgen.orient(g, 1, 1.0)
+    assert np.array_equal(both.off, g.off) and np.array_equal(both.adj, g.adj)
