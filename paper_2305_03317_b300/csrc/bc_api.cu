@@ -214,6 +214,7 @@ struct bc_graph {
     int n_heavy = -1;      // rows with degree > kChunk (a prefix of the new ids); -1 = not yet counted
     long long hchunk_total = 0;
     bool directed = false;
+    int max_in_deg = 0;  // directed: longest in-row (forward sums run over whole in-rows)
     DevBuf off, adj, perm, inv, hcum;
     DevBuf ioff, iadj;  // directed: in-CSR for the pull steps
     AllocHook hook;
@@ -303,6 +304,16 @@ static bool ws_ensure(Workspace* w, bc_graph* g, int K, bool ext, int nbatch, in
     return ws_ensure_dims(w, g->n, g->n_heavy, g->hchunk_total, K, ext, nbatch, njobs, capf, nteams, st);
 }
 
+// Bits of x (0 for 0): a sum of x terms below 2^(64 - bits_needed(x)) fits 64 bits.
+static int bits_needed(unsigned long long x) {
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
 // Matched columns from which an arc is cheaper summed column-mapped (one warp
 // step per arc) than as compacted pairs; measured on R-MAT scale 22 (one
 // batch per width): 48 of 128 and 32 of 64; at 32 columns the two forms tie.
@@ -363,6 +374,8 @@ static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_optio
     p.forward_only = 0;
     p.group = o.group_vertices > 0 ? o.group_vertices : 32;
     p.dense_min = o.dense_min > 0 ? o.dense_min : default_dense_min(w->K);
+    // forward sums have at most 1024 terms (chunked rows); directed graphs sum whole in-rows
+    p.sum_bits = g->directed ? 64 - bits_needed((unsigned long long)g->max_in_deg) : 64 - 10;
     p.trace = nullptr;
     p.trace_cap = 0;
     p.team_blocks = team_blocks;
@@ -996,6 +1009,7 @@ bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_
         return fail(BC_E_INVALID_GRAPH, "invalid CSR: %s", why[io.reason]);
     }
     g->max_deg = io.max_deg;
+    g->max_in_deg = io.max_in_deg;
     // rows are sorted by out-degree; in a directed graph a vertex without out-arcs
     // can still be reached, so every vertex takes part in the pull steps
     g->n_nz = directed ? n : io.n_nz;

@@ -92,6 +92,7 @@ struct KParams {
     long long* trace;          // optional phase trace: (tag, globaltimer ns) pairs; null = off
     int trace_cap;             // pairs the trace buffer holds
     int group;                 // light rows per warp task (1..32)
+    int sum_bits;              // forward terms below 2^sum_bits cannot make a sum wrap 64 bits
     int dense_min;             // matched columns from which an arc is summed column-mapped (K >= 32)
     // teams: gridDim.x = nteams * team_blocks; team t owns blocks [t*team_blocks, (t+1)*team_blocks)
     // and the workspace slice at +t*team_bytes of every per-team array; batches go round-robin
@@ -128,6 +129,7 @@ struct IngestOut {
     int* ioff;      // directed: [n+1] in-CSR (transpose of the relabelled CSR), else null
     int* iadj;      // directed: [m]
     int max_deg;
+    int max_in_deg; // directed: longest in-row, else 0
     int n_nz;
     int reason;     // 0 ok, else 1 offsets, 2 index range, 3 self-loop, 4 duplicate, 5 asymmetric
 };

@@ -540,16 +540,18 @@ __device__ __forceinline__ void gather_step(const KParams& p, WarpSmem<K, EXT>& 
                 if (r0 + 32 * i >= cnt) break;
                 if constexpr (!ORDERED) {
                     // integer path counts, order-free: two 32-bit shared atomics (the
-                    // low word's carry goes into the high word).  A term below 2^54
-                    // in sums of at most kChunk terms cannot carry out of 64 bits; a
-                    // larger term sends the batch to the extended form.
+                    // low word's carry goes into the high word).  A term below
+                    // 2^sum_bits cannot make a sum carry out of 64 bits (sum_bits
+                    // leaves room for the longest sum: 1024-arc chunks, or whole rows
+                    // where rows are not chunked); a larger term sends the batch to
+                    // the extended form.
                     if (valid[i]) {
                         unsigned int* a32 = reinterpret_cast<unsigned int*>(&ws.acc[slot[i]]);
                         const unsigned int xl = (unsigned int)x[i], xh = (unsigned int)(x[i] >> 32);
                         const unsigned int old = atomicAdd(a32, xl);
                         const unsigned int cy = (old + xl < old) ? 1u : 0u;
                         if (xh | cy) atomicAdd(a32 + 1, xh + cy);
-                        carry |= (x[i] >> 54) != 0ull;
+                        carry |= (x[i] >> p.sum_bits) != 0ull;
                     }
                 } else {
                     // ordered: lanes that share a slot add in lane (CSR) order.  A

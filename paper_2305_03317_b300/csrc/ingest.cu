@@ -94,6 +94,11 @@ __global__ void k_rev_keys(const int* noff, const int* nadj, int n, unsigned lon
             keys[e] = ((unsigned long long)(unsigned int)nadj[e] << 32) | (unsigned int)r;
 }
 
+__global__ void k_max_row(const int* noff, int n, int* out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) atomicMax(out, noff[r + 1] - noff[r]);
+}
+
 __global__ void k_fill_empty_offsets(int* noff, int n) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r <= n) noff[r] = 0;
@@ -316,7 +321,7 @@ cudaError_t ingest(const int* d_off, const int* d_adj, int n, long long m, bool 
     Pool pool{alloc, dfree, st};
     out->reason = 0;
     out->off = nullptr; out->adj = nullptr; out->perm = nullptr; out->inv = nullptr;
-    out->ioff = nullptr; out->iadj = nullptr;
+    out->ioff = nullptr; out->iadj = nullptr; out->max_in_deg = 0;
     out->max_deg = 0; out->n_nz = 0;
     *oom = false;
     int* d_err = (int*)pool.get(sizeof(int) * 5);
@@ -400,6 +405,15 @@ cudaError_t ingest(const int* d_off, const int* d_adj, int n, long long m, bool 
         } else {
             k_fill_empty_offsets<<<(n + 1 + 255) / 256, 256, 0, st>>>(out->ioff, n);
         }
+        cudaMemsetAsync(d_err + 4, 0, sizeof(int), st);
+        k_max_row<<<(n + 255) / 256, 256, 0, st>>>(out->ioff, n, d_err + 4);
+        int h_in = 0;
+        if ((e = cudaMemcpyAsync(&h_in, d_err + 4, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            cleanup_tmp();
+            return fail(e);
+        }
+        out->max_in_deg = h_in;
     }
     cudaMemsetAsync(d_err + 3, 0, sizeof(int), st);
     k_count_nz<<<(n + 255) / 256, 256, 0, st>>>(out->off, n, d_err + 3);

@@ -222,6 +222,7 @@ extern "C" bc_status bc_compute_noalloc(const int32_t* offsets, const int32_t* i
     p.beta = 24.0f;
     p.budget = 40000000000ll;
     p.group = 32;
+    p.sum_bits = 64 - 15;  // rows are never chunked here; no row has 2^15 arcs (n <= 32768)
     p.dense_min = 32;  // batch width 32: only arcs matching every column go column-mapped
 
     // the output accumulates every batch in source order; the job table points at it

@@ -447,3 +447,31 @@ def test_directed_invalid_inputs(bc):
     loop = (np.array([0, 1, 1], np.int32), np.array([0], np.int32))
     with pytest.raises(bc.BCError):
         bc.Graph(*loop, directed=True)
+
+
+def test_directed_long_in_row_sum_beyond_64_bits(bc):
+    """A sink with 4000 in-arcs from vertices of sigma = 2^53: its count 4000 * 2^53
+    passes 2^64.  Whole in-rows are summed unchunked, so the per-term bound that
+    sends the batch to the extended form must leave room for 4000 terms."""
+    L, M = 53, 4000
+    src, dst = [0, 0], [1, 2]
+    layer = lambda i: (1 + 2 * (i - 1), 2 + 2 * (i - 1))  # layer i in 1..L: sigma = 2^(i-1)
+    for i in range(1, L):
+        for a in layer(i):
+            for b in layer(i + 1):
+                src.append(a); dst.append(b)
+    mid0 = 1 + 2 * L
+    sink = mid0 + M
+    for k in range(M):
+        for a in layer(L):
+            src.append(a); dst.append(mid0 + k)  # sigma(mid) = 2 * 2^(L-1) = 2^53
+        src.append(mid0 + k); dst.append(sink)
+    g = bcgen.directed_csr(sink + 1, np.array(src), np.array(dst))
+    G = bc.Graph(g.off, g.adj, directed=True)
+    lev, mant, ex, st = G.bfs(np.array([0], np.int32), exponent=True)
+    assert st == bc.BC_W_SIGMA_INEXACT
+    got = np.ldexp(float(mant[0, sink].item()), int(ex[0, sink].item()))
+    assert got == M * 2.0 ** 53 and int(lev[0, sink].item()) == L + 2
+    out, st = G.compute(np.array([0, 1, 2], np.int32), batch_width=32)
+    assert st == bc.BC_W_SIGMA_INEXACT and G.stats()["ext_batches"] > 0
+    assert_bc_close(out.cpu().numpy(), oracle.bc_ld(g.off, g.adj, np.array([0, 1, 2])).astype(np.float64))
