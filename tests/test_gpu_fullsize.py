@@ -1,0 +1,117 @@
+"""GPU parity at the workloads' full sizes, in the launch configuration the
+benchmark times, on outputs the oracle can compute in bounded time.
+
+* 1024x1024 grid with 5% of edges removed: all 256 sampled sources at the
+  benchmark's tuned batch width (extended form: counts reach ~2^2040), against
+  the long-double oracle; the plain per-source form must agree bit for bit.
+* R-MAT scale 22, edge factor 16: the benchmark's first 128-source batch
+  (K = 128, the width the benchmark runs) against the oracle on the host cores.
+* The 2000-graph pool of uneven R-MAT graphs: sampled items (the smallest
+  graph, the largest all-sources graph, the largest graph) recorded into one
+  plan as the benchmark records the pool, each against the oracle.
+* Serving over the R-MAT scale 14-22 pool: a second of Poisson requests at
+  50 req/s, every request checked for success, sampled requests against the
+  oracle.
+
+Same tolerance as tests/test_gpu_parity.py: 1e-9 relative per vertex, exact
+zeros exact.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import bcgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-9
+THREADS = max(1, min(os.cpu_count() or 1, 64))
+
+
+@pytest.fixture(scope="module")
+def bc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_03317_b300 as m
+    m.load()
+    return m
+
+
+def assert_bc_close(got, want, rel=REL):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert got.shape == want.shape
+    zero = want == 0
+    assert np.all(got[zero] == 0), "exact zeros must stay zero"
+    err = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    assert np.all(err[~zero] <= rel), f"max rel err {err[~zero].max()}"
+
+
+def test_grid_1024_all_256_sources(bc):
+    g = bcgen.grid(1024, 1024, 0.05, 1)
+    src = bcgen.sample_sources(g, 256, 1)
+    G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(src, batch_width=32)  # the width the autotuner picks for this graph
+    assert st == bc.BC_W_SIGMA_INEXACT
+    got = out.cpu().numpy()
+    assert_bc_close(got, oracle.bc_ld(g.off, g.adj, src).astype(np.float64))
+    plain, _ = G.compute(src, batch_width=1)
+    assert np.array_equal(plain.cpu().numpy().view(np.uint64), got.view(np.uint64))
+
+
+def test_rmat22_first_benchmark_batch(bc):
+    g = bcgen.rmat(22, 16, 1)
+    src = bcgen.sample_sources(g, 4096, 1)[:128]
+    G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(src, batch_width=128)
+    assert st == bc.BC_OK
+    assert G.stats()["batches"] == 1
+    assert_bc_close(out.cpu().numpy(), oracle.bc(g.off, g.adj, src, threads=THREADS))
+
+
+def test_pool_of_2000_sampled_items_in_one_plan(bc):
+    import torch
+    pool = bcgen.rmat_sizes_pool(2000, seed=1)
+    ns = np.array([n for n, _, _ in pool])
+    small = int(np.argmin(ns))
+    all_src = int(np.argmax(np.where(ns <= 16384, ns, -1)))
+    large = int(np.argmax(ns))
+    items, want = [], []
+    for i in (small, all_src, large):
+        n, ef, sd = pool[i]
+        g = bcgen.rmat_n(n, ef, sd)
+        src = np.arange(g.n, dtype=np.int32) if g.n <= 16384 else bcgen.sample_sources(g, 256, sd)
+        out = torch.empty(max(g.n, 1), dtype=torch.float64, device="cuda")
+        items.append((bc.Graph(g.off, g.adj), src, out))
+        want.append(oracle.bc(g.off, g.adj, src, threads=THREADS))
+    plan = bc.ManyPlan(items)
+    st = plan.run()
+    assert all(int(s) in (bc.BC_OK, bc.BC_W_SIGMA_INEXACT) for s in st)
+    for (G, _, out), w in zip(items, want):
+        assert_bc_close(out.cpu().numpy()[: G.n], w)
+    plan.close()
+
+
+def test_serving_pool_14_to_22_sampled_requests(bc):
+    import torch
+    pool = [bcgen.rmat(s, 16, 1) for s in range(14, 23)]
+    Gs = [bc.Graph(g.off, g.adj) for g in pool]
+    reqs = bcgen.poisson_requests(50.0, 1.0, len(pool), seed=1)
+    srcs = [bcgen.sample_sources(pool[gi], k, 100 + i) for i, (_, gi, k) in enumerate(reqs)]
+    outs = [torch.empty(pool[gi].n, dtype=torch.float64, device="cuda") for _, gi, _ in reqs]
+    jobs = [Gs[gi].submit(s, o) for (_, gi, _), s, o in zip(reqs, srcs, outs)]
+    for j in jobs:
+        assert j.wait(600000) is not None
+    # sampled: requests the oracle finishes quickly (by source-arcs), one on the largest graph
+    work = np.array([len(s) * pool[gi].m for s, (_, gi, _) in zip(srcs, reqs)], dtype=np.float64)
+    picks = [int(i) for i in np.argsort(work)[:6]]
+    biggest = [i for i, (_, gi, _) in enumerate(reqs) if gi == len(pool) - 1]
+    if biggest:
+        picks.append(min(biggest, key=lambda i: len(srcs[i])))
+    for i in picks:
+        _, gi, _ = reqs[i]
+        g = pool[gi]
+        assert_bc_close(outs[i].cpu().numpy(), oracle.bc(g.off, g.adj, srcs[i], threads=THREADS))
