@@ -1124,11 +1124,8 @@ bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* lev
     std::lock_guard<std::mutex> lk(g->mu);
     g->last_stream = st;
     if (g->n == 0 || nsrc == 0) return BC_OK;
-    const size_t n = (size_t)g->n, cells = n * (size_t)nsrc;
-    cudaError_t e = cudaMemsetAsync(level, 0xFF, sizeof(int32_t) * cells, st);  // -1: unreachable
-    if (e == cudaSuccess && sigma) e = cudaMemsetAsync(sigma, 0, sizeof(double) * cells, st);
-    if (e == cudaSuccess && sigma_exp) e = cudaMemsetAsync(sigma_exp, 0, sizeof(int32_t) * cells, st);
-    if (e != cudaSuccess) return cuda_fail(e, "clear outputs");
+    const size_t n = (size_t)g->n;
+    cudaError_t e = cudaSuccess;  // every output cell is written by the extraction
     const int* d_src = sources;
     DevBuf tmp;
     if (!is_device_ptr(sources)) {
@@ -1151,7 +1148,10 @@ bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* lev
     auto& slot = g->ws[K];
     if (!slot) slot.reset(new Workspace());
     Workspace* w = slot.get();
-    bc_status r = buf_ensure(w->bc, sizeof(double) * n, st) ? BC_OK : fail(BC_E_NOMEM, "buffers");
+    DevBuf lvl;  // [n][K] uint16 level table of one batch
+    bc_status r = buf_ensure(w->bc, sizeof(double) * n, st) && buf_ensure(lvl, sizeof(unsigned short) * n * (size_t)K, st)
+                      ? BC_OK
+                      : fail(BC_E_NOMEM, "buffers");
     bool inexact = false;
     bc_run_stats total{};
     for (int b0 = 0; r >= 0 && b0 < nsrc; b0 += K) {
@@ -1176,8 +1176,8 @@ bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* lev
         total.teams = stats.teams;
         KParams p = make_params(g, w, 1, o, ext, 1);
         const size_t row0 = (size_t)b0 * n;
-        e = launch_bfs_extract(p, kused, levels, cnt, (const int*)g->perm.p, (long long)n, level + row0,
-                               sigma ? sigma + row0 : nullptr, sigma_exp ? sigma_exp + row0 : nullptr, st);
+        e = launch_bfs_extract(p, kused, levels, cnt, (const int*)g->inv.p, (long long)n, (unsigned short*)lvl.p,
+                               level + row0, sigma ? sigma + row0 : nullptr, sigma_exp ? sigma_exp + row0 : nullptr, st);
         if (e != cudaSuccess) r = cuda_fail(e, "bfs extract");
     }
     if (r >= 0) {
@@ -1186,6 +1186,7 @@ bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* lev
         g->last = total;
     }
     buf_release(tmp, st);
+    buf_release(lvl, st);
     if (r >= 0 && inexact) r = BC_W_SIGMA_INEXACT;
     return r;
 }

@@ -112,8 +112,8 @@ cudaError_t launch_collect_status(const Ctl* ctl, const int* bstat, int nbatch, 
 cudaError_t launch_team_reset(Ctl* ctl0, int* arr0, long long team_bytes, int nteams, int arr_ints, cudaStream_t st);
 cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, int n, int K, int* dst,
                                int nbatch, int* bad, cudaStream_t st);
-cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, const int* perm, long long n,
-                               int* level_out, double* sig_out, int* exp_out, cudaStream_t st);
+cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, const int* inv, long long n,
+                               unsigned short* lvl, int* level_out, double* sig_out, int* exp_out, cudaStream_t st);
 cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
                                  int* sige_rel, cudaStream_t st);
 

@@ -1650,39 +1650,70 @@ __global__ void k_debug_extract(KParams p, int K, int levels, int* level_rel, un
     }
 }
 
-// Multi-source BFS output of one batch (after a forward-only traversal): for
-// every level list entry (vertex v, columns at that level) and each of its
-// columns c < ncols, row c gets level[c][perm[v]] = l and the path count
-// (a double, or a mantissa in [0.5, 1) with a separate exponent).
-__global__ void k_bfs_extract(KParams p, int K, int levels, int ncols, const int* __restrict__ perm, long long n,
-                              int* level_out, double* sig_out, int* exp_out) {
+// Multi-source BFS output of one batch (after a forward-only traversal), in
+// two coalesced passes.  (1) k_bfs_levels: one warp per level-list entry
+// (vertex v, columns at level l) writes l into the relabelled table
+// lvl[v][c] (uint16, 0xFFFF = unreached), lanes mapped to columns.
+// (2) k_bfs_rows: one warp per 32 consecutive original ids u; lane i reads
+// the table row and path-count row of v = inv[u0 + i] a slice at a time and
+// the warp writes each column's 32 values as one contiguous run of row c of
+// the [ncols][n] outputs.
+__global__ void k_bfs_levels(KParams p, int K, int levels, unsigned short* lvl) {
     const int W = K >= 32 ? K / 32 : 1;
-    const long long nthr = (long long)gridDim.x * blockDim.x;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     for (int l = 0; l < levels; ++l) {
         const long long s = p.la.start[l], c = p.la.cnt[l], hs = p.la.hstart[l], hc = p.la.hcnt[l];
-        for (long long i = tid; i < c + hc; i += nthr) {
+        for (long long i = wid; i < c + hc; i += nw) {
             const int v = i < c ? p.ent[s + i] : p.hent[hs + (i - c)];
             const uint32_t* m = i < c ? p.emask + (size_t)(s + i) * W : p.hmask + (size_t)(hs + (i - c)) * W;
-            const long long vo = perm[v];
-            for (int t = 0; t < W; ++t) {
-                uint32_t bits = m[t];
-                while (bits) {
-                    const int col = t * 32 + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    if (col >= ncols) continue;
-                    const size_t o = (size_t)col * (size_t)n + (size_t)vo;
-                    level_out[o] = l;
-                    if (sig_out) {
-                        const unsigned long long x = p.sig[(size_t)v * K + col];
-                        const int xe = p.ext ? p.sig_e[(size_t)v * K + col] : 0;
-                        if (exp_out) {
-                            int e = 0;
-                            sig_out[o] = frexp((double)x, &e);
-                            exp_out[o] = x ? e + xe : 0;
-                        } else {
-                            sig_out[o] = ldexp((double)x, xe);
-                        }
+            for (int col = lane; col < K; col += 32)
+                if ((m[col >> 5] >> (col & 31)) & 1u) lvl[(size_t)v * K + col] = (unsigned short)l;
+        }
+    }
+}
+
+__global__ void k_bfs_rows(KParams p, int K, int ncols, const unsigned short* __restrict__ lvl,
+                           const int* __restrict__ inv, long long n, int* level_out, double* sig_out, int* exp_out) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long tiles = (n + 31) / 32;
+    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles; t += nw) {
+        const long long u = t * 32 + lane;
+        const bool ok = u < n;
+        const long long v = ok ? inv[u] : 0;
+        for (int c0 = 0; c0 < ncols; c0 += 8) {
+            unsigned short l8[8];
+            unsigned long long s8[8];
+            int e8[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int c = c0 + k;
+                l8[k] = 0xFFFFu;
+                s8[k] = 0ull;
+                e8[k] = 0;
+                if (ok && c < ncols) {
+                    l8[k] = lvl[(size_t)v * K + c];
+                    if (sig_out && l8[k] != 0xFFFFu) {
+                        s8[k] = p.sig[(size_t)v * K + c];
+                        if (p.ext) e8[k] = p.sig_e[(size_t)v * K + c];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int c = c0 + k;
+                if (!ok || c >= ncols) continue;
+                const size_t o = (size_t)c * (size_t)n + (size_t)u;
+                level_out[o] = l8[k] == 0xFFFFu ? -1 : (int)l8[k];
+                if (sig_out) {
+                    if (exp_out) {
+                        int e = 0;
+                        sig_out[o] = frexp((double)s8[k], &e);
+                        exp_out[o] = s8[k] ? e + e8[k] : 0;
+                    } else {
+                        sig_out[o] = ldexp((double)s8[k], e8[k]);
                     }
                 }
             }
@@ -1806,13 +1837,17 @@ cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, const int* perm, long long n,
-                               int* level_out, double* sig_out, int* exp_out, cudaStream_t st) {
-    if (n <= 0 || levels <= 0) return cudaSuccess;
+cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, const int* inv, long long n,
+                               unsigned short* lvl, int* level_out, double* sig_out, int* exp_out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_bfs_extract<<<4 * (sms > 0 ? sms : 1), 256, 0, st>>>(p, K, levels, ncols, perm, n, level_out, sig_out, exp_out);
+    const int blocks = 8 * (sms > 0 ? sms : 1);
+    cudaError_t e = cudaMemsetAsync(lvl, 0xFF, sizeof(unsigned short) * (size_t)n * (size_t)K, st);
+    if (e != cudaSuccess) return e;
+    if (levels > 0) k_bfs_levels<<<blocks, 256, 0, st>>>(p, K, levels, lvl);
+    k_bfs_rows<<<blocks, 256, 0, st>>>(p, K, ncols, lvl, inv, n, level_out, sig_out, exp_out);
     return cudaGetLastError();
 }
 
