@@ -18,6 +18,8 @@ Contents:
     BC(v) = sum_s sum_{t != s, v} sigma_st(v) / sigma_st written out.
   * ``relabel`` / ``validate`` -- the ingest rules (degree-descending stable
     relabelling; CSR validity) in their plain definitions.
+  * ``pagerank`` -- the paper's computePR (Appendix A, PR listing) in double
+    precision (``pagerank.c``), the change measured as an L1 norm.
 Every function here is pinned by ``tests/test_oracle*.py`` against closed
 forms, brute force and invariants.
 """
@@ -34,6 +36,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "brandes.c")
+_SRCS = [_SRC, os.path.join(_HERE, "pagerank.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -48,10 +51,10 @@ class _Detail(ctypes.Structure):
 def build(force: bool = False) -> str:
     """Compile brandes.c into liboracle.so (plain -O2; no fast-math)."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-pthread", "-o", tmp, *_SRCS, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -76,6 +79,8 @@ def _L():
             lib.oracle_relabel.argtypes = [i32, P, P, P, P, P, P]
             lib.oracle_validate_csr.restype = ctypes.c_int
             lib.oracle_validate_csr.argtypes = [i32, i64, P, P, ctypes.c_int]
+            lib.oracle_pagerank.restype = ctypes.c_int
+            lib.oracle_pagerank.argtypes = [i32, P, P, ctypes.c_double, ctypes.c_double, i32, P, P]
             _lib = lib
     return _lib
 
@@ -163,6 +168,18 @@ def relabel(off, adj):
     nadj = np.empty(max(m, 1), np.int32)
     _L().oracle_relabel(n, _p(off), _p(adj), _p(perm), _p(inv), _p(noff), _p(nadj))
     return perm[:n], inv[:n], noff, nadj[:m]
+
+
+def pagerank(off, adj, delta: float = 0.85, beta: float = 1e-10, max_iter: int = 100):
+    """The paper's computePR (pagerank.c): (ranks float64[n], sweeps run, last L1 change)."""
+    off, adj = _csr(off, adj)
+    n = off.shape[0] - 1
+    pr = np.zeros(max(n, 1), np.float64)
+    diff = ctypes.c_double()
+    it = _L().oracle_pagerank(n, _p(off), _p(adj), delta, beta, max_iter, _p(pr), ctypes.byref(diff))
+    if it < 0:
+        raise MemoryError("oracle_pagerank")
+    return pr[:n], int(it), float(diff.value)
 
 
 def validate(off, adj, undirected: bool = True) -> int:

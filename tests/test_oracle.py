@@ -327,3 +327,50 @@ def test_directed_closed_forms():
     g = bcgen.rmat(8, 4, 2)
     both = bcgen.orient(g, 1, 1.0)
     assert np.array_equal(both.off, g.off) and np.array_equal(both.adj, g.adj)
+
+
+# ----------------------------------------------------------------- PageRank (computePR)
+
+def _transition(g):
+    """Dense column-stochastic-like matrix M[v, u] = 1/outdeg(u) for each arc u -> v."""
+    n = g.n
+    M = np.zeros((n, n))
+    deg = np.diff(g.off)
+    for u in range(n):
+        for e in range(g.off[u], g.off[u + 1]):
+            M[g.adj[e], u] += 1.0 / deg[u]
+    return M
+
+
+def test_pagerank_sweeps_equal_dense_power_iteration():
+    """k sweeps of the listing = k steps of x <- (1-d)/n + d M x from x = 1/n (dense algebra)."""
+    for g in (bcgen.rmat(6, 4, 3), bcgen.orient(bcgen.gnp(30, 0.15, 2), 4, 0.3), bcgen.directed_csr(5, [0, 1, 2, 3], [1, 2, 3, 4])):
+        M = _transition(g)
+        x = np.full(g.n, 1.0 / g.n)
+        for k in range(1, 12):
+            x = (1 - 0.85) / g.n + 0.85 * (M @ x)
+            pr, it, diff = oracle.pagerank(g.off, g.adj, 0.85, 0.0, k)
+            assert it == k or (it < k and diff == 0.0)  # an exact fixed point stops the sweeps early
+            assert np.allclose(pr, x, rtol=1e-13, atol=0)
+
+
+def test_pagerank_fixed_point_and_closed_forms():
+    g = bcgen.rmat(7, 6, 5)
+    pr, it, diff = oracle.pagerank(g.off, g.adj, 0.85, 1e-14, 1000)
+    assert diff <= 1e-14 and it < 1000
+    n = g.n
+    want = np.linalg.solve(np.eye(n) - 0.85 * _transition(g), np.full(n, 0.15 / n))
+    assert np.allclose(pr, want, rtol=1e-11, atol=0)
+    # no vertex without out-arcs: rank mass stays 1
+    assert abs(pr.sum() - 1.0) < 1e-12 or np.any(np.diff(g.off) == 0)
+    # a regular graph keeps the uniform start: one sweep, no change
+    c = bcgen.cycle(50)
+    pr, it, diff = oracle.pagerank(c.off, c.adj, 0.85, 1e-12, 100)
+    assert it == 1 and diff < 1e-15 and np.allclose(pr, 1 / 50, rtol=1e-14)
+    # undirected star: centre c, leaves l solve c = (1-d)/n + d (n-1) l, l = (1-d)/n + d c/(n-1)
+    n, d = 41, 0.85
+    s = bcgen.star(n)
+    pr, _, _ = oracle.pagerank(s.off, s.adj, d, 1e-15, 5000)
+    A = np.array([[1.0, -d * (n - 1)], [-d / (n - 1), 1.0]])
+    cc, ll = np.linalg.solve(A, [(1 - d) / n, (1 - d) / n])
+    assert np.isclose(pr[0], cc, rtol=1e-12) and np.allclose(pr[1:], ll, rtol=1e-12)
