@@ -145,6 +145,20 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
 bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* level, double* sigma,
                  int32_t* sigma_exp, bc_stream_t stream);
 
+/*
+ * PageRank as the paper's computePR (Appendix A, PR listing): ranks start at
+ * 1/n; each sweep sets rank(v) = (1 - delta)/n + delta * sum over arcs u -> v
+ * of rank(u) / outdeg(u) (all vertices at once), and sweeps repeat while the
+ * L1 change of the sweep exceeds beta and fewer than max_iter have run.  No
+ * redistribution of the rank of vertices without out-arcs (as in the
+ * listing).  out_rank: device double[n], original ids.  iterations /
+ * last_diff (host, may be NULL): sweeps run and the last L1 change.  Every
+ * sum has a fixed order: repeated calls give the same bits.  Requires
+ * 0 <= delta <= 1, beta >= 0, max_iter >= 1.
+ */
+bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, double* out_rank,
+                      int32_t* iterations, double* last_diff, bc_stream_t stream);
+
 /* Per-call facts of the last bc_compute / bc_compute_ex / bc_bfs on this graph. */
 typedef struct {
     int32_t batch_width;     /* width used */

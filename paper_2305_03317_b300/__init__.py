@@ -80,6 +80,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_compute": [P, P, i32, P, P],
         "bc_compute_ex": [P, P, i32, P, P, ctypes.POINTER(bc_options)],
         "bc_bfs": [P, P, i32, P, P, P, P],
+        "bc_pagerank": [P, ctypes.c_double, ctypes.c_double, i32, P, ctypes.POINTER(i32),
+                        ctypes.POINTER(ctypes.c_double), P],
         "bc_last_run_stats": [P, ctypes.POINTER(bc_run_stats)],
         "bc_batch_submit": [P, P, i32, P, ctypes.POINTER(u64)],
         "bc_poll": [u64],
@@ -283,6 +285,17 @@ class Graph:
                           _ptr(ex) if ex is not None and ex.numel() else None, _stream_handle(stream))
         _check(s)
         return lev, sg, ex, s
+
+    def pagerank(self, delta: float = 0.85, beta: float = 1e-10, max_iter: int = 100, out=None, stream=None):
+        """The paper's computePR (bc_pagerank): (ranks float64[n] on the device, sweeps run, last L1 change)."""
+        import torch
+        if out is None:
+            out = torch.empty(max(self.n, 1), dtype=torch.float64, device="cuda")[: self.n]
+        it = ctypes.c_int32()
+        diff = ctypes.c_double()
+        _check(load().bc_pagerank(self._h, float(delta), float(beta), int(max_iter), _ptr(out) if self.n else None,
+                                  ctypes.byref(it), ctypes.byref(diff), _stream_handle(stream)))
+        return out, int(it.value), float(diff.value)
 
     def debug_source(self, s: int):
         """(level int32[n], sigma_mant float64[n], sigma_exp int32[n]) for one source."""

@@ -1191,6 +1191,89 @@ bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* lev
     return r;
 }
 
+// First relabelled row shorter than len arcs (rows are sorted by length, longest first).
+static int first_row_shorter(bc_graph* g, int len, cudaStream_t st, cudaError_t* err) {
+    int lo = 0, hi = g->n;
+    const int* off = (const int*)g->off.p;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        int two[2];
+        cudaError_t e = cudaMemcpyAsync(two, off + mid, sizeof two, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            *err = e;
+            return 0;
+        }
+        if (two[1] - two[0] >= len) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, double* out_rank, int32_t* iterations,
+                      double* last_diff, bc_stream_t stream) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    if (!(delta >= 0.0 && delta <= 1.0) || !(beta >= 0.0) || max_iter < 1)
+        return fail(BC_E_INVALID_ARG, "need 0 <= delta <= 1, beta >= 0 and max_iter >= 1");
+    if (g->n > 0 && !out_rank) return fail(BC_E_INVALID_ARG, "out_rank is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->last_stream = st;
+    if (iterations) *iterations = 0;
+    if (last_diff) *last_diff = 0.0;
+    if (g->n == 0) return BC_OK;
+    const size_t n = (size_t)g->n;
+    const int blocks = pagerank_blocks();
+    if (blocks < 1) return fail(BC_E_CUDA, "PageRank kernel cannot be resident");
+    DevBuf rank, scratch, ctl, small;
+    auto release = [&]() {
+        buf_release(rank, st);
+        buf_release(scratch, st);
+        buf_release(ctl, st);
+        buf_release(small, st);
+    };
+    if (!buf_ensure(rank, sizeof(double) * n, st) || !buf_ensure(scratch, sizeof(double) * (2 * n + blocks), st) ||
+        !buf_ensure(ctl, sizeof(Ctl), st) || !buf_ensure(small, 64, st)) {
+        release();
+        return fail(BC_E_NOMEM, "PageRank buffers");
+    }
+    cudaError_t e = cudaMemsetAsync(ctl.p, 0, sizeof(Ctl), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(small.p, 0, 64, st);
+    int* d_iters = (int*)small.p;
+    int* d_go = (int*)small.p + 1;
+    double* d_diff = (double*)small.p + 1;
+    const int* roff = g->directed ? (const int*)g->ioff.p : (const int*)g->off.p;
+    const int* radj = g->directed ? (const int*)g->iadj.p : (const int*)g->adj.p;
+    // undirected rows are sorted by length: row classes by the first row shorter than each bound
+    int cls[2] = {0, 0};
+    const int bounds[2] = {8192, 32};
+    if (!g->directed)
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) cls[i] = first_row_shorter(g, bounds[i], st, &e);
+    if (e == cudaSuccess)
+        e = launch_pagerank(g->n, (const int*)g->off.p, roff, radj, g->directed ? nullptr : cls, delta, beta, max_iter,
+                            (double*)rank.p, (double*)scratch.p, (Ctl*)ctl.p, d_iters, d_diff, d_go, 40000000000ll,
+                            blocks, st);
+    if (e == cudaSuccess) e = launch_unpermute((const double*)rank.p, (const int*)g->inv.p, out_rank, g->n, st);
+    int h_it = 0, h_err = 0;
+    double h_diff = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_it, d_iters, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_diff, d_diff, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, &((Ctl*)ctl.p)->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(e, "PageRank");
+    if (h_err & ERR_TIMEOUT) return fail(BC_E_TIMEOUT, "a grid-barrier wait exceeded its cycle budget");
+    if (h_err) return fail(BC_E_CUDA, "PageRank kernel error 0x%x", h_err);
+    if (iterations) *iterations = h_it;
+    if (last_diff) *last_diff = h_diff;
+    bc_run_stats s{};
+    s.kernel_launches = 2;
+    s.grid_blocks = blocks;
+    s.max_levels = h_it;
+    g->last = s;
+    return BC_OK;
+}
+
 bc_status bc_compute(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream) {
     return bc_compute_ex(g, sources, nsrc, out_bc, stream, nullptr);
 }

@@ -104,6 +104,52 @@ struct KParams {
     int level_slots;           // entries of each level array (>= levels + 3)
 };
 
+// ------------------------------------------------------------------ barrier
+// Barrier over the blocks of one team (a plain block barrier for one-block
+// teams); errors are read from the launch-wide control block.
+struct GridTeam {
+    Ctl* ctl;
+    Ctl* gctl;
+    int nblocks;
+    long long budget;
+
+    // Returns false when the launch has failed (timeout or a fatal error).
+    __device__ bool sync() {
+        __shared__ int s_bad;
+        __syncthreads();
+        if (nblocks == 1) {
+            if (threadIdx.x == 0) s_bad = *(volatile int*)&gctl->err != 0;
+            __syncthreads();
+            return !s_bad;
+        }
+        if (threadIdx.x == 0) {
+            int bad = 0;
+            volatile unsigned int* genp = &ctl->bar_gen;
+            volatile int* errp = &gctl->err;
+            unsigned int g = *genp;
+            __threadfence();
+            unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+            if (arrived == (unsigned int)nblocks - 1) {
+                atomicExch(&ctl->bar_count, 0u);
+                __threadfence();
+                atomicAdd(&ctl->bar_gen, 1u);
+            } else {
+                long long t0 = clock64();
+                while (*genp == g) {
+                    if (*errp) { bad = 1; break; }
+                    if (clock64() - t0 > budget) { atomicOr(&gctl->err, ERR_TIMEOUT); bad = 1; break; }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+            if (*errp) bad = 1;
+            s_bad = bad;
+        }
+        __syncthreads();
+        return !s_bad;
+    }
+};
+
 // Host-side launchers (bc_kernels.cu)
 cudaError_t launch_batches(int K, const KParams& p, int blocks, cudaStream_t st);
 int max_coop_blocks(int K, bool ext, int* per_sm);
@@ -116,6 +162,14 @@ cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, c
                                unsigned short* lvl, int* level_out, double* sig_out, int* exp_out, cudaStream_t st);
 cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
                                  int* sige_rel, cudaStream_t st);
+
+// PageRank (pagerank.cu): scratch holds 2n + blocks doubles
+int pagerank_blocks();
+// row_class (rows sorted by length; null = not sorted): first rows shorter than
+// 8192 and than 32 arcs
+cudaError_t launch_pagerank(int n, const int* off, const int* roff, const int* radj, const int* row_class,
+                            double delta, double beta, int max_iter, double* rank, double* scratch, Ctl* ctl, int* iters,
+                            double* diff_out, int* go, long long budget, int blocks, cudaStream_t st);
 
 // Thread-local detail returned by bc_last_error() (bc_api.cu)
 void set_last_error(const char* msg);

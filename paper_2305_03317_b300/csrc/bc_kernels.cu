@@ -53,52 +53,6 @@ namespace bcx {
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 
-// ------------------------------------------------------------------ barrier
-// Barrier over the blocks of one team (a plain block barrier for one-block
-// teams); errors are read from the launch-wide control block.
-struct GridTeam {
-    Ctl* ctl;
-    Ctl* gctl;
-    int nblocks;
-    long long budget;
-
-    // Returns false when the launch has failed (timeout or a fatal error).
-    __device__ bool sync() {
-        __shared__ int s_bad;
-        __syncthreads();
-        if (nblocks == 1) {
-            if (threadIdx.x == 0) s_bad = *(volatile int*)&gctl->err != 0;
-            __syncthreads();
-            return !s_bad;
-        }
-        if (threadIdx.x == 0) {
-            int bad = 0;
-            volatile unsigned int* genp = &ctl->bar_gen;
-            volatile int* errp = &gctl->err;
-            unsigned int g = *genp;
-            __threadfence();
-            unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-            if (arrived == (unsigned int)nblocks - 1) {
-                atomicExch(&ctl->bar_count, 0u);
-                __threadfence();
-                atomicAdd(&ctl->bar_gen, 1u);
-            } else {
-                long long t0 = clock64();
-                while (*genp == g) {
-                    if (*errp) { bad = 1; break; }
-                    if (clock64() - t0 > budget) { atomicOr(&gctl->err, ERR_TIMEOUT); bad = 1; break; }
-                    __nanosleep(32);
-                }
-            }
-            __threadfence();
-            if (*errp) bad = 1;
-            s_bad = bad;
-        }
-        __syncthreads();
-        return !s_bad;
-    }
-};
-
 // Phase trace: block 0 stamps the end of every grid-wide phase (after its barrier).
 __device__ __forceinline__ void trace_mark(const KParams& p, int kind, int level) {
     if (p.trace == nullptr || p.team != 0 || p.rank != 0 || threadIdx.x != 0) return;

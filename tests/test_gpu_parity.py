@@ -475,3 +475,38 @@ def test_directed_long_in_row_sum_beyond_64_bits(bc):
     out, st = G.compute(np.array([0, 1, 2], np.int32), batch_width=32)
     assert st == bc.BC_W_SIGMA_INEXACT and G.stats()["ext_batches"] > 0
     assert_bc_close(out.cpu().numpy(), oracle.bc_ld(g.off, g.adj, np.array([0, 1, 2])).astype(np.float64))
+
+
+# ----------------------------------------------------------------- PageRank (computePR)
+
+@pytest.mark.parametrize("gname", ["rmat12", "directed", "isolated"])
+def test_pagerank_matches_oracle_sweep_for_sweep(bc, gname):
+    g = {"rmat12": lambda: bcgen.rmat(12, 8, 1),
+         "directed": lambda: bcgen.orient(bcgen.rmat(11, 16, 2), 3, 0.3),  # has vertices without out-arcs
+         "isolated": lambda: bcgen.disjoint_union(bcgen.rmat(10, 4, 4), bcgen.empty_graph(7), bcgen.star(40))}[gname]()
+    G = bc.Graph(g.off, g.adj, directed=(gname == "directed"))
+    for k in (1, 2, 17):
+        got, it, diff = G.pagerank(0.85, 0.0, k)  # beta 0: exactly k sweeps unless a fixed point is hit
+        want, oit, odiff = oracle.pagerank(g.off, g.adj, 0.85, 0.0, k)
+        assert it == oit
+        assert_bc_close(got.cpu().numpy(), want)
+        assert abs(diff - odiff) <= 1e-9 * max(odiff, 1e-300) or odiff == 0.0
+
+
+def test_pagerank_convergence_repeatability_and_errors(bc):
+    g = bcgen.rmat(13, 16, 2)
+    G = bc.Graph(g.off, g.adj)
+    a, it, diff = G.pagerank(0.85, 1e-10, 500)
+    want, oit, _ = oracle.pagerank(g.off, g.adj, 0.85, 1e-10, 500)
+    assert diff <= 1e-10 and abs(it - oit) <= 1
+    assert_bc_close(a.cpu().numpy(), want, rel=1e-8)
+    b, it2, diff2 = G.pagerank(0.85, 1e-10, 500)
+    assert it2 == it and diff2 == diff
+    assert np.array_equal(a.cpu().numpy().view(np.uint64), b.cpu().numpy().view(np.uint64))
+    assert abs(float(a.sum().item()) - float(want.sum())) < 1e-12  # isolated vertices leak rank, as in the listing
+    grid = bcgen.grid(40, 40, 0.0)  # every vertex has out-arcs: the rank mass stays 1
+    r, _, _ = bc.Graph(grid.off, grid.adj).pagerank(0.85, 1e-12, 1000)
+    assert abs(float(r.sum().item()) - 1.0) < 1e-12
+    for bad in (dict(delta=1.5), dict(beta=-1.0), dict(max_iter=0)):
+        with pytest.raises(bc.BCError):
+            G.pagerank(**bad)
