@@ -142,7 +142,18 @@ class Clocks:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        note = None
+        if not any(len(x.split(",")) >= 9 for x in lines):
+            # the timed region was shorter than the sampling interval: one reading right after it
+            try:
+                out = subprocess.run(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                      "-i", str(self.dev)], capture_output=True, text=True, timeout=30).stdout
+                lines = out.splitlines()
+                note = "timed region shorter than the 200 ms sampling interval: one reading right after it"
+            except Exception:
+                lines = []
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -154,8 +165,11 @@ class Clocks:
             for nm, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        res = {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if note:
+            res["note"] = note
+        return res
 
 
 def dag_stats(G, g, src, nsample=4):
