@@ -7,20 +7,26 @@
  * BFS DAG accumulates the dependency
  *     delta_s(v) = sum over DAG successors w of (sigma_v / sigma_w)(1 + delta_s(w))
  * (the iterateInReverse body), and BC(v) += delta_s(v) for every v != s.
- * The graph is undirected, unweighted, given as int32 CSR (Section 3.1: the
- * backend keeps graphs in CSR).  The result is the raw sum over the listed
- * sources: no halving for undirected graphs, no normalisation, no
- * extrapolation from sampled sources.  A source listed twice counts twice.
+ * The graph is unweighted, undirected (symmetric) or directed, given as int32
+ * CSR (Section 3.1: the backend keeps graphs in CSR).  The result is the raw
+ * sum over the listed sources: no halving for undirected graphs, no
+ * normalisation, no extrapolation from sampled sources.  A source listed twice
+ * counts twice.
  *
- * Numerics: path counts are exact unsigned 64-bit integers (exact to 2^64);
- * counts beyond 2^64 switch the batch to an extended-range form (64-bit
- * mantissa, 32-bit exponent).  delta and BC are IEEE double.  BC_W_SIGMA_INEXACT
+ * Numerics: path counts are exact unsigned 64-bit integers; a batch whose
+ * counts could pass 2^64 is rerun in an extended-range form (64-bit mantissa,
+ * 32-bit exponent), which equals the plain form bit for bit while counts stay
+ * below 2^64.  delta and BC are IEEE double.  BC_W_SIGMA_INEXACT
  * reports that some count reached 2^53 (the double conversion in the backward
  * sweep then rounds).  Results are deterministic: every sum runs in a fixed
  * order (CSR row order, in fixed 1024-arc chunks; sources in list order).
  *
  * Threading: a bc_graph may be used by one host thread at a time for
- * bc_compute / bc_debug_source; bc_batch_submit / bc_poll are thread-safe.
+ * bc_compute / bc_bfs / bc_pagerank / bc_debug_source (calls on one graph
+ * serialise); bc_batch_submit / bc_poll are thread-safe.  Every traversal is
+ * a cooperative launch sized to its share of the GPU: a full-GPU call issued
+ * while serving slots run waits for their blocks, its bounded waits then
+ * limiting how long (BC_E_TIMEOUT past the barrier budget).
  * Error detail: bc_last_error() returns a thread-local message for the last
  * failing call on the calling thread.
  */
@@ -46,7 +52,8 @@ typedef enum {
     BC_W_SIGMA_INEXACT = 2,    /* finished; some path count >= 2^53, so delta used a rounded count */
     BC_E_INVALID_ARG = -1,     /* null pointer, negative size, unknown flag or option value */
     BC_E_INVALID_GRAPH = -2,   /* offsets not monotone / offsets[0] != 0 / offsets[n] != m, index out of
-                                  range, self-loop, duplicate arc, or an arc without its reverse */
+                                  range, self-loop, duplicate arc, or (BC_UNDIRECTED) an arc without its
+                                  reverse */
     BC_E_SOURCE = -3,          /* a source id outside [0, n) */
     BC_E_NOMEM = -4,           /* device allocation failed (allocator hook returned NULL) */
     BC_E_TIMEOUT = -5,         /* a bounded device wait (grid barrier) ran out; results not written */
@@ -185,7 +192,9 @@ bc_status bc_last_trace(const bc_graph* g, int64_t* out, int32_t cap, int32_t* c
 
 /*
  * Autotuner: measures the traversal on a sample of the given sources (host,
- * original ids; up to 512) for batch widths 1/32/64/128, the pull threshold
+ * original ids; the whole list, up to 8192, on graphs of at most 2^24 arcs,
+ * else the first 512) for batch widths 32/64/128 (and 1 for samples of at
+ * most 64 sources), the pull threshold
  * (alpha) and the light-row grouping, by coordinate descent, and records the
  * fastest setting for the graph's size bucket (log2 n, log2 average degree,
  * log2 max/average degree).  Later bc_compute / bc_compute_ex calls on graphs
