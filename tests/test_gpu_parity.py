@@ -510,3 +510,30 @@ def test_pagerank_convergence_repeatability_and_errors(bc):
     for bad in (dict(delta=1.5), dict(beta=-1.0), dict(max_iter=0)):
         with pytest.raises(bc.BCError):
             G.pagerank(**bad)
+
+
+# ----------------------------------------------------------------- depth limit (levels are 16-bit)
+
+def test_deepest_supported_and_too_deep_paths(bc):
+    n = 65000  # depth 64999 from an end: inside the 65534-level limit
+    g = bcgen.path(n)
+    G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(np.array([0], np.int32))
+    assert st == bc.BC_OK
+    want = np.array([0.0] + [float(n - 1 - v) for v in range(1, n - 1)] + [0.0])  # delta_0(v) = n - 1 - v
+    assert np.array_equal(out.cpu().numpy(), want)
+    assert G.stats()["max_levels"] == n
+    deep = bcgen.path(70000)
+    D = bc.Graph(deep.off, deep.adj)
+    with pytest.raises(bc.BCError) as ei:
+        D.compute(np.array([0], np.int32))
+    assert ei.value.status == bc.BC_E_LIMIT
+    # the middle source is only 35000 deep: fine, and the library stays usable
+    s0, nd = 35000, deep.n
+    mid, st = D.compute(np.array([s0], np.int32))
+    v = np.arange(nd, dtype=np.float64)
+    want_mid = np.where(v < s0, v, nd - 1 - v)  # vertices beyond v, seen from s0
+    want_mid[s0] = 0.0
+    assert st == bc.BC_OK and np.array_equal(mid.cpu().numpy(), want_mid)
+    got, _ = G.compute(np.array([n - 1], np.int32))
+    assert np.array_equal(got.cpu().numpy(), want[::-1])
