@@ -59,7 +59,8 @@ typedef enum {
     BC_E_TIMEOUT = -5,         /* a bounded device wait (grid barrier) ran out; results not written */
     BC_E_CUDA = -6,            /* a CUDA runtime call failed; bc_last_error() has the CUDA message */
     BC_E_SIGMA_RANGE = -7,     /* a path count exceeded even the extended range (2^(2^31)) */
-    BC_E_LIMIT = -8            /* a size limit: BFS depth > 65534 levels, or n/m beyond int32 */
+    BC_E_LIMIT = -8,           /* a size limit: BFS depth > 65534 levels, or n/m beyond int32 */
+    BC_E_BUSY = -9             /* bc_graph_destroy: a plan or an unfinished serving job still uses the graph */
 } bc_status;
 
 /* bc_graph_create flags */
@@ -91,6 +92,10 @@ bc_status bc_set_allocator(bc_alloc_fn alloc, bc_free_fn free_fn, void* ctx);
  */
 bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_t n, int64_t m,
                           uint32_t flags, bc_stream_t stream, bc_graph** out);
+/* Frees the graph and its workspaces.  Returns BC_E_BUSY (and frees nothing)
+ * while a bc_many_plan built over it exists or a serving job on it has not
+ * finished; destroy the plan / wait for the jobs first.  Not to be called
+ * concurrently with a bc_compute on the same graph. */
 bc_status bc_graph_destroy(bc_graph* g);
 
 /* Size facts of an ingested graph (any pointer may be NULL). */

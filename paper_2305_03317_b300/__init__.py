@@ -28,6 +28,7 @@ BC_E_TIMEOUT = -5
 BC_E_CUDA = -6
 BC_E_SIGMA_RANGE = -7
 BC_E_LIMIT = -8
+BC_E_BUSY = -9
 
 BC_UNDIRECTED = 1
 BC_INPUT_ON_DEVICE = 2
@@ -206,8 +207,9 @@ class Graph:
         self.n, self.m, self.max_degree, self.n_nonisolated = n_.value, m_.value, md.value, nnz.value
 
     def close(self):
+        """Frees the device graph; BCError(BC_E_BUSY) while a plan or an unfinished job uses it."""
         if getattr(self, "_h", None):
-            load().bc_graph_destroy(self._h)
+            _check(load().bc_graph_destroy(self._h))
             self._h = None
 
     def __del__(self):

@@ -226,6 +226,7 @@ struct bc_graph {
     bc_run_stats last{};
     std::vector<long long> last_trace;             // (tag, t_ns) pairs of the last traced call
     cudaStream_t last_stream = nullptr;
+    std::atomic<int> users{0};  // plans and queued serving jobs that refer to the graph
 };
 
 // ------------------------------------------------------------------ helpers
@@ -812,6 +813,7 @@ void worker_main(int slot) {
                 j->result = r;
                 j->done = true;
                 j->t_done = now;
+                j->g->users--;
             }
             S.running--;
             S.completed += (long long)batch.size();
@@ -1019,6 +1021,8 @@ bc_status bc_graph_create(const int32_t* offsets, const int32_t* indices, int32_
 
 bc_status bc_graph_destroy(bc_graph* g) {
     if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    if (g->users.load() > 0)
+        return fail(BC_E_BUSY, "graph still used by %d plan items or unfinished serving jobs", g->users.load());
     cudaStream_t st = g->last_stream;
     cudaStreamSynchronize(st);
     for (auto& kv : g->ws) kv.second->release(st);
@@ -1432,6 +1436,7 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(e, "plan set-up"));
     bc_status r = many_record(pl.get());
     if (r != BC_OK) return bail(r);
+    for (auto& it : pl->items) it.g->users++;
     *out = pl.release();
     return BC_OK;
 }
@@ -1472,6 +1477,7 @@ bc_status bc_many_run(bc_many_plan* pl, bc_stream_t stream, bc_status* item_stat
 bc_status bc_many_destroy(bc_many_plan* pl) {
     if (!pl) return fail(BC_E_INVALID_ARG, "plan is NULL");
     many_release(pl);
+    for (auto& it : pl->items) it.g->users--;
     delete pl;
     return BC_OK;
 }
@@ -1646,6 +1652,7 @@ bc_status bc_batch_submit(bc_graph* g, const int32_t* sources, int32_t nsrc, dou
             j->t_done = std::chrono::steady_clock::now();
             S.completed++;
         } else {
+            g->users++;
             S.queue.push_back(j);
         }
     }
@@ -1699,6 +1706,7 @@ const char* bc_status_string(bc_status st) {
         case BC_E_CUDA: return "BC_E_CUDA";
         case BC_E_SIGMA_RANGE: return "BC_E_SIGMA_RANGE";
         case BC_E_LIMIT: return "BC_E_LIMIT";
+        case BC_E_BUSY: return "BC_E_BUSY";
     }
     return "BC_UNKNOWN";
 }

@@ -324,6 +324,31 @@ def test_many_graphs_plan_matches_single_calls(bc):
             assert_bc_close(got, want)
     # the 70x70 full grid needs the extended form: its item is redone alone
     assert int(st[len(sizes)]) == bc.BC_W_SIGMA_INEXACT
+    # a graph a plan uses is not freed under it
+    with pytest.raises(bc.BCError) as ei:
+        items[0][0].close()
+    assert ei.value.status == bc.BC_E_BUSY
+    plan.close()
+    items[0][0].close()
+
+
+def test_graph_in_use_by_serving_job_is_not_freed(bc):
+    import torch
+    g = bcgen.rmat(13, 16, 5)
+    G = bc.Graph(g.off, g.adj)
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    src = bcgen.sample_sources(g, 512, 5)
+    job = G.submit(src, out)
+    try:
+        G.close()
+        closed_early = True  # the job finished before the call: allowed
+    except bc.BCError as e:
+        assert e.status == bc.BC_E_BUSY
+        closed_early = False
+    assert job.wait(600000) is not None
+    if not closed_early:
+        G.close()
+    assert_bc_close(out.cpu().numpy(), oracle.bc(g.off, g.adj, src))
 
 
 def test_autotune_changes_speed_not_results(bc, rmat12, tmp_path):
