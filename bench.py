@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--sources", type=int, default=0)
     ap.add_argument("--batch-width", type=int, default=0)
     ap.add_argument("--direction", type=int, default=0)
+    ap.add_argument("--source-order", type=int, default=0,
+                    help="bc_options.source_order: 0 auto, 1 as given, 2 grouped by hub distances")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library heuristics)")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: Poisson arrival rate (req/s)")
@@ -281,7 +283,7 @@ def run_ours(a):
     d_src = torch.from_numpy(src).cuda()
     out = torch.empty(g.n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    opts = dict(batch_width=a.batch_width, direction=a.direction)
+    opts = dict(batch_width=a.batch_width, direction=a.direction, source_order=a.source_order)
     tuned = None
     if a.batch_width == 0 and not a.no_tune:
         t_tune = time.perf_counter()
@@ -357,6 +359,7 @@ def run_ours(a):
         "config": dict(desc, step="one bc_compute over all sources on the resident graph",
                        batch_width=K, batches=nb, levels=stats["max_levels"], pull_levels=stats["pull_levels"],
                        push_levels=stats["push_levels"], teams=stats["teams"], ingest_s=round(ingest_s, 3),
+                       source_grouping_ms=round(stats["order_ms"], 3),
                        autotuned=tuned,
                        l2="inputs larger than L2 (CSR and per-batch state are GBs, L2 126 MB)",
                        parallelism=f"dp{world} (sources sharded per rank)" if world > 1 else "single GPU",

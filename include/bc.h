@@ -126,6 +126,15 @@ typedef struct {
     int32_t dense_min;       /* batch widths >= 32: an arc matching at least this many columns of its row's
                                 batch is summed by the whole warp, one lane per column group, instead of one
                                 (arc, column) pair per lane (0 = auto); results do not depend on it */
+    int32_t source_order;    /* bc_compute: 1 = batches take the sources in the order given; 2 = sources are
+                                first grouped by their distances to the graph's 32 highest-degree vertices
+                                (one extra 32-source forward traversal), so that a batch holds sources that
+                                reach most vertices at the same levels and more arcs are summed column-mapped;
+                                0 = auto: 2 on undirected graphs with at least 256 sources, 4096 non-isolated
+                                vertices and a maximum degree of at least 64 times the mean, else 1.  Only the
+                                order in which per-source dependencies are added to BC changes (rounding); the
+                                grouping depends on the graph and the source list alone, so results stay the
+                                same for every batch width and direction setting */
 } bc_options;
 
 /*
@@ -183,6 +192,8 @@ typedef struct {
     int32_t kernel_launches; /* kernels launched by the call */
     float kernel_ms;         /* device time of the persistent traversal launches (CUDA events on the call's stream) */
     int32_t teams;           /* teams of the last launch */
+    float order_ms;          /* device time of the source-grouping traversal (0 when the sources were not grouped;
+                                not part of kernel_ms) */
 } bc_run_stats;
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 

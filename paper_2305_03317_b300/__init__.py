@@ -47,14 +47,14 @@ class bc_options(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("direction", ctypes.c_int32), ("alpha", ctypes.c_float),
                 ("beta", ctypes.c_float), ("group_vertices", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("barrier_budget", ctypes.c_int64), ("trace", ctypes.c_int32), ("teams", ctypes.c_int32),
-                ("dense_min", ctypes.c_int32)]
+                ("dense_min", ctypes.c_int32), ("source_order", ctypes.c_int32)]
 
 
 class bc_run_stats(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("batches", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("pull_levels", ctypes.c_int32), ("push_levels", ctypes.c_int32), ("ext_batches", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("kernel_ms", ctypes.c_float), ("teams", ctypes.c_int32)]
+                ("kernel_ms", ctypes.c_float), ("teams", ctypes.c_int32), ("order_ms", ctypes.c_float)]
 
 
 class bc_item(ctypes.Structure):
@@ -220,7 +220,8 @@ class Graph:
 
     def compute(self, sources, out=None, stream=None, batch_width: int = 0, direction: int = 0,
                 alpha: float = 0.0, beta: float = 0.0, group_vertices: int = 0, blocks_per_sm: int = 0,
-                barrier_budget: int = 0, trace: bool = False, teams: int = 0, dense_min: int = 0):
+                barrier_budget: int = 0, trace: bool = False, teams: int = 0, dense_min: int = 0,
+                source_order: int = 0):
         """BC over ``sources`` (host numpy or device int32 tensor). Returns (out, status)."""
         import torch
         if out is None:
@@ -229,7 +230,7 @@ class Graph:
             sources = np.ascontiguousarray(sources, dtype=np.int32)
         nsrc = int(sources.shape[0]) if isinstance(sources, np.ndarray) else int(sources.numel())
         opt = bc_options(batch_width, direction, alpha, beta, group_vertices, blocks_per_sm, barrier_budget,
-                         1 if trace else 0, teams, dense_min)
+                         1 if trace else 0, teams, dense_min, source_order)
         s = load().bc_compute_ex(self._h, _ptr(sources) if nsrc else None, nsrc, _ptr(out) if self.n else None,
                                  _stream_handle(stream), ctypes.byref(opt))
         _check(s)

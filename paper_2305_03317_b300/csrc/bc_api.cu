@@ -415,6 +415,7 @@ static bc_status check_opts(const bc_options& o) {
     if (o.group_vertices < 0 || o.group_vertices > 32) return fail(BC_E_INVALID_ARG, "group_vertices must be in [0, 32]");
     if (o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0 || o.teams < 0 || o.dense_min < 0)
         return fail(BC_E_INVALID_ARG, "negative option value");
+    if (o.source_order < 0 || o.source_order > 2) return fail(BC_E_INVALID_ARG, "source_order must be 0, 1 or 2");
     return BC_OK;
 }
 
@@ -1058,6 +1059,82 @@ bc_status bc_graph_export(const bc_graph* g, int32_t* perm, int32_t* offsets, in
     return BC_OK;
 }
 
+// Source grouping (bc_options.source_order).  Two sources at the same
+// distances from the graph's hubs reach most vertices at the same levels, so
+// in one batch their columns match the same arcs: more arcs reach the
+// column-mapped threshold and fewer single (arc, column) pairs remain.  The
+// key of a source is its distance vector to the 32 highest-degree vertices
+// (relabelled ids 0..31), taken from one forward-only traversal of those 32
+// vertices (undirected: d(h, s) = d(s, h)); sources are stably sorted by it,
+// nearest-hub distance first.  Levels are exact integers, so the order does
+// not depend on the batch width that computed them.
+static bool want_grouping(const bc_graph* g, int nsrc, const bc_options& o) {
+    if (o.source_order == 1 || g->directed || g->n_nz < 32) return false;
+    if (o.source_order == 2) return true;
+    return nsrc >= 256 && g->n_nz >= 4096 && (double)g->max_deg * g->n_nz >= 64.0 * (double)g->m;
+}
+
+static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_src, int nsrc, cudaStream_t st,
+                               DevBuf& out, bc_run_stats* acc) {
+    constexpr int L = 32;
+    int Kw = K;
+    if (K < L) {  // the plain per-source width: a 32-wide workspace of its own
+        auto& slot = g->ws[L];
+        if (!slot) slot.reset(new Workspace());
+        w = slot.get();
+        Kw = L;
+    }
+    if (!buf_ensure(w->bc, sizeof(double) * (size_t)g->n, st)) return fail(BC_E_NOMEM, "output buffer");
+    bc_options o;
+    memset(&o, 0, sizeof o);
+    o.batch_width = Kw;
+    std::vector<double*> jb{(double*)w->bc.p};
+    bc_run_stats rs{};
+    int kused = 0, levels = 0;
+    bool ext = false;
+    bc_status r = run_jobs(g, w, (const int*)g->perm.p, L, o, 1, jb, nullptr, true, st, &rs, &kused, &ext, &levels);
+    if (r < 0) return r;
+    DevBuf lvl, keys;
+    std::vector<unsigned short> hk((size_t)nsrc * L);
+    std::vector<int> hs(nsrc);
+    auto release = [&]() {
+        buf_release(lvl, st);
+        buf_release(keys, st);
+    };
+    if (!buf_ensure(lvl, sizeof(unsigned short) * (size_t)g->n * Kw, st) ||
+        !buf_ensure(keys, sizeof(unsigned short) * hk.size(), st)) {
+        release();
+        return fail(BC_E_NOMEM, "grouping buffers");
+    }
+    KParams p = make_params(g, w, 1, o, ext, 1);
+    cudaError_t e = launch_level_keys(p, kused, levels, L, (unsigned short*)lvl.p, g->n, d_src, nsrc,
+                                      (const int*)g->inv.p, (unsigned short*)keys.p, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hk.data(), keys.p, sizeof(unsigned short) * hk.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), d_src, sizeof(int) * (size_t)nsrc, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(e, "source grouping");
+    std::vector<int> idx(nsrc);
+    for (int i = 0; i < nsrc; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        const unsigned short* ka = &hk[(size_t)a * L];
+        const unsigned short* kb = &hk[(size_t)b * L];
+        for (int j = 0; j < L; ++j)
+            if (ka[j] != kb[j]) return ka[j] < kb[j];
+        return false;
+    });
+    std::vector<int> grouped(nsrc);
+    for (int i = 0; i < nsrc; ++i) grouped[i] = hs[idx[i]];
+    if (!buf_ensure(out, sizeof(int) * (size_t)nsrc, st)) return fail(BC_E_NOMEM, "source buffer");
+    e = cudaMemcpyAsync(out.p, grouped.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "source copy");
+    acc->kernel_launches += rs.kernel_launches + 2;
+    acc->kernel_ms += rs.kernel_ms;
+    return BC_OK;
+}
+
 bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream,
                         const bc_options* opt) {
     if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
@@ -1103,9 +1180,22 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
         buf_release(tmp, st);
         return fail(BC_E_NOMEM, "output buffer");
     }
+    bc_run_stats pre{};
+    DevBuf grouped;
+    if (want_grouping(g, nsrc, o)) {
+        bc_status gr = group_sources(g, w, K, d_src, nsrc, st, grouped, &pre);
+        if (gr < 0) {
+            buf_release(tmp, st);
+            buf_release(grouped, st);
+            return gr;
+        }
+        d_src = (const int*)grouped.p;
+    }
     std::vector<double*> jb{(double*)w->bc.p};
     bc_run_stats stats{};
     bc_status r = run_jobs(g, w, d_src, nsrc, o, 1, jb, nullptr, false, st, &stats, nullptr, nullptr, nullptr);
+    stats.kernel_launches += pre.kernel_launches;
+    stats.order_ms = pre.kernel_ms;
     if (r >= 0) {
         cudaError_t e = launch_unpermute((const double*)w->bc.p, (const int*)g->inv.p, out_bc, g->n, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1114,6 +1204,7 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
         g->last = stats;
     }
     buf_release(tmp, st);
+    buf_release(grouped, st);
     return r;
 }
 

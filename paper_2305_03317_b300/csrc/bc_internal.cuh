@@ -160,6 +160,10 @@ cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, in
                                int nbatch, int* bad, cudaStream_t st);
 cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, const int* inv, long long n,
                                unsigned short* lvl, int* level_out, double* sig_out, int* exp_out, cudaStream_t st);
+// Level table of a forward-only batch, then the levels of columns [0, L) at
+// each of nsrc sources (original ids): keys[nsrc][L], 0xFFFF = unreached.
+cudaError_t launch_level_keys(const KParams& p, int K, int levels, int L, unsigned short* lvl, long long n,
+                              const int* src, int nsrc, const int* inv, unsigned short* keys, cudaStream_t st);
 cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
                                  int* sige_rel, cudaStream_t st);
 

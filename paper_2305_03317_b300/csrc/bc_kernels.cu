@@ -1805,6 +1805,32 @@ cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, c
     return cudaGetLastError();
 }
 
+// Source grouping keys: keys[i][j] = level of source i (original id src[i])
+// in the BFS of column j, read from the relabelled level table lvl[n][K];
+// 0xFFFF for unreached vertices and for ids outside [0, n) (the traversal's
+// own source check reports those).
+__global__ void k_level_keys(const unsigned short* __restrict__ lvl, int K, int L, const int* __restrict__ src,
+                             int nsrc, const int* __restrict__ inv, long long n, unsigned short* keys) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nsrc * L) return;
+    const int s = src[i / L], j = (int)(i % L);
+    keys[i] = (s >= 0 && s < n) ? lvl[(size_t)inv[s] * K + j] : (unsigned short)0xFFFFu;
+}
+
+cudaError_t launch_level_keys(const KParams& p, int K, int levels, int L, unsigned short* lvl, long long n,
+                              const int* src, int nsrc, const int* inv, unsigned short* keys, cudaStream_t st) {
+    if (n <= 0 || nsrc <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(lvl, 0xFF, sizeof(unsigned short) * (size_t)n * (size_t)K, st);
+    if (e != cudaSuccess) return e;
+    if (levels > 0) k_bfs_levels<<<8 * (sms > 0 ? sms : 1), 256, 0, st>>>(p, K, levels, lvl);
+    const long long tot = (long long)nsrc * L;
+    k_level_keys<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(lvl, K, L, src, nsrc, inv, n, keys);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
                                  int* sige_rel, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;

@@ -154,6 +154,33 @@ def test_rmat12_bitwise_across_widths_and_directions(bc, rmat12):
         assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
 
 
+def test_source_grouping_order_and_widths(bc, rmat12):
+    g, _ = rmat12
+    src = bcgen.sample_sources(g, 300, 4)
+    want = oracle.bc(g.off, g.adj, src)
+    ref, _, st = gpu_bc(bc, g, src, batch_width=64, source_order=2)
+    assert st["order_ms"] > 0
+    assert_bc_close(ref, want)
+    # the grouping itself, from oracle levels: stable sort of the sources by their
+    # distances to the 32 first relabelled (highest-degree) vertices, nearest first;
+    # BC summed in that order, as given, must be the same bits
+    G = bc.Graph(g.off, g.adj)
+    perm = G.export()[0]
+    G.close()
+    lv = np.stack([oracle.source_detail(g.off, g.adj, int(h))["level"][: g.n] for h in perm[:32]])  # [32][n]
+    keys = np.where(lv < 0, 0xFFFF, lv)[:, src]  # [32][nsrc]
+    order = np.lexsort(tuple(keys[j] for j in range(31, -1, -1)))
+    regrouped, _, st1 = gpu_bc(bc, g, src[order], batch_width=64, source_order=1)
+    assert st1["order_ms"] == 0
+    assert np.array_equal(regrouped.view(np.uint64), ref.view(np.uint64))
+    for kw in [dict(batch_width=1), dict(batch_width=32), dict(batch_width=128), dict(batch_width=64, direction=2),
+               dict(batch_width=32, teams=3)]:
+        got, _, _ = gpu_bc(bc, g, src, source_order=2, **kw)
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
+    with pytest.raises(bc.BCError):
+        gpu_bc(bc, g, src, source_order=3)
+
+
 def test_duplicate_sources_count_twice(bc):
     g = bcgen.rmat(10, 6, 3)
     src = np.array([5, 9, 5, 5, 100, 9], np.int32)
