@@ -130,8 +130,8 @@ typedef struct {
                                 first grouped by their distances to the graph's 32 highest-degree vertices
                                 (one extra 32-source forward traversal), so that a batch holds sources that
                                 reach most vertices at the same levels and more arcs are summed column-mapped;
-                                0 = auto: 2 on undirected graphs with at least 256 sources, 4096 non-isolated
-                                vertices and a maximum degree of at least 64 times the mean, else 1.  Only the
+                                0 = auto: 2 on undirected graphs with at least 256 sources, 2048 non-isolated
+                                vertices and a maximum degree of at least 16 times the mean, else 1.  Only the
                                 order in which per-source dependencies are added to BC changes (rounding); the
                                 grouping depends on the graph and the source list alone, so results stay the
                                 same for every batch width and direction setting */

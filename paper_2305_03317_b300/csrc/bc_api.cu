@@ -1071,7 +1071,7 @@ bc_status bc_graph_export(const bc_graph* g, int32_t* perm, int32_t* offsets, in
 static bool want_grouping(const bc_graph* g, int nsrc, const bc_options& o) {
     if (o.source_order == 1 || g->directed || g->n_nz < 32) return false;
     if (o.source_order == 2) return true;
-    return nsrc >= 256 && g->n_nz >= 4096 && (double)g->max_deg * g->n_nz >= 64.0 * (double)g->m;
+    return nsrc >= 256 && g->n_nz >= 2048 && (double)g->max_deg * g->n_nz >= 16.0 * (double)g->m;
 }
 
 static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_src, int nsrc, cudaStream_t st,
@@ -1115,15 +1115,46 @@ static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_sr
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     release();
     if (e != cudaSuccess) return cuda_fail(e, "source grouping");
-    std::vector<int> idx(nsrc);
+    // levels are below `levels`; 0xFFFF (unreached) ranks after them
+    std::vector<int> idx(nsrc), nxt(nsrc), cnt((size_t)levels + 2);
     for (int i = 0; i < nsrc; ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
-        const unsigned short* ka = &hk[(size_t)a * L];
-        const unsigned short* kb = &hk[(size_t)b * L];
-        for (int j = 0; j < L; ++j)
-            if (ka[j] != kb[j]) return ka[j] < kb[j];
-        return false;
-    });
+    auto digit = [&](int i, int j) {
+        const unsigned short v = hk[(size_t)i * L + j];
+        return v == 0xFFFFu || v > levels ? levels + 1 : (int)v;
+    };
+    if (levels + 1 < 16) {
+        // shallow graphs: 4 bits per landmark, the 32 digits packed most
+        // significant first into two words; ties keep the given order
+        struct Packed {
+            unsigned long long hi, lo;
+            int i;
+        };
+        std::vector<Packed> pk(nsrc);
+        for (int i = 0; i < nsrc; ++i) {
+            unsigned long long hi = 0, lo = 0;
+            for (int j = 0; j < 16; ++j) hi = hi << 4 | (unsigned long long)digit(i, j);
+            for (int j = 16; j < L; ++j) lo = lo << 4 | (unsigned long long)digit(i, j);
+            pk[i] = Packed{hi, lo, i};
+        }
+        std::sort(pk.begin(), pk.end(), [](const Packed& a, const Packed& b) {
+            if (a.hi != b.hi) return a.hi < b.hi;
+            if (a.lo != b.lo) return a.lo < b.lo;
+            return a.i < b.i;
+        });
+        for (int i = 0; i < nsrc; ++i) idx[i] = pk[i].i;
+    }
+    // deeper graphs: stable LSD counting sort, least significant landmark first
+    for (int j = L - 1; levels + 1 >= 16 && j >= 0; --j) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int i = 0; i < nsrc; ++i) cnt[digit(idx[i], j)]++;
+        for (int d = 0, run = 0; d < (int)cnt.size(); ++d) {
+            const int c = cnt[d];
+            cnt[d] = run;
+            run += c;
+        }
+        for (int i = 0; i < nsrc; ++i) nxt[cnt[digit(idx[i], j)]++] = idx[i];
+        idx.swap(nxt);
+    }
     std::vector<int> grouped(nsrc);
     for (int i = 0; i < nsrc; ++i) grouped[i] = hs[idx[i]];
     if (!buf_ensure(out, sizeof(int) * (size_t)nsrc, st)) return fail(BC_E_NOMEM, "source buffer");

@@ -164,12 +164,11 @@ def test_source_grouping_order_and_widths(bc, rmat12):
     # the grouping itself, from oracle levels: stable sort of the sources by their
     # distances to the 32 first relabelled (highest-degree) vertices, nearest first;
     # BC summed in that order, as given, must be the same bits
+    from grouping import grouped_order
     G = bc.Graph(g.off, g.adj)
     perm = G.export()[0]
     G.close()
-    lv = np.stack([oracle.source_detail(g.off, g.adj, int(h))["level"][: g.n] for h in perm[:32]])  # [32][n]
-    keys = np.where(lv < 0, 0xFFFF, lv)[:, src]  # [32][nsrc]
-    order = np.lexsort(tuple(keys[j] for j in range(31, -1, -1)))
+    order = grouped_order(g, perm, src)
     regrouped, _, st1 = gpu_bc(bc, g, src[order], batch_width=64, source_order=1)
     assert st1["order_ms"] == 0
     assert np.array_equal(regrouped.view(np.uint64), ref.view(np.uint64))
@@ -179,6 +178,24 @@ def test_source_grouping_order_and_widths(bc, rmat12):
         assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
     with pytest.raises(bc.BCError):
         gpu_bc(bc, g, src, source_order=3)
+    # auto: grouped on skewed undirected graphs with >= 256 sources, else as given
+    _, _, st = gpu_bc(bc, g, src)
+    assert st["order_ms"] > 0
+    _, _, st = gpu_bc(bc, g, src[:255])
+    assert st["order_ms"] == 0
+    grid = bcgen.grid(60, 60, 0.0)
+    gsrc = bcgen.sample_sources(grid, 300, 1)
+    plain, _, st = gpu_bc(bc, grid, gsrc)
+    assert st["order_ms"] == 0
+    # a deep graph (more than 15 levels) takes the other sort of the grouping
+    G = bc.Graph(grid.off, grid.adj)
+    gorder = grouped_order(grid, G.export()[0], gsrc)
+    G.close()
+    got, _, st = gpu_bc(bc, grid, gsrc, source_order=2, batch_width=32)
+    assert st["order_ms"] > 0 and st["max_levels"] > 16
+    again, _, _ = gpu_bc(bc, grid, gsrc[gorder], source_order=1, batch_width=32)
+    assert np.array_equal(got.view(np.uint64), again.view(np.uint64))
+    assert_bc_close(got, plain)
 
 
 def test_duplicate_sources_count_twice(bc):
