@@ -584,7 +584,7 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
         RunOut ro;
         bc_status r = run_core(g, w, d_src, nsrc, K, team_blocks, o, ext, job_bc, col_job, forward_only, st, &ro);
         if (r != BC_OK) return r;
-        s.kernel_launches += 2;
+        s.kernel_launches += 3;  // source mapping, control reset, traversal
         s.kernel_ms += ro.kernel_ms;
         s.max_levels = ro.ctl.max_levels;
         s.pull_levels += ro.ctl.pull_levels;
@@ -916,7 +916,7 @@ static bc_status many_record(bc_many_plan* pl) {
             (e = launch_unpermute((const double*)w->bc.p, (const int*)g->inv.p, it.out, g->n, st)) != cudaSuccess) {
             r = cuda_fail(e, "recording the many-graph sequence");
         }
-        launches += 4;
+        launches += 5;  // control reset, source mapping, traversal, status, unpermute
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(st, &graph);
@@ -1161,7 +1161,7 @@ static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_sr
     e = cudaMemcpyAsync(out.p, grouped.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "source copy");
-    acc->kernel_launches += rs.kernel_launches + 2;
+    acc->kernel_launches += rs.kernel_launches + (levels > 0 ? 2 : 1);  // level table, keys
     acc->kernel_ms += rs.kernel_ms;
     return BC_OK;
 }
@@ -1292,7 +1292,7 @@ bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* lev
         inexact |= r == BC_W_SIGMA_INEXACT;
         total.batch_width = kused;
         total.batches += 1;
-        total.kernel_launches += stats.kernel_launches + 1;
+        total.kernel_launches += stats.kernel_launches + (levels > 0 ? 2 : 1);  // level table, rows
         total.kernel_ms += stats.kernel_ms;
         total.max_levels = std::max(total.max_levels, levels);
         total.pull_levels += stats.pull_levels;
