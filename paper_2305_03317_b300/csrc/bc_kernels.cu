@@ -494,18 +494,18 @@ __device__ __forceinline__ void gather_step(const KParams& p, WarpSmem<K, EXT>& 
                 if (r0 + 32 * i >= cnt) break;
                 if constexpr (!ORDERED) {
                     // integer path counts, order-free: two 32-bit shared atomics (the
-                    // low word's carry goes into the high word).  A term below
-                    // 2^sum_bits cannot make a sum carry out of 64 bits (sum_bits
-                    // leaves room for the longest sum: 1024-arc chunks, or whole rows
-                    // where rows are not chunked); a larger term sends the batch to
-                    // the extended form.
+                    // low word's carry goes into the high word).  Terms are below
+                    // 2^sum_bits, which leaves room for the longest sum (1024-arc
+                    // chunks, or whole rows where rows are not chunked): a path
+                    // count at or above that bound sends the batch to the extended
+                    // form when it is written (write_columns), before any sum
+                    // takes it as a term.
                     if (valid[i]) {
                         unsigned int* a32 = reinterpret_cast<unsigned int*>(&ws.acc[slot[i]]);
                         const unsigned int xl = (unsigned int)x[i], xh = (unsigned int)(x[i] >> 32);
                         const unsigned int old = atomicAdd(a32, xl);
                         const unsigned int cy = (old + xl < old) ? 1u : 0u;
                         if (xh | cy) atomicAdd(a32 + 1, xh + cy);
-                        carry |= (x[i] >> p.sum_bits) != 0ull;
                     }
                 } else {
                     // ordered: lanes that share a slot add in lane (CSR) order.  A
@@ -664,7 +664,7 @@ __device__ __forceinline__ void write_columns(const KParams& p, const WarpSmem<K
     }
     const int Q = __shfl_sync(FULL_MASK, incl, 31);
     const int ex = incl - cnt;  // exclusive prefix of owner `lane`
-    bool inexact = false;
+    bool inexact = false, big = false;
     for (int r = 0; r < Q; r += 32) {
         const int q = r + lane;
         // owner: the largest o < ng with exclusive prefix <= q
@@ -690,6 +690,7 @@ __device__ __forceinline__ void write_columns(const KParams& p, const WarpSmem<K
                     p.sig_e[idx] = xe;
                 } else {
                     p.rho[idx] = __drcp_rn((double)x);  // 1 / sigma, used by the reverse sweep
+                    big |= (x >> p.sum_bits) != 0ull;  // a term too large for the plain sums
                 }
                 inexact |= (xe > 0 || x >= (1ull << 53));
             } else {
@@ -712,6 +713,7 @@ __device__ __forceinline__ void write_columns(const KParams& p, const WarpSmem<K
         }
     }
     if (DIR == FWD && __any_sync(FULL_MASK, inexact) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
+    if (DIR == FWD && __any_sync(FULL_MASK, big) && lane == 0) atomicOr(&p.ctl->flags, BST_NEED_EXT);
 }
 
 // Owner-level forward bookkeeping (lane o handles owner o): mark the newly

@@ -198,6 +198,29 @@ def test_source_grouping_order_and_widths(bc, rmat12):
     assert_bc_close(got, plain)
 
 
+def test_large_terms_in_column_mapped_sums_take_extended_form(bc):
+    # s, then 16 layers of 16 vertices, consecutive layers complete bipartite:
+    # sigma of layer i is 16^(i-1), so the last layer sums terms of 2^56.  128
+    # copies of s match every column of every arc: all forward sums run
+    # column-mapped, and a term >= 2^54 there must send the batch to the
+    # extended form as it does in the pair path (whose 32-bit atomics may share
+    # a sum with the column-mapped path).
+    a, layers = 16, 16
+    n = 1 + a * layers
+    u, v = [], []
+    for j in range(a):
+        u.append(0); v.append(1 + j)
+    for i in range(layers - 1):
+        for j in range(a):
+            for k in range(a):
+                u.append(1 + i * a + j); v.append(1 + (i + 1) * a + k)
+    g = bcgen.edges_to_csr(n, np.array(u), np.array(v), "layers16x16")
+    src = np.zeros(128, np.int32)
+    got, st, stats = gpu_bc(bc, g, src, batch_width=128, source_order=1)
+    assert stats["ext_batches"] == 1 and st == bc.BC_W_SIGMA_INEXACT
+    assert_bc_close(got, 128 * oracle.bc_ld(g.off, g.adj, src[:1]).astype(np.float64))
+
+
 def test_duplicate_sources_count_twice(bc):
     g = bcgen.rmat(10, 6, 3)
     src = np.array([5, 9, 5, 5, 100, 9], np.int32)
