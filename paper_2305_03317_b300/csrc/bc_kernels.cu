@@ -150,31 +150,6 @@ __device__ __forceinline__ void store_terms(unsigned long long* p, const unsigne
     }
 }
 
-// Asynchronous global -> shared copies: a warp keeps several rows' loads in
-// flight without holding them in registers.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// W consecutive 8-byte terms copied asynchronously (16-byte aligned when W >= 2)
-template <int W>
-__device__ __forceinline__ void stage_terms(unsigned long long* dst, const unsigned long long* src) {
-    if constexpr (W == 1) {
-        cp_async8(dst, src);
-    } else {
-#pragma unroll
-        for (int i = 0; i < W; i += 2) cp_async16(dst + i, src + i);
-    }
-}
-
 template <int W>
 __device__ __forceinline__ uint32_t pick(const uint32_t (&m)[W], int t) {
     uint32_t x = m[0];
@@ -267,7 +242,7 @@ struct __align__(16) WarpSmem {
     int sv[32];                   // neighbour of each arc of the current step
     int so[32];                   // owner of each arc of the current step
     uint32_t fw[32][W];           // matched columns of each arc of the step; slot tags in the rounds
-    alignas(16) uint32_t pr[Geo<K>::PCAP];  // expanded pairs: arc << 16 | column; staged dense terms
+    uint32_t pr[Geo<K>::PCAP];    // expanded pairs: arc << 16 | column
     int av[32];                   // append staging (pull): vertex
     uint32_t am[32][W];           // append staging: mask
     long long adeg;               // append staging: degree sum
@@ -277,9 +252,8 @@ using WS128 = WarpSmem<128, false>;
 using WS64 = WarpSmem<64, false>;
 using WS32 = WarpSmem<32, false>;
 static_assert(sizeof(WS128) % 16 == 0 && offsetof(WS128, acc) % 16 == 0 && sizeof(WS64) % 16 == 0 &&
-              offsetof(WS64, acc) % 16 == 0 && sizeof(WS32) % 16 == 0 && offsetof(WS32, acc) % 16 == 0 &&
-              offsetof(WS128, pr) % 16 == 0 && offsetof(WS64, pr) % 16 == 0 && offsetof(WS32, pr) % 16 == 0,
-              "accumulator rows and the staging buffer need 16-byte alignment");
+              offsetof(WS64, acc) % 16 == 0 && sizeof(WS32) % 16 == 0 && offsetof(WS32, acc) % 16 == 0,
+              "accumulator rows need 16-byte alignment");
 
 // Fill the owner table (lane i describes owner i < ng) and return the arc total.
 template <int K, bool EXT>
@@ -317,47 +291,45 @@ template <int K, bool EXT, int DIR>
 __device__ __forceinline__ void dense_arcs(WarpSmem<K, EXT>& ws, unsigned int db,
                                            const unsigned long long* __restrict__ termv, bool& carry) {
     constexpr int W = Geo<K>::W;
-    // The pair buffer is idle here: it stages NB arcs' terms, NB - 1 in flight
-    // while the oldest is added (a lane copies and later reads only its own
-    // columns, so its own cp.async waits suffice).
-    constexpr int NB = (Geo<K>::PCAP * (int)sizeof(uint32_t)) / (K * 8);
-    static_assert(K >= 32 && !EXT && NB >= 2, "column-mapped arcs need K >= 32 and the plain form");
-    unsigned long long* stage = reinterpret_cast<unsigned long long*>(ws.pr);
+    static_assert(K >= 32 && !EXT, "column-mapped arcs need K >= 32 and the plain form");
+    // Each lane reads its own W columns of every arc straight into registers,
+    // two arcs ahead of the one being added (three register buffers).
     const int lane = lane_id();
     const int word = (W * lane) >> 5;
-    unsigned int di = db;  // arcs still to issue (taken in CSR order)
-    int seq = 0;           // arcs issued so far
-    auto issue = [&]() {
+    unsigned int di = db;  // arcs still to read (taken in CSR order)
+    auto fetch = [&](unsigned long long (&x)[W]) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) x[i] = 0ull;
         if (di) {
             const int j = __ffs(di) - 1;
             di &= di - 1;
-            if (lane_field<W>(ws.fw[j][word], lane))
-                stage_terms<W>(stage + (seq % NB) * K + W * lane, termv + (size_t)ws.sv[j] * K + W * lane);
+            if (lane_field<W>(ws.fw[j][word], lane)) load_terms<W>(termv + (size_t)ws.sv[j] * K + W * lane, x);
         }
-        cp_async_commit();  // one group per slot, possibly empty
-        ++seq;
     };
-#pragma unroll
-    for (int i = 0; i < NB - 1; ++i) issue();
-    for (int acc_seq = 0; db; ++acc_seq) {
-        issue();
-        cp_async_wait<NB - 1>();  // the oldest staged arc has landed
+    unsigned long long xa[W], xb[W], xc[W];
+    fetch(xa);
+    fetch(xb);
+    while (db) {
+        fetch(xc);
         const int j = __ffs(db) - 1;
         db &= db - 1;
         const uint32_t b = lane_field<W>(ws.fw[j][word], lane);
         if (b) {
-            unsigned long long x[W], r[W];
-            load_terms<W>(stage + (acc_seq % NB) * K + W * lane, x);
+            unsigned long long r[W];
             unsigned long long* a = &ws.acc[ws.so[j] * K + W * lane];
             load_terms<W>(a, r);
             int e = 0;
 #pragma unroll
             for (int i = 0; i < W; ++i)
-                if ((b >> i) & 1u) acc_add<false, DIR>(r[i], e, x[i], 0, carry);
+                if ((b >> i) & 1u) acc_add<false, DIR>(r[i], e, xa[i], 0, carry);
             store_terms<W>(a, r);
         }
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            xa[i] = xb[i];
+            xb[i] = xc[i];
+        }
     }
-    cp_async_wait<0>();
     __syncwarp();
 }
 
