@@ -1075,7 +1075,7 @@ static bool want_grouping(const bc_graph* g, int nsrc, const bc_options& o) {
 }
 
 static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_src, int nsrc, cudaStream_t st,
-                               DevBuf& out, bc_run_stats* acc) {
+                               DevBuf& out, bc_run_stats* acc, std::vector<int>* host_out = nullptr) {
     constexpr int L = 32;
     int Kw = K;
     if (K < L) {  // the plain per-source width: a 32-wide workspace of its own
@@ -1157,6 +1157,7 @@ static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_sr
     }
     std::vector<int> grouped(nsrc);
     for (int i = 0; i < nsrc; ++i) grouped[i] = hs[idx[i]];
+    if (host_out) *host_out = grouped;
     if (!buf_ensure(out, sizeof(int) * (size_t)nsrc, st)) return fail(BC_E_NOMEM, "source buffer");
     e = cudaMemcpyAsync(out.p, grouped.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1501,6 +1502,25 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
         ManyItem it;
         it.g = g;
         it.src.assign(x.sources, x.sources + x.nsrc);
+        if (want_grouping(g, x.nsrc, o)) {
+            // the order bc_compute would use, fixed once here (a 32-wide
+            // workspace of its own, freed right after)
+            Workspace tmp;
+            DevBuf dsrc, grouped;
+            bc_run_stats gs{};
+            r = buf_ensure(dsrc, sizeof(int) * (size_t)x.nsrc, ust) ? BC_OK : fail(BC_E_NOMEM, "source buffer");
+            cudaError_t e = cudaSuccess;
+            if (r == BC_OK &&
+                (e = cudaMemcpyAsync(dsrc.p, x.sources, sizeof(int) * (size_t)x.nsrc, cudaMemcpyHostToDevice, ust)) !=
+                    cudaSuccess)
+                r = cuda_fail(e, "source copy");
+            if (r == BC_OK) r = group_sources(g, &tmp, 32, (const int*)dsrc.p, x.nsrc, ust, grouped, &gs, &it.src);
+            cudaStreamSynchronize(ust);
+            tmp.release(ust);
+            buf_release(dsrc, ust);
+            buf_release(grouped, ust);
+            if (r != BC_OK) return r;
+        }
         it.out = x.out_bc;
         it.K = choose_width(g->n, x.nsrc, o.batch_width);
         it.nbatch = (x.nsrc + it.K - 1) / it.K;

@@ -369,10 +369,12 @@ def test_many_graphs_plan_matches_single_calls(bc):
     import torch
     sizes = [(300, 6, 11), (1000, 12, 12), (2500, 20, 13), (4000, 8, 14), (700, 31, 15), (5000, 16, 16)]
     graphs = [bcgen.rmat_n(n, ef, seed) for n, ef, seed in sizes] + [bcgen.grid(70, 70, 0.0),
-                                                                      bcgen.star(2500)]
+                                                                      bcgen.star(2500), bcgen.rmat_n(6000, 16, 17)]
     items, refs, oracles = [], [], []
     for i, g in enumerate(graphs):
-        src = np.arange(g.n, dtype=np.int32) if g.n <= 1200 else bcgen.sample_sources(g, 100, 30 + i)
+        # the last item (400 sources on a skewed graph) has its sources grouped, as bc_compute groups them
+        nsrc = 400 if i == len(graphs) - 1 else 100
+        src = np.arange(g.n, dtype=np.int32) if g.n <= 1200 else bcgen.sample_sources(g, nsrc, 30 + i)
         G = bc.Graph(g.off, g.adj)
         out = torch.empty(g.n, dtype=torch.float64, device="cuda")
         items.append((G, src, out))
@@ -391,6 +393,9 @@ def test_many_graphs_plan_matches_single_calls(bc):
             assert_bc_close(got, want)
     # the 70x70 full grid needs the extended form: its item is redone alone
     assert int(st[len(sizes)]) == bc.BC_W_SIGMA_INEXACT
+    G, src, _ = items[-1]
+    G.compute(src)
+    assert G.stats()["order_ms"] > 0  # the single call grouped the same sources
     # a graph a plan uses is not freed under it
     with pytest.raises(bc.BCError) as ei:
         items[0][0].close()
