@@ -126,8 +126,9 @@ typedef struct {
     int32_t dense_min;       /* batch widths >= 32: an arc matching at least this many columns of its row's
                                 batch is summed by the whole warp, one lane per column group, instead of one
                                 (arc, column) pair per lane (0 = auto); results do not depend on it */
-    int32_t source_order;    /* bc_compute, bc_many_create (fixed once at creation): 1 = batches take the
-                                sources in the order given; 2 = sources are
+    int32_t source_order;    /* bc_compute, bc_many_create (fixed once at creation) and, with the automatic
+                                rule, each serving job: 1 = batches take the sources in the order given; 2 =
+                                sources are
                                 first grouped by their distances to the graph's 32 highest-degree vertices
                                 (one extra 32-source forward traversal), so that a batch holds sources that
                                 reach most vertices at the same levels and more arcs are summed column-mapped;

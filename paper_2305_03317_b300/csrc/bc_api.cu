@@ -670,6 +670,13 @@ static void apply_tuning(const bc_graph* g, int nsrc, bc_options& o) {
 // take queued jobs in arrival order as soon as a worker is free and the
 // device-memory budget admits its workspace; small jobs queued on the same
 // graph are packed into the same traversal (their columns side by side).
+// source grouping (defined with the C entry points below, used by the serving workers)
+extern "C" {
+static bool want_grouping(const bc_graph* g, int nsrc, const bc_options& o);
+static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_src, int nsrc, cudaStream_t st,
+                               DevBuf& out, bc_run_stats* acc, std::vector<int>* host_out);
+}
+
 namespace {
 
 struct Job {
@@ -679,6 +686,7 @@ struct Job {
     double* out = nullptr;
     bc_status result = BC_PENDING;
     bool done = false;
+    bool grouped = false;  // src already in the grouped order (source_order)
     std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
@@ -768,24 +776,46 @@ void worker_main(int slot) {
         }
         // run the packed jobs
         bc_graph* g = batch[0]->g;
+        int nsrc = 0;
+        for (auto& j : batch) nsrc += (int)j->src.size();
+        bc_options o;
+        memset(&o, 0, sizeof o);
+        apply_tuning(g, nsrc, o);
+        const int K = choose_width(g->n, nsrc, o.batch_width);
+        bc_status r = BC_OK;
+        // each job's sources in the order bc_compute would take them, so that a
+        // job's result is the same alone, packed or computed directly
+        for (auto& j : batch) {
+            if (r != BC_OK || j->grouped || !want_grouping(g, (int)j->src.size(), o)) continue;
+            const int n1 = (int)j->src.size();
+            DevBuf tmp;
+            if (!buf_ensure(dsrc, sizeof(int) * (size_t)n1, st)) {
+                r = fail(BC_E_NOMEM, "serving buffers");
+                break;
+            }
+            cudaError_t e = cudaMemcpyAsync(dsrc.p, j->src.data(), sizeof(int) * (size_t)n1, cudaMemcpyHostToDevice, st);
+            bc_run_stats gs{};
+            std::vector<int> grouped;
+            r = e == cudaSuccess ? group_sources(g, &ws, K >= 32 ? K : 32, (const int*)dsrc.p, n1, st, tmp, &gs, &grouped)
+                                 : cuda_fail(e, "source copy");
+            buf_release(tmp, st);
+            if (r == BC_OK) {
+                j->src.swap(grouped);
+                j->grouped = true;
+            }
+        }
         std::vector<int> all;
         std::vector<int> owner;  // job index per source
         for (size_t j = 0; j < batch.size(); ++j) {
             all.insert(all.end(), batch[j]->src.begin(), batch[j]->src.end());
             owner.insert(owner.end(), batch[j]->src.size(), (int)j);
         }
-        const int nsrc = (int)all.size();
-        bc_options o;
-        memset(&o, 0, sizeof o);
-        apply_tuning(g, nsrc, o);
-        const int K = choose_width(g->n, nsrc, o.batch_width);
         const int nbatch = (nsrc + K - 1) / K;
         std::vector<int> col_job((size_t)nbatch * K, 0);
         for (int i = 0; i < nbatch * K; ++i) col_job[i] = i < nsrc ? owner[i] : (int)batch.size() - 1;
-        bc_status r = BC_OK;
         const size_t nn = (size_t)(g->n > 0 ? g->n : 1);
-        if (!buf_ensure(dsrc, sizeof(int) * (size_t)nsrc, st) ||
-            !buf_ensure(jobbufs, sizeof(double) * nn * batch.size(), st)) {
+        if (r == BC_OK && (!buf_ensure(dsrc, sizeof(int) * (size_t)nsrc, st) ||
+                           !buf_ensure(jobbufs, sizeof(double) * nn * batch.size(), st))) {
             r = fail(BC_E_NOMEM, "serving buffers");
         }
         if (r == BC_OK) {
@@ -1075,7 +1105,7 @@ static bool want_grouping(const bc_graph* g, int nsrc, const bc_options& o) {
 }
 
 static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_src, int nsrc, cudaStream_t st,
-                               DevBuf& out, bc_run_stats* acc, std::vector<int>* host_out = nullptr) {
+                               DevBuf& out, bc_run_stats* acc, std::vector<int>* host_out) {
     constexpr int L = 32;
     int Kw = K;
     if (K < L) {  // the plain per-source width: a 32-wide workspace of its own
@@ -1215,7 +1245,7 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
     bc_run_stats pre{};
     DevBuf grouped;
     if (want_grouping(g, nsrc, o)) {
-        bc_status gr = group_sources(g, w, K, d_src, nsrc, st, grouped, &pre);
+        bc_status gr = group_sources(g, w, K, d_src, nsrc, st, grouped, &pre, nullptr);
         if (gr < 0) {
             buf_release(tmp, st);
             buf_release(grouped, st);

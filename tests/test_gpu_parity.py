@@ -323,6 +323,25 @@ def test_serving_alone_equals_mix(bc):
     assert done >= 4 * len(reqs)
 
 
+def test_served_job_equals_direct_call_with_grouped_sources(bc):
+    # a job large enough to be grouped (skewed graph, >= 256 sources): the same
+    # bits served alone, served packed with other jobs, and from bc_compute
+    import torch
+    g = bcgen.rmat(13, 16, 7)
+    G = bc.Graph(g.off, g.adj)
+    big = bcgen.sample_sources(g, 600, 7)
+    direct, _ = G.compute(big)
+    assert G.stats()["order_ms"] > 0
+    direct = direct.cpu().numpy().copy()
+    outs = [torch.empty(g.n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    jobs = [G.submit(big, outs[0]), G.submit(bcgen.sample_sources(g, 40, 8), outs[1]), G.submit(big, outs[2])]
+    for j in jobs:
+        assert j.wait(120000) is not None
+    for o in (outs[0], outs[2]):
+        assert np.array_equal(o.cpu().numpy().view(np.uint64), direct.view(np.uint64))
+    assert_bc_close(direct, oracle.bc(g.off, g.adj, big))
+
+
 # ----------------------------------------------------------------- rows above 1024 arcs (chunk tasks)
 
 @pytest.fixture(scope="module")
