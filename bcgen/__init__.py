@@ -182,6 +182,23 @@ def rmat(scale: int, edge_factor: float, seed: int = 1, a: float = RMAT_A, b: fl
     return edges_to_csr(n, u, v, name=f"rmat{scale}_ef{edge_factor:g}_s{seed}")
 
 
+def edge_weights(g: CSR, lo: int = 1, hi: int = 100, seed: int = 1) -> np.ndarray:
+    """Positive int32 weights parallel to g.adj, uniform in [lo, hi] per
+    undirected edge (both arcs of an edge get the same weight): a SplitMix64
+    hash of (min(u, v), max(u, v), seed)."""
+    n = g.n
+    deg = np.diff(g.off.astype(np.int64))
+    u = np.repeat(np.arange(n, dtype=np.uint64), deg)
+    v = g.adj.astype(np.uint64)
+    a, b = np.minimum(u, v), np.maximum(u, v)
+    with np.errstate(over="ignore"):
+        z = a * np.uint64(n) + b + np.uint64(seed) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (np.uint64(lo) + z % np.uint64(hi - lo + 1)).astype(np.int32)
+
+
 def grid(rows: int, cols: int, remove_frac: float = 0.0, seed: int = 1) -> CSR:
     """rows x cols 4-neighbour grid (id = r*cols + c) with round(remove_frac*E) edges removed."""
     n = rows * cols

@@ -18,6 +18,11 @@ Contents:
     BC(v) = sum_s sum_{t != s, v} sigma_st(v) / sigma_st written out.
   * ``relabel`` / ``validate`` -- the ingest rules (degree-descending stable
     relabelling; CSR validity) in their plain definitions.
+  * ``wbc`` / ``wsource_detail`` -- weighted BC (positive integer arc
+    weights, ``weighted.c``): the same accumulation over the shortest-path DAG
+    of Dijkstra distances, vertices taken in (distance, id) order; and
+    ``brute_force_wbc``, its exact rational definition by path enumeration
+    over Bellman-Ford distances.
   * ``pagerank`` -- the paper's computePR (Appendix A, PR listing) in double
     precision (``pagerank.c``), the change measured as an L1 norm.
 Every function here is pinned by ``tests/test_oracle*.py`` against closed
@@ -36,7 +41,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "brandes.c")
-_SRCS = [_SRC, os.path.join(_HERE, "pagerank.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "pagerank.c"), os.path.join(_HERE, "weighted.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -79,6 +84,10 @@ def _L():
             lib.oracle_relabel.argtypes = [i32, P, P, P, P, P, P]
             lib.oracle_validate_csr.restype = ctypes.c_int
             lib.oracle_validate_csr.argtypes = [i32, i64, P, P, ctypes.c_int]
+            lib.oracle_wbc_f64.restype = ctypes.c_int
+            lib.oracle_wbc_f64.argtypes = [i32, P, P, P, i32, P, P]
+            lib.oracle_wsource.restype = ctypes.c_int
+            lib.oracle_wsource.argtypes = [i32, P, P, P, i32, P, P, P]
             lib.oracle_pagerank.restype = ctypes.c_int
             lib.oracle_pagerank.argtypes = [i32, P, P, ctypes.c_double, ctypes.c_double, i32, P, P]
             _lib = lib
@@ -118,6 +127,33 @@ def bc_ld(off, adj, sources) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle rc={rc}")
     return out[:n]
+
+
+def wbc(off, adj, wt, sources) -> np.ndarray:
+    """Raw weighted BC (double) over ``sources``; ``wt`` parallel to ``adj``, positive int32."""
+    off, adj = _csr(off, adj)
+    wt = np.ascontiguousarray(wt, dtype=np.int32)
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    n = off.shape[0] - 1
+    out = np.zeros(max(n, 1), dtype=np.float64)
+    rc = _L().oracle_wbc_f64(n, _p(off), _p(adj), _p(wt), src.shape[0], _p(src), _p(out))
+    if rc:
+        raise ValueError(f"oracle rc={rc}")
+    return out[:n]
+
+
+def wsource_detail(off, adj, wt, s: int) -> dict:
+    """dist (int64, -1 unreached), sigma and delta of one source, weighted."""
+    off, adj = _csr(off, adj)
+    wt = np.ascontiguousarray(wt, dtype=np.int32)
+    n = off.shape[0] - 1
+    dist = np.empty(max(n, 1), np.int64)
+    sigma = np.empty(max(n, 1), np.float64)
+    delta = np.empty(max(n, 1), np.float64)
+    rc = _L().oracle_wsource(n, _p(off), _p(adj), _p(wt), int(s), _p(dist), _p(sigma), _p(delta))
+    if rc:
+        raise ValueError(f"oracle rc={rc}")
+    return {"dist": dist[:n], "sigma": sigma[:n], "delta": delta[:n]}
 
 
 def source_detail(off, adj, s: int, long_double: bool = False) -> dict:
@@ -287,3 +323,85 @@ def brute_force_sigma(off, adj, s):
             level[t] = len(ps[0]) - 1
             sigma[t] = len(ps)
     return level, sigma
+
+
+def _bellman_ford(off, adj, wt, s):
+    """Weighted distances from s by repeated relaxation of every arc (None = unreached)."""
+    n = len(off) - 1
+    d = [None] * n
+    d[s] = 0
+    for _ in range(n):
+        changed = False
+        for v in range(n):
+            if d[v] is None:
+                continue
+            for e in range(off[v], off[v + 1]):
+                x, c = adj[e], d[v] + wt[e]
+                if d[x] is None or c < d[x]:
+                    d[x] = c
+                    changed = True
+        if not changed:
+            break
+    return d
+
+
+def weighted_shortest_paths(off, adj, wt, s, t):
+    """Every minimum-weight s-t path (following arcs): DFS over arcs v -> x with
+    d(s, v) + w = d(s, x) and d(x, t) = d(v, t) - w."""
+    off = [int(x) for x in off]
+    adj = [int(x) for x in adj]
+    wt = [int(x) for x in wt]
+    ds = _bellman_ford(off, adj, wt, s)
+    if ds[t] is None:
+        return []
+    n = len(off) - 1
+    rows = [[] for _ in range(n)]
+    for v in range(n):
+        for e in range(off[v], off[v + 1]):
+            rows[adj[e]].append((v, wt[e]))
+    roff, radj, rwt = [0], [], []
+    for r in rows:
+        for v, w in r:
+            radj.append(v)
+            rwt.append(w)
+        roff.append(len(radj))
+    dt = _bellman_ford(roff, radj, rwt, t)
+    out = []
+
+    def walk(path):
+        v = path[-1]
+        if v == t:
+            out.append(tuple(path))
+            return
+        for e in range(off[v], off[v + 1]):
+            x = adj[e]
+            if ds[x] is not None and dt[x] is not None and ds[x] == ds[v] + wt[e] and dt[x] == dt[v] - wt[e]:
+                path.append(x)
+                walk(path)
+                path.pop()
+
+    walk([s])
+    return out
+
+
+def brute_force_wbc(off, adj, wt, sources):
+    """Exact rational weighted BC: sum over s in sources, t != s of
+    (#minimum-weight s-t paths through v) / (#minimum-weight s-t paths)."""
+    n = len(off) - 1
+    res = [Fraction(0)] * n
+    for s in sources:
+        s = int(s)
+        for t in range(n):
+            if t == s:
+                continue
+            ps = weighted_shortest_paths(off, adj, wt, s, t)
+            if not ps:
+                continue
+            cnt = [0] * n
+            for p in ps:
+                for v in p[1:-1]:
+                    cnt[v] += 1
+            for v in range(n):
+                if cnt[v]:
+                    res[v] += Fraction(cnt[v], len(ps))
+    return res

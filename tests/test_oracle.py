@@ -374,3 +374,79 @@ def test_pagerank_fixed_point_and_closed_forms():
     A = np.array([[1.0, -d * (n - 1)], [-d / (n - 1), 1.0]])
     cc, ll = np.linalg.solve(A, [(1 - d) / n, (1 - d) / n])
     assert np.isclose(pr[0], cc, rtol=1e-12) and np.allclose(pr[1:], ll, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- weighted BC (positive integer weights)
+
+WSMALL = [g for g in SMALL if g.m > 0]
+
+
+@pytest.mark.parametrize("g", WSMALL, ids=lambda g: g.name)
+@pytest.mark.parametrize("wmax", [1, 3])
+def test_weighted_bc_matches_brute_force(g, wmax):
+    # weights 1..3 make many ties between paths of different hop counts
+    wt = bcgen.edge_weights(g, 1, wmax, seed=g.n + wmax)
+    want = oracle.brute_force_wbc(g.off, g.adj, wt, range(g.n))
+    assert close(oracle.wbc(g.off, g.adj, wt, all_src(g)), [float(x) for x in want])
+
+
+def test_weighted_sigma_and_dist_match_enumeration():
+    g = bcgen.gnp(8, 0.6, 5)
+    wt = bcgen.edge_weights(g, 1, 2, 9)
+    for s in range(g.n):
+        d = oracle.wsource_detail(g.off, g.adj, wt, s)
+        for t in range(g.n):
+            ps = oracle.weighted_shortest_paths(g.off, g.adj, wt, s, t)
+            if t == s:
+                assert d["dist"][t] == 0 and d["sigma"][t] == 1
+            elif not ps:
+                assert d["dist"][t] == -1 and d["sigma"][t] == 0
+            else:
+                w = sum(int(wt[e]) for a, b in zip(ps[0], ps[0][1:])
+                        for e in range(g.off[a], g.off[a + 1]) if g.adj[e] == b)
+                assert d["dist"][t] == w and d["sigma"][t] == len(ps)
+
+
+@pytest.mark.parametrize("c", [1, 7])
+def test_equal_weights_give_unweighted_bc(c):
+    g = bcgen.rmat(10, 8, 3)
+    wt = np.full(g.m, c, np.int32)
+    src = bcgen.sample_sources(g, 200, 2)
+    assert close(oracle.wbc(g.off, g.adj, wt, src), oracle.bc(g.off, g.adj, src))
+
+
+def test_weight_scaling_leaves_bc_unchanged_bitwise():
+    g = bcgen.rmat(9, 8, 4)
+    wt = bcgen.edge_weights(g, 1, 20, 4)
+    src = all_src(g)
+    a = oracle.wbc(g.off, g.adj, wt, src)
+    b = oracle.wbc(g.off, g.adj, wt * 3, src)
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+@pytest.mark.parametrize("n,seed", [(50, 1), (400, 2)])
+def test_tree_plus_heavy_edges_is_the_tree(n, seed):
+    # a tree has unique paths whatever its weights; extra edges heavier than any
+    # tree path never lie on a shortest path, so BC is the tree's closed form
+    t = bcgen.random_tree(n, seed)
+    twt = bcgen.edge_weights(t, 1, 9, seed)
+    extra = bcgen.gnp(n, 0.02, seed + 10)
+    deg = np.diff(t.off.astype(np.int64))
+    u = np.concatenate([np.repeat(np.arange(n), deg), np.repeat(np.arange(n), np.diff(extra.off.astype(np.int64)))])
+    v = np.concatenate([t.adj, extra.adj])
+    heavy = 10 * n
+    w = {}
+    for a, b, x in zip(np.repeat(np.arange(n), deg), t.adj, twt):
+        w[(int(a), int(b))] = int(x)
+    g = bcgen.edges_to_csr(n, u, v)
+    gdeg = np.diff(g.off.astype(np.int64))
+    gw = np.array([w.get((int(a), int(b)), heavy) for a, b in zip(np.repeat(np.arange(n), gdeg), g.adj)], np.int32)
+    got = oracle.wbc(g.off, g.adj, gw, all_src(g)) / 2
+    assert close(got, tree_bc_half(t))
+
+
+def test_weighted_path_closed_form():
+    g = bcgen.path(30)
+    wt = bcgen.edge_weights(g, 1, 50, 1)
+    got = oracle.wbc(g.off, g.adj, wt, all_src(g)) / 2
+    assert close(got, [i * (29 - i) for i in range(30)])
