@@ -182,6 +182,32 @@ bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* lev
 bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, double* out_rank,
                       int32_t* iterations, double* last_diff, bc_stream_t stream);
 
+/*
+ * Weighted graphs (undirected, positive int32 arc weights).  weights[m] is
+ * parallel to indices[m] of the input CSR (host or device, as the flags say),
+ * whose rows must be sorted ascending; both arcs of an edge carry the same
+ * weight.  Checks (unless BC_SKIP_VALIDATION): the CSR rules of
+ * bc_graph_create, sorted rows, weights > 0, symmetric weights, else
+ * BC_E_INVALID_GRAPH.  The result is a regular graph (every unweighted call
+ * works on it, ignoring the weights) that bc_compute_weighted also accepts.
+ */
+bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indices, const int32_t* weights,
+                                   int32_t n, int64_t m, uint32_t flags, bc_stream_t stream, bc_graph** out);
+
+/*
+ * Weighted BC over a source list (original ids, host or device): the paper's
+ * BC accumulation (Appendix A, BC listing) over the shortest-path DAG of
+ * weighted distances, the distances found by the fixed-point Min relaxation
+ * of the paper's SSSP program (Section 2.3).  Path counts are exact below
+ * 2^64 (BC_W_SIGMA_INEXACT once one reaches 2^53, BC_E_SIGMA_RANGE at
+ * 2^64); BC is the raw sum over the listed sources, as for bc_compute.
+ * Batches of 32 sources, one launch each; results repeat bit for bit.
+ * BC_E_INVALID_ARG if the graph has no weights.  bc_last_run_stats reports
+ * max_levels / pull_levels / push_levels = passes of the distance, path-count
+ * and dependency loops (largest over batches).
+ */
+bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream);
+
 /* Per-call facts of the last bc_compute / bc_compute_ex / bc_bfs on this graph. */
 typedef struct {
     int32_t batch_width;     /* width used */

@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_set_allocator": [P, P, P],
         "bc_graph_create": [P, P, i32, i64, u32, P, ctypes.POINTER(P)],
         "bc_graph_destroy": [P],
+        "bc_graph_create_weighted": [P, P, P, i32, i64, u32, P, ctypes.POINTER(P)],
+        "bc_compute_weighted": [P, P, i32, P, P],
         "bc_graph_info": [P, P, P, P, P],
         "bc_graph_export": [P, P, P, P],
         "bc_compute": [P, P, i32, P, P],
@@ -185,22 +187,31 @@ class Job:
 class Graph:
     """A graph resident on the device (relabelled CSR; see bc_graph_create)."""
 
-    def __init__(self, off, adj, validate: bool = True, stream=None, directed: bool = False):
+    def __init__(self, off, adj, validate: bool = True, stream=None, directed: bool = False, weights=None):
+        """weights: positive int32 per arc, parallel to adj (rows sorted; undirected only)."""
         lib = load()
         self._h = ctypes.c_void_p()
         flags = (0 if directed else BC_UNDIRECTED) | (0 if validate else BC_SKIP_VALIDATION)
         if isinstance(off, np.ndarray):
             off = np.ascontiguousarray(off, dtype=np.int32)
             adj = np.ascontiguousarray(adj, dtype=np.int32)
-            self._keep = (off, adj)
+            if weights is not None:
+                weights = np.ascontiguousarray(weights, dtype=np.int32)
+            self._keep = (off, adj, weights)
             n, m = off.shape[0] - 1, adj.shape[0]
         else:  # torch tensors on the device
             flags |= BC_INPUT_ON_DEVICE
             n, m = off.numel() - 1, adj.numel()
-            self._keep = (off, adj)
+            self._keep = (off, adj, weights)
         st = _stream_handle(stream) if _has_cuda() else 0
-        _check(lib.bc_graph_create(_ptr(off), _ptr(adj) if m > 0 else None, n, m, flags, st,
-                                   ctypes.byref(self._h)))
+        if weights is None:
+            _check(lib.bc_graph_create(_ptr(off), _ptr(adj) if m > 0 else None, n, m, flags, st,
+                                       ctypes.byref(self._h)))
+        else:
+            _check(lib.bc_graph_create_weighted(_ptr(off), _ptr(adj) if m > 0 else None,
+                                                _ptr(weights) if m > 0 else None, n, m, flags, st,
+                                                ctypes.byref(self._h)))
+        self.weighted = weights is not None
         self._keep = None
         n_, m_, md, nnz = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib.bc_graph_info(self._h, ctypes.byref(n_), ctypes.byref(m_), ctypes.byref(md), ctypes.byref(nnz)))
@@ -233,6 +244,19 @@ class Graph:
                          1 if trace else 0, teams, dense_min, source_order)
         s = load().bc_compute_ex(self._h, _ptr(sources) if nsrc else None, nsrc, _ptr(out) if self.n else None,
                                  _stream_handle(stream), ctypes.byref(opt))
+        _check(s)
+        return out, s
+
+    def compute_weighted(self, sources, out=None, stream=None):
+        """Weighted BC over ``sources`` (host numpy or device int32 tensor). Returns (out, status)."""
+        import torch
+        if out is None:
+            out = torch.empty(max(self.n, 1), dtype=torch.float64, device="cuda")[: self.n]
+        if isinstance(sources, np.ndarray):
+            sources = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc = int(sources.shape[0]) if isinstance(sources, np.ndarray) else int(sources.numel())
+        s = load().bc_compute_weighted(self._h, _ptr(sources) if nsrc else None, nsrc, _ptr(out) if self.n else None,
+                                       _stream_handle(stream))
         _check(s)
         return out, s
 

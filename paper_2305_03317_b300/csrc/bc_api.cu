@@ -217,6 +217,8 @@ struct bc_graph {
     int max_in_deg = 0;  // directed: longest in-row (forward sums run over whole in-rows)
     DevBuf off, adj, perm, inv, hcum;
     DevBuf ioff, iadj;  // directed: in-CSR for the pull steps
+    DevBuf w;           // weighted graphs: arc weights in relabelled arc order (empty otherwise)
+    DevBuf wdist, wsa, wsb, wda, wdb, wrho, wbc, wctl, wsrc;  // weighted BC state, kept between calls
     AllocHook hook;
     std::mutex mu;                                 // bc_compute / plans: the per-width workspaces below
     std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
@@ -1062,10 +1064,167 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->perm, st);
     buf_release(g->ioff, st);
     buf_release(g->iadj, st);
+    for (DevBuf* b : {&g->w, &g->wdist, &g->wsa, &g->wsb, &g->wda, &g->wdb, &g->wrho, &g->wbc, &g->wctl, &g->wsrc})
+        buf_release(*b, st);
     buf_release(g->inv, st);
     cudaStreamSynchronize(st);
     delete g;
     return BC_OK;
+}
+
+bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indices, const int32_t* weights, int32_t n,
+                                   int64_t m, uint32_t flags, bc_stream_t stream, bc_graph** out) {
+    if (!out) return fail(BC_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!(flags & BC_UNDIRECTED)) return fail(BC_E_INVALID_ARG, "weighted graphs must be undirected (BC_UNDIRECTED)");
+    if (m > 0 && !weights) return fail(BC_E_INVALID_ARG, "weights NULL");
+    bc_graph* g = nullptr;
+    bc_status r = bc_graph_create(offsets, indices, n, m, flags, stream, &g);
+    if (r != BC_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool on_dev = (flags & BC_INPUT_ON_DEVICE) != 0;
+    DevBuf doff, dadj, dw, derr;
+    auto bail = [&](bc_status rr) {
+        buf_release(doff, st);
+        buf_release(dadj, st);
+        buf_release(dw, st);
+        buf_release(derr, st);
+        if (rr != BC_OK) bc_graph_destroy(g);
+        return rr;
+    };
+    if (!buf_ensure(g->w, sizeof(int) * (size_t)(m > 0 ? m : 1), st) || !buf_ensure(derr, sizeof(int), st))
+        return bail(fail(BC_E_NOMEM, "weight buffers"));
+    const int *ooff = offsets, *oadj = indices, *ow = weights;
+    cudaError_t e = cudaMemsetAsync(derr.p, 0, sizeof(int), st);
+    if (!on_dev && e == cudaSuccess) {
+        if (!buf_ensure(doff, sizeof(int) * ((size_t)n + 1), st) || !buf_ensure(dadj, sizeof(int) * (size_t)(m > 0 ? m : 1), st) ||
+            !buf_ensure(dw, sizeof(int) * (size_t)(m > 0 ? m : 1), st))
+            return bail(fail(BC_E_NOMEM, "weight ingest buffers"));
+        e = cudaMemcpyAsync(doff.p, offsets, sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(dadj.p, indices, sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(dw.p, weights, sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, st);
+        ooff = (const int*)doff.p;
+        oadj = (const int*)dadj.p;
+        ow = (const int*)dw.p;
+    }
+    if (e == cudaSuccess)
+        e = launch_weight_ingest(ooff, oadj, ow, (const int*)g->perm.p, (const int*)g->off.p, (const int*)g->adj.p, n,
+                                 (int*)g->w.p, (int*)derr.p, !(flags & BC_SKIP_VALIDATION), st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "weight ingest"));
+    if (!(flags & BC_SKIP_VALIDATION) && herr)
+        return bail(fail(BC_E_INVALID_GRAPH, "weights: %s%s%s", (herr & 1) ? "rows not sorted ascending; " : "",
+                         (herr & 2) ? "a weight <= 0; " : "", (herr & 4) ? "the two arcs of an edge differ" : ""));
+    *out = g;
+    return bail(BC_OK);
+}
+
+bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    if (!g->w.p) return fail(BC_E_INVALID_ARG, "the graph has no weights (bc_graph_create_weighted)");
+    if (nsrc < 0 || (nsrc > 0 && !sources)) return fail(BC_E_INVALID_ARG, "bad source list");
+    if (!out_bc && g->n > 0) return fail(BC_E_INVALID_ARG, "out_bc is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->last_stream = st;
+    if (g->n == 0) return BC_OK;
+    const size_t n = (size_t)g->n;
+    bc_status r = ensure_heavy(g, st);
+    if (r != BC_OK) return r;
+    constexpr int KW = 32;
+    const int nbatch = (nsrc + KW - 1) / KW;
+    const size_t cells = n * KW;
+    DevBuf hsrc;
+    const int* d_src = sources;
+    if (nsrc > 0 && !is_device_ptr(sources)) {
+        for (int i = 0; i < nsrc; ++i)
+            if (sources[i] < 0 || sources[i] >= g->n)
+                return fail(BC_E_SOURCE, "source %d (entry %d) is outside [0, %d)", sources[i], i, g->n);
+        if (!buf_ensure(hsrc, sizeof(int) * (size_t)nsrc, st)) return fail(BC_E_NOMEM, "source buffer");
+        cudaError_t e = cudaMemcpyAsync(hsrc.p, sources, sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            buf_release(hsrc, st);
+            return cuda_fail(e, "source copy");
+        }
+        d_src = (const int*)hsrc.p;
+    }
+    auto done = [&](bc_status rr) {
+        buf_release(hsrc, st);
+        return rr;
+    };
+    if (!buf_ensure(g->wdist, 8 * cells, st) || !buf_ensure(g->wsa, 8 * cells, st) || !buf_ensure(g->wsb, 8 * cells, st) ||
+        !buf_ensure(g->wda, 8 * cells, st) || !buf_ensure(g->wdb, 8 * cells, st) || !buf_ensure(g->wrho, 8 * cells, st) ||
+        !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int), st) ||
+        !buf_ensure(g->wsrc, sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * KW + sizeof(int), st))
+        return done(fail(BC_E_NOMEM, "weighted BC buffers"));
+    Ctl* ctl = (Ctl*)g->wctl.p;
+    int* changed = (int*)((char*)g->wctl.p + sizeof(Ctl));
+    int* passes = changed + 4;
+    int* bad = (int*)g->wsrc.p + (size_t)(nbatch > 0 ? nbatch : 1) * KW;
+    cudaError_t e = cudaMemsetAsync(g->wbc.p, 0, 8 * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->wctl.p, 0, sizeof(Ctl) + 8 * sizeof(int), st);
+    if (e == cudaSuccess && nbatch > 0) {
+        e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+        if (e == cudaSuccess)
+            e = launch_map_sources(d_src, nsrc, (const int*)g->inv.p, g->n, KW, (int*)g->wsrc.p, nbatch, bad, st);
+    }
+    int hbad = 0;
+    if (e == cudaSuccess && nbatch > 0) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(cuda_fail(e, "weighted set-up"));
+    if (hbad) return done(fail(BC_E_SOURCE, "a source id is outside [0, %d)", g->n));
+    const int blocks = wbc_blocks();
+    if (blocks < 1) return done(fail(BC_E_CUDA, "weighted BC kernel cannot be resident"));
+    cudaEvent_t ev[2];
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    cudaEventRecord(ev[0], st);
+    for (int b = 0; b < nbatch && e == cudaSuccess; ++b) {
+        // fresh barrier and pass flags per launch (passes accumulate the maximum)
+        e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(changed, 0, 4 * sizeof(int), st);
+        if (e == cudaSuccess)
+            e = launch_wbc(g->n, g->n_heavy, (const int*)g->off.p, (const int*)g->adj.p, (const int*)g->w.p,
+                           (const int*)g->wsrc.p + (size_t)b * KW, (long long*)g->wdist.p,
+                           (unsigned long long*)g->wsa.p, (unsigned long long*)g->wsb.p, (double*)g->wda.p,
+                           (double*)g->wdb.p, (double*)g->wrho.p, (double*)g->wbc.p, ctl, changed, passes,
+                           40000000000ll, blocks, st);
+        int herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && herr) {
+            cudaEventDestroy(ev[0]);
+            cudaEventDestroy(ev[1]);
+            if (herr & ERR_SIGMA_RANGE) return done(fail(BC_E_SIGMA_RANGE, "a weighted path count reached 2^64"));
+            if (herr & ERR_TIMEOUT) return done(fail(BC_E_TIMEOUT, "a grid-barrier wait exceeded its cycle budget"));
+            return done(fail(BC_E_CUDA, "weighted BC kernel error 0x%x", herr));
+        }
+    }
+    cudaEventRecord(ev[1], st);
+    int hp[3] = {0, 0, 0}, hflags = 0;
+    if (e == cudaSuccess) e = launch_unpermute((const double*)g->wbc.p, (const int*)g->inv.p, out_bc, g->n, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp, passes, sizeof hp, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, &ctl->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) return done(cuda_fail(e, "weighted BC"));
+    bc_run_stats s{};
+    s.batch_width = KW;
+    s.batches = nbatch;
+    s.max_levels = hp[0];    // passes of the distance loop (largest over batches)
+    s.pull_levels = hp[1];   // passes of the path-count loop
+    s.push_levels = hp[2];   // passes of the dependency loop
+    s.grid_blocks = blocks;
+    s.kernel_launches = 2 + nbatch;          // kernels only: source mapping, one launch per batch, unpermute
+    s.kernel_ms = ms;
+    s.teams = 1;
+    g->last = s;
+    return done((hflags & BST_INEXACT) ? BC_W_SIGMA_INEXACT : BC_OK);
 }
 
 bc_status bc_graph_info(const bc_graph* g, int32_t* n, int64_t* m, int32_t* max_degree, int32_t* n_nonisolated) {

@@ -160,6 +160,16 @@ cudaError_t launch_map_sources(const int* src_orig, int nsrc, const int* inv, in
                                int nbatch, int* bad, cudaStream_t st);
 cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, const int* inv, long long n,
                                unsigned short* lvl, int* level_out, double* sig_out, int* exp_out, cudaStream_t st);
+// Weighted BC (weighted.cu): one cooperative launch per batch of 32 sources;
+// weights of the relabelled arcs looked up from the original sorted CSR
+// (err bits: 1 rows not sorted, 2 a weight <= 0, 4 asymmetric weights).
+int wbc_blocks();
+cudaError_t launch_wbc(int n, int n_heavy, const int* off, const int* adj, const int* w, const int* src,
+                       long long* dist, unsigned long long* sa, unsigned long long* sb, double* da, double* db,
+                       double* rho, double* bc, Ctl* ctl, int* changed, int* passes, long long budget, int blocks,
+                       cudaStream_t st);
+cudaError_t launch_weight_ingest(const int* ooff, const int* oadj, const int* ow, const int* perm, const int* noff,
+                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, cudaStream_t st);
 // Level table of a forward-only batch, then the levels of columns [0, L) at
 // each of nsrc sources (original ids): keys[nsrc][L], 0xFFFF = unreached.
 cudaError_t launch_level_keys(const KParams& p, int K, int levels, int L, unsigned short* lvl, long long n,

@@ -1,0 +1,376 @@
+// Weighted betweenness centrality (positive integer arc weights) on the
+// resident graph: Brandes' accumulation over the shortest-path DAG of
+// weighted distances.  The paper's BC program (Appendix A, BC listing) walks
+// BFS levels; with weights the levels become distances, and the paper's own
+// SSSP program (Section 2.3, the Min construct inside a fixed-point loop)
+// gives them by Bellman-Ford relaxation.  Per batch of 32 sources (lane =
+// column), one cooperative persistent launch runs three fixed-point loops over
+// every row, each pass pulling from the row's neighbours:
+//   dist:  d(v) = min(d(v), min over arcs u-v of d(u) + w)      (in place)
+//   sigma: s'(v) = [v = source] + sum over u with d(u) + w = d(v) of s(u)
+//   delta: t'(v) = s(v) * sum over x with d(v) + w = d(x) of (1 + t(x)) / s(x)
+// until a pass changes nothing (the count of passes is the hop depth of the
+// DAG plus one); then BC(v) += t(v) for every non-source column, columns in
+// order.  Distance mins and integer path counts do not depend on the order of
+// their terms; every double sum runs in CSR order (heavy rows: contiguous
+// eighths of the row, combined in order), so results repeat bit for bit.
+// Rows above 1024 arcs (the relabelled prefix [0, n_heavy)) take one block
+// each, the others one warp each.  Grid barriers are bounded by a cycle
+// budget like the traversal kernel's.
+#include <climits>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bc_internal.cuh"
+
+namespace bcx {
+namespace {
+
+constexpr int kWThreads = 256;
+constexpr int kWWarps = kWThreads / 32;
+constexpr int KW = 32;  // sources per batch
+constexpr long long kInf = LLONG_MAX;
+constexpr unsigned int kAll = 0xffffffffu;
+
+struct WParams {
+    int n, n_heavy;
+    const int* off;
+    const int* adj;
+    const int* w;              // arc weights, relabelled arc order
+    const int* src;            // [32] relabelled sources, -1 = unused column
+    long long* dist;           // [n][32]
+    unsigned long long* sa;    // [n][32] path counts (two buffers)
+    unsigned long long* sb;
+    double* da;                // [n][32] dependencies (two buffers)
+    double* db;
+    double* rho;               // [n][32] (1 + delta) / sigma of the current pass
+    double* bc;                // [n] relabelled
+    Ctl* ctl;
+    int* changed;              // [3] rotating "a pass changed something" flags
+    int* passes;               // [3] passes run by each loop (out)
+    long long budget;
+    int max_passes;
+};
+
+__device__ __forceinline__ size_t at(int v, int lane) { return (size_t)v * KW + lane; }
+
+// One pass over every row: heavy rows one block each (warp k takes the k-th
+// eighth of the row, its partial lands in part[k]; warp 0 combines them in
+// order), light rows one warp each.
+template <class Arc, class Finish, class T>
+__device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, T (*part)[KW]) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int r = blockIdx.x; r < p.n_heavy; r += gridDim.x) {
+        const int b = p.off[r], e = p.off[r + 1];
+        const int seg = (e - b + kWWarps - 1) / kWWarps;
+        const int lo = b + wib * seg, hi = min(e, lo + seg);
+        T acc = init;
+#pragma unroll 4
+        for (int j = lo; j < hi; ++j) arc(r, j, acc);
+        part[wib][lane] = acc;
+        __syncthreads();
+        if (wib == 0) {
+            T all = part[0][lane];
+            for (int k = 1; k < kWWarps; ++k) all = Arc::combine(all, part[k][lane]);
+            finish(r, all);
+        }
+        __syncthreads();
+    }
+    const long long nw = (long long)gridDim.x * kWWarps;
+    for (long long r = p.n_heavy + (long long)blockIdx.x * kWWarps + wib; r < p.n; r += nw) {
+        const int b = p.off[r], e = p.off[r + 1];
+        T acc = init;
+#pragma unroll 4
+        for (int j = b; j < e; ++j) arc((int)r, j, acc);
+        finish((int)r, acc);
+    }
+}
+
+struct MinArc {
+    const WParams* p;
+    int lane;
+    __device__ void operator()(int v, int j, long long& best) const {
+        const long long du = p->dist[at(__ldg(p->adj + j), lane)];
+        if (du != kInf) {
+            const long long c = du + __ldg(p->w + j);
+            if (c < best) best = c;
+        }
+    }
+    __device__ static long long combine(long long a, long long b) { return a < b ? a : b; }
+};
+
+struct SigmaAcc {
+    unsigned long long s;
+    bool ovf;
+};
+
+struct SigmaArc {
+    const WParams* p;
+    const unsigned long long* cur;
+    int lane;
+    __device__ void operator()(int v, int j, SigmaAcc& a) const {
+        const long long dv = p->dist[at(v, lane)];
+        if (dv == kInf) return;
+        const int u = __ldg(p->adj + j);
+        const long long du = p->dist[at(u, lane)];
+        if (du != kInf && du + __ldg(p->w + j) == dv) {
+            const unsigned long long x = cur[at(u, lane)];
+            const unsigned long long s = a.s + x;
+            a.ovf |= s < x;
+            a.s = s;
+        }
+    }
+    __device__ static SigmaAcc combine(SigmaAcc a, SigmaAcc b) {
+        const unsigned long long s = a.s + b.s;
+        return SigmaAcc{s, a.ovf || b.ovf || s < b.s};
+    }
+};
+
+struct DeltaArc {
+    const WParams* p;
+    int lane;
+    __device__ void operator()(int v, int j, double& sum) const {
+        const long long dv = p->dist[at(v, lane)];
+        if (dv == kInf) return;
+        const int x = __ldg(p->adj + j);
+        const long long dx = p->dist[at(x, lane)];
+        if (dx != kInf && dv + __ldg(p->w + j) == dx) sum += p->rho[at(x, lane)];
+    }
+    __device__ static double combine(double a, double b) { return a + b; }
+};
+
+__global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
+    __shared__ long long s_min[kWWarps][KW];
+    __shared__ SigmaAcc s_sig[kWWarps][KW];
+    __shared__ double s_del[kWWarps][KW];
+    GridTeam team{p.ctl, p.ctl, (int)gridDim.x, p.budget};
+    const int lane = threadIdx.x & 31;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long cells = (long long)p.n * KW;
+    int pass = 0;
+    // true when the pass just ended changed something; false (and an error
+    // word) when the pass budget ran out or a barrier failed
+    bool fail = false;
+    auto end_pass = [&](bool mine) -> bool {
+        if (__any_sync(kAll, mine) && lane == 0) p.changed[pass % 3] = 1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) p.changed[(pass + 1) % 3] = 0;
+        if (!team.sync()) {
+            fail = true;
+            return false;
+        }
+        const int c = *(volatile int*)&p.changed[pass % 3];
+        ++pass;
+        return c != 0;
+    };
+    for (long long i = tid; i < cells; i += nthr) {
+        p.dist[i] = kInf;
+        p.sa[i] = 0ull;
+        p.sb[i] = 0ull;
+        p.da[i] = 0.0;
+        p.db[i] = 0.0;
+    }
+    if (!team.sync()) return;
+    if (tid < KW && p.src[tid] >= 0) p.dist[at(p.src[tid], (int)tid)] = 0;
+    if (!team.sync()) return;
+
+    // distances, in place
+    int np = 0;
+    for (bool more = true; more;) {
+        if (++np > p.max_passes) {
+            if (tid == 0) atomicOr(&p.ctl->err, ERR_INTERNAL);
+            return;
+        }
+        bool ch = false;
+        MinArc arc{&p, lane};
+        row_pass<MinArc>(p, kInf, arc, [&](int v, long long best) {
+            if (best < p.dist[at(v, lane)]) {
+                p.dist[at(v, lane)] = best;
+                ch = true;
+            }
+        }, s_min);
+        more = end_pass(ch);
+        if (fail) return;
+    }
+    const int pass_dist = np;
+
+    // path counts, from cur into nxt until nothing changes
+    unsigned long long* cur = p.sa;
+    unsigned long long* nxt = p.sb;
+    np = 0;
+    bool big = false;
+    for (bool more = true; more;) {
+        if (++np > p.max_passes) {
+            if (tid == 0) atomicOr(&p.ctl->err, ERR_INTERNAL);
+            return;
+        }
+        bool ch = false, ovf = false;
+        SigmaArc arc{&p, cur, lane};
+        row_pass<SigmaArc>(p, SigmaAcc{0ull, false}, arc, [&](int v, SigmaAcc a) {
+            unsigned long long s = a.s;
+            if (p.dist[at(v, lane)] != kInf && v == p.src[lane]) {
+                s += 1ull;
+                a.ovf |= s == 0ull;
+            }
+            ovf |= a.ovf;
+            big |= s >= (1ull << 53);
+            if (s != cur[at(v, lane)]) ch = true;
+            nxt[at(v, lane)] = s;
+        }, s_sig);
+        if (ovf) atomicOr(&p.ctl->err, ERR_SIGMA_RANGE);
+        more = end_pass(ch);
+        if (fail) return;
+        unsigned long long* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    const int pass_sigma = np;
+    if (__any_sync(kAll, big) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
+    // cur holds the counts; nxt becomes 1 / sigma (double bits)
+    double* inv = reinterpret_cast<double*>(nxt);
+    for (long long i = tid; i < cells; i += nthr) inv[i] = cur[i] ? 1.0 / (double)cur[i] : 0.0;
+    if (!team.sync()) return;
+
+    // dependencies, from dc into dn until nothing changes
+    double* dc = p.da;
+    double* dn = p.db;
+    np = 0;
+    for (bool more = true; more;) {
+        if (++np > p.max_passes) {
+            if (tid == 0) atomicOr(&p.ctl->err, ERR_INTERNAL);
+            return;
+        }
+        for (long long i = tid; i < cells; i += nthr) p.rho[i] = (1.0 + dc[i]) * inv[i];
+        if (!team.sync()) return;
+        bool ch = false;
+        DeltaArc arc{&p, lane};
+        row_pass<DeltaArc>(p, 0.0, arc, [&](int v, double sum) {
+            const double d = (double)cur[at(v, lane)] * sum;
+            if (__double_as_longlong(d) != __double_as_longlong(dc[at(v, lane)])) ch = true;
+            dn[at(v, lane)] = d;
+        }, s_del);
+        more = end_pass(ch);
+        if (fail) return;
+        double* t = dc;
+        dc = dn;
+        dn = t;
+    }
+    const int pass_delta = np;
+
+    // BC += delta of every non-source column, columns in order
+    for (long long v = tid; v < p.n; v += nthr) {
+        double acc = p.bc[v];
+        for (int c = 0; c < KW; ++c)
+            if (p.src[c] >= 0 && p.src[c] != v) acc += dc[at((int)v, c)];
+        p.bc[v] = acc;
+    }
+    if (tid == 0) {
+        p.passes[0] = max(p.passes[0], pass_dist);
+        p.passes[1] = max(p.passes[1], pass_sigma);
+        p.passes[2] = max(p.passes[2], pass_delta);
+    }
+}
+
+// Weights of the relabelled arcs, looked up in the original CSR (rows sorted
+// ascending): relabelled arc (r, c) is original (perm[r], perm[c]).
+__global__ void k_weight_lookup(const int* __restrict__ ooff, const int* __restrict__ oadj,
+                                const int* __restrict__ ow, const int* __restrict__ perm, const int* __restrict__ noff,
+                                const int* __restrict__ nadj, int n, int* nw, int* err) {
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += nthr) {
+        const int u = perm[r];
+        const int b = ooff[u], e = ooff[u + 1];
+        for (int j = noff[r]; j < noff[r + 1]; ++j) {
+            const int v = perm[nadj[j]];
+            int lo = b, hi = e;  // first position with oadj >= v
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (oadj[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < e && oadj[lo] == v) {
+                nw[j] = ow[lo];
+                if (ow[lo] <= 0) atomicOr(err, 2);
+            } else {
+                nw[j] = 1;
+                atomicOr(err, 1);  // rows not sorted
+            }
+        }
+    }
+}
+
+// Both arcs of an undirected edge must carry the same weight.
+__global__ void k_weight_symmetry(const int* __restrict__ noff, const int* __restrict__ nadj,
+                                  const int* __restrict__ nw, int n, int* err) {
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += nthr) {
+        for (int j = noff[r]; j < noff[r + 1]; ++j) {
+            const int c = nadj[j];
+            int lo = noff[c], hi = noff[c + 1];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (nadj[mid] < (int)r) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= noff[c + 1] || nadj[lo] != (int)r || nw[lo] != nw[j]) atomicOr(err, 4);
+        }
+    }
+}
+
+}  // namespace
+
+int wbc_blocks() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wbc, kWThreads, 0);
+    if (per > 4) per = 4;
+    return sms * per;
+}
+
+cudaError_t launch_wbc(int n, int n_heavy, const int* off, const int* adj, const int* w, const int* src,
+                       long long* dist, unsigned long long* sa, unsigned long long* sb, double* da, double* db,
+                       double* rho, double* bc, Ctl* ctl, int* changed, int* passes, long long budget, int blocks,
+                       cudaStream_t st) {
+    WParams p;
+    p.n = n;
+    p.n_heavy = n_heavy;
+    p.off = off;
+    p.adj = adj;
+    p.w = w;
+    p.src = src;
+    p.dist = dist;
+    p.sa = sa;
+    p.sb = sb;
+    p.da = da;
+    p.db = db;
+    p.rho = rho;
+    p.bc = bc;
+    p.ctl = ctl;
+    p.changed = changed;
+    p.passes = passes;
+    p.budget = budget;
+    p.max_passes = n + 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kWThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_wbc, p);
+}
+
+cudaError_t launch_weight_ingest(const int* ooff, const int* oadj, const int* ow, const int* perm, const int* noff,
+                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    k_weight_lookup<<<blocks, 256, 0, st>>>(ooff, oadj, ow, perm, noff, nadj, n, nw, err);
+    if (check_symmetry) k_weight_symmetry<<<blocks, 256, 0, st>>>(noff, nadj, nw, n, err);
+    return cudaGetLastError();
+}
+
+}  // namespace bcx
