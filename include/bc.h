@@ -204,7 +204,7 @@ bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indice
  * Batches of 32 sources, one launch each; results repeat bit for bit.
  * BC_E_INVALID_ARG if the graph has no weights.  bc_last_run_stats reports
  * max_levels / pull_levels / push_levels = passes of the distance, path-count
- * and dependency loops (largest over batches).
+ * and dependency loops, summed over batches.
  */
 bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream);
 

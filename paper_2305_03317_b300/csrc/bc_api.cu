@@ -1182,7 +1182,7 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     cudaEventCreate(&ev[1]);
     cudaEventRecord(ev[0], st);
     for (int b = 0; b < nbatch && e == cudaSuccess; ++b) {
-        // fresh barrier and pass flags per launch (passes accumulate the maximum)
+        // fresh barrier and pass flags per launch (pass counts accumulate)
         e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(changed, 0, 4 * sizeof(int), st);
         if (e == cudaSuccess)
@@ -1216,7 +1216,7 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     bc_run_stats s{};
     s.batch_width = KW;
     s.batches = nbatch;
-    s.max_levels = hp[0];    // passes of the distance loop (largest over batches)
+    s.max_levels = hp[0];    // passes of the distance loop, summed over batches
     s.pull_levels = hp[1];   // passes of the path-count loop
     s.push_levels = hp[2];   // passes of the dependency loop
     s.grid_blocks = blocks;

@@ -47,7 +47,7 @@ struct WParams {
     double* bc;                // [n] relabelled
     Ctl* ctl;
     int* changed;              // [3] rotating "a pass changed something" flags
-    int* passes;               // [3] passes run by each loop (out)
+    int* passes;               // [3] passes run by each loop, summed over launches (out)
     long long budget;
     int max_passes;
 };
@@ -64,9 +64,11 @@ __device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, T (*p
         const int b = p.off[r], e = p.off[r + 1];
         const int seg = (e - b + kWWarps - 1) / kWWarps;
         const int lo = b + wib * seg, hi = min(e, lo + seg);
-        T acc = init;
+        T acc = arc.start(r, init);
+        if (__any_sync(kAll, arc.live(acc))) {
 #pragma unroll 4
-        for (int j = lo; j < hi; ++j) arc(r, j, acc);
+            for (int j = lo; j < hi; ++j) arc(j, acc);
+        }
         part[wib][lane] = acc;
         __syncthreads();
         if (wib == 0) {
@@ -79,17 +81,25 @@ __device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, T (*p
     const long long nw = (long long)gridDim.x * kWWarps;
     for (long long r = p.n_heavy + (long long)blockIdx.x * kWWarps + wib; r < p.n; r += nw) {
         const int b = p.off[r], e = p.off[r + 1];
-        T acc = init;
+        T acc = arc.start((int)r, init);
+        if (__any_sync(kAll, arc.live(acc))) {
 #pragma unroll 4
-        for (int j = b; j < e; ++j) arc((int)r, j, acc);
+            for (int j = b; j < e; ++j) arc(j, acc);
+        }
         finish((int)r, acc);
     }
 }
 
+// Arc functors: start(v, init) gives a row's running state, live(state)
+// whether the lane's column needs the row's arcs at all (a warp skips a row
+// no lane needs), operator()(j, state) takes arc j, combine joins the
+// partials of a heavy row in order.
 struct MinArc {
     const WParams* p;
     int lane;
-    __device__ void operator()(int v, int j, long long& best) const {
+    __device__ long long start(int, long long init) const { return init; }
+    __device__ bool live(long long) const { return true; }
+    __device__ void operator()(int j, long long& best) const {
         const long long du = p->dist[at(__ldg(p->adj + j), lane)];
         if (du != kInf) {
             const long long c = du + __ldg(p->w + j);
@@ -101,6 +111,7 @@ struct MinArc {
 
 struct SigmaAcc {
     unsigned long long s;
+    long long dv;  // the row's own distance
     bool ovf;
 };
 
@@ -108,12 +119,16 @@ struct SigmaArc {
     const WParams* p;
     const unsigned long long* cur;
     int lane;
-    __device__ void operator()(int v, int j, SigmaAcc& a) const {
-        const long long dv = p->dist[at(v, lane)];
-        if (dv == kInf) return;
+    __device__ SigmaAcc start(int v, SigmaAcc init) const {
+        init.dv = p->dist[at(v, lane)];
+        return init;
+    }
+    __device__ bool live(const SigmaAcc& a) const { return a.dv != kInf && a.dv != 0; }
+    __device__ void operator()(int j, SigmaAcc& a) const {
+        if (a.dv == kInf) return;
         const int u = __ldg(p->adj + j);
         const long long du = p->dist[at(u, lane)];
-        if (du != kInf && du + __ldg(p->w + j) == dv) {
+        if (du != kInf && du + __ldg(p->w + j) == a.dv) {
             const unsigned long long x = cur[at(u, lane)];
             const unsigned long long s = a.s + x;
             a.ovf |= s < x;
@@ -122,27 +137,36 @@ struct SigmaArc {
     }
     __device__ static SigmaAcc combine(SigmaAcc a, SigmaAcc b) {
         const unsigned long long s = a.s + b.s;
-        return SigmaAcc{s, a.ovf || b.ovf || s < b.s};
+        return SigmaAcc{s, a.dv, a.ovf || b.ovf || s < b.s};
     }
+};
+
+struct DeltaAcc {
+    double sum;
+    long long dv;
 };
 
 struct DeltaArc {
     const WParams* p;
     int lane;
-    __device__ void operator()(int v, int j, double& sum) const {
-        const long long dv = p->dist[at(v, lane)];
-        if (dv == kInf) return;
+    __device__ DeltaAcc start(int v, DeltaAcc init) const {
+        init.dv = p->dist[at(v, lane)];
+        return init;
+    }
+    __device__ bool live(const DeltaAcc& a) const { return a.dv != kInf; }
+    __device__ void operator()(int j, DeltaAcc& a) const {
+        if (a.dv == kInf) return;
         const int x = __ldg(p->adj + j);
         const long long dx = p->dist[at(x, lane)];
-        if (dx != kInf && dv + __ldg(p->w + j) == dx) sum += p->rho[at(x, lane)];
+        if (dx != kInf && a.dv + __ldg(p->w + j) == dx) a.sum += p->rho[at(x, lane)];
     }
-    __device__ static double combine(double a, double b) { return a + b; }
+    __device__ static DeltaAcc combine(DeltaAcc a, DeltaAcc b) { return DeltaAcc{a.sum + b.sum, a.dv}; }
 };
 
 __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
     __shared__ long long s_min[kWWarps][KW];
     __shared__ SigmaAcc s_sig[kWWarps][KW];
-    __shared__ double s_del[kWWarps][KW];
+    __shared__ DeltaAcc s_del[kWWarps][KW];
     GridTeam team{p.ctl, p.ctl, (int)gridDim.x, p.budget};
     const int lane = threadIdx.x & 31;
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -206,7 +230,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         }
         bool ch = false, ovf = false;
         SigmaArc arc{&p, cur, lane};
-        row_pass<SigmaArc>(p, SigmaAcc{0ull, false}, arc, [&](int v, SigmaAcc a) {
+        row_pass<SigmaArc>(p, SigmaAcc{0ull, kInf, false}, arc, [&](int v, SigmaAcc a) {
             unsigned long long s = a.s;
             if (p.dist[at(v, lane)] != kInf && v == p.src[lane]) {
                 s += 1ull;
@@ -244,8 +268,8 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         if (!team.sync()) return;
         bool ch = false;
         DeltaArc arc{&p, lane};
-        row_pass<DeltaArc>(p, 0.0, arc, [&](int v, double sum) {
-            const double d = (double)cur[at(v, lane)] * sum;
+        row_pass<DeltaArc>(p, DeltaAcc{0.0, kInf}, arc, [&](int v, DeltaAcc a) {
+            const double d = (double)cur[at(v, lane)] * a.sum;
             if (__double_as_longlong(d) != __double_as_longlong(dc[at(v, lane)])) ch = true;
             dn[at(v, lane)] = d;
         }, s_del);
@@ -264,10 +288,10 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
             if (p.src[c] >= 0 && p.src[c] != v) acc += dc[at((int)v, c)];
         p.bc[v] = acc;
     }
-    if (tid == 0) {
-        p.passes[0] = max(p.passes[0], pass_dist);
-        p.passes[1] = max(p.passes[1], pass_sigma);
-        p.passes[2] = max(p.passes[2], pass_delta);
+    if (tid == 0) {  // batches run one after another: plain sums
+        p.passes[0] += pass_dist;
+        p.passes[1] += pass_sigma;
+        p.passes[2] += pass_delta;
     }
 }
 
