@@ -218,7 +218,7 @@ struct bc_graph {
     DevBuf off, adj, perm, inv, hcum;
     DevBuf ioff, iadj;  // directed: in-CSR for the pull steps
     DevBuf w;           // weighted graphs: arc weights in relabelled arc order (empty otherwise)
-    DevBuf wdist, wsa, wsb, wda, wdb, wrho, wbc, wctl, wsrc;  // weighted BC state, kept between calls
+    DevBuf wdist, wsa, wsb, wda, wdb, wrho, wbc, wctl, wsrc, wscr, warr;  // weighted BC state, kept between calls
     AllocHook hook;
     std::mutex mu;                                 // bc_compute / plans: the per-width workspaces below
     std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
@@ -1064,7 +1064,8 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->perm, st);
     buf_release(g->ioff, st);
     buf_release(g->iadj, st);
-    for (DevBuf* b : {&g->w, &g->wdist, &g->wsa, &g->wsb, &g->wda, &g->wdb, &g->wrho, &g->wbc, &g->wctl, &g->wsrc})
+    for (DevBuf* b : {&g->w, &g->wdist, &g->wsa, &g->wsb, &g->wda, &g->wdb, &g->wrho, &g->wbc, &g->wctl, &g->wsrc,
+                      &g->wscr, &g->warr})
         buf_release(*b, st);
     buf_release(g->inv, st);
     cudaStreamSynchronize(st);
@@ -1157,7 +1158,9 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     if (!buf_ensure(g->wdist, 8 * cells, st) || !buf_ensure(g->wsa, 8 * cells, st) || !buf_ensure(g->wsb, 8 * cells, st) ||
         !buf_ensure(g->wda, 8 * cells, st) || !buf_ensure(g->wdb, 8 * cells, st) || !buf_ensure(g->wrho, 8 * cells, st) ||
         !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int), st) ||
-        !buf_ensure(g->wsrc, sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * KW + sizeof(int), st))
+        !buf_ensure(g->wsrc, sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * KW + sizeof(int), st) ||
+        !buf_ensure(g->wscr, 24 * KW * (size_t)(g->hchunk_total > 0 ? g->hchunk_total : 1), st) ||
+        !buf_ensure(g->warr, sizeof(int) * (size_t)(g->n_heavy > 0 ? g->n_heavy : 1), st))
         return done(fail(BC_E_NOMEM, "weighted BC buffers"));
     Ctl* ctl = (Ctl*)g->wctl.p;
     int* changed = (int*)((char*)g->wctl.p + sizeof(Ctl));
@@ -1185,8 +1188,10 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
         // fresh barrier and pass flags per launch (pass counts accumulate)
         e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(changed, 0, 4 * sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->warr.p, 0, sizeof(int) * (size_t)(g->n_heavy > 0 ? g->n_heavy : 1), st);
         if (e == cudaSuccess)
-            e = launch_wbc(g->n, g->n_heavy, (const int*)g->off.p, (const int*)g->adj.p, (const int*)g->w.p,
+            e = launch_wbc(g->n, g->n_heavy, g->hchunk_total, (const int*)g->hcum.p, (int*)g->warr.p, g->wscr.p,
+                           (const int*)g->off.p, (const int*)g->adj.p, (const int*)g->w.p,
                            (const int*)g->wsrc.p + (size_t)b * KW, (long long*)g->wdist.p,
                            (unsigned long long*)g->wsa.p, (unsigned long long*)g->wsb.p, (double*)g->wda.p,
                            (double*)g->wdb.p, (double*)g->wrho.p, (double*)g->wbc.p, ctl, changed, passes,

@@ -164,7 +164,8 @@ cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, c
 // weights of the relabelled arcs looked up from the original sorted CSR
 // (err bits: 1 rows not sorted, 2 a weight <= 0, 4 asymmetric weights).
 int wbc_blocks();
-cudaError_t launch_wbc(int n, int n_heavy, const int* off, const int* adj, const int* w, const int* src,
+cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, int* arr, void* scratch,
+                       const int* off, const int* adj, const int* w, const int* src,
                        long long* dist, unsigned long long* sa, unsigned long long* sb, double* da, double* db,
                        double* rho, double* bc, Ctl* ctl, int* changed, int* passes, long long budget, int blocks,
                        cudaStream_t st);

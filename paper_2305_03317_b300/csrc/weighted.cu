@@ -12,10 +12,11 @@
 // until a pass changes nothing (the count of passes is the hop depth of the
 // DAG plus one); then BC(v) += t(v) for every non-source column, columns in
 // order.  Distance mins and integer path counts do not depend on the order of
-// their terms; every double sum runs in CSR order (heavy rows: contiguous
-// eighths of the row, combined in order), so results repeat bit for bit.
-// Rows above 1024 arcs (the relabelled prefix [0, n_heavy)) take one block
-// each, the others one warp each.  Grid barriers are bounded by a cycle
+// their terms; every double sum runs in CSR order (long rows: per chunk,
+// chunks combined in order), so results repeat bit for bit.
+// Every task is one warp: a row of at most 1024 arcs, or a 1024-arc chunk of
+// a longer row (the relabelled prefix [0, n_heavy)), whose partials the
+// row's last chunk combines in chunk order.  Grid barriers are bounded by a cycle
 // budget like the traversal kernel's.
 #include <climits>
 #include <cstdint>
@@ -27,13 +28,16 @@ namespace bcx {
 namespace {
 
 constexpr int kWThreads = 256;
-constexpr int kWWarps = kWThreads / 32;
 constexpr int KW = 32;  // sources per batch
 constexpr long long kInf = LLONG_MAX;
 constexpr unsigned int kAll = 0xffffffffu;
 
 struct WParams {
     int n, n_heavy;
+    long long hchunks;         // chunk tasks of the heavy rows
+    const int* hcum;           // [n_heavy + 1] chunk prefix of the heavy rows
+    int* arr;                  // [n_heavy] chunk arrival counters
+    void* scratch;             // [hchunks][32] partials (24 bytes each at most)
     const int* off;
     const int* adj;
     const int* w;              // arc weights, relabelled arc order
@@ -54,39 +58,67 @@ struct WParams {
 
 __device__ __forceinline__ size_t at(int v, int lane) { return (size_t)v * KW + lane; }
 
-// One pass over every row: heavy rows one block each (warp k takes the k-th
-// eighth of the row, its partial lands in part[k]; warp 0 combines them in
-// order), light rows one warp each.
+// Reads another warp's partial from L2 (its writer fenced before arriving).
+template <class T>
+__device__ __forceinline__ T load_cg(const T* q) {
+    static_assert(sizeof(T) % 8 == 0, "partials are whole 8-byte words");
+    T x;
+    long long* d = reinterpret_cast<long long*>(&x);
+    const long long* s = reinterpret_cast<const long long*>(q);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 8); ++i) d[i] = __ldcg(s + i);
+    return x;
+}
+
+// One pass over every row, one warp per task: a light row, or a 1024-arc
+// chunk of a heavy row (chunk slots hcum[r] .. hcum[r+1]).  A chunk's partial
+// goes to its scratch slot; the warp that finishes a row's last chunk (arrival
+// counter) combines the partials in chunk order and finishes the row.
 template <class Arc, class Finish, class T>
-__device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, T (*part)[KW]) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    for (int r = blockIdx.x; r < p.n_heavy; r += gridDim.x) {
-        const int b = p.off[r], e = p.off[r + 1];
-        const int seg = (e - b + kWWarps - 1) / kWWarps;
-        const int lo = b + wib * seg, hi = min(e, lo + seg);
-        T acc = arc.start(r, init);
-        if (__any_sync(kAll, arc.live(acc))) {
+__device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish) {
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long tasks = p.hchunks + (p.n - p.n_heavy);
+    T* scratch = reinterpret_cast<T*>(p.scratch);
+    for (long long t = wid; t < tasks; t += nw) {
+        if (t < p.hchunks) {
+            int lo = 0, hi = p.n_heavy;  // hcum[lo] <= t < hcum[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (p.hcum[mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            const int r = lo, c0 = p.hcum[r], nch = p.hcum[r + 1] - c0;
+            const int b = p.off[r] + (int)(t - c0) * kChunk, e = min(p.off[r + 1], b + kChunk);
+            T acc = arc.start(r, init);
+            if (__any_sync(kAll, arc.live(acc))) {
 #pragma unroll 4
-            for (int j = lo; j < hi; ++j) arc(j, acc);
-        }
-        part[wib][lane] = acc;
-        __syncthreads();
-        if (wib == 0) {
-            T all = part[0][lane];
-            for (int k = 1; k < kWWarps; ++k) all = Arc::combine(all, part[k][lane]);
-            finish(r, all);
-        }
-        __syncthreads();
-    }
-    const long long nw = (long long)gridDim.x * kWWarps;
-    for (long long r = p.n_heavy + (long long)blockIdx.x * kWWarps + wib; r < p.n; r += nw) {
-        const int b = p.off[r], e = p.off[r + 1];
-        T acc = arc.start((int)r, init);
-        if (__any_sync(kAll, arc.live(acc))) {
+                for (int j = b; j < e; ++j) arc(j, acc);
+            }
+            scratch[(size_t)t * KW + lane] = acc;
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&p.arr[r], 1) == nch - 1;
+            last = __shfl_sync(kAll, last, 0);
+            if (last) {
+                __threadfence();
+                T all = load_cg(&scratch[(size_t)c0 * KW + lane]);
+                for (int k = 1; k < nch; ++k) all = Arc::combine(all, load_cg(&scratch[(size_t)(c0 + k) * KW + lane]));
+                finish(r, all);
+                if (lane == 0) p.arr[r] = 0;  // ready for the next pass (after its barrier)
+            }
+        } else {
+            const int r = p.n_heavy + (int)(t - p.hchunks);
+            const int b = p.off[r], e = p.off[r + 1];
+            T acc = arc.start(r, init);
+            if (__any_sync(kAll, arc.live(acc))) {
 #pragma unroll 4
-            for (int j = b; j < e; ++j) arc(j, acc);
+                for (int j = b; j < e; ++j) arc(j, acc);
+            }
+            finish(r, acc);
         }
-        finish((int)r, acc);
     }
 }
 
@@ -164,9 +196,6 @@ struct DeltaArc {
 };
 
 __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
-    __shared__ long long s_min[kWWarps][KW];
-    __shared__ SigmaAcc s_sig[kWWarps][KW];
-    __shared__ DeltaAcc s_del[kWWarps][KW];
     GridTeam team{p.ctl, p.ctl, (int)gridDim.x, p.budget};
     const int lane = threadIdx.x & 31;
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -212,7 +241,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
                 p.dist[at(v, lane)] = best;
                 ch = true;
             }
-        }, s_min);
+        });
         more = end_pass(ch);
         if (fail) return;
     }
@@ -240,7 +269,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
             big |= s >= (1ull << 53);
             if (s != cur[at(v, lane)]) ch = true;
             nxt[at(v, lane)] = s;
-        }, s_sig);
+        });
         if (ovf) atomicOr(&p.ctl->err, ERR_SIGMA_RANGE);
         more = end_pass(ch);
         if (fail) return;
@@ -272,7 +301,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
             const double d = (double)cur[at(v, lane)] * a.sum;
             if (__double_as_longlong(d) != __double_as_longlong(dc[at(v, lane)])) ch = true;
             dn[at(v, lane)] = d;
-        }, s_del);
+        });
         more = end_pass(ch);
         if (fail) return;
         double* t = dc;
@@ -352,13 +381,18 @@ int wbc_blocks() {
     return sms * per;
 }
 
-cudaError_t launch_wbc(int n, int n_heavy, const int* off, const int* adj, const int* w, const int* src,
+cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, int* arr, void* scratch,
+                       const int* off, const int* adj, const int* w, const int* src,
                        long long* dist, unsigned long long* sa, unsigned long long* sb, double* da, double* db,
                        double* rho, double* bc, Ctl* ctl, int* changed, int* passes, long long budget, int blocks,
                        cudaStream_t st) {
     WParams p;
     p.n = n;
     p.n_heavy = n_heavy;
+    p.hchunks = hchunks;
+    p.hcum = hcum;
+    p.arr = arr;
+    p.scratch = scratch;
     p.off = off;
     p.adj = adj;
     p.w = w;
