@@ -222,6 +222,8 @@ typedef struct {
     int32_t teams;           /* teams of the last launch */
     float order_ms;          /* device time of the source-grouping traversal (0 when the sources were not grouped;
                                 not part of kernel_ms) */
+    int64_t arcs_visited;    /* bc_compute_weighted: arcs read by all passes of all batches (0 otherwise) */
+    int64_t rows_visited;    /* bc_compute_weighted: rows recomputed by all passes of all batches */
 } bc_run_stats;
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 

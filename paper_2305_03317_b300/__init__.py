@@ -54,7 +54,8 @@ class bc_run_stats(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("batches", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("pull_levels", ctypes.c_int32), ("push_levels", ctypes.c_int32), ("ext_batches", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("kernel_ms", ctypes.c_float), ("teams", ctypes.c_int32), ("order_ms", ctypes.c_float)]
+                ("kernel_ms", ctypes.c_float), ("teams", ctypes.c_int32), ("order_ms", ctypes.c_float),
+                ("arcs_visited", ctypes.c_int64), ("rows_visited", ctypes.c_int64)]
 
 
 class bc_item(ctypes.Structure):

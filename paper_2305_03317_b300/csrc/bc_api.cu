@@ -218,7 +218,7 @@ struct bc_graph {
     DevBuf off, adj, perm, inv, hcum;
     DevBuf ioff, iadj;  // directed: in-CSR for the pull steps
     DevBuf w;           // weighted graphs: arc weights in relabelled arc order (empty otherwise)
-    DevBuf wdist, wsa, wsb, wda, wdb, wrho, wbc, wctl, wsrc, wscr, warr;  // weighted BC state, kept between calls
+    DevBuf wdist, wsig, winv, wdel, wrho, wmark, wbc, wctl, wsrc, wscr, warr;  // weighted BC state, kept between calls
     AllocHook hook;
     std::mutex mu;                                 // bc_compute / plans: the per-width workspaces below
     std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
@@ -1064,7 +1064,7 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->perm, st);
     buf_release(g->ioff, st);
     buf_release(g->iadj, st);
-    for (DevBuf* b : {&g->w, &g->wdist, &g->wsa, &g->wsb, &g->wda, &g->wdb, &g->wrho, &g->wbc, &g->wctl, &g->wsrc,
+    for (DevBuf* b : {&g->w, &g->wdist, &g->wsig, &g->winv, &g->wdel, &g->wrho, &g->wmark, &g->wbc, &g->wctl, &g->wsrc,
                       &g->wscr, &g->warr})
         buf_release(*b, st);
     buf_release(g->inv, st);
@@ -1155,9 +1155,9 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
         buf_release(hsrc, st);
         return rr;
     };
-    if (!buf_ensure(g->wdist, 8 * cells, st) || !buf_ensure(g->wsa, 8 * cells, st) || !buf_ensure(g->wsb, 8 * cells, st) ||
-        !buf_ensure(g->wda, 8 * cells, st) || !buf_ensure(g->wdb, 8 * cells, st) || !buf_ensure(g->wrho, 8 * cells, st) ||
-        !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int), st) ||
+    if (!buf_ensure(g->wdist, 8 * cells, st) || !buf_ensure(g->wsig, 8 * cells, st) || !buf_ensure(g->winv, 8 * cells, st) ||
+        !buf_ensure(g->wdel, 8 * cells, st) || !buf_ensure(g->wrho, 8 * cells, st) || !buf_ensure(g->wmark, 8 * n, st) ||
+        !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int) + 16, st) ||
         !buf_ensure(g->wsrc, sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * KW + sizeof(int), st) ||
         !buf_ensure(g->wscr, 24 * KW * (size_t)(g->hchunk_total > 0 ? g->hchunk_total : 1), st) ||
         !buf_ensure(g->warr, sizeof(int) * (size_t)(g->n_heavy > 0 ? g->n_heavy : 1), st))
@@ -1165,9 +1165,11 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     Ctl* ctl = (Ctl*)g->wctl.p;
     int* changed = (int*)((char*)g->wctl.p + sizeof(Ctl));
     int* passes = changed + 4;
+    static_assert((sizeof(Ctl) + 8 * sizeof(int)) % 8 == 0, "visited counters need 8-byte alignment");
+    unsigned long long* visited = (unsigned long long*)(changed + 8);  // arcs, rows
     int* bad = (int*)g->wsrc.p + (size_t)(nbatch > 0 ? nbatch : 1) * KW;
     cudaError_t e = cudaMemsetAsync(g->wbc.p, 0, 8 * n, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->wctl.p, 0, sizeof(Ctl) + 8 * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->wctl.p, 0, sizeof(Ctl) + 8 * sizeof(int) + 16, st);
     if (e == cudaSuccess && nbatch > 0) {
         e = cudaMemsetAsync(bad, 0, sizeof(int), st);
         if (e == cudaSuccess)
@@ -1189,12 +1191,13 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
         e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(changed, 0, 4 * sizeof(int), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(g->warr.p, 0, sizeof(int) * (size_t)(g->n_heavy > 0 ? g->n_heavy : 1), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->wmark.p, 0, 8 * n, st);
         if (e == cudaSuccess)
             e = launch_wbc(g->n, g->n_heavy, g->hchunk_total, (const int*)g->hcum.p, (int*)g->warr.p, g->wscr.p,
                            (const int*)g->off.p, (const int*)g->adj.p, (const int*)g->w.p,
                            (const int*)g->wsrc.p + (size_t)b * KW, (long long*)g->wdist.p,
-                           (unsigned long long*)g->wsa.p, (unsigned long long*)g->wsb.p, (double*)g->wda.p,
-                           (double*)g->wdb.p, (double*)g->wrho.p, (double*)g->wbc.p, ctl, changed, passes,
+                           (unsigned long long*)g->wsig.p, (double*)g->winv.p, (double*)g->wdel.p,
+                           (double*)g->wrho.p, (int*)g->wmark.p, (double*)g->wbc.p, ctl, changed, passes, visited,
                            40000000000ll, blocks, st);
         int herr = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1209,8 +1212,10 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     }
     cudaEventRecord(ev[1], st);
     int hp[3] = {0, 0, 0}, hflags = 0;
+    unsigned long long hv[2] = {0, 0};
     if (e == cudaSuccess) e = launch_unpermute((const double*)g->wbc.p, (const int*)g->inv.p, out_bc, g->n, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hp, passes, sizeof hp, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hv, visited, sizeof hv, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, &ctl->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     float ms = 0.f;
@@ -1228,6 +1233,8 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     s.kernel_launches = 2 + nbatch;          // kernels only: source mapping, one launch per batch, unpermute
     s.kernel_ms = ms;
     s.teams = 1;
+    s.arcs_visited = (int64_t)hv[0];
+    s.rows_visited = (int64_t)hv[1];
     g->last = s;
     return done((hflags & BST_INEXACT) ? BC_W_SIGMA_INEXACT : BC_OK);
 }

@@ -166,9 +166,9 @@ cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, c
 int wbc_blocks();
 cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, int* arr, void* scratch,
                        const int* off, const int* adj, const int* w, const int* src,
-                       long long* dist, unsigned long long* sa, unsigned long long* sb, double* da, double* db,
-                       double* rho, double* bc, Ctl* ctl, int* changed, int* passes, long long budget, int blocks,
-                       cudaStream_t st);
+                       long long* dist, unsigned long long* sig, double* inv, double* del, double* rho, int* mark,
+                       double* bc, Ctl* ctl, int* changed, int* passes, unsigned long long* visited, long long budget,
+                       int blocks, cudaStream_t st);
 cudaError_t launch_weight_ingest(const int* ooff, const int* oadj, const int* ow, const int* perm, const int* noff,
                                  const int* nadj, int n, int* nw, int* err, bool check_symmetry, cudaStream_t st);
 // Level table of a forward-only batch, then the levels of columns [0, L) at

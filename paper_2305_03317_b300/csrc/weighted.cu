@@ -43,15 +43,16 @@ struct WParams {
     const int* w;              // arc weights, relabelled arc order
     const int* src;            // [32] relabelled sources, -1 = unused column
     long long* dist;           // [n][32]
-    unsigned long long* sa;    // [n][32] path counts (two buffers)
-    unsigned long long* sb;
-    double* da;                // [n][32] dependencies (two buffers)
-    double* db;
-    double* rho;               // [n][32] (1 + delta) / sigma of the current pass
+    unsigned long long* sig;   // [n][32] path counts
+    double* inv;               // [n][32] 1 / sigma
+    double* del;               // [n][32] dependencies
+    double* rho;               // [n][32] (1 + delta) / sigma, kept with delta
+    int* mark;                 // [2][n] pass stamps: rows next to a row that changed
     double* bc;                // [n] relabelled
     Ctl* ctl;
     int* changed;              // [3] rotating "a pass changed something" flags
     int* passes;               // [3] passes run by each loop, summed over launches (out)
+    unsigned long long* visited;  // [2] arcs and rows the passes read, summed over launches (out)
     long long budget;
     int max_passes;
 };
@@ -74,13 +75,24 @@ __device__ __forceinline__ T load_cg(const T* q) {
 // chunk of a heavy row (chunk slots hcum[r] .. hcum[r+1]).  A chunk's partial
 // goes to its scratch slot; the warp that finishes a row's last chunk (arrival
 // counter) combines the partials in chunk order and finishes the row.
+//
+// Active rows: a pass recomputes only the rows stamped by the previous pass
+// (every pass when `all`): a row whose value changed stamps its neighbours for
+// the next pass, in the other of two stamp arrays, so no stamp a pass reads
+// changes during it.
 template <class Arc, class Finish, class T>
-__device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish) {
+__device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, int pass, bool all) {
+    const int* mprev = p.mark + (size_t)(pass & 1) * p.n;
+    int* mnext = p.mark + (size_t)((pass + 1) & 1) * p.n;
+    auto stamp = [&](int r) {
+        for (int j = p.off[r] + (threadIdx.x & 31); j < p.off[r + 1]; j += 32) mnext[__ldg(p.adj + j)] = pass + 1;
+    };
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long tasks = p.hchunks + (p.n - p.n_heavy);
     T* scratch = reinterpret_cast<T*>(p.scratch);
+    unsigned long long arcs = 0, rows = 0;  // read by this warp (lane 0 reports)
     for (long long t = wid; t < tasks; t += nw) {
         if (t < p.hchunks) {
             int lo = 0, hi = p.n_heavy;  // hcum[lo] <= t < hcum[hi]
@@ -90,11 +102,13 @@ __device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish) {
                 else hi = mid;
             }
             const int r = lo, c0 = p.hcum[r], nch = p.hcum[r + 1] - c0;
+            if (!all && mprev[r] != pass) continue;  // the same answer for every chunk of the row
             const int b = p.off[r] + (int)(t - c0) * kChunk, e = min(p.off[r + 1], b + kChunk);
             T acc = arc.start(r, init);
             if (__any_sync(kAll, arc.live(acc))) {
 #pragma unroll 4
                 for (int j = b; j < e; ++j) arc(j, acc);
+                arcs += e - b;
             }
             scratch[(size_t)t * KW + lane] = acc;
             __threadfence();
@@ -104,22 +118,28 @@ __device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish) {
             last = __shfl_sync(kAll, last, 0);
             if (last) {
                 __threadfence();
-                T all = load_cg(&scratch[(size_t)c0 * KW + lane]);
-                for (int k = 1; k < nch; ++k) all = Arc::combine(all, load_cg(&scratch[(size_t)(c0 + k) * KW + lane]));
-                finish(r, all);
+                T tot = load_cg(&scratch[(size_t)c0 * KW + lane]);
+                for (int k = 1; k < nch; ++k) tot = Arc::combine(tot, load_cg(&scratch[(size_t)(c0 + k) * KW + lane]));
+                ++rows;
+                if (__any_sync(kAll, finish(r, tot))) stamp(r);
                 if (lane == 0) p.arr[r] = 0;  // ready for the next pass (after its barrier)
             }
         } else {
             const int r = p.n_heavy + (int)(t - p.hchunks);
+            if (!all && mprev[r] != pass) continue;
             const int b = p.off[r], e = p.off[r + 1];
             T acc = arc.start(r, init);
+            ++rows;
             if (__any_sync(kAll, arc.live(acc))) {
 #pragma unroll 4
                 for (int j = b; j < e; ++j) arc(j, acc);
+                arcs += e - b;
             }
-            finish(r, acc);
+            if (__any_sync(kAll, finish(r, acc))) stamp(r);
         }
     }
+    if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
+    if (lane == 0 && rows) atomicAdd(&p.visited[1], rows);
 }
 
 // Arc functors: start(v, init) gives a row's running state, live(state)
@@ -149,7 +169,6 @@ struct SigmaAcc {
 
 struct SigmaArc {
     const WParams* p;
-    const unsigned long long* cur;
     int lane;
     __device__ SigmaAcc start(int v, SigmaAcc init) const {
         init.dv = p->dist[at(v, lane)];
@@ -161,7 +180,7 @@ struct SigmaArc {
         const int u = __ldg(p->adj + j);
         const long long du = p->dist[at(u, lane)];
         if (du != kInf && du + __ldg(p->w + j) == a.dv) {
-            const unsigned long long x = cur[at(u, lane)];
+            const unsigned long long x = p->sig[at(u, lane)];
             const unsigned long long s = a.s + x;
             a.ovf |= s < x;
             a.s = s;
@@ -218,16 +237,14 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
     };
     for (long long i = tid; i < cells; i += nthr) {
         p.dist[i] = kInf;
-        p.sa[i] = 0ull;
-        p.sb[i] = 0ull;
-        p.da[i] = 0.0;
-        p.db[i] = 0.0;
+        p.sig[i] = 0ull;
+        p.del[i] = 0.0;
     }
     if (!team.sync()) return;
     if (tid < KW && p.src[tid] >= 0) p.dist[at(p.src[tid], (int)tid)] = 0;
     if (!team.sync()) return;
 
-    // distances, in place
+    // distances, in place (stale reads are valid upper bounds)
     int np = 0;
     for (bool more = true; more;) {
         if (++np > p.max_passes) {
@@ -240,16 +257,16 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
             if (best < p.dist[at(v, lane)]) {
                 p.dist[at(v, lane)] = best;
                 ch = true;
+                return true;
             }
-        });
+            return false;
+        }, pass, np == 1);
         more = end_pass(ch);
         if (fail) return;
     }
     const int pass_dist = np;
 
-    // path counts, from cur into nxt until nothing changes
-    unsigned long long* cur = p.sa;
-    unsigned long long* nxt = p.sb;
+    // path counts, in place: every value only grows towards the DAG sums
     np = 0;
     bool big = false;
     for (bool more = true; more;) {
@@ -258,7 +275,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
             return;
         }
         bool ch = false, ovf = false;
-        SigmaArc arc{&p, cur, lane};
+        SigmaArc arc{&p, lane};
         row_pass<SigmaArc>(p, SigmaAcc{0ull, kInf, false}, arc, [&](int v, SigmaAcc a) {
             unsigned long long s = a.s;
             if (p.dist[at(v, lane)] != kInf && v == p.src[lane]) {
@@ -267,46 +284,47 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
             }
             ovf |= a.ovf;
             big |= s >= (1ull << 53);
-            if (s != cur[at(v, lane)]) ch = true;
-            nxt[at(v, lane)] = s;
-        });
+            if (s != p.sig[at(v, lane)]) {
+                p.sig[at(v, lane)] = s;
+                ch = true;
+                return true;
+            }
+            return false;
+        }, pass, np == 1);
         if (ovf) atomicOr(&p.ctl->err, ERR_SIGMA_RANGE);
         more = end_pass(ch);
         if (fail) return;
-        unsigned long long* t = cur;
-        cur = nxt;
-        nxt = t;
     }
     const int pass_sigma = np;
     if (__any_sync(kAll, big) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
-    // cur holds the counts; nxt becomes 1 / sigma (double bits)
-    double* inv = reinterpret_cast<double*>(nxt);
-    for (long long i = tid; i < cells; i += nthr) inv[i] = cur[i] ? 1.0 / (double)cur[i] : 0.0;
+    for (long long i = tid; i < cells; i += nthr) {
+        const double iv = p.sig[i] ? 1.0 / (double)p.sig[i] : 0.0;
+        p.inv[i] = iv;
+        p.rho[i] = iv;  // delta = 0
+    }
     if (!team.sync()) return;
 
-    // dependencies, from dc into dn until nothing changes
-    double* dc = p.da;
-    double* dn = p.db;
+    // dependencies, in place, rho rewritten with each new delta
     np = 0;
     for (bool more = true; more;) {
         if (++np > p.max_passes) {
             if (tid == 0) atomicOr(&p.ctl->err, ERR_INTERNAL);
             return;
         }
-        for (long long i = tid; i < cells; i += nthr) p.rho[i] = (1.0 + dc[i]) * inv[i];
-        if (!team.sync()) return;
         bool ch = false;
         DeltaArc arc{&p, lane};
         row_pass<DeltaArc>(p, DeltaAcc{0.0, kInf}, arc, [&](int v, DeltaAcc a) {
-            const double d = (double)cur[at(v, lane)] * a.sum;
-            if (__double_as_longlong(d) != __double_as_longlong(dc[at(v, lane)])) ch = true;
-            dn[at(v, lane)] = d;
-        });
+            const double d = (double)p.sig[at(v, lane)] * a.sum;
+            if (__double_as_longlong(d) != __double_as_longlong(p.del[at(v, lane)])) {
+                p.del[at(v, lane)] = d;
+                p.rho[at(v, lane)] = (1.0 + d) * p.inv[at(v, lane)];
+                ch = true;
+                return true;
+            }
+            return false;
+        }, pass, np == 1);
         more = end_pass(ch);
         if (fail) return;
-        double* t = dc;
-        dc = dn;
-        dn = t;
     }
     const int pass_delta = np;
 
@@ -314,7 +332,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
     for (long long v = tid; v < p.n; v += nthr) {
         double acc = p.bc[v];
         for (int c = 0; c < KW; ++c)
-            if (p.src[c] >= 0 && p.src[c] != v) acc += dc[at((int)v, c)];
+            if (p.src[c] >= 0 && p.src[c] != v) acc += p.del[at((int)v, c)];
         p.bc[v] = acc;
     }
     if (tid == 0) {  // batches run one after another: plain sums
@@ -383,9 +401,9 @@ int wbc_blocks() {
 
 cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, int* arr, void* scratch,
                        const int* off, const int* adj, const int* w, const int* src,
-                       long long* dist, unsigned long long* sa, unsigned long long* sb, double* da, double* db,
-                       double* rho, double* bc, Ctl* ctl, int* changed, int* passes, long long budget, int blocks,
-                       cudaStream_t st) {
+                       long long* dist, unsigned long long* sig, double* inv, double* del, double* rho, int* mark,
+                       double* bc, Ctl* ctl, int* changed, int* passes, unsigned long long* visited, long long budget,
+                       int blocks, cudaStream_t st) {
     WParams p;
     p.n = n;
     p.n_heavy = n_heavy;
@@ -398,15 +416,16 @@ cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, i
     p.w = w;
     p.src = src;
     p.dist = dist;
-    p.sa = sa;
-    p.sb = sb;
-    p.da = da;
-    p.db = db;
+    p.sig = sig;
+    p.inv = inv;
+    p.del = del;
     p.rho = rho;
+    p.mark = mark;
     p.bc = bc;
     p.ctl = ctl;
     p.changed = changed;
     p.passes = passes;
+    p.visited = visited;
     p.budget = budget;
     p.max_passes = n + 2;
     cudaLaunchConfig_t cfg = {};

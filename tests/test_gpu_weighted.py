@@ -79,10 +79,12 @@ def test_rmat_all_sources_and_repeatable(bc):
     assert np.array_equal(a.view(np.uint64), b.cpu().numpy().view(np.uint64))
     assert st == bc.BC_OK and stats["batches"] == (g.n + 31) // 32
     assert stats["max_levels"] >= 2 and stats["pull_levels"] >= 2 and stats["push_levels"] >= 2
+    # the first pass of each of the three loops reads every arc of every batch
+    assert stats["arcs_visited"] >= 3 * stats["batches"] * g.m * 0.9 and stats["rows_visited"] >= 3 * g.n
     assert_bc_close(a, oracle.wbc(g.off, g.adj, wt, src))
 
 
-def test_heavy_rows_take_the_block_path(bc):
+def test_long_rows_take_the_chunk_path(bc):
     # hubs above 1024 arcs: a weighted star and an R-MAT graph with big hubs
     s = bcgen.star(3000)
     wt = bcgen.edge_weights(s, 1, 5, 2)
