@@ -1577,8 +1577,29 @@ bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, 
     const int bounds[2] = {8192, 32};
     if (!g->directed)
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) cls[i] = first_row_shorter(g, bounds[i], st, &e);
+    // chunk slots of the long rows (2048 arcs each)
+    DevBuf ccum, cpart, carr;
+    std::vector<int> hoff((size_t)cls[0] + 1), hc((size_t)cls[0] + 1, 0);
+    if (e == cudaSuccess && cls[0] > 0) {
+        e = cudaMemcpyAsync(hoff.data(), g->off.p, sizeof(int) * ((size_t)cls[0] + 1), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        for (int r = 0; r < cls[0]; ++r) hc[r + 1] = hc[r] + (hoff[r + 1] - hoff[r] + 2047) / 2048;
+    }
+    const long long nchunks = hc[cls[0]];
+    if (e == cudaSuccess &&
+        (!buf_ensure(ccum, sizeof(int) * hc.size(), st) || !buf_ensure(cpart, sizeof(double) * (size_t)(nchunks + 1), st) ||
+         !buf_ensure(carr, sizeof(int) * (size_t)(cls[0] + 1), st))) {
+        release();
+        buf_release(ccum, st);
+        buf_release(cpart, st);
+        buf_release(carr, st);
+        return fail(BC_E_NOMEM, "PageRank buffers");
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ccum.p, hc.data(), sizeof(int) * hc.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(carr.p, 0, sizeof(int) * (size_t)(cls[0] + 1), st);
     if (e == cudaSuccess)
-        e = launch_pagerank(g->n, (const int*)g->off.p, roff, radj, g->directed ? nullptr : cls, delta, beta, max_iter,
+        e = launch_pagerank(g->n, (const int*)g->off.p, roff, radj, g->directed ? nullptr : cls, nchunks,
+                            (const int*)ccum.p, (double*)cpart.p, (int*)carr.p, delta, beta, max_iter,
                             (double*)rank.p, (double*)scratch.p, (Ctl*)ctl.p, d_iters, d_diff, d_go, 40000000000ll,
                             blocks, st);
     if (e == cudaSuccess) e = launch_unpermute((const double*)rank.p, (const int*)g->inv.p, out_rank, g->n, st);
@@ -1589,6 +1610,9 @@ bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, &((Ctl*)ctl.p)->err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     release();
+    buf_release(ccum, st);
+    buf_release(cpart, st);
+    buf_release(carr, st);
     if (e != cudaSuccess) return cuda_fail(e, "PageRank");
     if (h_err & ERR_TIMEOUT) return fail(BC_E_TIMEOUT, "a grid-barrier wait exceeded its cycle budget");
     if (h_err) return fail(BC_E_CUDA, "PageRank kernel error 0x%x", h_err);

@@ -183,6 +183,7 @@ int pagerank_blocks();
 // row_class (rows sorted by length; null = not sorted): first rows shorter than
 // 8192 and than 32 arcs
 cudaError_t launch_pagerank(int n, const int* off, const int* roff, const int* radj, const int* row_class,
+                            long long nchunks, const int* ccum, double* cpart, int* carr,
                             double delta, double beta, int max_iter, double* rank, double* scratch, Ctl* ctl, int* iters,
                             double* diff_out, int* go, long long budget, int blocks, cudaStream_t st);
 

@@ -9,7 +9,8 @@
 // c(u) = rank(u) / outdeg(u); (2) a pull over in-rows (the CSR itself for an
 // undirected graph, the transpose for a directed one).  The relabelled rows
 // of an undirected graph are sorted by length, so they split into a prefix of
-// rows of at least 8192 arcs (one block per row), then rows of at least 32
+// rows of at least 8192 arcs (2048-arc warp tasks whose sums the row's last
+// task adds in chunk order), then rows of at least 32
 // (one warp per row) and the rest (one thread per row, CSR order; measured
 // faster than 16/8/4/2-lane groups per row); in-rows of
 // a directed graph are taken 32 at a time per warp, the long ones summed by
@@ -45,9 +46,15 @@ struct PrParams {
     double* diff_out;  // last change
     int* go;           // 1 while another sweep follows
     long long budget;
-    int n_block_rows;  // sorted rows: [0, n_block_rows) one block each,
+    int n_block_rows;  // sorted rows: [0, n_block_rows) in chunks,
     int n_warp_rows;   // [n_block_rows, n_warp_rows) one warp each, the rest one thread each; -1 = unsorted
+    long long nchunks;  // warp tasks of the long rows: chunk slots ccum[r] .. ccum[r+1]
+    const int* ccum;
+    double* cpart;      // [nchunks] chunk sums
+    int* carr;          // [n_block_rows] chunk arrival counters
 };
+
+constexpr int kPrChunk = 2048;  // arcs per warp task of a long row
 
 __device__ double block_sum(double x, double* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -82,15 +89,35 @@ __global__ void __launch_bounds__(kPrThreads) k_pagerank(PrParams p) {
         if (!team.sync()) return;
         double mine = 0.0;  // |change| of the rows this lane finished
         if (p.n_warp_rows >= 0) {
-            for (int r = blockIdx.x; r < p.n_block_rows; r += gridDim.x) {
-                const int b = p.roff[r], l = p.roff[r + 1] - b;
+            // long rows: 2048-arc warp tasks; a chunk's sum (lane-strided,
+            // then a fixed xor tree) goes to its slot, and the warp that
+            // finishes a row's last chunk adds the slots in chunk order
+            for (long long t = wid; t < p.nchunks; t += nwarps) {
+                int lo = 0, hi = p.n_block_rows;  // ccum[lo] <= t < ccum[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (p.ccum[mid] <= t) lo = mid;
+                    else hi = mid;
+                }
+                const int r = lo, c0 = p.ccum[r], nch = p.ccum[r + 1] - c0;
+                const int b = p.roff[r] + (int)(t - c0) * kPrChunk, e = min(p.roff[r + 1], b + kPrChunk);
                 double s = 0.0;
-                for (int e = b + threadIdx.x; e < b + l; e += blockDim.x) s += p.contrib[p.radj[e]];
-                s = block_sum(s, sh);
-                if (threadIdx.x == 0) {
-                    const double val = base + p.delta * s;
-                    mine += fabs(val - rank[r]);
-                    nxt[r] = val;
+                for (int j = b + lane; j < e; j += 32) s += p.contrib[p.radj[j]];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kAllLanes, s, o);
+                int last = 0;
+                if (lane == 0) {
+                    p.cpart[t] = s;
+                    __threadfence();
+                    last = atomicAdd(&p.carr[r], 1) == nch - 1;
+                }
+                last = __shfl_sync(kAllLanes, last, 0);
+                if (last && lane == 0) {
+                    __threadfence();
+                    double tot = __ldcg(&p.cpart[c0]);
+                    for (int k = 1; k < nch; ++k) tot += __ldcg(&p.cpart[c0 + k]);
+                    nxt[r] = base + p.delta * tot;
+                    p.carr[r] = 0;  // ready for the next sweep (after its barriers)
                 }
             }
             for (long long r = p.n_block_rows + wid; r < p.n_warp_rows; r += nwarps) {
@@ -145,6 +172,11 @@ __global__ void __launch_bounds__(kPrThreads) k_pagerank(PrParams p) {
                 }
             }
         }
+        if (p.n_block_rows > 0) {
+            // the long rows' changes, once their sums are in, by a fixed thread each
+            if (!team.sync()) return;
+            for (long long r = tid; r < p.n_block_rows; r += nthr) mine += fabs(nxt[r] - rank[r]);
+        }
         const double bs = block_sum(mine, sh);
         if (threadIdx.x == 0) p.partial[blockIdx.x] = bs;
         if (!team.sync()) return;
@@ -178,9 +210,14 @@ int pagerank_blocks() {
 }
 
 cudaError_t launch_pagerank(int n, const int* off, const int* roff, const int* radj, const int* row_class,
+                            long long nchunks, const int* ccum, double* cpart, int* carr,
                             double delta, double beta, int max_iter, double* rank, double* scratch, Ctl* ctl, int* iters,
                             double* diff_out, int* go, long long budget, int blocks, cudaStream_t st) {
     PrParams p;
+    p.nchunks = row_class ? nchunks : 0;
+    p.ccum = ccum;
+    p.cpart = cpart;
+    p.carr = carr;
     p.n_block_rows = row_class ? row_class[0] : -1;
     p.n_warp_rows = row_class ? row_class[1] : -1;
     p.n = n;
