@@ -4,20 +4,24 @@
 // BFS levels; with weights the levels become distances, and the paper's own
 // SSSP program (Section 2.3, the Min construct inside a fixed-point loop)
 // gives them by Bellman-Ford relaxation.  Per batch of 32 sources (lane =
-// column), one cooperative persistent launch runs three fixed-point loops over
-// every row, each pass pulling from the row's neighbours:
-//   dist:  d(v) = min(d(v), min over arcs u-v of d(u) + w)      (in place)
-//   sigma: s'(v) = [v = source] + sum over u with d(u) + w = d(v) of s(u)
-//   delta: t'(v) = s(v) * sum over x with d(v) + w = d(x) of (1 + t(x)) / s(x)
-// until a pass changes nothing (the count of passes is the hop depth of the
-// DAG plus one); then BC(v) += t(v) for every non-source column, columns in
-// order.  Distance mins and integer path counts do not depend on the order of
-// their terms; every double sum runs in CSR order (long rows: per chunk,
-// chunks combined in order), so results repeat bit for bit.
-// Every task is one warp: a row of at most 1024 arcs, or a 1024-arc chunk of
-// a longer row (the relabelled prefix [0, n_heavy)), whose partials the
-// row's last chunk combines in chunk order.  Grid barriers are bounded by a cycle
-// budget like the traversal kernel's.
+// column), one cooperative persistent launch runs three fixed-point loops,
+// each pass pulling into a row from its neighbours, all in place:
+//   dist:  d(v) = min(d(v), min over arcs u-v of d(u) + w)
+//   sigma: s(v) = [v = source] + sum over u with d(u) + w = d(v) of s(u)
+//   delta: t(v) = s(v) * sum over x with d(v) + w = d(x) of rho(x),
+//          rho(x) = (1 + t(x)) / s(x), rewritten with each new t(x)
+// until a pass changes nothing; then BC(v) += t(v) for every non-source
+// column, columns in order.  Distances only fall and counts and dependencies
+// only grow towards the DAG values, so a read of a neighbour another warp is
+// rewriting is always a valid bound and the fixed point is the unique one,
+// whatever the timing.  After a loop's first pass, a pass recomputes only the
+// rows next to a row that changed (stamps).  Distance mins and integer path
+// counts do not depend on the order of their terms; every double sum runs in
+// CSR order (long rows: per chunk, chunks combined in order), so results
+// repeat bit for bit.  Every task is one warp: a row of at most 1024 arcs, or
+// a 1024-arc chunk of a longer row (the relabelled prefix [0, n_heavy)),
+// whose partials the row's last chunk combines.  Grid barriers are bounded by
+// a cycle budget like the traversal kernel's.
 #include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
