@@ -1615,17 +1615,43 @@ __global__ void k_bfs_rows(KParams p, int K, int ncols, const unsigned short* __
             unsigned short l8[8];
             unsigned long long s8[8];
             int e8[8];
+            if (K % 8 == 0 && ok) {
+                // the 8 columns of the row slice with 16-byte reads (rows are
+                // K * 2 and K * 8 bytes, K a multiple of 8); path counts of
+                // unreached columns are read but not used
+                const uint4 lv = *reinterpret_cast<const uint4*>(lvl + (size_t)v * K + c0);
+                const unsigned int w4[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int c = c0 + k;
-                l8[k] = 0xFFFFu;
-                s8[k] = 0ull;
-                e8[k] = 0;
-                if (ok && c < ncols) {
-                    l8[k] = lvl[(size_t)v * K + c];
-                    if (sig_out && l8[k] != 0xFFFFu) {
-                        s8[k] = p.sig[(size_t)v * K + c];
-                        if (p.ext) e8[k] = p.sig_e[(size_t)v * K + c];
+                for (int k = 0; k < 8; ++k) {
+                    l8[k] = c0 + k < ncols ? (unsigned short)(w4[k >> 1] >> (16 * (k & 1))) : (unsigned short)0xFFFFu;
+                    e8[k] = 0;
+                    s8[k] = 0ull;
+                }
+                if (sig_out) {
+                    const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(p.sig + (size_t)v * K + c0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const ulonglong2 x = sp[k];
+                        s8[2 * k] = x.x;
+                        s8[2 * k + 1] = x.y;
+                    }
+                    if (p.ext)
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) e8[k] = p.sig_e[(size_t)v * K + c0 + k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int c = c0 + k;
+                    l8[k] = 0xFFFFu;
+                    s8[k] = 0ull;
+                    e8[k] = 0;
+                    if (ok && c < ncols) {
+                        l8[k] = lvl[(size_t)v * K + c];
+                        if (sig_out && l8[k] != 0xFFFFu) {
+                            s8[k] = p.sig[(size_t)v * K + c];
+                            if (p.ext) e8[k] = p.sig_e[(size_t)v * K + c];
+                        }
                     }
                 }
             }
@@ -1636,12 +1662,13 @@ __global__ void k_bfs_rows(KParams p, int K, int ncols, const unsigned short* __
                 const size_t o = (size_t)c * (size_t)n + (size_t)u;
                 level_out[o] = l8[k] == 0xFFFFu ? -1 : (int)l8[k];
                 if (sig_out) {
+                    const unsigned long long sv = l8[k] == 0xFFFFu ? 0ull : s8[k];
                     if (exp_out) {
                         int e = 0;
-                        sig_out[o] = frexp((double)s8[k], &e);
-                        exp_out[o] = s8[k] ? e + e8[k] : 0;
+                        sig_out[o] = frexp((double)sv, &e);
+                        exp_out[o] = sv ? e + e8[k] : 0;
                     } else {
-                        sig_out[o] = ldexp((double)s8[k], e8[k]);
+                        sig_out[o] = e8[k] ? ldexp((double)sv, e8[k]) : (double)sv;
                     }
                 }
             }
