@@ -8,7 +8,8 @@
  *     delta_s(v) = sum over DAG successors w of (sigma_v / sigma_w)(1 + delta_s(w))
  * (the iterateInReverse body), and BC(v) += delta_s(v) for every v != s.
  * The graph is unweighted, undirected (symmetric) or directed, given as int32
- * CSR (Section 3.1: the backend keeps graphs in CSR).  The result is the raw
+ * CSR (Section 3.1: the backend keeps graphs in CSR); bc_compute_weighted
+ * covers undirected graphs with positive integer arc weights.  The result is the raw
  * sum over the listed sources: no halving for undirected graphs, no
  * normalisation, no extrapolation from sampled sources.  A source listed twice
  * counts twice.
@@ -19,11 +20,13 @@
  * below 2^64.  delta and BC are IEEE double.  BC_W_SIGMA_INEXACT
  * reports that some count reached 2^53 (the double conversion in the backward
  * sweep then rounds).  Results are deterministic: every sum runs in a fixed
- * order (CSR row order, in fixed 1024-arc chunks; sources in list order).
+ * order (CSR row order, in fixed 1024-arc chunks; sources in list order, or in
+ * the grouped order of bc_options.source_order, which depends only on the
+ * graph and the list, so a direct call, a plan and a served job agree).
  *
  * Threading: a bc_graph may be used by one host thread at a time for
- * bc_compute / bc_bfs / bc_pagerank / bc_debug_source (calls on one graph
- * serialise); bc_batch_submit / bc_poll are thread-safe.  Every traversal is
+ * bc_compute / bc_bfs / bc_pagerank / bc_compute_weighted / bc_debug_source
+ * (calls on one graph serialise); bc_batch_submit / bc_poll are thread-safe.  Every traversal is
  * a cooperative launch sized to its share of the GPU: a full-GPU call issued
  * while serving slots run waits for their blocks, its bounded waits then
  * limiting how long (BC_E_TIMEOUT past the barrier budget).
