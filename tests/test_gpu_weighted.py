@@ -174,3 +174,22 @@ def test_invalid_weighted_inputs(bc):
     a, _ = W.compute(np.arange(5))
     b, _ = G.compute(np.arange(5))
     assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_device_inputs_and_skip_validation(bc):
+    import torch
+    g = bcgen.rmat(10, 8, 6)
+    wt = bcgen.edge_weights(g, 1, 30, 6)
+    src = bcgen.sample_sources(g, 40, 6)
+    want = oracle.wbc(g.off, g.adj, wt, src)
+    host, _, _ = wgpu(bc, g, wt, src)
+    # CSR and weights already on the device (BC_INPUT_ON_DEVICE)
+    G = bc.Graph(torch.from_numpy(g.off).cuda(), torch.from_numpy(g.adj).cuda(),
+                 weights=torch.from_numpy(wt).cuda())
+    dev, _ = G.compute_weighted(torch.from_numpy(src).cuda())
+    assert np.array_equal(dev.cpu().numpy().view(np.uint64), host.view(np.uint64))
+    # valid input with the checks skipped gives the same result
+    S = bc.Graph(g.off, g.adj, weights=wt, validate=False)
+    skip, _ = S.compute_weighted(src)
+    assert np.array_equal(skip.cpu().numpy().view(np.uint64), host.view(np.uint64))
+    assert_bc_close(host, want)
