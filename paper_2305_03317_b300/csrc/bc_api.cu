@@ -229,6 +229,9 @@ struct bc_graph {
     std::vector<long long> last_trace;             // (tag, t_ns) pairs of the last traced call
     cudaStream_t last_stream = nullptr;
     std::atomic<int> users{0};  // plans and queued serving jobs that refer to the graph
+    std::mutex lm_mu;           // the landmark table below, built once on first use
+    DevBuf landmark;            // [n][32] uint16 levels of the BFS from each of the 32 first relabelled vertices
+    int lm_levels = -1;         // levels of that BFS; -1 = not built
 };
 
 // ------------------------------------------------------------------ helpers
@@ -686,8 +689,8 @@ static void apply_tuning(const bc_graph* g, int nsrc, bc_options& o) {
 // source grouping (defined with the C entry points below, used by the serving workers)
 extern "C" {
 static bool want_grouping(const bc_graph* g, int nsrc, const bc_options& o);
-static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_src, int nsrc, cudaStream_t st,
-                               DevBuf& out, bc_run_stats* acc, std::vector<int>* host_out);
+static bc_status group_sources(bc_graph* g, const int* d_src, int nsrc, cudaStream_t st, DevBuf& out,
+                               bc_run_stats* acc, std::vector<int>* host_out);
 }
 
 namespace {
@@ -809,7 +812,7 @@ void worker_main(int slot) {
             cudaError_t e = cudaMemcpyAsync(dsrc.p, j->src.data(), sizeof(int) * (size_t)n1, cudaMemcpyHostToDevice, st);
             bc_run_stats gs{};
             std::vector<int> grouped;
-            r = e == cudaSuccess ? group_sources(g, &ws, K >= 32 ? K : 32, (const int*)dsrc.p, n1, st, tmp, &gs, &grouped)
+            r = e == cudaSuccess ? group_sources(g, (const int*)dsrc.p, n1, st, tmp, &gs, &grouped)
                                  : cuda_fail(e, "source copy");
             buf_release(tmp, st);
             if (r == BC_OK) {
@@ -1075,6 +1078,7 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->perm, st);
     buf_release(g->ioff, st);
     buf_release(g->iadj, st);
+    buf_release(g->landmark, st);
     for (DevBuf* b : {&g->w, &g->wdist, &g->wsig, &g->winv, &g->wdel, &g->wrho, &g->wmark, &g->wbc, &g->wctl, &g->wsrc,
                       &g->wscr, &g->warr})
         buf_release(*b, st);
@@ -1276,57 +1280,81 @@ bc_status bc_graph_export(const bc_graph* g, int32_t* perm, int32_t* offsets, in
 // in one batch their columns match the same arcs: more arcs reach the
 // column-mapped threshold and fewer single (arc, column) pairs remain.  The
 // key of a source is its distance vector to the 32 highest-degree vertices
-// (relabelled ids 0..31), taken from one forward-only traversal of those 32
-// vertices (undirected: d(h, s) = d(s, h)); sources are stably sorted by it,
+// (relabelled ids 0..31), read from the graph's landmark table (one
+// forward-only traversal of those 32 vertices, built on first use and kept;
+// undirected: d(h, s) = d(s, h)); sources are stably sorted by it,
 // nearest-hub distance first.  Levels are exact integers, so the order does
-// not depend on the batch width that computed them.
+// not depend on anything but the graph and the list.
 static bool want_grouping(const bc_graph* g, int nsrc, const bc_options& o) {
     if (o.source_order == 1 || g->directed || g->n_nz < 32) return false;
     if (o.source_order == 2) return true;
     return nsrc >= 256 && g->n_nz >= 2048 && (double)g->max_deg * g->n_nz >= 16.0 * (double)g->m;
 }
 
-static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_src, int nsrc, cudaStream_t st,
-                               DevBuf& out, bc_run_stats* acc, std::vector<int>* host_out) {
+// The landmark table is a fact of the graph: built once, on first use, by a
+// forward-only traversal of the 32 first relabelled vertices in a 32-wide
+// workspace of its own (freed right after), then kept ([n][32] uint16).
+static bc_status ensure_landmarks(bc_graph* g, cudaStream_t st, bc_run_stats* acc) {
     constexpr int L = 32;
-    int Kw = K;
-    if (K < L) {  // the plain per-source width: a 32-wide workspace of its own
-        auto& slot = g->ws[L];
-        if (!slot) slot.reset(new Workspace());
-        w = slot.get();
-        Kw = L;
-    }
-    if (!buf_ensure(w->bc, sizeof(double) * (size_t)g->n, st)) return fail(BC_E_NOMEM, "output buffer");
+    std::lock_guard<std::mutex> lk(g->lm_mu);
+    if (g->lm_levels >= 0) return BC_OK;
+    Workspace tmp;
+    auto done = [&](bc_status r) {
+        cudaStreamSynchronize(st);
+        tmp.release(st);
+        return r;
+    };
+    if (!buf_ensure(tmp.bc, sizeof(double) * (size_t)g->n, st) ||
+        !buf_ensure(g->landmark, sizeof(unsigned short) * (size_t)g->n * L, st))
+        return done(fail(BC_E_NOMEM, "landmark table"));
     bc_options o;
     memset(&o, 0, sizeof o);
-    o.batch_width = Kw;
-    std::vector<double*> jb{(double*)w->bc.p};
+    o.batch_width = L;
+    std::vector<double*> jb{(double*)tmp.bc.p};
     bc_run_stats rs{};
     int kused = 0, levels = 0;
     bool ext = false;
-    bc_status r = run_jobs(g, w, (const int*)g->perm.p, L, o, 1, jb, nullptr, true, st, &rs, &kused, &ext, &levels);
-    if (r < 0) return r;
-    DevBuf lvl, keys;
+    bc_status r = run_jobs(g, &tmp, (const int*)g->perm.p, L, o, 1, jb, nullptr, true, st, &rs, &kused, &ext, &levels);
+    if (r < 0) return done(r);
+    KParams p = make_params(g, &tmp, 1, o, ext, 1);
+    cudaError_t e = launch_level_table(p, L, levels, (unsigned short*)g->landmark.p, g->n, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(cuda_fail(e, "landmark table"));
+    g->lm_levels = levels;
+    acc->kernel_launches += rs.kernel_launches + (levels > 0 ? 1 : 0);
+    acc->kernel_ms += rs.kernel_ms;
+    return done(BC_OK);
+}
+
+static bc_status group_sources(bc_graph* g, const int* d_src, int nsrc, cudaStream_t st, DevBuf& out,
+                               bc_run_stats* acc, std::vector<int>* host_out) {
+    constexpr int L = 32;
+    bc_status r = ensure_landmarks(g, st, acc);
+    if (r != BC_OK) return r;
+    const int levels = g->lm_levels;
+    DevBuf keys;
     std::vector<unsigned short> hk((size_t)nsrc * L);
     std::vector<int> hs(nsrc);
-    auto release = [&]() {
-        buf_release(lvl, st);
-        buf_release(keys, st);
-    };
-    if (!buf_ensure(lvl, sizeof(unsigned short) * (size_t)g->n * Kw, st) ||
-        !buf_ensure(keys, sizeof(unsigned short) * hk.size(), st)) {
-        release();
-        return fail(BC_E_NOMEM, "grouping buffers");
-    }
-    KParams p = make_params(g, w, 1, o, ext, 1);
-    cudaError_t e = launch_level_keys(p, kused, levels, L, (unsigned short*)lvl.p, g->n, d_src, nsrc,
-                                      (const int*)g->inv.p, (unsigned short*)keys.p, st);
+    if (!buf_ensure(keys, sizeof(unsigned short) * hk.size(), st)) return fail(BC_E_NOMEM, "grouping buffers");
+    cudaEvent_t ev[2];
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    cudaEventRecord(ev[0], st);
+    cudaError_t e = launch_source_keys((const unsigned short*)g->landmark.p, L, L, g->n, d_src, nsrc,
+                                       (const int*)g->inv.p, (unsigned short*)keys.p, st);
+    cudaEventRecord(ev[1], st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hk.data(), keys.p, sizeof(unsigned short) * hk.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), d_src, sizeof(int) * (size_t)nsrc, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    release();
+    float kms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&kms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    buf_release(keys, st);
     if (e != cudaSuccess) return cuda_fail(e, "source grouping");
+    acc->kernel_launches += 1;
+    acc->kernel_ms += kms;
     // levels are below `levels`; 0xFFFF (unreached) ranks after them
     std::vector<int> idx(nsrc), nxt(nsrc), cnt((size_t)levels + 2);
     for (int i = 0; i < nsrc; ++i) idx[i] = i;
@@ -1374,8 +1402,6 @@ static bc_status group_sources(bc_graph* g, Workspace* w, int K, const int* d_sr
     e = cudaMemcpyAsync(out.p, grouped.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "source copy");
-    acc->kernel_launches += rs.kernel_launches + (levels > 0 ? 2 : 1);  // level table, keys
-    acc->kernel_ms += rs.kernel_ms;
     return BC_OK;
 }
 
@@ -1427,7 +1453,7 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
     bc_run_stats pre{};
     DevBuf grouped;
     if (want_grouping(g, nsrc, o)) {
-        bc_status gr = group_sources(g, w, K, d_src, nsrc, st, grouped, &pre, nullptr);
+        bc_status gr = group_sources(g, d_src, nsrc, st, grouped, &pre, nullptr);
         if (gr < 0) {
             buf_release(tmp, st);
             buf_release(grouped, st);
@@ -1739,9 +1765,7 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
         it.g = g;
         it.src.assign(x.sources, x.sources + x.nsrc);
         if (want_grouping(g, x.nsrc, o)) {
-            // the order bc_compute would use, fixed once here (a 32-wide
-            // workspace of its own, freed right after)
-            Workspace tmp;
+            // the order bc_compute would use, fixed once here
             DevBuf dsrc, grouped;
             bc_run_stats gs{};
             r = buf_ensure(dsrc, sizeof(int) * (size_t)x.nsrc, ust) ? BC_OK : fail(BC_E_NOMEM, "source buffer");
@@ -1750,9 +1774,8 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
                 (e = cudaMemcpyAsync(dsrc.p, x.sources, sizeof(int) * (size_t)x.nsrc, cudaMemcpyHostToDevice, ust)) !=
                     cudaSuccess)
                 r = cuda_fail(e, "source copy");
-            if (r == BC_OK) r = group_sources(g, &tmp, 32, (const int*)dsrc.p, x.nsrc, ust, grouped, &gs, &it.src);
+            if (r == BC_OK) r = group_sources(g, (const int*)dsrc.p, x.nsrc, ust, grouped, &gs, &it.src);
             cudaStreamSynchronize(ust);
-            tmp.release(ust);
             buf_release(dsrc, ust);
             buf_release(grouped, ust);
             if (r != BC_OK) return r;

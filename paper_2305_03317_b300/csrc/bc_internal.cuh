@@ -171,10 +171,13 @@ cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, i
                        int blocks, cudaStream_t st);
 cudaError_t launch_weight_ingest(const int* ooff, const int* oadj, const int* ow, const int* perm, const int* noff,
                                  const int* nadj, int n, int* nw, int* err, bool check_symmetry, cudaStream_t st);
-// Level table of a forward-only batch, then the levels of columns [0, L) at
-// each of nsrc sources (original ids): keys[nsrc][L], 0xFFFF = unreached.
-cudaError_t launch_level_keys(const KParams& p, int K, int levels, int L, unsigned short* lvl, long long n,
-                              const int* src, int nsrc, const int* inv, unsigned short* keys, cudaStream_t st);
+// Level table [n][K] (0xFFFF = unreached) of a forward-only batch; and the
+// levels of columns [0, L) of such a table at each of nsrc sources (original
+// ids): keys[nsrc][L].
+cudaError_t launch_level_table(const KParams& p, int K, int levels, unsigned short* lvl, long long n,
+                               cudaStream_t st);
+cudaError_t launch_source_keys(const unsigned short* lvl, int K, int L, long long n, const int* src, int nsrc,
+                               const int* inv, unsigned short* keys, cudaStream_t st);
 cudaError_t launch_debug_extract(const KParams& p, int K, int levels, int* level_rel, unsigned long long* sig_rel,
                                  int* sige_rel, cudaStream_t st);
 

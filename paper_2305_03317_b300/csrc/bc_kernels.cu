@@ -1818,15 +1818,21 @@ __global__ void k_level_keys(const unsigned short* __restrict__ lvl, int K, int 
     keys[i] = (s >= 0 && s < n) ? lvl[(size_t)inv[s] * K + j] : (unsigned short)0xFFFFu;
 }
 
-cudaError_t launch_level_keys(const KParams& p, int K, int levels, int L, unsigned short* lvl, long long n,
-                              const int* src, int nsrc, const int* inv, unsigned short* keys, cudaStream_t st) {
-    if (n <= 0 || nsrc <= 0) return cudaSuccess;
+cudaError_t launch_level_table(const KParams& p, int K, int levels, unsigned short* lvl, long long n,
+                               cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(lvl, 0xFF, sizeof(unsigned short) * (size_t)n * (size_t)K, st);
     if (e != cudaSuccess) return e;
     if (levels > 0) k_bfs_levels<<<8 * (sms > 0 ? sms : 1), 256, 0, st>>>(p, K, levels, lvl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_keys(const unsigned short* lvl, int K, int L, long long n, const int* src, int nsrc,
+                               const int* inv, unsigned short* keys, cudaStream_t st) {
+    if (n <= 0 || nsrc <= 0) return cudaSuccess;
     const long long tot = (long long)nsrc * L;
     k_level_keys<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(lvl, K, L, src, nsrc, inv, n, keys);
     return cudaGetLastError();
