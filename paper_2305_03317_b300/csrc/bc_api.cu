@@ -720,7 +720,8 @@ struct Server {
     long long completed = 0;
     bc_job next_id = 1;
     bool started = false;
-    int pack_limit = 256;  // sources per packed traversal
+    int pack_limit = 1024;  // sources per packed traversal (saturated R-MAT 14-22 pool, source-arcs/s:
+                            // 256 -> 3.06e11, 1024 -> 3.2e11, 4096 -> 3.17e11)
 };
 
 Server& server() {
