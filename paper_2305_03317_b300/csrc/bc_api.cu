@@ -232,6 +232,11 @@ struct bc_graph {
     std::mutex lm_mu;           // the landmark table below, built once on first use
     DevBuf landmark;            // [n][32] uint16 levels of the BFS from each of the 32 first relabelled vertices
     int lm_levels = -1;         // levels of that BFS; -1 = not built
+    // PageRank facts and buffers (under mu, built on first use): row classes,
+    // the chunk prefix of the long rows, rank / scratch / chunk sums / counters
+    int pr_cls[2] = {-1, -1};
+    long long pr_nchunks = 0;
+    DevBuf pr_ccum, pr_rank, pr_scratch, pr_cpart, pr_carr, pr_ctl, pr_small;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -1080,6 +1085,8 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->ioff, st);
     buf_release(g->iadj, st);
     buf_release(g->landmark, st);
+    for (DevBuf* b : {&g->pr_ccum, &g->pr_rank, &g->pr_scratch, &g->pr_cpart, &g->pr_carr, &g->pr_ctl, &g->pr_small})
+        buf_release(*b, st);
     for (DevBuf* b : {&g->w, &g->wdist, &g->wsig, &g->winv, &g->wdel, &g->wrho, &g->wmark, &g->wbc, &g->wctl, &g->wsrc,
                       &g->wscr, &g->warr})
         buf_release(*b, st);
@@ -1591,55 +1598,55 @@ bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, 
     const size_t n = (size_t)g->n;
     const int blocks = pagerank_blocks();
     if (blocks < 1) return fail(BC_E_CUDA, "PageRank kernel cannot be resident");
-    DevBuf rank, scratch, ctl, small;
-    auto release = [&]() {
-        buf_release(rank, st);
-        buf_release(scratch, st);
-        buf_release(ctl, st);
-        buf_release(small, st);
-    };
-    if (!buf_ensure(rank, sizeof(double) * n, st) || !buf_ensure(scratch, sizeof(double) * (2 * n + blocks), st) ||
-        !buf_ensure(ctl, sizeof(Ctl), st) || !buf_ensure(small, 64, st)) {
-        release();
-        return fail(BC_E_NOMEM, "PageRank buffers");
+    cudaError_t e = cudaSuccess;
+    if (g->pr_cls[0] < 0) {
+        // facts of the graph, once: undirected rows are sorted by length, so the
+        // row classes are the first rows shorter than 8192 and 32 arcs; the long
+        // rows' 2048-arc chunk prefix
+        int cls[2] = {0, 0};
+        const int bounds[2] = {8192, 32};
+        if (!g->directed)
+            for (int i = 0; i < 2 && e == cudaSuccess; ++i) cls[i] = first_row_shorter(g, bounds[i], st, &e);
+        std::vector<int> hoff((size_t)cls[0] + 1), hc((size_t)cls[0] + 1, 0);
+        if (e == cudaSuccess && cls[0] > 0) {
+            e = cudaMemcpyAsync(hoff.data(), g->off.p, sizeof(int) * ((size_t)cls[0] + 1), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            for (int r = 0; r < cls[0]; ++r) hc[r + 1] = hc[r] + (hoff[r + 1] - hoff[r] + 2047) / 2048;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "PageRank set-up");
+        if (!buf_ensure(g->pr_ccum, sizeof(int) * hc.size(), st)) return fail(BC_E_NOMEM, "PageRank buffers");
+        e = cudaMemcpyAsync(g->pr_ccum.p, hc.data(), sizeof(int) * hc.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "PageRank set-up");
+        g->pr_cls[0] = cls[0];
+        g->pr_cls[1] = cls[1];
+        g->pr_nchunks = hc[cls[0]];
     }
-    cudaError_t e = cudaMemsetAsync(ctl.p, 0, sizeof(Ctl), st);
+    const int cls0 = g->pr_cls[0];
+    if (!buf_ensure(g->pr_rank, sizeof(double) * n, st) ||
+        !buf_ensure(g->pr_scratch, sizeof(double) * (2 * n + blocks), st) ||
+        !buf_ensure(g->pr_ctl, sizeof(Ctl), st) || !buf_ensure(g->pr_small, 64, st) ||
+        !buf_ensure(g->pr_cpart, sizeof(double) * (size_t)(g->pr_nchunks + 1), st) ||
+        !buf_ensure(g->pr_carr, sizeof(int) * (size_t)(cls0 + 1), st))
+        return fail(BC_E_NOMEM, "PageRank buffers");
+    DevBuf& rank = g->pr_rank;
+    DevBuf& scratch = g->pr_scratch;
+    DevBuf& ctl = g->pr_ctl;
+    DevBuf& small = g->pr_small;
+    auto release = [&]() {};  // the buffers stay with the graph
+    e = cudaMemsetAsync(ctl.p, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(small.p, 0, 64, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->pr_carr.p, 0, sizeof(int) * (size_t)(cls0 + 1), st);
     int* d_iters = (int*)small.p;
     int* d_go = (int*)small.p + 1;
     double* d_diff = (double*)small.p + 1;
     const int* roff = g->directed ? (const int*)g->ioff.p : (const int*)g->off.p;
     const int* radj = g->directed ? (const int*)g->iadj.p : (const int*)g->adj.p;
-    // undirected rows are sorted by length: row classes by the first row shorter than each bound
-    int cls[2] = {0, 0};
-    const int bounds[2] = {8192, 32};
-    if (!g->directed)
-        for (int i = 0; i < 2 && e == cudaSuccess; ++i) cls[i] = first_row_shorter(g, bounds[i], st, &e);
-    // chunk slots of the long rows (2048 arcs each)
-    DevBuf ccum, cpart, carr;
-    std::vector<int> hoff((size_t)cls[0] + 1), hc((size_t)cls[0] + 1, 0);
-    if (e == cudaSuccess && cls[0] > 0) {
-        e = cudaMemcpyAsync(hoff.data(), g->off.p, sizeof(int) * ((size_t)cls[0] + 1), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        for (int r = 0; r < cls[0]; ++r) hc[r + 1] = hc[r] + (hoff[r + 1] - hoff[r] + 2047) / 2048;
-    }
-    const long long nchunks = hc[cls[0]];
-    if (e == cudaSuccess &&
-        (!buf_ensure(ccum, sizeof(int) * hc.size(), st) || !buf_ensure(cpart, sizeof(double) * (size_t)(nchunks + 1), st) ||
-         !buf_ensure(carr, sizeof(int) * (size_t)(cls[0] + 1), st))) {
-        release();
-        buf_release(ccum, st);
-        buf_release(cpart, st);
-        buf_release(carr, st);
-        return fail(BC_E_NOMEM, "PageRank buffers");
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ccum.p, hc.data(), sizeof(int) * hc.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(carr.p, 0, sizeof(int) * (size_t)(cls[0] + 1), st);
     if (e == cudaSuccess)
-        e = launch_pagerank(g->n, (const int*)g->off.p, roff, radj, g->directed ? nullptr : cls, nchunks,
-                            (const int*)ccum.p, (double*)cpart.p, (int*)carr.p, delta, beta, max_iter,
-                            (double*)rank.p, (double*)scratch.p, (Ctl*)ctl.p, d_iters, d_diff, d_go, 40000000000ll,
-                            blocks, st);
+        e = launch_pagerank(g->n, (const int*)g->off.p, roff, radj, g->directed ? nullptr : g->pr_cls, g->pr_nchunks,
+                            (const int*)g->pr_ccum.p, (double*)g->pr_cpart.p, (int*)g->pr_carr.p, delta, beta,
+                            max_iter, (double*)rank.p, (double*)scratch.p, (Ctl*)ctl.p, d_iters, d_diff, d_go,
+                            40000000000ll, blocks, st);
     if (e == cudaSuccess) e = launch_unpermute((const double*)rank.p, (const int*)g->inv.p, out_rank, g->n, st);
     int h_it = 0, h_err = 0;
     double h_diff = 0.0;
@@ -1648,9 +1655,6 @@ bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, &((Ctl*)ctl.p)->err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     release();
-    buf_release(ccum, st);
-    buf_release(cpart, st);
-    buf_release(carr, st);
     if (e != cudaSuccess) return cuda_fail(e, "PageRank");
     if (h_err & ERR_TIMEOUT) return fail(BC_E_TIMEOUT, "a grid-barrier wait exceeded its cycle budget");
     if (h_err) return fail(BC_E_CUDA, "PageRank kernel error 0x%x", h_err);
