@@ -70,6 +70,23 @@ static void* dev_alloc_raw(size_t bytes, cudaStream_t st, AllocHook* used) {
     if (used) *used = h;
     if (bytes == 0) bytes = 16;
     if (h.alloc) return h.alloc(bytes, (bc_stream_t)st, h.ctx);
+    {
+        // the device's default pool keeps up to 256 MB of freed memory between
+        // synchronisations (default 0: every sync returns it, and the next
+        // call's small buffers are mapped anew); a process-local setting
+        static std::once_flag once[64];
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64)
+            std::call_once(once[dev], [dev]() {
+                cudaMemPool_t pool;
+                if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                    unsigned long long keep = 256ull << 20;
+                    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+                }
+                cudaGetLastError();
+            });
+    }
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
         cudaGetLastError();
