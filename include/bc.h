@@ -131,15 +131,16 @@ typedef struct {
                                 (arc, column) pair per lane (0 = auto); results do not depend on it */
     int32_t source_order;    /* bc_compute, bc_many_create (fixed once at creation) and, with the automatic
                                 rule, each serving job: 1 = batches take the sources in the order given; 2 =
-                                sources are
-                                first grouped by their distances to the graph's 32 highest-degree vertices
-                                (one extra 32-source forward traversal), so that a batch holds sources that
+                                sources are first grouped by their distances to the graph's 32 highest-degree
+                                vertices (a 32-source forward traversal, once per graph), so that a batch holds
+                                sources that
                                 reach most vertices at the same levels and more arcs are summed column-mapped;
                                 0 = auto: 2 on undirected graphs with at least 256 sources, 2048 non-isolated
                                 vertices and a maximum degree of at least 16 times the mean, else 1.  Only the
                                 order in which per-source dependencies are added to BC changes (rounding); the
                                 grouping depends on the graph and the source list alone, so results stay the
-                                same for every batch width and direction setting */
+                                same for every batch width and direction setting.  The landmark levels are
+                                kept with the graph ([n][32] uint16), built on the first grouped call */
 } bc_options;
 
 /*
@@ -223,8 +224,9 @@ typedef struct {
     int32_t kernel_launches; /* kernels launched by the call */
     float kernel_ms;         /* device time of the persistent traversal launches (CUDA events on the call's stream) */
     int32_t teams;           /* teams of the last launch */
-    float order_ms;          /* device time of the source-grouping traversal (0 when the sources were not grouped;
-                                not part of kernel_ms) */
+    float order_ms;          /* device time of the source grouping: the key gather, plus the graph's landmark
+                                traversal on the first grouped call (0 when the sources were not grouped; not
+                                part of kernel_ms) */
     int64_t arcs_visited;    /* bc_compute_weighted: arcs read by all passes of all batches (0 otherwise) */
     int64_t rows_visited;    /* bc_compute_weighted: rows recomputed by all passes of all batches */
 } bc_run_stats;
