@@ -135,7 +135,17 @@ __global__ void __launch_bounds__(kPrThreads) k_pagerank(PrParams p) {
             for (long long v = p.n_warp_rows + tid; v < p.n; v += nthr) {
                 const int b = p.roff[v], l = p.roff[v + 1] - b;
                 double s = 0.0;
-                for (int e = b; e < b + l; ++e) s += p.contrib[p.radj[e]];
+                // four arcs' loads in flight, added in CSR order
+                int e = b;
+                for (; e + 4 <= b + l; e += 4) {
+                    const int u0 = p.radj[e], u1 = p.radj[e + 1], u2 = p.radj[e + 2], u3 = p.radj[e + 3];
+                    const double c0 = p.contrib[u0], c1 = p.contrib[u1], c2 = p.contrib[u2], c3 = p.contrib[u3];
+                    s += c0;
+                    s += c1;
+                    s += c2;
+                    s += c3;
+                }
+                for (; e < b + l; ++e) s += p.contrib[p.radj[e]];
                 const double val = base + p.delta * s;
                 mine += fabs(val - rank[v]);
                 nxt[v] = val;
