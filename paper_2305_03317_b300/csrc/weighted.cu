@@ -110,8 +110,9 @@ __device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, int p
             const int b = p.off[r] + (int)(t - c0) * kChunk, e = min(p.off[r + 1], b + kChunk);
             T acc = arc.start(r, init);
             if (__any_sync(kAll, arc.live(acc))) {
-#pragma unroll 4
-                for (int j = b; j < e; ++j) arc(j, acc);
+                int j = b;
+                for (; j + 4 <= e; j += 4) arc.quad(j, acc);
+                for (; j < e; ++j) arc(j, acc);
                 arcs += e - b;
             }
             scratch[(size_t)t * KW + lane] = acc;
@@ -135,8 +136,9 @@ __device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, int p
             T acc = arc.start(r, init);
             ++rows;
             if (__any_sync(kAll, arc.live(acc))) {
-#pragma unroll 4
-                for (int j = b; j < e; ++j) arc(j, acc);
+                int j = b;
+                for (; j + 4 <= e; j += 4) arc.quad(j, acc);
+                for (; j < e; ++j) arc(j, acc);
                 arcs += e - b;
             }
             if (__any_sync(kAll, finish(r, acc))) stamp(r);
@@ -161,6 +163,19 @@ struct MinArc {
             const long long c = du + __ldg(p->w + j);
             if (c < best) best = c;
         }
+    }
+    // arcs j..j+3, their loads issued together
+    __device__ void quad(int j, long long& best) const {
+        long long du[4];
+        int w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            du[q] = p->dist[at(__ldg(p->adj + j + q), lane)];
+            w[q] = __ldg(p->w + j + q);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (du[q] != kInf && du[q] + w[q] < best) best = du[q] + w[q];
     }
     __device__ static long long combine(long long a, long long b) { return a < b ? a : b; }
 };
@@ -190,6 +205,26 @@ struct SigmaArc {
             a.s = s;
         }
     }
+    __device__ void quad(int j, SigmaAcc& a) const {
+        if (a.dv == kInf) return;
+        int u[4];
+        bool pred[4];
+        unsigned long long x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            u[q] = __ldg(p->adj + j + q);
+            const long long du = p->dist[at(u[q], lane)];
+            pred[q] = du != kInf && du + __ldg(p->w + j + q) == a.dv;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = pred[q] ? p->sig[at(u[q], lane)] : 0ull;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const unsigned long long s = a.s + x[q];
+            a.ovf |= s < x[q];
+            a.s = s;
+        }
+    }
     __device__ static SigmaAcc combine(SigmaAcc a, SigmaAcc b) {
         const unsigned long long s = a.s + b.s;
         return SigmaAcc{s, a.dv, a.ovf || b.ovf || s < b.s};
@@ -214,6 +249,23 @@ struct DeltaArc {
         const int x = __ldg(p->adj + j);
         const long long dx = p->dist[at(x, lane)];
         if (dx != kInf && a.dv + __ldg(p->w + j) == dx) a.sum += p->rho[at(x, lane)];
+    }
+    __device__ void quad(int j, DeltaAcc& a) const {
+        if (a.dv == kInf) return;
+        int x[4];
+        bool succ[4];
+        double r[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x[q] = __ldg(p->adj + j + q);
+            const long long dx = p->dist[at(x[q], lane)];
+            succ[q] = dx != kInf && a.dv + __ldg(p->w + j + q) == dx;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = succ[q] ? p->rho[at(x[q], lane)] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (succ[q]) a.sum += r[q];  // CSR order
     }
     __device__ static DeltaAcc combine(DeltaAcc a, DeltaAcc b) { return DeltaAcc{a.sum + b.sum, a.dv}; }
 };
