@@ -182,15 +182,16 @@ def rmat(scale: int, edge_factor: float, seed: int = 1, a: float = RMAT_A, b: fl
     return edges_to_csr(n, u, v, name=f"rmat{scale}_ef{edge_factor:g}_s{seed}")
 
 
-def edge_weights(g: CSR, lo: int = 1, hi: int = 100, seed: int = 1) -> np.ndarray:
+def edge_weights(g: CSR, lo: int = 1, hi: int = 100, seed: int = 1, per_arc: bool = False) -> np.ndarray:
     """Positive int32 weights parallel to g.adj, uniform in [lo, hi] per
     undirected edge (both arcs of an edge get the same weight): a SplitMix64
-    hash of (min(u, v), max(u, v), seed)."""
+    hash of (min(u, v), max(u, v), seed).  per_arc: per arc instead, a hash of
+    (u, v, seed), so u -> v and v -> u differ (directed graphs)."""
     n = g.n
     deg = np.diff(g.off.astype(np.int64))
     u = np.repeat(np.arange(n, dtype=np.uint64), deg)
     v = g.adj.astype(np.uint64)
-    a, b = np.minimum(u, v), np.maximum(u, v)
+    a, b = (u, v) if per_arc else (np.minimum(u, v), np.maximum(u, v))
     with np.errstate(over="ignore"):
         z = a * np.uint64(n) + b + np.uint64(seed) * np.uint64(0x9E3779B97F4A7C15)
         z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)

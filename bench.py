@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--direction", type=int, default=0)
     ap.add_argument("--source-order", type=int, default=0,
                     help="bc_options.source_order: 0 auto, 1 as given, 2 grouped by hub distances")
+    ap.add_argument("--directed", action="store_true",
+                    help="weighted: orient the R-MAT graph (each edge one way, a quarter both ways), weights per arc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library heuristics)")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: Poisson arrival rate (req/s)")
@@ -522,13 +524,16 @@ def run_pagerank(a, bc, torch):
 
 
 def run_weighted(a, bc, torch):
-    """Weighted BC (bc_compute_weighted) on R-MAT with seeded integer weights 1..100."""
+    """Weighted BC (bc_compute_weighted) on R-MAT with seeded integer weights 1..100
+    (--directed: the R-MAT graph oriented, weights per arc)."""
     import bcgen
     g = bcgen.rmat(a.scale, a.ef, 1)
-    wt = bcgen.edge_weights(g, 1, 100, 1)
+    if a.directed:
+        g = bcgen.orient(g, seed=1)
+    wt = bcgen.edge_weights(g, 1, 100, 1, per_arc=a.directed)
     src = bcgen.sample_sources(g, a.sources or 256, 1)
     t0 = time.perf_counter()
-    G = bc.Graph(g.off, g.adj, weights=wt)
+    G = bc.Graph(g.off, g.adj, weights=wt, directed=a.directed)
     torch.cuda.synchronize()
     ingest_s = time.perf_counter() - t0
     d_src = torch.from_numpy(src).cuda()
@@ -575,8 +580,12 @@ def run_weighted(a, bc, torch):
             "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"weighted_rmat{a.scale}_ef{a.ef:g}", "n": g.n, "m": g.m, "sources": len(src),
-                       "weights": "integer 1..100 per undirected edge (SplitMix64 of the edge, seed 1)",
+            "config": {"workload": f"weighted_{'directed_' if a.directed else ''}rmat{a.scale}_ef{a.ef:g}", "n": g.n,
+                       "m": g.m, "sources": len(src),
+                       "graph": ("R-MAT oriented: each edge one way, a quarter of them both ways (seed 1)"
+                                 if a.directed else "undirected R-MAT"),
+                       "weights": ("integer 1..100 per arc (SplitMix64 of the arc, seed 1)" if a.directed else
+                                   "integer 1..100 per undirected edge (SplitMix64 of the edge, seed 1)"),
                        "batches": s["batches"], "passes": {"dist": s["max_levels"], "sigma": s["pull_levels"],
                                                            "delta": s["push_levels"]},
                        "ingest_s": round(ingest_s, 3), "statuses": sorted(int(x) for x in statuses),

@@ -9,7 +9,7 @@
  * (the iterateInReverse body), and BC(v) += delta_s(v) for every v != s.
  * The graph is unweighted, undirected (symmetric) or directed, given as int32
  * CSR (Section 3.1: the backend keeps graphs in CSR); bc_compute_weighted
- * covers undirected graphs with positive integer arc weights.  The result is the raw
+ * covers graphs (undirected or directed) with positive integer arc weights.  The result is the raw
  * sum over the listed sources: no halving for undirected graphs, no
  * normalisation, no extrapolation from sampled sources.  A source listed twice
  * counts twice.
@@ -187,13 +187,16 @@ bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, 
                       int32_t* iterations, double* last_diff, bc_stream_t stream);
 
 /*
- * Weighted graphs (undirected, positive int32 arc weights).  weights[m] is
- * parallel to indices[m] of the input CSR (host or device, as the flags say),
- * whose rows must be sorted ascending; both arcs of an edge carry the same
- * weight.  Checks (unless BC_SKIP_VALIDATION): the CSR rules of
- * bc_graph_create, sorted rows, weights > 0, symmetric weights, else
- * BC_E_INVALID_GRAPH.  The result is a regular graph (every unweighted call
- * works on it, ignoring the weights) that bc_compute_weighted also accepts.
+ * Weighted graphs (positive int32 arc weights), undirected (BC_UNDIRECTED) or
+ * directed.  weights[m] is parallel to indices[m] of the input CSR (host or
+ * device, as the flags say), whose rows must be sorted ascending.  Undirected:
+ * both arcs of an edge carry the same weight.  Directed: each arc has its own
+ * weight, and the library keeps a second copy, in the order of the in-CSR it
+ * builds for the directed pulls (4 m bytes more).  Checks (unless
+ * BC_SKIP_VALIDATION): the CSR rules of bc_graph_create, sorted rows,
+ * weights > 0, symmetric weights when undirected, else BC_E_INVALID_GRAPH.
+ * The result is a regular graph (every unweighted call works on it, ignoring
+ * the weights) that bc_compute_weighted also accepts.
  */
 bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indices, const int32_t* weights,
                                    int32_t n, int64_t m, uint32_t flags, bc_stream_t stream, bc_graph** out);
@@ -205,6 +208,8 @@ bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indice
  * of the paper's SSSP program (Section 2.3).  Path counts are exact below
  * 2^64 (BC_W_SIGMA_INEXACT once one reaches 2^53, BC_E_SIGMA_RANGE at
  * 2^64); BC is the raw sum over the listed sources, as for bc_compute.
+ * On a directed graph paths follow the arcs: distances and path counts pull
+ * over in-arcs, dependencies over out-arcs.
  * Batches of 32 sources, one launch each; results repeat bit for bit.
  * BC_E_INVALID_ARG if the graph has no weights.  bc_last_run_stats reports
  * max_levels / pull_levels / push_levels = passes of the distance, path-count

@@ -189,7 +189,8 @@ class Graph:
     """A graph resident on the device (relabelled CSR; see bc_graph_create)."""
 
     def __init__(self, off, adj, validate: bool = True, stream=None, directed: bool = False, weights=None):
-        """weights: positive int32 per arc, parallel to adj (rows sorted; undirected only)."""
+        """weights: positive int32 per arc, parallel to adj (rows sorted; equal on the two arcs of an
+        undirected edge, free per arc when directed)."""
         lib = load()
         self._h = ctypes.c_void_p()
         flags = (0 if directed else BC_UNDIRECTED) | (0 if validate else BC_SKIP_VALIDATION)

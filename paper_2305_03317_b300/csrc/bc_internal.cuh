@@ -163,14 +163,30 @@ cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, c
 // Weighted BC (weighted.cu): one cooperative launch per batch of 32 sources;
 // weights of the relabelled arcs looked up from the original sorted CSR
 // (err bits: 1 rows not sorted, 2 a weight <= 0, 4 asymmetric weights).
+// One direction of a weighted graph for weighted BC: rows with their arc
+// weights, split into heavy rows (more than kChunk arcs, run as kChunk-arc
+// chunk tasks) and light ones.
+struct WCsr {
+    const int* off;
+    const int* adj;
+    const int* w;
+    int n_heavy;        // heavy rows
+    long long hchunks;  // their chunk tasks
+    const int* hcum;    // [n_heavy + 1] chunk prefix
+    const int* hrow;    // heavy row ids; nullptr = rows [0, n_heavy)
+    const int* lrow;    // light row ids, ascending; nullptr = rows [n_heavy, n)
+};
 int wbc_blocks();
-cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, int* arr, void* scratch,
-                       const int* off, const int* adj, const int* w, const int* src,
+cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* scratch, const int* src,
                        long long* dist, unsigned long long* sig, double* inv, double* del, double* rho, int* mark,
                        double* bc, Ctl* ctl, int* changed, int* passes, unsigned long long* visited, long long budget,
                        int blocks, cudaStream_t st);
+// Weights of the relabelled arcs (and, when ioff is set, of the in-CSR's
+// arcs); err bits: 1 rows not sorted, 2 a weight <= 0, 4 asymmetric weights,
+// 8 the in-CSR is not the transpose.
 cudaError_t launch_weight_ingest(const int* ooff, const int* oadj, const int* ow, const int* perm, const int* noff,
-                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, cudaStream_t st);
+                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, const int* ioff,
+                                 const int* iadj, int* iw, cudaStream_t st);
 // Level table [n][K] (0xFFFF = unreached) of a forward-only batch; and the
 // levels of columns [0, L) of such a table at each of nsrc sources (original
 // ids): keys[nsrc][L].

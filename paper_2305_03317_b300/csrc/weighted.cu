@@ -6,21 +6,26 @@
 // gives them by Bellman-Ford relaxation.  Per batch of 32 sources (lane =
 // column), one cooperative persistent launch runs three fixed-point loops,
 // each pass pulling into a row from its neighbours, all in place:
-//   dist:  d(v) = min(d(v), min over arcs u-v of d(u) + w)
-//   sigma: s(v) = [v = source] + sum over u with d(u) + w = d(v) of s(u)
-//   delta: t(v) = s(v) * sum over x with d(v) + w = d(x) of rho(x),
+//   dist:  d(v) = min(d(v), min over arcs u -> v of d(u) + w)
+//   sigma: s(v) = [v = source] + sum over arcs u -> v with d(u) + w = d(v) of s(u)
+//   delta: t(v) = s(v) * sum over arcs v -> x with d(v) + w = d(x) of rho(x),
 //          rho(x) = (1 + t(x)) / s(x), rewritten with each new t(x)
+// The first two pull over in-arcs, the third over out-arcs: on a directed
+// graph they read the in-CSR (the transpose, with its own copy of the
+// weights) and the out-CSR; on an undirected graph both are the one CSR.
 // until a pass changes nothing; then BC(v) += t(v) for every non-source
 // column, columns in order.  Distances only fall and counts and dependencies
 // only grow towards the DAG values, so a read of a neighbour another warp is
 // rewriting is always a valid bound and the fixed point is the unique one,
 // whatever the timing.  After a loop's first pass, a pass recomputes only the
-// rows next to a row that changed (stamps).  Distance mins and integer path
+// rows that read a row that changed (stamps, through the other direction's
+// CSR).  Distance mins and integer path
 // counts do not depend on the order of their terms; every double sum runs in
 // CSR order (long rows: per chunk, chunks combined in order), so results
 // repeat bit for bit.  Every task is one warp: a row of at most 1024 arcs, or
-// a 1024-arc chunk of a longer row (the relabelled prefix [0, n_heavy)),
-// whose partials the row's last chunk combines.  Grid barriers are bounded by
+// a 1024-arc chunk of a longer row (heavy rows: the relabelled prefix
+// [0, n_heavy) of the out-CSR, a listed set of the in-CSR), whose partials
+// the row's last chunk combines.  Grid barriers are bounded by
 // a cycle budget like the traversal kernel's.
 #include <climits>
 #include <cstdint>
@@ -37,14 +42,10 @@ constexpr long long kInf = LLONG_MAX;
 constexpr unsigned int kAll = 0xffffffffu;
 
 struct WParams {
-    int n, n_heavy;
-    long long hchunks;         // chunk tasks of the heavy rows
-    const int* hcum;           // [n_heavy + 1] chunk prefix of the heavy rows
-    int* arr;                  // [n_heavy] chunk arrival counters
-    void* scratch;             // [hchunks][32] partials (24 bytes each at most)
-    const int* off;
-    const int* adj;
-    const int* w;              // arc weights, relabelled arc order
+    int n;
+    WCsr out, in;              // out-arcs and in-arcs (the same CSR when undirected)
+    int* arr;                  // [heavy rows] chunk arrival counters, by heavy index
+    void* scratch;             // [chunk tasks][32] partials (24 bytes each at most)
     const int* src;            // [32] relabelled sources, -1 = unused column
     long long* dist;           // [n][32]
     unsigned long long* sig;   // [n][32] path counts
@@ -75,70 +76,72 @@ __device__ __forceinline__ T load_cg(const T* q) {
     return x;
 }
 
-// One pass over every row, one warp per task: a light row, or a 1024-arc
-// chunk of a heavy row (chunk slots hcum[r] .. hcum[r+1]).  A chunk's partial
-// goes to its scratch slot; the warp that finishes a row's last chunk (arrival
-// counter) combines the partials in chunk order and finishes the row.
+// One pass over every row of `rd`, one warp per task: a light row, or a
+// 1024-arc chunk of a heavy row (chunk slots hcum[k] .. hcum[k+1] of heavy
+// row k).  A chunk's partial goes to its scratch slot; the warp that finishes
+// a row's last chunk (arrival counter) combines the partials in chunk order
+// and finishes the row.
 //
 // Active rows: a pass recomputes only the rows stamped by the previous pass
-// (every pass when `all`): a row whose value changed stamps its neighbours for
-// the next pass, in the other of two stamp arrays, so no stamp a pass reads
-// changes during it.
+// (every pass when `all`): a row whose value changed stamps the rows that read
+// it (its row in `sc`, the transpose of `rd`) for the next pass, in the other
+// of two stamp arrays, so no stamp a pass reads changes during it.
 template <class Arc, class Finish, class T>
-__device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, int pass, bool all) {
+__device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const WCsr& sc, T init, Arc arc, Finish finish, int pass,
+                         bool all) {
     const int* mprev = p.mark + (size_t)(pass & 1) * p.n;
     int* mnext = p.mark + (size_t)((pass + 1) & 1) * p.n;
     auto stamp = [&](int r) {
-        for (int j = p.off[r] + (threadIdx.x & 31); j < p.off[r + 1]; j += 32) mnext[__ldg(p.adj + j)] = pass + 1;
+        for (int j = sc.off[r] + (threadIdx.x & 31); j < sc.off[r + 1]; j += 32) mnext[__ldg(sc.adj + j)] = pass + 1;
     };
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long tasks = p.hchunks + (p.n - p.n_heavy);
+    const long long tasks = rd.hchunks + (p.n - rd.n_heavy);
     T* scratch = reinterpret_cast<T*>(p.scratch);
     unsigned long long arcs = 0, rows = 0;  // read by this warp (lane 0 reports)
     for (long long t = wid; t < tasks; t += nw) {
-        if (t < p.hchunks) {
-            int lo = 0, hi = p.n_heavy;  // hcum[lo] <= t < hcum[hi]
+        if (t < rd.hchunks) {
+            int lo = 0, hi = rd.n_heavy;  // hcum[lo] <= t < hcum[hi]
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
-                if (p.hcum[mid] <= t) lo = mid;
+                if (rd.hcum[mid] <= t) lo = mid;
                 else hi = mid;
             }
-            const int r = lo, c0 = p.hcum[r], nch = p.hcum[r + 1] - c0;
+            const int k = lo, r = rd.hrow ? __ldg(rd.hrow + k) : k, c0 = rd.hcum[k], nch = rd.hcum[k + 1] - c0;
             if (!all && mprev[r] != pass) continue;  // the same answer for every chunk of the row
-            const int b = p.off[r] + (int)(t - c0) * kChunk, e = min(p.off[r + 1], b + kChunk);
+            const int b = rd.off[r] + (int)(t - c0) * kChunk, e = min(rd.off[r + 1], b + kChunk);
             T acc = arc.start(r, init);
             if (__any_sync(kAll, arc.live(acc))) {
                 int j = b;
-                for (; j + 4 <= e; j += 4) arc.quad(j, acc);
-                for (; j < e; ++j) arc(j, acc);
+                for (; j + 4 <= e; j += 4) arc.quad(j, rd.adj, rd.w, acc);
+                for (; j < e; ++j) arc(j, rd.adj, rd.w, acc);
                 arcs += e - b;
             }
             scratch[(size_t)t * KW + lane] = acc;
             __threadfence();
             __syncwarp();
             int last = 0;
-            if (lane == 0) last = atomicAdd(&p.arr[r], 1) == nch - 1;
+            if (lane == 0) last = atomicAdd(&p.arr[k], 1) == nch - 1;
             last = __shfl_sync(kAll, last, 0);
             if (last) {
                 __threadfence();
                 T tot = load_cg(&scratch[(size_t)c0 * KW + lane]);
-                for (int k = 1; k < nch; ++k) tot = Arc::combine(tot, load_cg(&scratch[(size_t)(c0 + k) * KW + lane]));
+                for (int q = 1; q < nch; ++q) tot = Arc::combine(tot, load_cg(&scratch[(size_t)(c0 + q) * KW + lane]));
                 ++rows;
                 if (__any_sync(kAll, finish(r, tot))) stamp(r);
-                if (lane == 0) p.arr[r] = 0;  // ready for the next pass (after its barrier)
+                if (lane == 0) p.arr[k] = 0;  // ready for the next pass (after its barrier)
             }
         } else {
-            const int r = p.n_heavy + (int)(t - p.hchunks);
+            const int i = (int)(t - rd.hchunks), r = rd.lrow ? __ldg(rd.lrow + i) : rd.n_heavy + i;
             if (!all && mprev[r] != pass) continue;
-            const int b = p.off[r], e = p.off[r + 1];
+            const int b = rd.off[r], e = rd.off[r + 1];
             T acc = arc.start(r, init);
             ++rows;
             if (__any_sync(kAll, arc.live(acc))) {
                 int j = b;
-                for (; j + 4 <= e; j += 4) arc.quad(j, acc);
-                for (; j < e; ++j) arc(j, acc);
+                for (; j + 4 <= e; j += 4) arc.quad(j, rd.adj, rd.w, acc);
+                for (; j < e; ++j) arc(j, rd.adj, rd.w, acc);
                 arcs += e - b;
             }
             if (__any_sync(kAll, finish(r, acc))) stamp(r);
@@ -150,32 +153,32 @@ __device__ void row_pass(const WParams& p, T init, Arc arc, Finish finish, int p
 
 // Arc functors: start(v, init) gives a row's running state, live(state)
 // whether the lane's column needs the row's arcs at all (a warp skips a row
-// no lane needs), operator()(j, state) takes arc j, combine joins the
-// partials of a heavy row in order.
+// no lane needs), operator()(j, adj, w, state) takes arc j of the CSR the pass
+// reads, combine joins the partials of a heavy row in order.
 struct MinArc {
     const WParams* p;
     int lane;
     __device__ long long start(int, long long init) const { return init; }
     __device__ bool live(long long) const { return true; }
-    __device__ void operator()(int j, long long& best) const {
-        const long long du = p->dist[at(__ldg(p->adj + j), lane)];
+    __device__ void operator()(int j, const int* adj, const int* w, long long& best) const {
+        const long long du = p->dist[at(__ldg(adj + j), lane)];
         if (du != kInf) {
-            const long long c = du + __ldg(p->w + j);
+            const long long c = du + __ldg(w + j);
             if (c < best) best = c;
         }
     }
     // arcs j..j+3, their loads issued together
-    __device__ void quad(int j, long long& best) const {
+    __device__ void quad(int j, const int* adj, const int* w, long long& best) const {
         long long du[4];
-        int w[4];
+        int wq[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            du[q] = p->dist[at(__ldg(p->adj + j + q), lane)];
-            w[q] = __ldg(p->w + j + q);
+            du[q] = p->dist[at(__ldg(adj + j + q), lane)];
+            wq[q] = __ldg(w + j + q);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (du[q] != kInf && du[q] + w[q] < best) best = du[q] + w[q];
+            if (du[q] != kInf && du[q] + wq[q] < best) best = du[q] + wq[q];
     }
     __device__ static long long combine(long long a, long long b) { return a < b ? a : b; }
 };
@@ -194,27 +197,27 @@ struct SigmaArc {
         return init;
     }
     __device__ bool live(const SigmaAcc& a) const { return a.dv != kInf && a.dv != 0; }
-    __device__ void operator()(int j, SigmaAcc& a) const {
+    __device__ void operator()(int j, const int* adj, const int* w, SigmaAcc& a) const {
         if (a.dv == kInf) return;
-        const int u = __ldg(p->adj + j);
+        const int u = __ldg(adj + j);
         const long long du = p->dist[at(u, lane)];
-        if (du != kInf && du + __ldg(p->w + j) == a.dv) {
+        if (du != kInf && du + __ldg(w + j) == a.dv) {
             const unsigned long long x = p->sig[at(u, lane)];
             const unsigned long long s = a.s + x;
             a.ovf |= s < x;
             a.s = s;
         }
     }
-    __device__ void quad(int j, SigmaAcc& a) const {
+    __device__ void quad(int j, const int* adj, const int* w, SigmaAcc& a) const {
         if (a.dv == kInf) return;
         int u[4];
         bool pred[4];
         unsigned long long x[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            u[q] = __ldg(p->adj + j + q);
+            u[q] = __ldg(adj + j + q);
             const long long du = p->dist[at(u[q], lane)];
-            pred[q] = du != kInf && du + __ldg(p->w + j + q) == a.dv;
+            pred[q] = du != kInf && du + __ldg(w + j + q) == a.dv;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) x[q] = pred[q] ? p->sig[at(u[q], lane)] : 0ull;
@@ -244,22 +247,22 @@ struct DeltaArc {
         return init;
     }
     __device__ bool live(const DeltaAcc& a) const { return a.dv != kInf; }
-    __device__ void operator()(int j, DeltaAcc& a) const {
+    __device__ void operator()(int j, const int* adj, const int* w, DeltaAcc& a) const {
         if (a.dv == kInf) return;
-        const int x = __ldg(p->adj + j);
+        const int x = __ldg(adj + j);
         const long long dx = p->dist[at(x, lane)];
-        if (dx != kInf && a.dv + __ldg(p->w + j) == dx) a.sum += p->rho[at(x, lane)];
+        if (dx != kInf && a.dv + __ldg(w + j) == dx) a.sum += p->rho[at(x, lane)];
     }
-    __device__ void quad(int j, DeltaAcc& a) const {
+    __device__ void quad(int j, const int* adj, const int* w, DeltaAcc& a) const {
         if (a.dv == kInf) return;
         int x[4];
         bool succ[4];
         double r[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            x[q] = __ldg(p->adj + j + q);
+            x[q] = __ldg(adj + j + q);
             const long long dx = p->dist[at(x[q], lane)];
-            succ[q] = dx != kInf && a.dv + __ldg(p->w + j + q) == dx;
+            succ[q] = dx != kInf && a.dv + __ldg(w + j + q) == dx;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) r[q] = succ[q] ? p->rho[at(x[q], lane)] : 0.0;
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         }
         bool ch = false;
         MinArc arc{&p, lane};
-        row_pass<MinArc>(p, kInf, arc, [&](int v, long long best) {
+        row_pass<MinArc>(p, p.in, p.out, kInf, arc, [&](int v, long long best) {
             if (best < p.dist[at(v, lane)]) {
                 p.dist[at(v, lane)] = best;
                 ch = true;
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         }
         bool ch = false, ovf = false;
         SigmaArc arc{&p, lane};
-        row_pass<SigmaArc>(p, SigmaAcc{0ull, kInf, false}, arc, [&](int v, SigmaAcc a) {
+        row_pass<SigmaArc>(p, p.in, p.out, SigmaAcc{0ull, kInf, false}, arc, [&](int v, SigmaAcc a) {
             unsigned long long s = a.s;
             if (p.dist[at(v, lane)] != kInf && v == p.src[lane]) {
                 s += 1ull;
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         }
         bool ch = false;
         DeltaArc arc{&p, lane};
-        row_pass<DeltaArc>(p, DeltaAcc{0.0, kInf}, arc, [&](int v, DeltaAcc a) {
+        row_pass<DeltaArc>(p, p.out, p.in, DeltaAcc{0.0, kInf}, arc, [&](int v, DeltaAcc a) {
             const double d = (double)p.sig[at(v, lane)] * a.sum;
             if (__double_as_longlong(d) != __double_as_longlong(p.del[at(v, lane)])) {
                 p.del[at(v, lane)] = d;
@@ -444,6 +447,31 @@ __global__ void k_weight_symmetry(const int* __restrict__ noff, const int* __res
     }
 }
 
+// Weights of the in-arcs of a directed graph: in-arc u -> v of row v carries
+// the weight of out-arc u -> v (out rows sorted ascending).
+__global__ void k_weight_transpose(const int* __restrict__ noff, const int* __restrict__ nadj,
+                                   const int* __restrict__ nw, const int* __restrict__ ioff,
+                                   const int* __restrict__ iadj, int n, int* iw, int* err) {
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += nthr) {
+        for (int j = ioff[v]; j < ioff[v + 1]; ++j) {
+            const int u = iadj[j];
+            int lo = noff[u], hi = noff[u + 1];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (nadj[mid] < (int)v) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < noff[u + 1] && nadj[lo] == (int)v) {
+                iw[j] = nw[lo];
+            } else {
+                iw[j] = 1;
+                atomicOr(err, 8);  // the in-CSR is not the transpose
+            }
+        }
+    }
+}
+
 }  // namespace
 
 int wbc_blocks() {
@@ -455,21 +483,16 @@ int wbc_blocks() {
     return sms * per;
 }
 
-cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, int* arr, void* scratch,
-                       const int* off, const int* adj, const int* w, const int* src,
+cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* scratch, const int* src,
                        long long* dist, unsigned long long* sig, double* inv, double* del, double* rho, int* mark,
                        double* bc, Ctl* ctl, int* changed, int* passes, unsigned long long* visited, long long budget,
                        int blocks, cudaStream_t st) {
     WParams p;
     p.n = n;
-    p.n_heavy = n_heavy;
-    p.hchunks = hchunks;
-    p.hcum = hcum;
+    p.out = out;
+    p.in = in;
     p.arr = arr;
     p.scratch = scratch;
-    p.off = off;
-    p.adj = adj;
-    p.w = w;
     p.src = src;
     p.dist = dist;
     p.sig = sig;
@@ -498,11 +521,13 @@ cudaError_t launch_wbc(int n, int n_heavy, long long hchunks, const int* hcum, i
 }
 
 cudaError_t launch_weight_ingest(const int* ooff, const int* oadj, const int* ow, const int* perm, const int* noff,
-                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, cudaStream_t st) {
+                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, const int* ioff,
+                                 const int* iadj, int* iw, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
     k_weight_lookup<<<blocks, 256, 0, st>>>(ooff, oadj, ow, perm, noff, nadj, n, nw, err);
     if (check_symmetry) k_weight_symmetry<<<blocks, 256, 0, st>>>(noff, nadj, nw, n, err);
+    if (ioff) k_weight_transpose<<<blocks, 256, 0, st>>>(noff, nadj, nw, ioff, iadj, n, iw, err);
     return cudaGetLastError();
 }
 

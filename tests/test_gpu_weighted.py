@@ -1,5 +1,6 @@
 """GPU parity for weighted BC (bc_graph_create_weighted / bc_compute_weighted)
-against the weighted CPU oracle (Dijkstra distances, the same accumulation).
+against the weighted CPU oracle (Dijkstra distances, the same accumulation),
+on undirected graphs and on directed ones (per-arc weights).
 
 Tolerance as for the unweighted path: 1e-9 relative per vertex, exact zeros
 exact.  Weights 1..3 on the small graphs make many equal-weight paths of
@@ -157,9 +158,9 @@ def test_invalid_weighted_inputs(bc):
     with pytest.raises(bc.BCError) as ei:
         bc.Graph(g.off, adj, weights=wt)
     assert ei.value.status == bc.BC_E_INVALID_GRAPH
-    with pytest.raises(bc.BCError) as ei:
-        bc.Graph(g.off, g.adj, weights=wt, directed=True)
-    assert ei.value.status == bc.BC_E_INVALID_ARG
+    with pytest.raises(bc.BCError) as ei:  # directed: weights are per arc, still positive
+        bc.Graph(g.off, g.adj, weights=np.where(np.arange(g.m) == 5, -2, wt).astype(np.int32), directed=True)
+    assert ei.value.status == bc.BC_E_INVALID_GRAPH
     G = bc.Graph(g.off, g.adj)
     with pytest.raises(bc.BCError) as ei:
         G.compute_weighted(np.arange(3))
@@ -193,3 +194,96 @@ def test_device_inputs_and_skip_validation(bc):
     skip, _ = S.compute_weighted(src)
     assert np.array_equal(skip.cpu().numpy().view(np.uint64), host.view(np.uint64))
     assert_bc_close(host, want)
+
+
+# ------------------------------------------------------------ directed graphs
+
+DSMALL = [bcgen.orient(g, seed=i + 1, p_both=0.3) for i, g in enumerate(SMALL)]
+
+
+def wgpu_dir(bc, g, wt, src):
+    G = bc.Graph(g.off, g.adj, weights=wt, directed=True)
+    out, st = G.compute_weighted(np.asarray(src, np.int32))
+    res = out.cpu().numpy().copy()
+    stats = G.stats()
+    G.close()
+    return res, st, stats
+
+
+@pytest.mark.parametrize("g", DSMALL, ids=lambda g: g.name)
+@pytest.mark.parametrize("wmax", [1, 3])
+def test_directed_small_graphs_all_sources(bc, g, wmax):
+    wt = bcgen.edge_weights(g, 1, wmax, seed=g.n + 1, per_arc=True)
+    got, st, _ = wgpu_dir(bc, g, wt, np.arange(g.n))
+    assert st == bc.BC_OK
+    assert_bc_close(got, oracle.wbc(g.off, g.adj, wt, np.arange(g.n)))
+
+
+def test_directed_tiny_graph_brute_force(bc):
+    g = bcgen.orient(bcgen.gnp(9, 0.6, 6), seed=2, p_both=0.4)
+    wt = bcgen.edge_weights(g, 1, 2, 3, per_arc=True)
+    got, _, _ = wgpu_dir(bc, g, wt, np.arange(g.n))
+    assert_bc_close(got, [float(x) for x in oracle.brute_force_wbc(g.off, g.adj, wt, range(g.n))])
+
+
+def _in_and_out_hubs(n, seed):
+    # vertex 0: in-arcs from everyone, no out-arcs (relabelled last: a heavy
+    # in-row outside the prefix); vertex 1: out-arcs to everyone (a heavy
+    # out-row); plus an oriented random graph
+    rest = bcgen.orient(bcgen.gnp(n, 4.0 / n, seed), seed=seed, p_both=0.2)
+    deg = np.diff(rest.off.astype(np.int64))
+    u = np.repeat(np.arange(n), deg)
+    keep = (u != 0) & (rest.adj != 1) & (u != 1) & (rest.adj != 0)
+    su = np.concatenate([np.arange(1, n), np.full(n - 2, 1), u[keep]])
+    sv = np.concatenate([np.zeros(n - 1, np.int64), np.arange(2, n), rest.adj[keep]])
+    return bcgen.directed_csr(n, su, sv, f"hubs{n}")
+
+
+def test_directed_heavy_in_rows_outside_the_prefix(bc):
+    g = _in_and_out_hubs(3000, 4)
+    indeg = np.bincount(g.adj, minlength=g.n)
+    assert indeg[0] > 2048 and np.diff(g.off)[0] == 0 and np.diff(g.off)[1] > 2048
+    wt = bcgen.edge_weights(g, 1, 6, 5, per_arc=True)
+    src = np.concatenate([[1, 0], bcgen.sample_sources(g, 62, 5)])
+    got, st, stats = wgpu_dir(bc, g, wt, src)
+    assert st == bc.BC_OK and stats["batches"] == 2
+    assert_bc_close(got, oracle.wbc(g.off, g.adj, wt, src))
+
+
+def test_directed_rmat_all_sources_repeatable(bc):
+    g = bcgen.orient(bcgen.rmat(12, 8, 3), seed=4)
+    wt = bcgen.edge_weights(g, 1, 100, 3, per_arc=True)
+    src = np.arange(g.n)
+    G = bc.Graph(g.off, g.adj, weights=wt, directed=True)
+    a, st = G.compute_weighted(src)
+    a = a.cpu().numpy().copy()
+    stats = G.stats()
+    b, _ = G.compute_weighted(src)
+    assert np.array_equal(a.view(np.uint64), b.cpu().numpy().view(np.uint64))
+    assert st == bc.BC_OK and stats["batches"] == (g.n + 31) // 32
+    assert stats["arcs_visited"] >= 3 * stats["batches"] * g.m * 0.9
+    assert_bc_close(a, oracle.wbc(g.off, g.adj, wt, src))
+
+
+def test_directed_long_rows_both_directions(bc):
+    g = bcgen.orient(bcgen.rmat(15, 16, 2), seed=3, p_both=0.5)
+    indeg = np.bincount(g.adj, minlength=g.n)
+    assert np.diff(g.off).max() > 1024 and indeg.max() > 1024
+    wt = bcgen.edge_weights(g, 1, 7, 2, per_arc=True)
+    src = bcgen.sample_sources(g, 40, 3)
+    got, _, _ = wgpu_dir(bc, g, wt, src)
+    assert_bc_close(got, oracle.wbc(g.off, g.adj, wt, src))
+
+
+def test_directed_equal_weights_match_unweighted_bc(bc):
+    g = bcgen.orient(bcgen.rmat(11, 8, 6), seed=7)
+    src = bcgen.sample_sources(g, 90, 2)
+    got, _, _ = wgpu_dir(bc, g, np.full(g.m, 3, np.int32), src)
+    G = bc.Graph(g.off, g.adj, directed=True)
+    unw, _ = G.compute(src)
+    assert_bc_close(got, unw.cpu().numpy())
+    # the transpose's arcs carry their own weights: an unweighted directed
+    # call on the same graph ignores them
+    W = bc.Graph(g.off, g.adj, weights=bcgen.edge_weights(g, 1, 9, 1, per_arc=True), directed=True)
+    a, _ = W.compute(src)
+    assert np.array_equal(a.cpu().numpy(), unw.cpu().numpy())

@@ -450,3 +450,43 @@ def test_weighted_path_closed_form():
     wt = bcgen.edge_weights(g, 1, 50, 1)
     got = oracle.wbc(g.off, g.adj, wt, all_src(g)) / 2
     assert close(got, [i * (29 - i) for i in range(30)])
+
+
+# ------------------------------------------------ weighted BC on directed graphs (per-arc weights)
+
+WDIR = [bcgen.orient(g, seed=i + 3, p_both=0.3) for i, g in enumerate(WSMALL[:5])]
+
+
+@pytest.mark.parametrize("g", WDIR, ids=lambda g: g.name)
+def test_directed_weighted_bc_matches_brute_force(g):
+    wt = bcgen.edge_weights(g, 1, 3, seed=g.n, per_arc=True)
+    want = oracle.brute_force_wbc(g.off, g.adj, wt, range(g.n))
+    assert close(oracle.wbc(g.off, g.adj, wt, all_src(g)), [float(x) for x in want])
+
+
+def test_directed_weighted_chain_closed_form():
+    # 0 -> 1 -> ... -> n-1: one path per ordered pair s < t, through every v between
+    n = 40
+    g = bcgen.directed_csr(n, np.arange(n - 1), np.arange(1, n))
+    wt = bcgen.edge_weights(g, 1, 50, 2, per_arc=True)
+    assert close(oracle.wbc(g.off, g.adj, wt, all_src(g)), [v * (n - 1 - v) for v in range(n)])
+
+
+def test_directed_equal_weights_give_unweighted_bc():
+    g = bcgen.orient(bcgen.rmat(10, 8, 5), seed=2)
+    src = bcgen.sample_sources(g, 150, 3)
+    assert close(oracle.wbc(g.off, g.adj, np.full(g.m, 4, np.int32), src), oracle.bc(g.off, g.adj, src))
+
+
+def test_directed_weighted_reversal_over_all_sources():
+    # every s -> t shortest path of G is a t -> s shortest path of its transpose
+    # (arcs keep their weights), so the all-source sums agree
+    g = bcgen.orient(bcgen.gnp(60, 0.08, 11), seed=5, p_both=0.2)
+    wt = bcgen.edge_weights(g, 1, 4, 7, per_arc=True)
+    deg = np.diff(g.off.astype(np.int64))
+    u = np.repeat(np.arange(g.n), deg)
+    order = np.lexsort((u, g.adj))  # arcs sorted by (head, tail): the transpose's CSR order
+    r = bcgen.directed_csr(g.n, g.adj[order], u[order])
+    rw = wt[order]
+    assert np.array_equal(r.adj, u[order])
+    assert close(oracle.wbc(r.off, r.adj, rw, all_src(r)), oracle.wbc(g.off, g.adj, wt, all_src(g)))
