@@ -241,6 +241,7 @@ struct bc_graph {
     long long wi_hchunks = 0;       // their chunk tasks
     bool wi_prefix = true;          // heavy in-rows are the ids [0, wi_heavy) (no id lists)
     DevBuf wdist, wsig, winv, wdel, wrho, wmark, wbc, wctl, wsrc, wscr, warr;  // weighted BC state, kept between calls
+    DevBuf word, whist;  // weighted BC: row order by mean distance, its bucket counts
     AllocHook hook;
     std::mutex mu;                                 // bc_compute / plans: the per-width workspaces below
     std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
@@ -1110,7 +1111,7 @@ bc_status bc_graph_destroy(bc_graph* g) {
     for (DevBuf* b : {&g->pr_ccum, &g->pr_rank, &g->pr_scratch, &g->pr_cpart, &g->pr_carr, &g->pr_ctl, &g->pr_small})
         buf_release(*b, st);
     for (DevBuf* b : {&g->w, &g->wi, &g->wihcum, &g->wihrow, &g->wilrow, &g->wdist, &g->wsig, &g->winv, &g->wdel,
-                      &g->wrho, &g->wmark, &g->wbc, &g->wctl, &g->wsrc, &g->wscr, &g->warr})
+                      &g->wrho, &g->wmark, &g->wbc, &g->wctl, &g->wsrc, &g->wscr, &g->warr, &g->word, &g->whist})
         buf_release(*b, st);
     buf_release(g->inv, st);
     cudaStreamSynchronize(st);
@@ -1240,7 +1241,8 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
         !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int) + 16, st) ||
         !buf_ensure(g->wsrc, sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * KW + sizeof(int), st) ||
         !buf_ensure(g->wscr, 24 * KW * (size_t)std::max(1ll, std::max(g->hchunk_total, g->wi_hchunks)), st) ||
-        !buf_ensure(g->warr, sizeof(int) * (size_t)std::max(1, std::max(g->n_heavy, g->wi_heavy)), st))
+        !buf_ensure(g->warr, sizeof(int) * (size_t)std::max(1, std::max(g->n_heavy, g->wi_heavy)), st) ||
+        !buf_ensure(g->word, sizeof(int) * n, st) || !buf_ensure(g->whist, sizeof(unsigned int) * kWbcHistWords, st))
         return done(fail(BC_E_NOMEM, "weighted BC buffers"));
     const WCsr wout{(const int*)g->off.p, (const int*)g->adj.p, (const int*)g->w.p, g->n_heavy, g->hchunk_total,
                     (const int*)g->hcum.p, nullptr, nullptr};
@@ -1284,7 +1286,8 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
             e = launch_wbc(g->n, wout, win, (int*)g->warr.p, g->wscr.p, (const int*)g->wsrc.p + (size_t)b * KW,
                            (long long*)g->wdist.p,
                            (unsigned long long*)g->wsig.p, (double*)g->winv.p, (double*)g->wdel.p,
-                           (double*)g->wrho.p, (int*)g->wmark.p, (double*)g->wbc.p, ctl, changed, passes, visited,
+                           (double*)g->wrho.p, (int*)g->wmark.p, (int*)g->word.p, (unsigned int*)g->whist.p,
+                           (double*)g->wbc.p, ctl, changed, passes, visited,
                            40000000000ll, blocks, st);
         int herr = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -40,6 +40,9 @@ constexpr int kWThreads = 256;
 constexpr int KW = 32;  // sources per batch
 constexpr long long kInf = LLONG_MAX;
 constexpr unsigned int kAll = 0xffffffffu;
+constexpr int kBuckets = 4096;  // distance buckets of the row order
+static_assert(kWbcHistWords == kBuckets + 2, "bucket counts and an 8-byte largest key");
+static_assert(kBuckets % kWThreads == 0, "the prefix gives each thread whole buckets");
 
 struct WParams {
     int n;
@@ -53,6 +56,9 @@ struct WParams {
     double* del;               // [n][32] dependencies
     double* rho;               // [n][32] (1 + delta) / sigma, kept with delta
     int* mark;                 // [2][n] pass stamps: rows next to a row that changed
+    int* ord;                  // [n] rows by mean distance (path-count and dependency passes)
+    unsigned int* hist;        // [kBuckets] bucket counts, then cursors
+    unsigned long long* keymax;  // [1] largest mean distance
     double* bc;                // [n] relabelled
     Ctl* ctl;
     int* changed;              // [3] rotating "a pass changed something" flags
@@ -86,9 +92,13 @@ __device__ __forceinline__ T load_cg(const T* q) {
 // (every pass when `all`): a row whose value changed stamps the rows that read
 // it (its row in `sc`, the transpose of `rd`) for the next pass, in the other
 // of two stamp arrays, so no stamp a pass reads changes during it.
+//
+// Light rows run in id order, or, given `ord`, in that order (reversed when
+// `rev`), every row listed and the heavy ones skipped there.
 template <class Arc, class Finish, class T>
-__device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const WCsr& sc, T init, Arc arc, Finish finish, int pass,
-                         bool all) {
+__device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const WCsr& sc, T init, Arc arc,
+                                         Finish finish, int pass, bool all, const int* ord = nullptr,
+                                         bool rev = false) {
     const int* mprev = p.mark + (size_t)(pass & 1) * p.n;
     int* mnext = p.mark + (size_t)((pass + 1) & 1) * p.n;
     auto stamp = [&](int r) {
@@ -97,7 +107,7 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long tasks = rd.hchunks + (p.n - rd.n_heavy);
+    const long long tasks = rd.hchunks + (ord ? p.n : p.n - rd.n_heavy);
     T* scratch = reinterpret_cast<T*>(p.scratch);
     unsigned long long arcs = 0, rows = 0;  // read by this warp (lane 0 reports)
     for (long long t = wid; t < tasks; t += nw) {
@@ -133,9 +143,11 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
                 if (lane == 0) p.arr[k] = 0;  // ready for the next pass (after its barrier)
             }
         } else {
-            const int i = (int)(t - rd.hchunks), r = rd.lrow ? __ldg(rd.lrow + i) : rd.n_heavy + i;
+            const int i = (int)(t - rd.hchunks);
+            const int r = ord ? ord[rev ? p.n - 1 - i : i] : rd.lrow ? __ldg(rd.lrow + i) : rd.n_heavy + i;
             if (!all && mprev[r] != pass) continue;
             const int b = rd.off[r], e = rd.off[r + 1];
+            if (ord && e - b > kChunk) continue;  // a heavy row: its chunk tasks ran it
             T acc = arc.start(r, init);
             ++rows;
             if (__any_sync(kAll, arc.live(acc))) {
@@ -299,6 +311,8 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         p.sig[i] = 0ull;
         p.del[i] = 0.0;
     }
+    for (long long i = tid; i < kBuckets; i += nthr) p.hist[i] = 0u;
+    if (tid == 0) *p.keymax = 0ull;
     if (!team.sync()) return;
     if (tid < KW && p.src[tid] >= 0) p.dist[at(p.src[tid], (int)tid)] = 0;
     if (!team.sync()) return;
@@ -325,6 +339,58 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
     }
     const int pass_dist = np;
 
+    // Row order for the next two loops: rows by the mean of their finite
+    // distances over the batch's columns, in kBuckets buckets.  A DAG
+    // predecessor is closer in its column, so in this order (reversed for the
+    // dependencies) an in-place pass mostly meets a row's inputs already
+    // updated.  The order within a bucket follows the scatter's timing; it
+    // changes pass counts only, never the values.
+    {
+        long long* key = reinterpret_cast<long long*>(p.inv);  // free until the counts are final
+        const long long wid = tid >> 5, nw = nthr >> 5;
+        unsigned long long kmax = 0;
+        for (long long v = wid; v < p.n; v += nw) {
+            const long long d = p.dist[at((int)v, lane)];
+            long long sum = d != kInf ? d : 0;
+            const int cnt = __popc(__ballot_sync(kAll, d != kInf));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o);
+            const long long k = cnt ? sum / cnt : 0;
+            if (lane == 0) key[v] = k;
+            kmax = (unsigned long long)k > kmax ? (unsigned long long)k : kmax;
+        }
+        if (lane == 0 && kmax) atomicMax(p.keymax, kmax);
+        if (!team.sync()) return;
+        const unsigned long long km = *(volatile unsigned long long*)p.keymax;
+        auto bucket = [&](long long k) {  // k <= km, so the ratio is at most 1
+            return km ? (int)((double)k / (double)km * (kBuckets - 1)) : 0;
+        };
+        for (long long v = tid; v < p.n; v += nthr) atomicAdd(&p.hist[bucket(key[v])], 1u);
+        if (!team.sync()) return;
+        if (blockIdx.x == 0) {  // exclusive prefix of the bucket counts, in place
+            __shared__ unsigned int part[kWThreads];
+            constexpr int per = kBuckets / kWThreads;
+            unsigned int loc[per], run = 0;
+#pragma unroll
+            for (int q = 0; q < per; ++q) {
+                loc[q] = *(volatile unsigned int*)&p.hist[threadIdx.x * per + q];
+                run += loc[q];
+            }
+            part[threadIdx.x] = run;
+            __syncthreads();
+            unsigned int base = 0;
+            for (int q = 0; q < (int)threadIdx.x; ++q) base += part[q];
+#pragma unroll
+            for (int q = 0; q < per; ++q) {
+                p.hist[threadIdx.x * per + q] = base;
+                base += loc[q];
+            }
+        }
+        if (!team.sync()) return;
+        for (long long v = tid; v < p.n; v += nthr) p.ord[atomicAdd(&p.hist[bucket(key[v])], 1u)] = (int)v;
+        if (!team.sync()) return;
+    }
+
     // path counts, in place: every value only grows towards the DAG sums
     np = 0;
     bool big = false;
@@ -349,7 +415,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
                 return true;
             }
             return false;
-        }, pass, np == 1);
+        }, pass, np == 1, p.ord, false);
         if (ovf) atomicOr(&p.ctl->err, ERR_SIGMA_RANGE);
         more = end_pass(ch);
         if (fail) return;
@@ -381,7 +447,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
                 return true;
             }
             return false;
-        }, pass, np == 1);
+        }, pass, np == 1, p.ord, true);
         more = end_pass(ch);
         if (fail) return;
     }
@@ -485,8 +551,8 @@ int wbc_blocks() {
 
 cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* scratch, const int* src,
                        long long* dist, unsigned long long* sig, double* inv, double* del, double* rho, int* mark,
-                       double* bc, Ctl* ctl, int* changed, int* passes, unsigned long long* visited, long long budget,
-                       int blocks, cudaStream_t st) {
+                       int* ord, unsigned int* hist, double* bc, Ctl* ctl, int* changed, int* passes,
+                       unsigned long long* visited, long long budget, int blocks, cudaStream_t st) {
     WParams p;
     p.n = n;
     p.out = out;
@@ -500,6 +566,9 @@ cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* s
     p.del = del;
     p.rho = rho;
     p.mark = mark;
+    p.ord = ord;
+    p.hist = hist;
+    p.keymax = reinterpret_cast<unsigned long long*>(hist + kBuckets);
     p.bc = bc;
     p.ctl = ctl;
     p.changed = changed;
