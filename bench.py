@@ -589,6 +589,7 @@ def run_weighted(a, bc, torch):
                        "batches": s["batches"], "passes": {"dist": s["max_levels"], "sigma": s["pull_levels"],
                                                            "delta": s["push_levels"]},
                        "ingest_s": round(ingest_s, 3), "statuses": sorted(int(x) for x in statuses),
+                       "source_grouping_ms": round(s["order_ms"], 3),
                        "step": "one bc_compute_weighted over all sources on the resident graph",
                        "l2": "per-batch state (n x 32 x 48 B) is far above L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -209,7 +209,9 @@ bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indice
  * 2^64 (BC_W_SIGMA_INEXACT once one reaches 2^53, BC_E_SIGMA_RANGE at
  * 2^64); BC is the raw sum over the listed sources, as for bc_compute.
  * On a directed graph paths follow the arcs: distances and path counts pull
- * over in-arcs, dependencies over out-arcs.
+ * over in-arcs, dependencies over out-arcs.  Sources are batched in the
+ * grouped order of bc_compute's automatic rule (undirected skewed graphs,
+ * 256 sources or more); the order changes rounding only.
  * Batches of 32 sources, one launch each; results repeat bit for bit.
  * BC_E_INVALID_ARG if the graph has no weights.  bc_last_run_stats reports
  * max_levels / pull_levels / push_levels = passes of the distance, path-count

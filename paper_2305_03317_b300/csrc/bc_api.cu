@@ -1232,10 +1232,24 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
         }
         d_src = (const int*)hsrc.p;
     }
+    DevBuf grouped;
     auto done = [&](bc_status rr) {
         buf_release(hsrc, st);
+        buf_release(grouped, st);
         return rr;
     };
+    // batches of sources with similar hub distances (the rule and order of
+    // bc_compute): their 32 columns then agree on the row order below
+    bc_run_stats pre{};
+    {
+        bc_options o;
+        memset(&o, 0, sizeof o);
+        if (nbatch > 1 && want_grouping(g, nsrc, o)) {
+            bc_status gr = group_sources(g, d_src, nsrc, st, grouped, &pre, nullptr);
+            if (gr < 0) return done(gr);
+            d_src = (const int*)grouped.p;
+        }
+    }
     if (!buf_ensure(g->wdist, 8 * cells, st) || !buf_ensure(g->wsig, 8 * cells, st) || !buf_ensure(g->winv, 8 * cells, st) ||
         !buf_ensure(g->wdel, 8 * cells, st) || !buf_ensure(g->wrho, 8 * cells, st) || !buf_ensure(g->wmark, 8 * n, st) ||
         !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int) + 16, st) ||
@@ -1320,8 +1334,9 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     s.pull_levels = hp[1];   // passes of the path-count loop
     s.push_levels = hp[2];   // passes of the dependency loop
     s.grid_blocks = blocks;
-    s.kernel_launches = 2 + nbatch;          // kernels only: source mapping, one launch per batch, unpermute
+    s.kernel_launches = 2 + nbatch + pre.kernel_launches;  // source mapping, one per batch, unpermute, grouping
     s.kernel_ms = ms;
+    s.order_ms = pre.kernel_ms;
     s.teams = 1;
     s.arcs_visited = (int64_t)hv[0];
     s.rows_visited = (int64_t)hv[1];
