@@ -5,21 +5,23 @@
 // SSSP program (Section 2.3, the Min construct inside a fixed-point loop)
 // gives them by Bellman-Ford relaxation.  Per batch of 32 sources (lane =
 // column), one cooperative persistent launch runs three fixed-point loops,
-// each pass pulling into a row from its neighbours, all in place:
-//   dist:  d(v) = min(d(v), min over arcs u -> v of d(u) + w)
-//   sigma: s(v) = [v = source] + sum over arcs u -> v with d(u) + w = d(v) of s(u)
+// all in place:
+//   dist:  d(v) = min(d(v), min over arcs u -> v of d(u) + w), pushed: the
+//          rows that changed relax their out-arcs with an atomic min;
+//   sigma: s(v) = [v = source] + sum over arcs u -> v with d(u) + w = d(v) of s(u),
+//          pulled over in-arcs;
 //   delta: t(v) = s(v) * sum over arcs v -> x with d(v) + w = d(x) of rho(x),
-//          rho(x) = (1 + t(x)) / s(x), rewritten with each new t(x)
-// The first two pull over in-arcs, the third over out-arcs: on a directed
-// graph they read the in-CSR (the transpose, with its own copy of the
-// weights) and the out-CSR; on an undirected graph both are the one CSR.
-// until a pass changes nothing; then BC(v) += t(v) for every non-source
-// column, columns in order.  Distances only fall and counts and dependencies
+//          rho(x) = (1 + t(x)) / s(x), rewritten with each new t(x), pulled
+//          over out-arcs.
+// On a directed graph the in-arcs are the in-CSR (the transpose, with its own
+// copy of the weights); on an undirected graph both are the one CSR.  Each
+// loop runs until a pass changes nothing; then BC(v) += t(v) for every
+// non-source column, columns in order.  Distances only fall and counts and dependencies
 // only grow towards the DAG values, so a read of a neighbour another warp is
 // rewriting is always a valid bound and the fixed point is the unique one,
 // whatever the timing.  After a loop's first pass, a pass recomputes only the
-// rows that read a row that changed (stamps, through the other direction's
-// CSR).  Distance mins and integer path
+// rows that read a row that changed, or pushes only from the rows that
+// changed (stamps).  Distance mins and integer path
 // counts do not depend on the order of their terms; every double sum runs in
 // CSR order (long rows: per chunk, chunks combined in order), so results
 // repeat bit for bit.  Every task is one warp: a row of at most 1024 arcs, or
@@ -167,34 +169,6 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
 // whether the lane's column needs the row's arcs at all (a warp skips a row
 // no lane needs), operator()(j, adj, w, state) takes arc j of the CSR the pass
 // reads, combine joins the partials of a heavy row in order.
-struct MinArc {
-    const WParams* p;
-    int lane;
-    __device__ long long start(int, long long init) const { return init; }
-    __device__ bool live(long long) const { return true; }
-    __device__ void operator()(int j, const int* adj, const int* w, long long& best) const {
-        const long long du = p->dist[at(__ldg(adj + j), lane)];
-        if (du != kInf) {
-            const long long c = du + __ldg(w + j);
-            if (c < best) best = c;
-        }
-    }
-    // arcs j..j+3, their loads issued together
-    __device__ void quad(int j, const int* adj, const int* w, long long& best) const {
-        long long du[4];
-        int wq[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            du[q] = p->dist[at(__ldg(adj + j + q), lane)];
-            wq[q] = __ldg(w + j + q);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (du[q] != kInf && du[q] + wq[q] < best) best = du[q] + wq[q];
-    }
-    __device__ static long long combine(long long a, long long b) { return a < b ? a : b; }
-};
-
 struct SigmaAcc {
     unsigned long long s;
     long long dv;  // the row's own distance
@@ -285,6 +259,78 @@ struct DeltaArc {
     __device__ static DeltaAcc combine(DeltaAcc a, DeltaAcc b) { return DeltaAcc{a.sum + b.sum, a.dv}; }
 };
 
+// One pass of the distance loop in push form: every row whose distance changed
+// in the previous pass (every reached row on the first pass) relaxes its
+// out-arcs, d(v) = min(d(v), d(u) + w) by a 64-bit atomic min per column, and
+// a row it lowers is stamped for the next pass.  The min of a set does not
+// depend on the order of its terms, so the fixed point is the pull form's;
+// a row is read when its own distance changed, not whenever a neighbour's
+// did (hubs change rarely and have the longest rows).  Tasks as in row_pass
+// (heavy out-rows in kChunk-arc chunks, which need no combining here).
+__device__ __forceinline__ bool push_min_pass(const WParams& p, int pass, bool all) {
+    const WCsr& g = p.out;
+    const int* mprev = p.mark + (size_t)(pass & 1) * p.n;
+    int* mnext = p.mark + (size_t)((pass + 1) & 1) * p.n;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long tasks = g.hchunks + (p.n - g.n_heavy);
+    unsigned long long arcs = 0, rows = 0;
+    bool ch = false;
+    for (long long t = wid; t < tasks; t += nw) {
+        int r, b, e;
+        if (t < g.hchunks) {
+            int lo = 0, hi = g.n_heavy;  // hcum[lo] <= t < hcum[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (g.hcum[mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            r = g.hrow ? __ldg(g.hrow + lo) : lo;
+            b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
+            e = min(g.off[r + 1], b + kChunk);
+        } else {
+            const int i = (int)(t - g.hchunks);
+            r = g.lrow ? __ldg(g.lrow + i) : g.n_heavy + i;
+            b = g.off[r];
+            e = g.off[r + 1];
+        }
+        if (!all && mprev[r] != pass) continue;
+        const long long du = p.dist[at(r, lane)];
+        if (!__any_sync(kAll, du != kInf)) continue;
+        ++rows;
+        arcs += e - b;
+        if (du == kInf) continue;  // this column has nothing to push
+        auto relax = [&](int v, long long c, long long dv) {
+            if (c < dv && atomicMin(&p.dist[at(v, lane)], c) > c) {
+                mnext[v] = pass + 1;
+                ch = true;
+            }
+        };
+        int j = b;
+        for (; j + 4 <= e; j += 4) {
+            int v[4];
+            long long c[4], dv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[q] = __ldg(g.adj + j + q);
+                c[q] = du + __ldg(g.w + j + q);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dv[q] = p.dist[at(v[q], lane)];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) relax(v[q], c[q], dv[q]);
+        }
+        for (; j < e; ++j) {
+            const int v = __ldg(g.adj + j);
+            relax(v, du + __ldg(g.w + j), p.dist[at(v, lane)]);
+        }
+    }
+    if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
+    if (lane == 0 && rows) atomicAdd(&p.visited[1], rows);
+    return ch;
+}
+
 __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
     GridTeam team{p.ctl, p.ctl, (int)gridDim.x, p.budget};
     const int lane = threadIdx.x & 31;
@@ -317,24 +363,16 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
     if (tid < KW && p.src[tid] >= 0) p.dist[at(p.src[tid], (int)tid)] = 0;
     if (!team.sync()) return;
 
-    // distances, in place (stale reads are valid upper bounds)
+    // distances, pushed from the rows that changed (stale reads are valid
+    // upper bounds: a read below the truth never happens, one above it only
+    // costs an atomic that lowers nothing)
     int np = 0;
     for (bool more = true; more;) {
         if (++np > p.max_passes) {
             if (tid == 0) atomicOr(&p.ctl->err, ERR_INTERNAL);
             return;
         }
-        bool ch = false;
-        MinArc arc{&p, lane};
-        row_pass<MinArc>(p, p.in, p.out, kInf, arc, [&](int v, long long best) {
-            if (best < p.dist[at(v, lane)]) {
-                p.dist[at(v, lane)] = best;
-                ch = true;
-                return true;
-            }
-            return false;
-        }, pass, np == 1);
-        more = end_pass(ch);
+        more = end_pass(push_min_pass(p, pass, np == 1));
         if (fail) return;
     }
     const int pass_dist = np;
