@@ -169,57 +169,6 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
 // whether the lane's column needs the row's arcs at all (a warp skips a row
 // no lane needs), operator()(j, adj, w, state) takes arc j of the CSR the pass
 // reads, combine joins the partials of a heavy row in order.
-struct SigmaAcc {
-    unsigned long long s;
-    long long dv;  // the row's own distance
-    bool ovf;
-};
-
-struct SigmaArc {
-    const WParams* p;
-    int lane;
-    __device__ SigmaAcc start(int v, SigmaAcc init) const {
-        init.dv = p->dist[at(v, lane)];
-        return init;
-    }
-    __device__ bool live(const SigmaAcc& a) const { return a.dv != kInf && a.dv != 0; }
-    __device__ void operator()(int j, const int* adj, const int* w, SigmaAcc& a) const {
-        if (a.dv == kInf) return;
-        const int u = __ldg(adj + j);
-        const long long du = p->dist[at(u, lane)];
-        if (du != kInf && du + __ldg(w + j) == a.dv) {
-            const unsigned long long x = p->sig[at(u, lane)];
-            const unsigned long long s = a.s + x;
-            a.ovf |= s < x;
-            a.s = s;
-        }
-    }
-    __device__ void quad(int j, const int* adj, const int* w, SigmaAcc& a) const {
-        if (a.dv == kInf) return;
-        int u[4];
-        bool pred[4];
-        unsigned long long x[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            u[q] = __ldg(adj + j + q);
-            const long long du = p->dist[at(u[q], lane)];
-            pred[q] = du != kInf && du + __ldg(w + j + q) == a.dv;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] = pred[q] ? p->sig[at(u[q], lane)] : 0ull;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const unsigned long long s = a.s + x[q];
-            a.ovf |= s < x[q];
-            a.s = s;
-        }
-    }
-    __device__ static SigmaAcc combine(SigmaAcc a, SigmaAcc b) {
-        const unsigned long long s = a.s + b.s;
-        return SigmaAcc{s, a.dv, a.ovf || b.ovf || s < b.s};
-    }
-};
-
 struct DeltaAcc {
     double sum;
     long long dv;
@@ -331,6 +280,105 @@ __device__ __forceinline__ bool push_min_pass(const WParams& p, int pass, bool a
     return ch;
 }
 
+// Path counts in push form, one pass: every row stamped by the previous pass
+// (every row on the first) adds the growth of its count since its last push,
+// inc = sigma(u) - pushed(u), to each DAG successor v (d(u) + w = d(v)) with a
+// 64-bit integer atomic add, and stamps v.  Integer sums do not depend on the
+// order of their terms, so the counts are the pull form's, bit for bit; a
+// wrap of an add (a count reaching 2^64) sets `ovf`.  A heavy row's chunks
+// must push the same increment: `hinc` holds the heavy rows' increments,
+// taken before the pass (heavy_increments) behind a grid barrier; a light row
+// takes its own inline, as one warp owns it.  Adds that land on a row after
+// it took its increment are pushed in a later pass (the add stamps it).
+__device__ __forceinline__ void heavy_increments(const WParams& p, int pass, bool all,
+                                                 unsigned long long* pushed, unsigned long long* hinc) {
+    const WCsr& g = p.out;
+    const int* mprev = p.mark + (size_t)(pass & 1) * p.n;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = wid; k < g.n_heavy; k += nw) {
+        const int r = g.hrow ? __ldg(g.hrow + k) : (int)k;
+        if (!all && mprev[r] != pass) continue;
+        const unsigned long long s = p.sig[at(r, lane)];
+        hinc[(size_t)k * KW + lane] = s - pushed[at(r, lane)];
+        pushed[at(r, lane)] = s;
+    }
+}
+
+__device__ __forceinline__ bool push_sigma_pass(const WParams& p, int pass, bool all, unsigned long long* pushed,
+                                                const unsigned long long* hinc, bool& ovf) {
+    const WCsr& g = p.out;
+    const int* mprev = p.mark + (size_t)(pass & 1) * p.n;
+    int* mnext = p.mark + (size_t)((pass + 1) & 1) * p.n;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long tasks = g.hchunks + (p.n - g.n_heavy);
+    unsigned long long arcs = 0, rows = 0;
+    bool ch = false;
+    for (long long t = wid; t < tasks; t += nw) {
+        int r, b, e;
+        unsigned long long inc;
+        if (t < g.hchunks) {
+            int lo = 0, hi = g.n_heavy;  // hcum[lo] <= t < hcum[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (g.hcum[mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            r = g.hrow ? __ldg(g.hrow + lo) : lo;
+            if (!all && mprev[r] != pass) continue;
+            b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
+            e = min(g.off[r + 1], b + kChunk);
+            inc = hinc[(size_t)lo * KW + lane];
+        } else {
+            const int i = (int)(t - g.hchunks);
+            r = g.lrow ? __ldg(g.lrow + i) : g.n_heavy + i;
+            if (!all && mprev[r] != pass) continue;
+            b = g.off[r];
+            e = g.off[r + 1];
+            const unsigned long long s = p.sig[at(r, lane)];
+            inc = s - pushed[at(r, lane)];
+            pushed[at(r, lane)] = s;
+        }
+        if (!__any_sync(kAll, inc != 0ull)) continue;
+        ++rows;
+        arcs += e - b;
+        if (inc == 0ull) continue;  // this column has nothing to push
+        const long long du = p.dist[at(r, lane)];
+        auto add = [&](int v, long long c, long long dv) {
+            if (c == dv) {
+                const unsigned long long old = atomicAdd(&p.sig[at(v, lane)], inc);
+                ovf |= old + inc < old;
+                mnext[v] = pass + 1;
+                ch = true;
+            }
+        };
+        int j = b;
+        for (; j + 4 <= e; j += 4) {
+            int v[4];
+            long long c[4], dv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[q] = __ldg(g.adj + j + q);
+                c[q] = du + __ldg(g.w + j + q);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dv[q] = p.dist[at(v[q], lane)];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) add(v[q], c[q], dv[q]);
+        }
+        for (; j < e; ++j) {
+            const int v = __ldg(g.adj + j);
+            add(v, du + __ldg(g.w + j), p.dist[at(v, lane)]);
+        }
+    }
+    if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
+    if (lane == 0 && rows) atomicAdd(&p.visited[1], rows);
+    return ch;
+}
+
 __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
     GridTeam team{p.ctl, p.ctl, (int)gridDim.x, p.budget};
     const int lane = threadIdx.x & 31;
@@ -356,11 +404,15 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         p.dist[i] = kInf;
         p.sig[i] = 0ull;
         p.del[i] = 0.0;
+        p.rho[i] = 0.0;  // all-zero bits: the pushed path counts start at 0
     }
     for (long long i = tid; i < kBuckets; i += nthr) p.hist[i] = 0u;
     if (tid == 0) *p.keymax = 0ull;
     if (!team.sync()) return;
-    if (tid < KW && p.src[tid] >= 0) p.dist[at(p.src[tid], (int)tid)] = 0;
+    if (tid < KW && p.src[tid] >= 0) {
+        p.dist[at(p.src[tid], (int)tid)] = 0;
+        p.sig[at(p.src[tid], (int)tid)] = 1ull;  // the path of length 0
+    }
     if (!team.sync()) return;
 
     // distances, pushed from the rows that changed (stale reads are valid
@@ -429,42 +481,36 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         if (!team.sync()) return;
     }
 
-    // path counts, in place: every value only grows towards the DAG sums
+    // path counts, pushed along the DAG arcs in exact integer increments
+    // (pushed counts in the rho array, the heavy rows' increments in the
+    // chunk scratch, both free until the dependencies)
     np = 0;
-    bool big = false;
-    for (bool more = true; more;) {
-        if (++np > p.max_passes) {
-            if (tid == 0) atomicOr(&p.ctl->err, ERR_INTERNAL);
-            return;
+    {
+        unsigned long long* pushed = reinterpret_cast<unsigned long long*>(p.rho);
+        unsigned long long* hinc = reinterpret_cast<unsigned long long*>(p.scratch);
+        for (bool more = true; more;) {
+            if (++np > p.max_passes) {
+                if (tid == 0) atomicOr(&p.ctl->err, ERR_INTERNAL);
+                return;
+            }
+            heavy_increments(p, pass, np == 1, pushed, hinc);
+            if (!team.sync()) return;
+            bool ovf = false;
+            const bool ch = push_sigma_pass(p, pass, np == 1, pushed, hinc, ovf);
+            if (ovf) atomicOr(&p.ctl->err, ERR_SIGMA_RANGE);
+            more = end_pass(ch);
+            if (fail) return;
         }
-        bool ch = false, ovf = false;
-        SigmaArc arc{&p, lane};
-        row_pass<SigmaArc>(p, p.in, p.out, SigmaAcc{0ull, kInf, false}, arc, [&](int v, SigmaAcc a) {
-            unsigned long long s = a.s;
-            if (p.dist[at(v, lane)] != kInf && v == p.src[lane]) {
-                s += 1ull;
-                a.ovf |= s == 0ull;
-            }
-            ovf |= a.ovf;
-            big |= s >= (1ull << 53);
-            if (s != p.sig[at(v, lane)]) {
-                p.sig[at(v, lane)] = s;
-                ch = true;
-                return true;
-            }
-            return false;
-        }, pass, np == 1, p.ord, false);
-        if (ovf) atomicOr(&p.ctl->err, ERR_SIGMA_RANGE);
-        more = end_pass(ch);
-        if (fail) return;
     }
     const int pass_sigma = np;
-    if (__any_sync(kAll, big) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
+    bool big = false;
     for (long long i = tid; i < cells; i += nthr) {
+        big |= p.sig[i] >= (1ull << 53);
         const double iv = p.sig[i] ? 1.0 / (double)p.sig[i] : 0.0;
         p.inv[i] = iv;
         p.rho[i] = iv;  // delta = 0
     }
+    if (__any_sync(kAll, big) && lane == 0) atomicOr(&p.ctl->flags, BST_INEXACT);
     if (!team.sync()) return;
 
     // dependencies, in place, rho rewritten with each new delta
