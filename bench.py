@@ -559,10 +559,14 @@ def run_weighted(a, bc, torch):
     clk = clocks.stop()
     t = float(np.mean(ms))
     s = G.stats()
-    # bytes the passes must move: every arc a pass reads brings its index and
-    # weight (8 B) and the neighbour's 32-column row (256 B); every row a pass
-    # recomputes writes its 32 columns (256 B); summed over the call's passes
-    model = 264.0 * s["arcs_visited"] + 256.0 * s["rows_visited"]
+    # bytes the passes must move: an arc read with its neighbour's distances
+    # brings its index and weight (8 B) and the neighbour's 32-column row
+    # (256 B); an arc the dependency loop reads through its DAG mask brings its
+    # index and mask (8 B) and one 8-byte rho per column the mask selects;
+    # every row a pass recomputes writes its 32 columns (256 B); summed over
+    # the call's passes
+    full = s["arcs_visited"] - s["mask_arcs"]
+    model = 264.0 * full + 8.0 * s["mask_arcs"] + 8.0 * s["mask_lanes"] + 256.0 * s["rows_visited"]
     kt = float(np.mean(kms))
     peak, peak_src = measured_peak()
     achieved = model / (kt / 1e3) / 1e9
@@ -594,8 +598,10 @@ def run_weighted(a, bc, torch):
                        "l2": "per-batch state (n x 32 x 48 B) is far above L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "k_wbc", "kernel_ms": kt, "model_bytes": model,
-                         "model": "264 B per arc read + 256 B per row recomputed, over the passes the call ran "
-                                  f"({s['arcs_visited']:.3e} arcs, {s['rows_visited']:.3e} rows)",
+                         "model": "264 B per arc read with its neighbour's distance row, 8 B per arc read through a "
+                                  "DAG mask + 8 B per column it selects, 256 B per row recomputed, over the passes the "
+                                  f"call ran ({full:.3e} + {s['mask_arcs']:.3e} arcs, {s['mask_lanes']:.3e} mask "
+                                  f"columns, {s['rows_visited']:.3e} rows)",
                          "peak_source": peak_src},
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                            "what": "per bc_compute_weighted call"},

@@ -55,7 +55,8 @@ class bc_run_stats(ctypes.Structure):
                 ("pull_levels", ctypes.c_int32), ("push_levels", ctypes.c_int32), ("ext_batches", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_float), ("teams", ctypes.c_int32), ("order_ms", ctypes.c_float),
-                ("arcs_visited", ctypes.c_int64), ("rows_visited", ctypes.c_int64)]
+                ("arcs_visited", ctypes.c_int64), ("rows_visited", ctypes.c_int64),
+                ("mask_arcs", ctypes.c_int64), ("mask_lanes", ctypes.c_int64)]
 
 
 class bc_item(ctypes.Structure):

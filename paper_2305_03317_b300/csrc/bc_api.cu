@@ -242,6 +242,7 @@ struct bc_graph {
     bool wi_prefix = true;          // heavy in-rows are the ids [0, wi_heavy) (no id lists)
     DevBuf wdist, wsig, winv, wdel, wrho, wmark, wbc, wctl, wsrc, wscr, warr;  // weighted BC state, kept between calls
     DevBuf word, whist;  // weighted BC: row order by mean distance, its bucket counts
+    DevBuf wdag;         // weighted BC: per out-arc DAG masks of the current batch
     AllocHook hook;
     std::mutex mu;                                 // bc_compute / plans: the per-width workspaces below
     std::map<int, std::unique_ptr<Workspace>> ws;  // by batch width
@@ -1111,7 +1112,7 @@ bc_status bc_graph_destroy(bc_graph* g) {
     for (DevBuf* b : {&g->pr_ccum, &g->pr_rank, &g->pr_scratch, &g->pr_cpart, &g->pr_carr, &g->pr_ctl, &g->pr_small})
         buf_release(*b, st);
     for (DevBuf* b : {&g->w, &g->wi, &g->wihcum, &g->wihrow, &g->wilrow, &g->wdist, &g->wsig, &g->winv, &g->wdel,
-                      &g->wrho, &g->wmark, &g->wbc, &g->wctl, &g->wsrc, &g->wscr, &g->warr, &g->word, &g->whist})
+                      &g->wrho, &g->wmark, &g->wbc, &g->wctl, &g->wsrc, &g->wscr, &g->warr, &g->word, &g->whist, &g->wdag})
         buf_release(*b, st);
     buf_release(g->inv, st);
     cudaStreamSynchronize(st);
@@ -1252,11 +1253,12 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     }
     if (!buf_ensure(g->wdist, 8 * cells, st) || !buf_ensure(g->wsig, 8 * cells, st) || !buf_ensure(g->winv, 8 * cells, st) ||
         !buf_ensure(g->wdel, 8 * cells, st) || !buf_ensure(g->wrho, 8 * cells, st) || !buf_ensure(g->wmark, 8 * n, st) ||
-        !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int) + 16, st) ||
+        !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int) + 32, st) ||
         !buf_ensure(g->wsrc, sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * KW + sizeof(int), st) ||
         !buf_ensure(g->wscr, 24 * KW * (size_t)std::max(1ll, std::max(g->hchunk_total, g->wi_hchunks)), st) ||
         !buf_ensure(g->warr, sizeof(int) * (size_t)std::max(1, std::max(g->n_heavy, g->wi_heavy)), st) ||
-        !buf_ensure(g->word, sizeof(int) * n, st) || !buf_ensure(g->whist, sizeof(unsigned int) * kWbcHistWords, st))
+        !buf_ensure(g->word, sizeof(int) * n, st) || !buf_ensure(g->whist, sizeof(unsigned int) * kWbcHistWords, st) ||
+        !buf_ensure(g->wdag, sizeof(unsigned int) * (size_t)(g->m > 0 ? g->m : 1), st))
         return done(fail(BC_E_NOMEM, "weighted BC buffers"));
     const WCsr wout{(const int*)g->off.p, (const int*)g->adj.p, (const int*)g->w.p, g->n_heavy, g->hchunk_total,
                     (const int*)g->hcum.p, nullptr, nullptr};
@@ -1270,10 +1272,10 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     int* changed = (int*)((char*)g->wctl.p + sizeof(Ctl));
     int* passes = changed + 4;
     static_assert((sizeof(Ctl) + 8 * sizeof(int)) % 8 == 0, "visited counters need 8-byte alignment");
-    unsigned long long* visited = (unsigned long long*)(changed + 8);  // arcs, rows
+    unsigned long long* visited = (unsigned long long*)(changed + 8);  // arcs, rows, mask arcs, mask lanes
     int* bad = (int*)g->wsrc.p + (size_t)(nbatch > 0 ? nbatch : 1) * KW;
     cudaError_t e = cudaMemsetAsync(g->wbc.p, 0, 8 * n, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->wctl.p, 0, sizeof(Ctl) + 8 * sizeof(int) + 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->wctl.p, 0, sizeof(Ctl) + 8 * sizeof(int) + 32, st);
     if (e == cudaSuccess && nbatch > 0) {
         e = cudaMemsetAsync(bad, 0, sizeof(int), st);
         if (e == cudaSuccess)
@@ -1301,7 +1303,7 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
                            (long long*)g->wdist.p,
                            (unsigned long long*)g->wsig.p, (double*)g->winv.p, (double*)g->wdel.p,
                            (double*)g->wrho.p, (int*)g->wmark.p, (int*)g->word.p, (unsigned int*)g->whist.p,
-                           (double*)g->wbc.p, ctl, changed, passes, visited,
+                           (unsigned int*)g->wdag.p, (double*)g->wbc.p, ctl, changed, passes, visited,
                            40000000000ll, blocks, st);
         int herr = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1316,7 +1318,7 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     }
     cudaEventRecord(ev[1], st);
     int hp[3] = {0, 0, 0}, hflags = 0;
-    unsigned long long hv[2] = {0, 0};
+    unsigned long long hv[4] = {0, 0, 0, 0};
     if (e == cudaSuccess) e = launch_unpermute((const double*)g->wbc.p, (const int*)g->inv.p, out_bc, g->n, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hp, passes, sizeof hp, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hv, visited, sizeof hv, cudaMemcpyDeviceToHost, st);
@@ -1340,6 +1342,8 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
     s.teams = 1;
     s.arcs_visited = (int64_t)hv[0];
     s.rows_visited = (int64_t)hv[1];
+    s.mask_arcs = (int64_t)hv[2];
+    s.mask_lanes = (int64_t)hv[3];
     g->last = s;
     return done((hflags & BST_INEXACT) ? BC_W_SIGMA_INEXACT : BC_OK);
 }

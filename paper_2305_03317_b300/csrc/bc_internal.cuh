@@ -177,12 +177,13 @@ struct WCsr {
     const int* lrow;    // light row ids, ascending; nullptr = rows [n_heavy, n)
 };
 int wbc_blocks();
-// ord: [n] ints; hist: kWbcHistWords words (bucket counts and the largest key).
+// ord: [n] ints; hist: kWbcHistWords words (bucket counts and the largest key);
+// dag: [m] words; visited: [4] counters.
 constexpr int kWbcHistWords = 4096 + 2;
 cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* scratch, const int* src,
                        long long* dist, unsigned long long* sig, double* inv, double* del, double* rho, int* mark,
-                       int* ord, unsigned int* hist, double* bc, Ctl* ctl, int* changed, int* passes,
-                       unsigned long long* visited, long long budget, int blocks, cudaStream_t st);
+                       int* ord, unsigned int* hist, unsigned int* dag, double* bc, Ctl* ctl, int* changed,
+                       int* passes, unsigned long long* visited, long long budget, int blocks, cudaStream_t st);
 // Weights of the relabelled arcs (and, when ioff is set, of the in-CSR's
 // arcs); err bits: 1 rows not sorted, 2 a weight <= 0, 4 asymmetric weights,
 // 8 the in-CSR is not the transpose.

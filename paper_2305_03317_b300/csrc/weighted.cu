@@ -58,14 +58,16 @@ struct WParams {
     double* del;               // [n][32] dependencies
     double* rho;               // [n][32] (1 + delta) / sigma, kept with delta
     int* mark;                 // [2][n] pass stamps: rows next to a row that changed
-    int* ord;                  // [n] rows by mean distance (path-count and dependency passes)
+    int* ord;                  // [n] rows by mean distance (dependency passes)
+    unsigned int* dag;         // [m] out-arc DAG masks of the batch (bit c: a DAG arc of column c)
     unsigned int* hist;        // [kBuckets] bucket counts, then cursors
     unsigned long long* keymax;  // [1] largest mean distance
     double* bc;                // [n] relabelled
     Ctl* ctl;
     int* changed;              // [3] rotating "a pass changed something" flags
     int* passes;               // [3] passes run by each loop, summed over launches (out)
-    unsigned long long* visited;  // [2] arcs and rows the passes read, summed over launches (out)
+    unsigned long long* visited;  // [4] arcs and rows the passes read, arcs read through DAG masks and
+                                  // the (arc, column) pairs those select, summed over launches (out)
     long long budget;
     int max_passes;
 };
@@ -112,6 +114,7 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
     const long long tasks = rd.hchunks + (ord ? p.n : p.n - rd.n_heavy);
     T* scratch = reinterpret_cast<T*>(p.scratch);
     unsigned long long arcs = 0, rows = 0;  // read by this warp (lane 0 reports)
+    unsigned long long marcs = 0, lanes = 0;  // of those, arcs read through masks; the columns they select
     for (long long t = wid; t < tasks; t += nw) {
         if (t < rd.hchunks) {
             int lo = 0, hi = rd.n_heavy;  // hcum[lo] <= t < hcum[hi]
@@ -126,9 +129,10 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
             T acc = arc.start(r, init);
             if (__any_sync(kAll, arc.live(acc))) {
                 int j = b;
-                for (; j + 4 <= e; j += 4) arc.quad(j, rd.adj, rd.w, acc);
-                for (; j < e; ++j) arc(j, rd.adj, rd.w, acc);
+                for (; j + 4 <= e; j += 4) arc.quad(j, rd.adj, rd.w, acc, lanes);
+                for (; j < e; ++j) arc(j, rd.adj, rd.w, acc, lanes);
                 arcs += e - b;
+                if (Arc::kMasked) marcs += e - b;
             }
             scratch[(size_t)t * KW + lane] = acc;
             __threadfence();
@@ -154,27 +158,38 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
             ++rows;
             if (__any_sync(kAll, arc.live(acc))) {
                 int j = b;
-                for (; j + 4 <= e; j += 4) arc.quad(j, rd.adj, rd.w, acc);
-                for (; j < e; ++j) arc(j, rd.adj, rd.w, acc);
+                for (; j + 4 <= e; j += 4) arc.quad(j, rd.adj, rd.w, acc, lanes);
+                for (; j < e; ++j) arc(j, rd.adj, rd.w, acc, lanes);
                 arcs += e - b;
+                if (Arc::kMasked) marcs += e - b;
             }
             if (__any_sync(kAll, finish(r, acc))) stamp(r);
         }
     }
     if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
     if (lane == 0 && rows) atomicAdd(&p.visited[1], rows);
+    if (lane == 0 && marcs) atomicAdd(&p.visited[2], marcs);
+    if (lane == 0 && lanes) atomicAdd(&p.visited[3], lanes);
 }
 
 // Arc functors: start(v, init) gives a row's running state, live(state)
 // whether the lane's column needs the row's arcs at all (a warp skips a row
-// no lane needs), operator()(j, adj, w, state) takes arc j of the CSR the pass
-// reads, combine joins the partials of a heavy row in order.
+// no lane needs), operator()(j, adj, w, state, lanes) takes arc j of the CSR
+// the pass reads, combine joins the partials of a heavy row in order.
 struct DeltaAcc {
     double sum;
     long long dv;
 };
 
+// The dependency loop's arcs.  The first pass tests each arc against the
+// distances (v -> x is a DAG arc of column c when d_c(v) + w = d_c(x)) and
+// keeps the warp's 32 answers as the arc's mask; later passes of the batch
+// read the 4-byte mask instead of x's 256-byte distance row, and x's index
+// only when some column has the arc.  The terms and their order are the same
+// either way.  `lanes` counts the (arc, column) pairs the masks select.
+template <bool kFirst>
 struct DeltaArc {
+    static constexpr bool kMasked = !kFirst;
     const WParams* p;
     int lane;
     __device__ DeltaAcc start(int v, DeltaAcc init) const {
@@ -182,28 +197,60 @@ struct DeltaArc {
         return init;
     }
     __device__ bool live(const DeltaAcc& a) const { return a.dv != kInf; }
-    __device__ void operator()(int j, const int* adj, const int* w, DeltaAcc& a) const {
-        if (a.dv == kInf) return;
-        const int x = __ldg(adj + j);
-        const long long dx = p->dist[at(x, lane)];
-        if (dx != kInf && a.dv + __ldg(w + j) == dx) a.sum += p->rho[at(x, lane)];
+    __device__ void operator()(int j, const int* adj, const int* w, DeltaAcc& a, unsigned long long& lanes) const {
+        int x;
+        bool s;
+        if (kFirst) {
+            x = __ldg(adj + j);
+            const long long dx = p->dist[at(x, lane)];
+            s = a.dv != kInf && dx != kInf && a.dv + __ldg(w + j) == dx;
+            const unsigned int m = __ballot_sync(kAll, s);
+            if (lane == 0) p->dag[j] = m;
+        } else {
+            const unsigned int m = p->dag[j];
+            x = m ? __ldg(adj + j) : 0;
+            s = (m >> lane) & 1u;
+            lanes += __popc(m);
+        }
+        if (s) a.sum += p->rho[at(x, lane)];
     }
-    __device__ void quad(int j, const int* adj, const int* w, DeltaAcc& a) const {
-        if (a.dv == kInf) return;
+    // arcs j..j+3, their loads issued together
+    __device__ void quad(int j, const int* adj, const int* w, DeltaAcc& a, unsigned long long& lanes) const {
         int x[4];
-        bool succ[4];
+        bool s[4];
         double r[4];
+        if (kFirst) {
+            long long dx[4];
+            int wq[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            x[q] = __ldg(adj + j + q);
-            const long long dx = p->dist[at(x[q], lane)];
-            succ[q] = dx != kInf && a.dv + __ldg(w + j + q) == dx;
+            for (int q = 0; q < 4; ++q) {
+                x[q] = __ldg(adj + j + q);
+                wq[q] = __ldg(w + j + q);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dx[q] = p->dist[at(x[q], lane)];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                s[q] = a.dv != kInf && dx[q] != kInf && a.dv + wq[q] == dx[q];
+                const unsigned int m = __ballot_sync(kAll, s[q]);
+                if (lane == 0) p->dag[j + q] = m;
+            }
+        } else {
+            unsigned int m[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) m[q] = p->dag[j + q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                x[q] = m[q] ? __ldg(adj + j + q) : 0;
+                s[q] = (m[q] >> lane) & 1u;
+                lanes += __popc(m[q]);
+            }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) r[q] = succ[q] ? p->rho[at(x[q], lane)] : 0.0;
+        for (int q = 0; q < 4; ++q) r[q] = s[q] ? p->rho[at(x[q], lane)] : 0.0;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (succ[q]) a.sum += r[q];  // CSR order
+            if (s[q]) a.sum += r[q];  // CSR order
     }
     __device__ static DeltaAcc combine(DeltaAcc a, DeltaAcc b) { return DeltaAcc{a.sum + b.sum, a.dv}; }
 };
@@ -521,8 +568,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
             return;
         }
         bool ch = false;
-        DeltaArc arc{&p, lane};
-        row_pass<DeltaArc>(p, p.out, p.in, DeltaAcc{0.0, kInf}, arc, [&](int v, DeltaAcc a) {
+        auto finish = [&](int v, DeltaAcc a) {
             const double d = (double)p.sig[at(v, lane)] * a.sum;
             if (__double_as_longlong(d) != __double_as_longlong(p.del[at(v, lane)])) {
                 p.del[at(v, lane)] = d;
@@ -531,7 +577,14 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
                 return true;
             }
             return false;
-        }, pass, np == 1, p.ord, true);
+        };
+        if (np == 1) {
+            DeltaArc<true> arc{&p, lane};
+            row_pass<DeltaArc<true>>(p, p.out, p.in, DeltaAcc{0.0, kInf}, arc, finish, pass, true, p.ord, true);
+        } else {
+            DeltaArc<false> arc{&p, lane};
+            row_pass<DeltaArc<false>>(p, p.out, p.in, DeltaAcc{0.0, kInf}, arc, finish, pass, false, p.ord, true);
+        }
         more = end_pass(ch);
         if (fail) return;
     }
@@ -635,8 +688,8 @@ int wbc_blocks() {
 
 cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* scratch, const int* src,
                        long long* dist, unsigned long long* sig, double* inv, double* del, double* rho, int* mark,
-                       int* ord, unsigned int* hist, double* bc, Ctl* ctl, int* changed, int* passes,
-                       unsigned long long* visited, long long budget, int blocks, cudaStream_t st) {
+                       int* ord, unsigned int* hist, unsigned int* dag, double* bc, Ctl* ctl, int* changed,
+                       int* passes, unsigned long long* visited, long long budget, int blocks, cudaStream_t st) {
     WParams p;
     p.n = n;
     p.out = out;
@@ -651,6 +704,7 @@ cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* s
     p.rho = rho;
     p.mark = mark;
     p.ord = ord;
+    p.dag = dag;
     p.hist = hist;
     p.keymax = reinterpret_cast<unsigned long long*>(hist + kBuckets);
     p.bc = bc;
