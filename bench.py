@@ -561,8 +561,9 @@ def run_weighted(a, bc, torch):
     s = G.stats()
     # bytes the passes must move: an arc read with its neighbour's distances
     # brings its index and weight (8 B) and the neighbour's 32-column row
-    # (256 B); an arc the dependency loop reads through its DAG mask brings its
-    # index and mask (8 B) and one 8-byte rho per column the mask selects;
+    # (256 B); an arc the path-count or dependency loop reads through its DAG
+    # mask brings its index and mask (8 B) and 8 B per column it uses (one
+    # count add or one rho);
     # every row a pass recomputes writes its 32 columns (256 B); summed over
     # the call's passes
     full = s["arcs_visited"] - s["mask_arcs"]
@@ -599,7 +600,7 @@ def run_weighted(a, bc, torch):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "k_wbc", "kernel_ms": kt, "model_bytes": model,
                          "model": "264 B per arc read with its neighbour's distance row, 8 B per arc read through a "
-                                  "DAG mask + 8 B per column it selects, 256 B per row recomputed, over the passes the "
+                                  "DAG mask + 8 B per column it uses, 256 B per row recomputed, over the passes the "
                                   f"call ran ({full:.3e} + {s['mask_arcs']:.3e} arcs, {s['mask_lanes']:.3e} mask "
                                   f"columns, {s['rows_visited']:.3e} rows)",
                          "peak_source": peak_src},

@@ -236,9 +236,11 @@ typedef struct {
                                 part of kernel_ms) */
     int64_t arcs_visited;    /* bc_compute_weighted: arcs read by all passes of all batches (0 otherwise) */
     int64_t rows_visited;    /* bc_compute_weighted: rows recomputed by all passes of all batches */
-    int64_t mask_arcs;       /* bc_compute_weighted: of arcs_visited, the dependency-loop arcs read through their
-                                DAG masks (an index and a mask word, no neighbour distance row) */
-    int64_t mask_lanes;      /* bc_compute_weighted: (arc, column) pairs those masks selected (one rho read each) */
+    int64_t mask_arcs;       /* bc_compute_weighted: of arcs_visited, the arcs the path-count and dependency
+                                loops read through the batch's DAG masks (an index and a mask word, no
+                                neighbour distance row) */
+    int64_t mask_lanes;      /* bc_compute_weighted: (arc, column) pairs those reads used (one count add or one
+                                rho read each) */
 } bc_run_stats;
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 

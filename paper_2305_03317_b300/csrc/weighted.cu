@@ -181,15 +181,11 @@ struct DeltaAcc {
     long long dv;
 };
 
-// The dependency loop's arcs.  The first pass tests each arc against the
-// distances (v -> x is a DAG arc of column c when d_c(v) + w = d_c(x)) and
-// keeps the warp's 32 answers as the arc's mask; later passes of the batch
-// read the 4-byte mask instead of x's 256-byte distance row, and x's index
-// only when some column has the arc.  The terms and their order are the same
-// either way.  `lanes` counts the (arc, column) pairs the masks select.
-template <bool kFirst>
+// The dependency loop's arcs, read through the batch's DAG masks (dag_masks):
+// x's index only when some column has the arc, x's rho in those columns.
+// `lanes` counts the (arc, column) pairs the masks select.
 struct DeltaArc {
-    static constexpr bool kMasked = !kFirst;
+    static constexpr bool kMasked = true;
     const WParams* p;
     int lane;
     __device__ DeltaAcc start(int v, DeltaAcc init) const {
@@ -197,63 +193,89 @@ struct DeltaArc {
         return init;
     }
     __device__ bool live(const DeltaAcc& a) const { return a.dv != kInf; }
-    __device__ void operator()(int j, const int* adj, const int* w, DeltaAcc& a, unsigned long long& lanes) const {
-        int x;
-        bool s;
-        if (kFirst) {
-            x = __ldg(adj + j);
-            const long long dx = p->dist[at(x, lane)];
-            s = a.dv != kInf && dx != kInf && a.dv + __ldg(w + j) == dx;
-            const unsigned int m = __ballot_sync(kAll, s);
-            if (lane == 0) p->dag[j] = m;
-        } else {
-            const unsigned int m = p->dag[j];
-            x = m ? __ldg(adj + j) : 0;
-            s = (m >> lane) & 1u;
-            lanes += __popc(m);
-        }
-        if (s) a.sum += p->rho[at(x, lane)];
+    __device__ void operator()(int j, const int* adj, const int*, DeltaAcc& a, unsigned long long& lanes) const {
+        const unsigned int m = p->dag[j];
+        lanes += __popc(m);
+        if ((m >> lane) & 1u) a.sum += p->rho[at(__ldg(adj + j), lane)];
     }
     // arcs j..j+3, their loads issued together
-    __device__ void quad(int j, const int* adj, const int* w, DeltaAcc& a, unsigned long long& lanes) const {
-        int x[4];
-        bool s[4];
+    __device__ void quad(int j, const int* adj, const int*, DeltaAcc& a, unsigned long long& lanes) const {
+        unsigned int m[4];
         double r[4];
-        if (kFirst) {
-            long long dx[4];
-            int wq[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                x[q] = __ldg(adj + j + q);
-                wq[q] = __ldg(w + j + q);
-            }
+        for (int q = 0; q < 4; ++q) m[q] = p->dag[j + q];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dx[q] = p->dist[at(x[q], lane)];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                s[q] = a.dv != kInf && dx[q] != kInf && a.dv + wq[q] == dx[q];
-                const unsigned int m = __ballot_sync(kAll, s[q]);
-                if (lane == 0) p->dag[j + q] = m;
-            }
-        } else {
-            unsigned int m[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) m[q] = p->dag[j + q];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                x[q] = m[q] ? __ldg(adj + j + q) : 0;
-                s[q] = (m[q] >> lane) & 1u;
-                lanes += __popc(m[q]);
-            }
+        for (int q = 0; q < 4; ++q) {
+            const bool s = (m[q] >> lane) & 1u;
+            lanes += __popc(m[q]);
+            r[q] = s ? p->rho[at(__ldg(adj + j + q), lane)] : 0.0;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) r[q] = s[q] ? p->rho[at(x[q], lane)] : 0.0;
-#pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (s[q]) a.sum += r[q];  // CSR order
+            if ((m[q] >> lane) & 1u) a.sum += r[q];  // CSR order
     }
     __device__ static DeltaAcc combine(DeltaAcc a, DeltaAcc b) { return DeltaAcc{a.sum + b.sum, a.dv}; }
 };
+
+// The batch's DAG masks, once the distances are final: for every out-arc
+// v -> x, bit c set when d_c(v) + w = d_c(x) (a shortest-path DAG arc of
+// column c).  One warp per task as in the passes (lane = column, a ballot per
+// arc); rows no column reaches keep stale words, which nothing reads (their
+// counts never grow and the dependency loop skips them).
+__device__ __forceinline__ void dag_masks(const WParams& p) {
+    const WCsr& g = p.out;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long tasks = g.hchunks + (p.n - g.n_heavy);
+    unsigned long long arcs = 0;
+    for (long long t = wid; t < tasks; t += nw) {
+        int r, b, e;
+        if (t < g.hchunks) {
+            int lo = 0, hi = g.n_heavy;  // hcum[lo] <= t < hcum[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (g.hcum[mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            r = g.hrow ? __ldg(g.hrow + lo) : lo;
+            b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
+            e = min(g.off[r + 1], b + kChunk);
+        } else {
+            const int i = (int)(t - g.hchunks);
+            r = g.lrow ? __ldg(g.lrow + i) : g.n_heavy + i;
+            b = g.off[r];
+            e = g.off[r + 1];
+        }
+        const long long dv = p.dist[at(r, lane)];
+        if (!__any_sync(kAll, dv != kInf)) continue;
+        arcs += e - b;
+        int j = b;
+        for (; j + 4 <= e; j += 4) {
+            int x[4], wq[4];
+            long long dx[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                x[q] = __ldg(g.adj + j + q);
+                wq[q] = __ldg(g.w + j + q);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dx[q] = p.dist[at(x[q], lane)];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned int m = __ballot_sync(kAll, dv != kInf && dx[q] != kInf && dv + wq[q] == dx[q]);
+                if (lane == 0) p.dag[j + q] = m;
+            }
+        }
+        for (; j < e; ++j) {
+            const int x = __ldg(g.adj + j);
+            const long long dx = p.dist[at(x, lane)];
+            const unsigned int m = __ballot_sync(kAll, dv != kInf && dx != kInf && dv + __ldg(g.w + j) == dx);
+            if (lane == 0) p.dag[j] = m;
+        }
+    }
+    if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
+}
 
 // One pass of the distance loop in push form: every row whose distance changed
 // in the previous pass (every reached row on the first pass) relaxes its
@@ -355,6 +377,7 @@ __device__ __forceinline__ void heavy_increments(const WParams& p, int pass, boo
 
 __device__ __forceinline__ bool push_sigma_pass(const WParams& p, int pass, bool all, unsigned long long* pushed,
                                                 const unsigned long long* hinc, bool& ovf) {
+    unsigned long long adds = 0;  // this lane's (arc, column) adds
     const WCsr& g = p.out;
     const int* mprev = p.mark + (size_t)(pass & 1) * p.n;
     int* mnext = p.mark + (size_t)((pass + 1) & 1) * p.n;
@@ -393,36 +416,37 @@ __device__ __forceinline__ bool push_sigma_pass(const WParams& p, int pass, bool
         ++rows;
         arcs += e - b;
         if (inc == 0ull) continue;  // this column has nothing to push
-        const long long du = p.dist[at(r, lane)];
-        auto add = [&](int v, long long c, long long dv) {
-            if (c == dv) {
+        auto add = [&](int v, unsigned int m) {
+            if ((m >> lane) & 1u) {
                 const unsigned long long old = atomicAdd(&p.sig[at(v, lane)], inc);
                 ovf |= old + inc < old;
                 mnext[v] = pass + 1;
                 ch = true;
+                ++adds;
             }
         };
         int j = b;
         for (; j + 4 <= e; j += 4) {
+            unsigned int m[4];
             int v[4];
-            long long c[4], dv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                v[q] = __ldg(g.adj + j + q);
-                c[q] = du + __ldg(g.w + j + q);
-            }
+            for (int q = 0; q < 4; ++q) m[q] = p.dag[j + q];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dv[q] = p.dist[at(v[q], lane)];
+            for (int q = 0; q < 4; ++q) v[q] = m[q] ? __ldg(g.adj + j + q) : 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) add(v[q], c[q], dv[q]);
+            for (int q = 0; q < 4; ++q) add(v[q], m[q]);
         }
         for (; j < e; ++j) {
-            const int v = __ldg(g.adj + j);
-            add(v, du + __ldg(g.w + j), p.dist[at(v, lane)]);
+            const unsigned int m = p.dag[j];
+            add(m ? __ldg(g.adj + j) : 0, m);
         }
     }
     if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
     if (lane == 0 && rows) atomicAdd(&p.visited[1], rows);
+    if (lane == 0 && arcs) atomicAdd(&p.visited[2], arcs);  // every arc here is read through its mask
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) adds += __shfl_xor_sync(kAll, adds, o);
+    if (lane == 0 && adds) atomicAdd(&p.visited[3], adds);
     return ch;
 }
 
@@ -475,6 +499,7 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
         if (fail) return;
     }
     const int pass_dist = np;
+    dag_masks(p);  // read after the row-order barriers below
 
     // Row order for the next two loops: rows by the mean of their finite
     // distances over the batch's columns, in kBuckets buckets.  A DAG
@@ -578,13 +603,8 @@ __global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
             }
             return false;
         };
-        if (np == 1) {
-            DeltaArc<true> arc{&p, lane};
-            row_pass<DeltaArc<true>>(p, p.out, p.in, DeltaAcc{0.0, kInf}, arc, finish, pass, true, p.ord, true);
-        } else {
-            DeltaArc<false> arc{&p, lane};
-            row_pass<DeltaArc<false>>(p, p.out, p.in, DeltaAcc{0.0, kInf}, arc, finish, pass, false, p.ord, true);
-        }
+        DeltaArc arc{&p, lane};
+        row_pass<DeltaArc>(p, p.out, p.in, DeltaAcc{0.0, kInf}, arc, finish, pass, np == 1, p.ord, true);
         more = end_pass(ch);
         if (fail) return;
     }
