@@ -50,14 +50,16 @@ struct WParams {
     int n;
     WCsr out, in;              // out-arcs and in-arcs (the same CSR when undirected)
     int* arr;                  // [heavy rows] chunk arrival counters, by heavy index
-    void* scratch;             // [chunk tasks][32] partials (24 bytes each at most)
+    void* scratch;             // [chunk tasks][32] partials (24 bytes each at most); in the
+                               // path-count loop, the heavy rows' increments [heavy rows][32]
     const int* src;            // [32] relabelled sources, -1 = unused column
     long long* dist;           // [n][32]
     unsigned long long* sig;   // [n][32] path counts
     double* inv;               // [n][32] 1 / sigma
     double* del;               // [n][32] dependencies
     double* rho;               // [n][32] (1 + delta) / sigma, kept with delta
-    int* mark;                 // [2][n] pass stamps: rows next to a row that changed
+    int* mark;                 // [2][n] pass stamps: the rows the next pass visits (rows that
+                               // changed, in push form; rows that read one, in pull form)
     int* ord;                  // [n] rows by mean distance (dependency passes)
     unsigned int* dag;         // [m] out-arc DAG masks of the batch (bit c: a DAG arc of column c)
     unsigned int* hist;        // [kBuckets] bucket counts, then cursors
@@ -93,7 +95,7 @@ __device__ __forceinline__ T load_cg(const T* q) {
 // and finishes the row.
 //
 // Active rows: a pass recomputes only the rows stamped by the previous pass
-// (every pass when `all`): a row whose value changed stamps the rows that read
+// (every row when `all`): a row whose value changed stamps the rows that read
 // it (its row in `sc`, the transpose of `rd`) for the next pass, in the other
 // of two stamp arrays, so no stamp a pass reads changes during it.
 //
