@@ -287,3 +287,35 @@ def test_directed_equal_weights_match_unweighted_bc(bc):
     W = bc.Graph(g.off, g.adj, weights=bcgen.edge_weights(g, 1, 9, 1, per_arc=True), directed=True)
     a, _ = W.compute(src)
     assert np.array_equal(a.cpu().numpy(), unw.cpu().numpy())
+
+
+def test_directed_device_inputs_and_skip_validation(bc):
+    import torch
+    g = bcgen.orient(bcgen.rmat(10, 8, 8), seed=9)
+    wt = bcgen.edge_weights(g, 1, 30, 8, per_arc=True)
+    src = bcgen.sample_sources(g, 40, 8)
+    host, _, _ = wgpu_dir(bc, g, wt, src)
+    D = bc.Graph(torch.from_numpy(g.off).cuda(), torch.from_numpy(g.adj).cuda(),
+                 weights=torch.from_numpy(wt).cuda(), directed=True)
+    dev, _ = D.compute_weighted(torch.from_numpy(src).cuda())
+    assert np.array_equal(dev.cpu().numpy().view(np.uint64), host.view(np.uint64))
+    S = bc.Graph(g.off, g.adj, weights=wt, validate=False, directed=True)
+    skip, _ = S.compute_weighted(src)
+    assert np.array_equal(skip.cpu().numpy().view(np.uint64), host.view(np.uint64))
+    assert_bc_close(host, oracle.wbc(g.off, g.adj, wt, src))
+
+
+def test_directed_sinks_isolated_and_edgeless(bc):
+    # sources that are sinks (no out-arcs) or isolated give zero terms; a
+    # graph with no arcs gives zeros
+    g = bcgen.disjoint_union(bcgen.orient(bcgen.gnp(60, 0.08, 3), seed=2, p_both=0.1), bcgen.empty_graph(4))
+    wt = bcgen.edge_weights(g, 1, 5, 4, per_arc=True)
+    sinks = np.flatnonzero(np.diff(g.off) == 0)
+    assert len(sinks) > 4
+    src = np.concatenate([sinks[:6], np.arange(0, g.n, 5)]).astype(np.int32)
+    got, st, _ = wgpu_dir(bc, g, wt, src)
+    assert st == bc.BC_OK
+    assert_bc_close(got, oracle.wbc(g.off, g.adj, wt, src))
+    e = bcgen.empty_graph(7)
+    zero, st, _ = wgpu_dir(bc, e, np.zeros(0, np.int32), np.arange(7))
+    assert st == bc.BC_OK and not zero.any()
