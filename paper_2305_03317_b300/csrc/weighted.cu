@@ -88,6 +88,33 @@ __device__ __forceinline__ T load_cg(const T* q) {
     return x;
 }
 
+// The light rows a pass visits, in the same warp-interleaved order as one row
+// per warp step (slot i goes to warp i mod nw): each lane of a warp reads the
+// row and stamp of one of the warp's next 32 slots, so 32 stamp reads are in
+// flight together, and the warp runs `body` on the stamped rows in slot order.
+// Light slots are the rows of `g` in id order (or its light-row list), or the
+// `ord` list (reversed when `rev`).
+template <class Body>
+__device__ __forceinline__ void stamped_light_rows(const WParams& p, const WCsr& g, const int* ord, bool rev,
+                                                   int pass, bool all, Body body) {
+    const int* mprev = p.mark + (size_t)(pass & 1) * p.n;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long nl = ord ? p.n : p.n - g.n_heavy;
+    for (long long s0 = 0; wid + s0 * nw < nl; s0 += 32) {
+        const long long i = wid + (s0 + lane) * nw;
+        int r = -1;
+        if (i < nl) r = ord ? ord[rev ? p.n - 1 - i : i] : g.lrow ? __ldg(g.lrow + i) : g.n_heavy + (int)i;
+        unsigned int bits = __ballot_sync(kAll, r >= 0 && (all || mprev[r] == pass));
+        while (bits) {
+            const int j = __ffs(bits) - 1;
+            bits &= bits - 1;
+            body(__shfl_sync(kAll, r, j));
+        }
+    }
+}
+
 // One pass over every row of `rd`, one warp per task: a light row, or a
 // 1024-arc chunk of a heavy row (chunk slots hcum[k] .. hcum[k+1] of heavy
 // row k).  A chunk's partial goes to its scratch slot; the warp that finishes
@@ -113,12 +140,11 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long tasks = rd.hchunks + (ord ? p.n : p.n - rd.n_heavy);
     T* scratch = reinterpret_cast<T*>(p.scratch);
     unsigned long long arcs = 0, rows = 0;  // read by this warp (lane 0 reports)
     unsigned long long marcs = 0, lanes = 0;  // of those, arcs read through masks; the columns they select
-    for (long long t = wid; t < tasks; t += nw) {
-        if (t < rd.hchunks) {
+    for (long long t = wid; t < rd.hchunks; t += nw) {
+        {
             int lo = 0, hi = rd.n_heavy;  // hcum[lo] <= t < hcum[hi]
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
@@ -150,24 +176,22 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
                 if (__any_sync(kAll, finish(r, tot))) stamp(r);
                 if (lane == 0) p.arr[k] = 0;  // ready for the next pass (after its barrier)
             }
-        } else {
-            const int i = (int)(t - rd.hchunks);
-            const int r = ord ? ord[rev ? p.n - 1 - i : i] : rd.lrow ? __ldg(rd.lrow + i) : rd.n_heavy + i;
-            if (!all && mprev[r] != pass) continue;
-            const int b = rd.off[r], e = rd.off[r + 1];
-            if (ord && e - b > kChunk) continue;  // a heavy row: its chunk tasks ran it
-            T acc = arc.start(r, init);
-            ++rows;
-            if (__any_sync(kAll, arc.live(acc))) {
-                int j = b;
-                for (; j + 4 <= e; j += 4) arc.quad(j, rd.adj, rd.w, acc, lanes);
-                for (; j < e; ++j) arc(j, rd.adj, rd.w, acc, lanes);
-                arcs += e - b;
-                if (Arc::kMasked) marcs += e - b;
-            }
-            if (__any_sync(kAll, finish(r, acc))) stamp(r);
         }
     }
+    stamped_light_rows(p, rd, ord, rev, pass, all, [&](int r) {
+        const int b = rd.off[r], e = rd.off[r + 1];
+        if (ord && e - b > kChunk) return;  // a heavy row: its chunk tasks ran it
+        T acc = arc.start(r, init);
+        ++rows;
+        if (__any_sync(kAll, arc.live(acc))) {
+            int j = b;
+            for (; j + 4 <= e; j += 4) arc.quad(j, rd.adj, rd.w, acc, lanes);
+            for (; j < e; ++j) arc(j, rd.adj, rd.w, acc, lanes);
+            arcs += e - b;
+            if (Arc::kMasked) marcs += e - b;
+        }
+        if (__any_sync(kAll, finish(r, acc))) stamp(r);
+    });
     if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
     if (lane == 0 && rows) atomicAdd(&p.visited[1], rows);
     if (lane == 0 && marcs) atomicAdd(&p.visited[2], marcs);
@@ -294,33 +318,14 @@ __device__ __forceinline__ bool push_min_pass(const WParams& p, int pass, bool a
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long tasks = g.hchunks + (p.n - g.n_heavy);
     unsigned long long arcs = 0, rows = 0;
     bool ch = false;
-    for (long long t = wid; t < tasks; t += nw) {
-        int r, b, e;
-        if (t < g.hchunks) {
-            int lo = 0, hi = g.n_heavy;  // hcum[lo] <= t < hcum[hi]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (g.hcum[mid] <= t) lo = mid;
-                else hi = mid;
-            }
-            r = g.hrow ? __ldg(g.hrow + lo) : lo;
-            b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
-            e = min(g.off[r + 1], b + kChunk);
-        } else {
-            const int i = (int)(t - g.hchunks);
-            r = g.lrow ? __ldg(g.lrow + i) : g.n_heavy + i;
-            b = g.off[r];
-            e = g.off[r + 1];
-        }
-        if (!all && mprev[r] != pass) continue;
+    auto work = [&](int r, int b, int e) {
         const long long du = p.dist[at(r, lane)];
-        if (!__any_sync(kAll, du != kInf)) continue;
+        if (!__any_sync(kAll, du != kInf)) return;
         ++rows;
         arcs += e - b;
-        if (du == kInf) continue;  // this column has nothing to push
+        if (du == kInf) return;  // this column has nothing to push
         auto relax = [&](int v, long long c, long long dv) {
             if (c < dv && atomicMin(&p.dist[at(v, lane)], c) > c) {
                 mnext[v] = pass + 1;
@@ -345,7 +350,20 @@ __device__ __forceinline__ bool push_min_pass(const WParams& p, int pass, bool a
             const int v = __ldg(g.adj + j);
             relax(v, du + __ldg(g.w + j), p.dist[at(v, lane)]);
         }
+    };
+    for (long long t = wid; t < g.hchunks; t += nw) {
+        int lo = 0, hi = g.n_heavy;  // hcum[lo] <= t < hcum[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (g.hcum[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int r = g.hrow ? __ldg(g.hrow + lo) : lo;
+        if (!all && mprev[r] != pass) continue;
+        const int b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
+        work(r, b, min(g.off[r + 1], b + kChunk));
     }
+    stamped_light_rows(p, g, nullptr, false, pass, all, [&](int r) { work(r, g.off[r], g.off[r + 1]); });
     if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
     if (lane == 0 && rows) atomicAdd(&p.visited[1], rows);
     return ch;
@@ -386,38 +404,13 @@ __device__ __forceinline__ bool push_sigma_pass(const WParams& p, int pass, bool
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long tasks = g.hchunks + (p.n - g.n_heavy);
     unsigned long long arcs = 0, rows = 0;
     bool ch = false;
-    for (long long t = wid; t < tasks; t += nw) {
-        int r, b, e;
-        unsigned long long inc;
-        if (t < g.hchunks) {
-            int lo = 0, hi = g.n_heavy;  // hcum[lo] <= t < hcum[hi]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (g.hcum[mid] <= t) lo = mid;
-                else hi = mid;
-            }
-            r = g.hrow ? __ldg(g.hrow + lo) : lo;
-            if (!all && mprev[r] != pass) continue;
-            b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
-            e = min(g.off[r + 1], b + kChunk);
-            inc = hinc[(size_t)lo * KW + lane];
-        } else {
-            const int i = (int)(t - g.hchunks);
-            r = g.lrow ? __ldg(g.lrow + i) : g.n_heavy + i;
-            if (!all && mprev[r] != pass) continue;
-            b = g.off[r];
-            e = g.off[r + 1];
-            const unsigned long long s = p.sig[at(r, lane)];
-            inc = s - pushed[at(r, lane)];
-            pushed[at(r, lane)] = s;
-        }
-        if (!__any_sync(kAll, inc != 0ull)) continue;
+    auto work = [&](int b, int e, unsigned long long inc) {
+        if (!__any_sync(kAll, inc != 0ull)) return;
         ++rows;
         arcs += e - b;
-        if (inc == 0ull) continue;  // this column has nothing to push
+        if (inc == 0ull) return;  // this column has nothing to push
         auto add = [&](int v, unsigned int m) {
             if ((m >> lane) & 1u) {
                 const unsigned long long old = atomicAdd(&p.sig[at(v, lane)], inc);
@@ -442,7 +435,25 @@ __device__ __forceinline__ bool push_sigma_pass(const WParams& p, int pass, bool
             const unsigned int m = p.dag[j];
             add(m ? __ldg(g.adj + j) : 0, m);
         }
+    };
+    for (long long t = wid; t < g.hchunks; t += nw) {
+        int lo = 0, hi = g.n_heavy;  // hcum[lo] <= t < hcum[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (g.hcum[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int r = g.hrow ? __ldg(g.hrow + lo) : lo;
+        if (!all && mprev[r] != pass) continue;
+        const int b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
+        work(b, min(g.off[r + 1], b + kChunk), hinc[(size_t)lo * KW + lane]);
     }
+    stamped_light_rows(p, g, nullptr, false, pass, all, [&](int r) {
+        const unsigned long long s = p.sig[at(r, lane)];
+        const unsigned long long inc = s - pushed[at(r, lane)];
+        pushed[at(r, lane)] = s;
+        work(g.off[r], g.off[r + 1], inc);
+    });
     if (lane == 0 && arcs) atomicAdd(&p.visited[0], arcs);
     if (lane == 0 && rows) atomicAdd(&p.visited[1], rows);
     if (lane == 0 && arcs) atomicAdd(&p.visited[2], arcs);  // every arc here is read through its mask
