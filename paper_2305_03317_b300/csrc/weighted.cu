@@ -463,7 +463,7 @@ __device__ __forceinline__ bool push_sigma_pass(const WParams& p, int pass, bool
     return ch;
 }
 
-__global__ void __launch_bounds__(kWThreads) k_wbc(WParams p) {
+__global__ void __launch_bounds__(kWThreads, 5) k_wbc(WParams p) {
     GridTeam team{p.ctl, p.ctl, (int)gridDim.x, p.budget};
     const int lane = threadIdx.x & 31;
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -715,7 +715,7 @@ int wbc_blocks() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wbc, kWThreads, 0);
-    if (per > 4) per = 4;
+    if (per > 5) per = 5;
     return sms * per;
 }
 
