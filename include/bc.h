@@ -191,8 +191,7 @@ bc_status bc_pagerank(bc_graph* g, double delta, double beta, int32_t max_iter, 
  * directed.  weights[m] is parallel to indices[m] of the input CSR (host or
  * device, as the flags say), whose rows must be sorted ascending.  Undirected:
  * both arcs of an edge carry the same weight.  Directed: each arc has its own
- * weight, and the library keeps a second copy, in the order of the in-CSR it
- * builds for the directed pulls (4 m bytes more).  Checks (unless
+ * weight.  Checks (unless
  * BC_SKIP_VALIDATION): the CSR rules of bc_graph_create, sorted rows,
  * weights > 0, symmetric weights when undirected, else BC_E_INVALID_GRAPH.
  * The result is a regular graph (every unweighted call works on it, ignoring
@@ -208,8 +207,8 @@ bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indice
  * of the paper's SSSP program (Section 2.3).  Path counts are exact below
  * 2^64 (BC_W_SIGMA_INEXACT once one reaches 2^53, BC_E_SIGMA_RANGE at
  * 2^64); BC is the raw sum over the listed sources, as for bc_compute.
- * On a directed graph paths follow the arcs: distances and path counts pull
- * over in-arcs, dependencies over out-arcs.  Sources are batched in the
+ * On a directed graph paths follow the arcs: distances and path counts are
+ * pushed along out-arcs, dependencies pulled over them.  Sources are batched in the
  * grouped order of bc_compute's automatic rule (undirected skewed graphs,
  * 256 sources or more); the order changes rounding only.
  * Batches of 32 sources, one launch each; results repeat bit for bit.

@@ -235,11 +235,6 @@ struct bc_graph {
     DevBuf off, adj, perm, inv, hcum;
     DevBuf ioff, iadj;  // directed: in-CSR for the pull steps
     DevBuf w;           // weighted graphs: arc weights in relabelled arc order (empty otherwise)
-    DevBuf wi;          // directed weighted graphs: weights of the in-CSR's arcs
-    DevBuf wihcum, wihrow, wilrow;  // and the in-CSR's heavy rows: chunk prefix, ids, light row ids
-    int wi_heavy = 0;               // heavy in-rows (more than kChunk arcs)
-    long long wi_hchunks = 0;       // their chunk tasks
-    bool wi_prefix = true;          // heavy in-rows are the ids [0, wi_heavy) (no id lists)
     DevBuf wdist, wsig, winv, wdel, wrho, wmark, wbc, wctl, wsrc, wscr, warr;  // weighted BC state, kept between calls
     DevBuf word, whist;  // weighted BC: row order by mean distance, its bucket counts
     DevBuf wdag;         // weighted BC: per out-arc DAG masks of the current batch
@@ -1111,7 +1106,7 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->landmark, st);
     for (DevBuf* b : {&g->pr_ccum, &g->pr_rank, &g->pr_scratch, &g->pr_cpart, &g->pr_carr, &g->pr_ctl, &g->pr_small})
         buf_release(*b, st);
-    for (DevBuf* b : {&g->w, &g->wi, &g->wihcum, &g->wihrow, &g->wilrow, &g->wdist, &g->wsig, &g->winv, &g->wdel,
+    for (DevBuf* b : {&g->w, &g->wdist, &g->wsig, &g->winv, &g->wdel,
                       &g->wrho, &g->wmark, &g->wbc, &g->wctl, &g->wsrc, &g->wscr, &g->warr, &g->word, &g->whist, &g->wdag})
         buf_release(*b, st);
     buf_release(g->inv, st);
@@ -1139,8 +1134,7 @@ bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indice
         if (rr != BC_OK) bc_graph_destroy(g);
         return rr;
     };
-    if (!buf_ensure(g->w, sizeof(int) * (size_t)(m > 0 ? m : 1), st) || !buf_ensure(derr, sizeof(int), st) ||
-        (g->directed && !buf_ensure(g->wi, sizeof(int) * (size_t)(m > 0 ? m : 1), st)))
+    if (!buf_ensure(g->w, sizeof(int) * (size_t)(m > 0 ? m : 1), st) || !buf_ensure(derr, sizeof(int), st))
         return bail(fail(BC_E_NOMEM, "weight buffers"));
     const int *ooff = offsets, *oadj = indices, *ow = weights;
     cudaError_t e = cudaMemsetAsync(derr.p, 0, sizeof(int), st);
@@ -1157,49 +1151,14 @@ bc_status bc_graph_create_weighted(const int32_t* offsets, const int32_t* indice
     }
     if (e == cudaSuccess)
         e = launch_weight_ingest(ooff, oadj, ow, (const int*)g->perm.p, (const int*)g->off.p, (const int*)g->adj.p, n,
-                                 (int*)g->w.p, (int*)derr.p, !g->directed && !(flags & BC_SKIP_VALIDATION),
-                                 g->directed ? (const int*)g->ioff.p : nullptr,
-                                 g->directed ? (const int*)g->iadj.p : nullptr, (int*)g->wi.p, st);
+                                 (int*)g->w.p, (int*)derr.p, !g->directed && !(flags & BC_SKIP_VALIDATION), st);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(e, "weight ingest"));
-    if (herr & 8) return bail(fail(BC_E_CUDA, "in-arc weights: the in-CSR is not the transpose"));
     if (!(flags & BC_SKIP_VALIDATION) && herr)
         return bail(fail(BC_E_INVALID_GRAPH, "weights: %s%s%s", (herr & 1) ? "rows not sorted ascending; " : "",
                          (herr & 2) ? "a weight <= 0; " : "", (herr & 4) ? "the two arcs of an edge differ" : ""));
-    if (g->directed && n > 0) {
-        // heavy in-rows: in-degrees do not follow the (out-degree) relabelling,
-        // so they are listed unless they happen to be a prefix of the ids
-        std::vector<int> io((size_t)n + 1);
-        e = cudaMemcpyAsync(io.data(), g->ioff.p, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "in-row offsets"));
-        std::vector<int> hrow, lrow, cum(1, 0);
-        for (int v = 0; v < n; ++v) {
-            const int len = io[(size_t)v + 1] - io[v];
-            if (len > kChunk) {
-                hrow.push_back(v);
-                cum.push_back(cum.back() + (len + kChunk - 1) / kChunk);
-            } else {
-                lrow.push_back(v);
-            }
-        }
-        g->wi_heavy = (int)hrow.size();
-        g->wi_hchunks = cum.back();
-        g->wi_prefix = hrow.empty() || hrow.back() == (int)hrow.size() - 1;
-        auto up = [&](DevBuf& b, const std::vector<int>& v) {
-            if (!buf_ensure(b, sizeof(int) * (v.empty() ? 1 : v.size()), st)) return cudaErrorMemoryAllocation;
-            if (v.empty()) return cudaSuccess;
-            cudaError_t r2 = cudaMemcpyAsync(b.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, st);
-            return r2 == cudaSuccess ? cudaStreamSynchronize(st) : r2;
-        };
-        e = up(g->wihcum, cum);
-        if (e == cudaSuccess && !g->wi_prefix) e = up(g->wihrow, hrow);
-        if (e == cudaSuccess && !g->wi_prefix) e = up(g->wilrow, lrow);
-        if (e == cudaErrorMemoryAllocation) return bail(fail(BC_E_NOMEM, "in-row tables"));
-        if (e != cudaSuccess) return bail(cuda_fail(e, "in-row tables"));
-    }
     *out = g;
     return bail(BC_OK);
 }
@@ -1255,19 +1214,18 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
         !buf_ensure(g->wdel, 8 * cells, st) || !buf_ensure(g->wrho, 8 * cells, st) || !buf_ensure(g->wmark, 8 * n, st) ||
         !buf_ensure(g->wbc, 8 * n, st) || !buf_ensure(g->wctl, sizeof(Ctl) + 8 * sizeof(int) + 32, st) ||
         !buf_ensure(g->wsrc, sizeof(int) * (size_t)(nbatch > 0 ? nbatch : 1) * KW + sizeof(int), st) ||
-        !buf_ensure(g->wscr, 24 * KW * (size_t)std::max(1ll, std::max(g->hchunk_total, g->wi_hchunks)), st) ||
-        !buf_ensure(g->warr, sizeof(int) * (size_t)std::max(1, std::max(g->n_heavy, g->wi_heavy)), st) ||
+        !buf_ensure(g->wscr, 24 * KW * (size_t)std::max(1ll, g->hchunk_total), st) ||
+        !buf_ensure(g->warr, sizeof(int) * (size_t)std::max(1, g->n_heavy), st) ||
         !buf_ensure(g->word, sizeof(int) * n, st) || !buf_ensure(g->whist, sizeof(unsigned int) * kWbcHistWords, st) ||
         !buf_ensure(g->wdag, sizeof(unsigned int) * (size_t)(g->m > 0 ? g->m : 1), st))
         return done(fail(BC_E_NOMEM, "weighted BC buffers"));
     const WCsr wout{(const int*)g->off.p, (const int*)g->adj.p, (const int*)g->w.p, g->n_heavy, g->hchunk_total,
                     (const int*)g->hcum.p, nullptr, nullptr};
+    // in-arcs serve only the dependency loop's stamps (rows and indices)
     const WCsr win = !g->directed ? wout
-                                  : WCsr{(const int*)g->ioff.p, (const int*)g->iadj.p, (const int*)g->wi.p,
-                                         g->wi_heavy, g->wi_hchunks, (const int*)g->wihcum.p,
-                                         g->wi_prefix ? nullptr : (const int*)g->wihrow.p,
-                                         g->wi_prefix ? nullptr : (const int*)g->wilrow.p};
-    const size_t narr = (size_t)std::max(1, std::max(g->n_heavy, g->wi_heavy));
+                                  : WCsr{(const int*)g->ioff.p, (const int*)g->iadj.p, nullptr, 0, 0, nullptr,
+                                         nullptr, nullptr};
+    const size_t narr = (size_t)std::max(1, g->n_heavy);
     Ctl* ctl = (Ctl*)g->wctl.p;
     int* changed = (int*)((char*)g->wctl.p + sizeof(Ctl));
     int* passes = changed + 4;

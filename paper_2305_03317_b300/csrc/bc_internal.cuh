@@ -184,12 +184,10 @@ cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* s
                        long long* dist, unsigned long long* sig, double* inv, double* del, double* rho, int* mark,
                        int* ord, unsigned int* hist, unsigned int* dag, double* bc, Ctl* ctl, int* changed,
                        int* passes, unsigned long long* visited, long long budget, int blocks, cudaStream_t st);
-// Weights of the relabelled arcs (and, when ioff is set, of the in-CSR's
-// arcs); err bits: 1 rows not sorted, 2 a weight <= 0, 4 asymmetric weights,
-// 8 the in-CSR is not the transpose.
+// Weights of the relabelled arcs; err bits: 1 rows not sorted, 2 a weight
+// <= 0, 4 asymmetric weights.
 cudaError_t launch_weight_ingest(const int* ooff, const int* oadj, const int* ow, const int* perm, const int* noff,
-                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, const int* ioff,
-                                 const int* iadj, int* iw, cudaStream_t st);
+                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, cudaStream_t st);
 // Level table [n][K] (0xFFFF = unreached) of a forward-only batch; and the
 // levels of columns [0, L) of such a table at each of nsrc sources (original
 // ids): keys[nsrc][L].

@@ -13,8 +13,9 @@
 //   delta: t(v) = s(v) * sum over arcs v -> x with d(v) + w = d(x) of rho(x),
 //          rho(x) = (1 + t(x)) / s(x), rewritten with each new t(x), pulled
 //          over out-arcs.
-// On a directed graph the in-arcs are the in-CSR (the transpose, with its own
-// copy of the weights); on an undirected graph both are the one CSR.  Each
+// Pushes run along out-arcs, so only the dependency loop's stamps (a changed
+// row stamps its in-neighbours) read in-arcs: on a directed graph the rows and
+// indices of the in-CSR built at ingest, on an undirected one the CSR.  Each
 // loop runs until a pass changes nothing; then BC(v) += t(v) for every
 // non-source column, columns in order.  Distances only fall and counts and dependencies
 // only grow towards the DAG values, so a read of a neighbour another warp is
@@ -26,8 +27,8 @@
 // CSR order (long rows: per chunk, chunks combined in order), so results
 // repeat bit for bit.  Every task is one warp: a row of at most 1024 arcs, or
 // a 1024-arc chunk of a longer row (heavy rows: the relabelled prefix
-// [0, n_heavy) of the out-CSR, a listed set of the in-CSR), whose partials
-// the row's last chunk combines.  Grid barriers are bounded by
+// [0, n_heavy)), whose partials (dependency loop) the row's last chunk
+// combines.  Grid barriers are bounded by
 // a cycle budget like the traversal kernel's.
 #include <climits>
 #include <cstdint>
@@ -48,7 +49,9 @@ static_assert(kBuckets % kWThreads == 0, "the prefix gives each thread whole buc
 
 struct WParams {
     int n;
-    WCsr out, in;              // out-arcs and in-arcs (the same CSR when undirected)
+    WCsr out;                  // out-arcs with their weights
+    WCsr in;                   // in-arcs (the same CSR when undirected): rows and indices only,
+                               // for the dependency loop's stamps
     int* arr;                  // [heavy rows] chunk arrival counters, by heavy index
     void* scratch;             // [chunk tasks][32] partials (24 bytes each at most); in the
                                // path-count loop, the heavy rows' increments [heavy rows][32]
@@ -683,31 +686,6 @@ __global__ void k_weight_symmetry(const int* __restrict__ noff, const int* __res
     }
 }
 
-// Weights of the in-arcs of a directed graph: in-arc u -> v of row v carries
-// the weight of out-arc u -> v (out rows sorted ascending).
-__global__ void k_weight_transpose(const int* __restrict__ noff, const int* __restrict__ nadj,
-                                   const int* __restrict__ nw, const int* __restrict__ ioff,
-                                   const int* __restrict__ iadj, int n, int* iw, int* err) {
-    const long long nthr = (long long)gridDim.x * blockDim.x;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += nthr) {
-        for (int j = ioff[v]; j < ioff[v + 1]; ++j) {
-            const int u = iadj[j];
-            int lo = noff[u], hi = noff[u + 1];
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (nadj[mid] < (int)v) lo = mid + 1;
-                else hi = mid;
-            }
-            if (lo < noff[u + 1] && nadj[lo] == (int)v) {
-                iw[j] = nw[lo];
-            } else {
-                iw[j] = 1;
-                atomicOr(err, 8);  // the in-CSR is not the transpose
-            }
-        }
-    }
-}
-
 }  // namespace
 
 int wbc_blocks() {
@@ -761,13 +739,11 @@ cudaError_t launch_wbc(int n, const WCsr& out, const WCsr& in, int* arr, void* s
 }
 
 cudaError_t launch_weight_ingest(const int* ooff, const int* oadj, const int* ow, const int* perm, const int* noff,
-                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, const int* ioff,
-                                 const int* iadj, int* iw, cudaStream_t st) {
+                                 const int* nadj, int n, int* nw, int* err, bool check_symmetry, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
     k_weight_lookup<<<blocks, 256, 0, st>>>(ooff, oadj, ow, perm, noff, nadj, n, nw, err);
     if (check_symmetry) k_weight_symmetry<<<blocks, 256, 0, st>>>(noff, nadj, nw, n, err);
-    if (ioff) k_weight_transpose<<<blocks, 256, 0, st>>>(noff, nadj, nw, ioff, iadj, n, iw, err);
     return cudaGetLastError();
 }
 
