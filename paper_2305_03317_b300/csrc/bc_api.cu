@@ -1220,11 +1220,10 @@ bc_status bc_compute_weighted(bc_graph* g, const int32_t* sources, int32_t nsrc,
         !buf_ensure(g->wdag, sizeof(unsigned int) * (size_t)(g->m > 0 ? g->m : 1), st))
         return done(fail(BC_E_NOMEM, "weighted BC buffers"));
     const WCsr wout{(const int*)g->off.p, (const int*)g->adj.p, (const int*)g->w.p, g->n_heavy, g->hchunk_total,
-                    (const int*)g->hcum.p, nullptr, nullptr};
+                    (const int*)g->hcum.p};
     // in-arcs serve only the dependency loop's stamps (rows and indices)
     const WCsr win = !g->directed ? wout
-                                  : WCsr{(const int*)g->ioff.p, (const int*)g->iadj.p, nullptr, 0, 0, nullptr,
-                                         nullptr, nullptr};
+                                  : WCsr{(const int*)g->ioff.p, (const int*)g->iadj.p, nullptr, 0, 0, nullptr};
     const size_t narr = (size_t)std::max(1, g->n_heavy);
     Ctl* ctl = (Ctl*)g->wctl.p;
     int* changed = (int*)((char*)g->wctl.p + sizeof(Ctl));

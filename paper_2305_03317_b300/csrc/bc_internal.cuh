@@ -164,17 +164,15 @@ cudaError_t launch_bfs_extract(const KParams& p, int K, int levels, int ncols, c
 // weights of the relabelled arcs looked up from the original sorted CSR
 // (err bits: 1 rows not sorted, 2 a weight <= 0, 4 asymmetric weights).
 // One direction of a weighted graph for weighted BC: rows with their arc
-// weights, split into heavy rows (more than kChunk arcs, run as kChunk-arc
-// chunk tasks) and light ones.
+// weights, split into heavy rows (more than kChunk arcs, the relabelled
+// prefix [0, n_heavy), run as kChunk-arc chunk tasks) and light ones.
 struct WCsr {
     const int* off;
     const int* adj;
-    const int* w;
+    const int* w;       // nullptr where only rows and indices are read
     int n_heavy;        // heavy rows
     long long hchunks;  // their chunk tasks
     const int* hcum;    // [n_heavy + 1] chunk prefix
-    const int* hrow;    // heavy row ids; nullptr = rows [0, n_heavy)
-    const int* lrow;    // light row ids, ascending; nullptr = rows [n_heavy, n)
 };
 int wbc_blocks();
 // ord: [n] ints; hist: kWbcHistWords words (bucket counts and the largest key);

@@ -95,8 +95,8 @@ __device__ __forceinline__ T load_cg(const T* q) {
 // per warp step (slot i goes to warp i mod nw): each lane of a warp reads the
 // row and stamp of one of the warp's next 32 slots, so 32 stamp reads are in
 // flight together, and the warp runs `body` on the stamped rows in slot order.
-// Light slots are the rows of `g` in id order (or its light-row list), or the
-// `ord` list (reversed when `rev`).
+// Light slots are the rows [n_heavy, n) of `g` in id order, or the `ord` list
+// (reversed when `rev`).
 template <class Body>
 __device__ __forceinline__ void stamped_light_rows(const WParams& p, const WCsr& g, const int* ord, bool rev,
                                                    int pass, bool all, Body body) {
@@ -108,7 +108,7 @@ __device__ __forceinline__ void stamped_light_rows(const WParams& p, const WCsr&
     for (long long s0 = 0; wid + s0 * nw < nl; s0 += 32) {
         const long long i = wid + (s0 + lane) * nw;
         int r = -1;
-        if (i < nl) r = ord ? ord[rev ? p.n - 1 - i : i] : g.lrow ? __ldg(g.lrow + i) : g.n_heavy + (int)i;
+        if (i < nl) r = ord ? ord[rev ? p.n - 1 - i : i] : g.n_heavy + (int)i;
         unsigned int bits = __ballot_sync(kAll, r >= 0 && (all || mprev[r] == pass));
         while (bits) {
             const int j = __ffs(bits) - 1;
@@ -154,7 +154,7 @@ __device__ __forceinline__ void row_pass(const WParams& p, const WCsr& rd, const
                 if (rd.hcum[mid] <= t) lo = mid;
                 else hi = mid;
             }
-            const int k = lo, r = rd.hrow ? __ldg(rd.hrow + k) : k, c0 = rd.hcum[k], nch = rd.hcum[k + 1] - c0;
+            const int k = lo, r = k, c0 = rd.hcum[k], nch = rd.hcum[k + 1] - c0;
             if (!all && mprev[r] != pass) continue;  // the same answer for every chunk of the row
             const int b = rd.off[r] + (int)(t - c0) * kChunk, e = min(rd.off[r + 1], b + kChunk);
             T acc = arc.start(r, init);
@@ -267,12 +267,12 @@ __device__ __forceinline__ void dag_masks(const WParams& p) {
                 if (g.hcum[mid] <= t) lo = mid;
                 else hi = mid;
             }
-            r = g.hrow ? __ldg(g.hrow + lo) : lo;
+            r = lo;
             b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
             e = min(g.off[r + 1], b + kChunk);
         } else {
             const int i = (int)(t - g.hchunks);
-            r = g.lrow ? __ldg(g.lrow + i) : g.n_heavy + i;
+            r = g.n_heavy + i;
             b = g.off[r];
             e = g.off[r + 1];
         }
@@ -361,7 +361,7 @@ __device__ __forceinline__ bool push_min_pass(const WParams& p, int pass, bool a
             if (g.hcum[mid] <= t) lo = mid;
             else hi = mid;
         }
-        const int r = g.hrow ? __ldg(g.hrow + lo) : lo;
+        const int r = lo;
         if (!all && mprev[r] != pass) continue;
         const int b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
         work(r, b, min(g.off[r + 1], b + kChunk));
@@ -390,7 +390,7 @@ __device__ __forceinline__ void heavy_increments(const WParams& p, int pass, boo
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long k = wid; k < g.n_heavy; k += nw) {
-        const int r = g.hrow ? __ldg(g.hrow + k) : (int)k;
+        const int r = (int)k;
         if (!all && mprev[r] != pass) continue;
         const unsigned long long s = p.sig[at(r, lane)];
         hinc[(size_t)k * KW + lane] = s - pushed[at(r, lane)];
@@ -446,7 +446,7 @@ __device__ __forceinline__ bool push_sigma_pass(const WParams& p, int pass, bool
             if (g.hcum[mid] <= t) lo = mid;
             else hi = mid;
         }
-        const int r = g.hrow ? __ldg(g.hrow + lo) : lo;
+        const int r = lo;
         if (!all && mprev[r] != pass) continue;
         const int b = g.off[r] + (int)(t - g.hcum[lo]) * kChunk;
         work(b, min(g.off[r + 1], b + kChunk), hinc[(size_t)lo * KW + lane]);
