@@ -23,8 +23,10 @@ Contents:
     of Dijkstra distances, vertices taken in (distance, id) order; and
     ``brute_force_wbc``, its exact rational definition by path enumeration
     over Bellman-Ford distances.
-  * ``pagerank`` -- the paper's computePR (Appendix A, PR listing) in double
-    precision (``pagerank.c``), the change measured as an L1 norm.
+  * ``pagerank`` -- PageRank by its definition, the power iteration
+    x <- (1 - delta)/n + delta P^T x with P = D^-1 A (``pagerank.c``), with
+    the parameters and stopping rule of the paper's computePR (Appendix A):
+    damping, an L1-change tolerance and an iteration cap; double precision.
 Every function here is pinned by ``tests/test_oracle*.py`` against closed
 forms, brute force and invariants.
 """
@@ -207,7 +209,7 @@ def relabel(off, adj):
 
 
 def pagerank(off, adj, delta: float = 0.85, beta: float = 1e-10, max_iter: int = 100):
-    """The paper's computePR (pagerank.c): (ranks float64[n], sweeps run, last L1 change)."""
+    """PageRank by power iteration (pagerank.c): (ranks float64[n], iterations run, last L1 change)."""
     off, adj = _csr(off, adj)
     n = off.shape[0] - 1
     pr = np.zeros(max(n, 1), np.float64)
