@@ -18,7 +18,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "../../include/bc.h"
 #include "bc_internal.cuh"
@@ -90,12 +89,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
+// flags[0]: NA_* bits; flags[1]: the longest row (arcs), which bounds every
+// path-count sum (rows are summed whole here, and a row may repeat an arc).
 __global__ void k_na_check_csr(const int* off, const int* adj, int n, long long m, int* flags) {
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid == 0 && (off[0] != 0 || (long long)off[n] != m)) atomicOr(flags, NA_BAD_OFFSETS);
-    for (long long v = tid; v < n; v += nthr)
-        if (off[v + 1] < off[v]) atomicOr(flags, NA_BAD_OFFSETS);
+    int longest = 0;
+    for (long long v = tid; v < n; v += nthr) {
+        const int d = off[v + 1] - off[v];
+        if (d < 0) atomicOr(flags, NA_BAD_OFFSETS);
+        else longest = d > longest ? d : longest;
+    }
+    if (longest > 0) atomicMax(flags + 1, longest);
     for (long long e = tid; e < m; e += nthr) {
         const int w = adj[e];
         if (w < 0 || w >= n) atomicOr(flags, NA_BAD_INDEX);
@@ -119,26 +125,26 @@ __global__ void k_na_sources(const int* src, int count, int total, int n, int* d
 
 __global__ void k_na_job(double** slot, double* out) { *slot = out; }
 
-// Device address of the scratch array, looked up once per device (with that
-// device current) by the first call made on it.
-constexpr int kNaMaxDevices = 64;
-std::mutex g_na_mu;
-unsigned char* g_na_addr[kNaMaxDevices] = {};
-
+// Device address of the scratch array on the current device.  Host code
+// cannot use the symbol's name as a device pointer, so every call asks the
+// runtime (with the caller's device current) instead of caching the address:
+// after cudaDeviceReset the module is loaded again and the array may move.
 cudaError_t scratch_address(unsigned char** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_na_addr[dev] = (unsigned char*)p;
-    }
-    *out = g_na_addr[dev];
+    *out = (unsigned char*)p;
     return cudaSuccess;
+}
+
+// Bits of x (0 for 0): a sum of x terms below 2^(64 - na_bits(x)) fits 64 bits.
+int na_bits(unsigned long long x) {
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
 }
 
 bc_status na_fail(bc_status st, const char* msg) {
@@ -163,14 +169,16 @@ extern "C" bc_status bc_compute_noalloc(const int32_t* offsets, const int32_t* i
     if (n == 0) return BC_OK;
 
     // the caller's CSR must be safe to index
-    if ((e = cudaMemsetAsync(flags, 0, sizeof(int), st)) != cudaSuccess) return na_fail(BC_E_CUDA, cudaGetErrorString(e));
+    if ((e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), st)) != cudaSuccess)
+        return na_fail(BC_E_CUDA, cudaGetErrorString(e));
     k_na_check_csr<<<592, 256, 0, st>>>(offsets, indices, n, m, flags);
-    int hflags = 0;
+    int hcheck[2] = {0, 0};
     if ((e = cudaGetLastError()) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hcheck, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return na_fail(BC_E_CUDA, cudaGetErrorString(e));
-    if (hflags) return na_fail(BC_E_INVALID_GRAPH, "offsets not monotone or an index outside [0, n)");
+    if (hcheck[0]) return na_fail(BC_E_INVALID_GRAPH, "offsets not monotone or an index outside [0, n)");
+    int hflags = 0;
 
     KParams p;
     memset(&p, 0, sizeof p);
@@ -222,7 +230,10 @@ extern "C" bc_status bc_compute_noalloc(const int32_t* offsets, const int32_t* i
     p.beta = 24.0f;
     p.budget = 40000000000ll;
     p.group = 32;
-    p.sum_bits = 64 - 15;  // rows are never chunked here; no row has 2^15 arcs (n <= 32768)
+    // rows are summed whole (never chunked here), and nothing stops a row from
+    // repeating an arc, so the bound comes from the longest row: a sum of
+    // `longest` terms below 2^sum_bits cannot wrap 64 bits
+    p.sum_bits = 64 - na_bits((unsigned long long)(hcheck[1] > 1 ? hcheck[1] : 1));
     p.dense_min = 32;  // batch width 32: only arcs matching every column go column-mapped
 
     // the output accumulates every batch in source order; the job table points at it
