@@ -7,7 +7,8 @@ benchmark times, on outputs the oracle can compute in bounded time.
 * R-MAT scale 22, edge factor 16: the benchmark's first 128-source batch
   (K = 128, the width the benchmark runs; the first 128 of its 4096 sources
   once grouped by hub distances, as bc_compute groups them) against the oracle
-  on the host cores.
+  on the host cores; and three of its batches (the first two and the last of
+  the grouped order) in one call on two teams, as the benchmark runs its 32.
 * The 2000-graph pool of uneven R-MAT graphs: sampled items (the smallest
   graph, the largest all-sources graph, the largest graph) recorded into one
   plan as the benchmark records the pool, each against the oracle.
@@ -73,6 +74,23 @@ def test_rmat22_first_benchmark_batch(bc):
     out, st = G.compute(src, batch_width=128)
     assert st == bc.BC_OK
     assert G.stats()["batches"] == 1
+    assert_bc_close(out.cpu().numpy(), oracle.bc(g.off, g.adj, src, threads=THREADS))
+
+
+def test_rmat22_batches_on_two_teams_with_the_last_grouped_batch(bc):
+    # the benchmark's call runs its 32 batches on 2 teams, batches adding into BC
+    # in batch order through a turn counter: here 3 batches on 2 teams, the
+    # first two of the grouped order and its last one
+    from grouping import grouped_order
+    g = bcgen.rmat(22, 16, 1)
+    G = bc.Graph(g.off, g.adj)
+    allsrc = bcgen.sample_sources(g, 4096, 1)
+    order = grouped_order(g, G.export()[0], allsrc, threads=THREADS)
+    src = np.concatenate([allsrc[order[:256]], allsrc[order[-128:]]])
+    out, st = G.compute(src, batch_width=128, teams=2)  # 384 sources: grouped again, the same relative order
+    assert st == bc.BC_OK
+    s = G.stats()
+    assert s["batches"] == 3 and s["teams"] == 2
     assert_bc_close(out.cpu().numpy(), oracle.bc(g.off, g.adj, src, threads=THREADS))
 
 
