@@ -176,20 +176,6 @@ class Clocks:
         return res
 
 
-def dag_stats(G, g, src, nsample=4):
-    """Mean E_dag and reached count per source for the byte model, from the
-    library's own levels (bc_debug_source) on a few sources."""
-    deg = np.diff(g.off.astype(np.int64))
-    row = np.repeat(np.arange(g.n, dtype=np.int64), deg)
-    ed, ns = [], []
-    for s in src[:: max(1, len(src) // nsample)][:nsample]:
-        lev, _, _, _ = G.debug_source(int(s))
-        lv, lw = lev[row], lev[g.adj]
-        ed.append(int(np.count_nonzero((lv >= 0) & (lw == lv + 1))))
-        ns.append(int(np.count_nonzero(lev >= 0)))
-    return float(np.mean(ed)), float(np.mean(ns))
-
-
 def cpu_baseline(g, src, per_core=1, max_threads=64):
     import oracle
     cores = max(1, min(os.cpu_count() or 1, max_threads))
@@ -231,11 +217,11 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------------ sharding (N GPUs, one rank each)
-def shard_sources(g, count, rank, world):
-    """Weak scaling: every rank traverses its own `count` sources (seed 1 + rank);
-    rank 0 of a 1-GPU run gets the single-GPU workload's list."""
+def job_sources(g, per_rank, world):
+    """The job: per_rank sources for every rank (weak scaling), seed 1; a 1-GPU
+    run gets the single-GPU workload's list."""
     import bcgen
-    return bcgen.sample_sources(g, count, 1 + (rank if world > 1 else 0))
+    return bcgen.sample_sources(g, per_rank * world, 1)
 
 
 def max_over_ranks(ms, dist, device):
@@ -246,11 +232,6 @@ def max_over_ranks(ms, dist, device):
     t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
-
-
-def aggregate_rate(world, nsrc_per_rank, m, ms):
-    """Whole-job throughput: every rank's sources times arcs over the slowest time."""
-    return world * nsrc_per_rank * m / (ms / 1e3)
 
 
 # ------------------------------------------------------------------ our arm
@@ -278,8 +259,9 @@ def run_ours(a):
         return run_weighted(a, bc, torch)
 
     g, src, desc = make_workload(a)
-    if world > 1:  # weak scaling: every rank runs its own sources of the same size
-        src = shard_sources(g, len(src), rank, world)
+    per_rank = len(src)
+    if world > 1:  # weak scaling: one job of per_rank sources per rank, split by batch over the ranks
+        src = job_sources(g, per_rank, world)
     t0 = time.perf_counter()
     G = bc.Graph(g.off, g.adj)
     torch.cuda.synchronize()
@@ -294,8 +276,19 @@ def run_ours(a):
         tuned = G.autotune(src)  # per size bucket; knobs left at 0 below come from it
         tuned["seconds"] = round(time.perf_counter() - t_tune, 2)
 
+    if world > 1:
+        from paper_2305_03317_b300 import sharded
+
+        def step(sources):  # this rank's batches, the status exchange, the gather, the rank-order sum
+            return sharded.compute(G, sources, out=out, **opts)
+        order, K_job = G.source_batches(src, batch_width=a.batch_width, source_order=a.source_order)
+        n_rank_src = len(sharded.shard_of(order, K_job, rank, world))
+    else:
+        def step(sources):
+            return G.compute(sources, out=out, **opts)
+        n_rank_src = len(src)
     for _ in range(max(a.warmup, 0)):
-        G.compute(d_src, out=out, **opts)
+        step(d_src)
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
@@ -309,7 +302,7 @@ def run_ours(a):
     for _ in range(a.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, st = G.compute(d_src, out=out, **opts)
+        _, st = step(d_src)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -325,7 +318,7 @@ def run_ours(a):
     total_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     stats = G.stats()
     ms = total_ms / a.steps
-    value = aggregate_rate(world, len(src), g.m, ms)
+    value = len(src) * g.m / (ms / 1e3)  # every rank's sources x arcs over the slowest rank's time
 
     # end to end: pinned host sources in, pinned host result out, through the public call
     h_src = torch.from_numpy(src).pin_memory()
@@ -335,7 +328,7 @@ def run_ours(a):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        G.compute(h_src.numpy(), out=out, **opts)
+        step(h_src.numpy())
         h_out.copy_(out, non_blocking=True)
         stream.synchronize()
     e1.record(stream)
@@ -348,9 +341,10 @@ def run_ours(a):
         return
     # roofline of the persistent traversal kernel
     K = stats["batch_width"]
-    ed, ns = dag_stats(G, g, src)
     nb = stats["batches"]
-    model_bytes = nb * (8.0 * g.m + K * g.m / 4.0) + len(src) * (16.0 * ed + 24.0 * ns)
+    # this rank's launch: sum over its sources of E_dag(s) and n_s, counted exactly by the kernel
+    dag, reached = stats["dag_arcs"], stats["reached"]
+    model_bytes = nb * (8.0 * g.m + K * g.m / 4.0) + 16.0 * dag + 24.0 * reached
     kms = float(np.mean(kern_ms))
     peak, peak_src = measured_peak()
     achieved = model_bytes / (kms / 1e3) / 1e9
@@ -366,15 +360,18 @@ def run_ours(a):
                        source_grouping_ms=round(stats["order_ms"], 3),
                        autotuned=tuned,
                        l2="inputs larger than L2 (CSR and per-batch state are GBs, L2 126 MB)",
-                       parallelism=f"dp{world} (sources sharded per rank)" if world > 1 else "single GPU",
+                       parallelism=(f"dp{world}: one job of {len(src)} sources, batches round-robin over the "
+                                    f"ranks, partial BC all-gathered and summed in rank order (bc_reduce_ranks)"
+                                    if world > 1 else "single GPU"),
                        statuses=sorted(int(x) for x in statuses)),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "what": "per bc_compute step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (tr * len(src)) if tr is not None else None,
+                     "traffic": (tr * n_rank_src) if tr is not None else None,
                      "kernel": kname, "kernel_ms": kms, "model_bytes": model_bytes,
-                     "model": f"per source 8m/k + m/4 + 16*E_dag + 24*n_s; E_dag={ed:.0f}, n_s={ns:.0f} "
-                              f"(mean of 4 sources' levels)", "peak_source": peak_src},
+                     "model": f"per source 8m/k + m/4 + 16*E_dag + 24*n_s over the launch's {n_rank_src} sources; "
+                              f"E_dag={dag / n_rank_src:.0f}, n_s={reached / n_rank_src:.0f} per source (exact "
+                              f"kernel counts: sum E_dag {dag}, sum n_s {reached})", "peak_source": peak_src},
         "e2e": {"value": len(src) * g.m / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(4 * len(src)),
                 "d2h_bytes_per_step": int(8 * g.n), "ms_per_step": e2e_ms},
         "gpu_launches": launches,

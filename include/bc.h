@@ -156,6 +156,33 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
                         bc_stream_t stream, const bc_options* opt);
 
 /*
+ * Splitting one job over several GPUs (sources are independent: the paper's
+ * computeBC loops over its source set, Appendix A, and BC is a sum over it).
+ * Every rank holds the same graph, takes a share of the job's batches, runs
+ * bc_compute_ex on its share, and the ranks' partial BC vectors are summed.
+ *
+ * bc_source_batches: the order in which bc_compute_ex(g, sources, nsrc, ..., opt)
+ * would batch the list (grouped by hub distances under the automatic rule of
+ * bc_options.source_order, else as given; it depends on the graph and the list
+ * alone) and the batch width it would use.  sources: host or device, original
+ * ids; order: HOST int32[nsrc], written; batch_width: host, may be NULL.
+ * Batch b is order[b*K, (b+1)*K).  A rank that runs a sub-list of whole
+ * batches with batch_width = K and source_order = 1 gets, per column, the
+ * bits the full call computes.  BC_E_SOURCE for an id outside [0, n).
+ */
+bc_status bc_source_batches(bc_graph* g, const int32_t* sources, int32_t nsrc, const bc_options* opt,
+                            int32_t* order, int32_t* batch_width, bc_stream_t stream);
+
+/*
+ * Sum of per-rank partial results in a fixed order: out[v] = parts[0][v] +
+ * parts[1][v] + ... + parts[nranks-1][v], added left to right (device arrays;
+ * parts is [nranks][n] row-major, out[n]; out may not overlap parts).  The
+ * order is that of the ranks, whatever order the parts arrived in, so the
+ * result repeats bit for bit.  Returns when out is final.
+ */
+bc_status bc_reduce_ranks(const double* parts, int32_t nranks, int64_t n, double* out, bc_stream_t stream);
+
+/*
  * Multi-source BFS: the forward sweep of bc_compute alone (Section 2.3.2,
  * iterateInBFS: levels and shortest-path counts) for each listed source, the
  * same kernels and batching.  sources: nsrc original ids (host or device).
@@ -240,6 +267,10 @@ typedef struct {
                                 neighbour distance row) */
     int64_t mask_lanes;      /* bc_compute_weighted: (arc, column) pairs those reads used (one count add or one
                                 rho read each) */
+    int64_t dag_arcs;        /* unweighted calls: terms of the forward path-count sums, i.e. the sum over the
+                                call's sources of E_dag(s) = #{arcs (v, w): d_s(w) = d_s(v) + 1} (last launch) */
+    int64_t reached;         /* unweighted calls: sum over the call's sources of the vertices reached, source
+                                included (last launch) */
 } bc_run_stats;
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 
@@ -335,18 +366,22 @@ bc_status bc_debug_source(bc_graph* g, int32_t s, int32_t* level, double* sigma_
  * and forbids other allocations (to hold a hard memory cap), or a
  * latency-critical path that must never enter the CUDA allocator.  Such a
  * caller passes everything on the device: offsets[n+1] and indices[m] (int32
- * undirected CSR, used as given: offsets and index range are checked, symmetry,
- * self-loops and duplicates are not), sources[nsrc] (original ids), and
- * out_bc[n] (overwritten with the same raw BC as bc_compute, within 1e-9
- * relative).  All working state lives in one static device array of about
- * 37 MB that every GPU loading the library holds until exit; hence
+ * undirected CSR, used as given: offsets and index range are checked
+ * (BC_E_INVALID_GRAPH), symmetry, self-loops and duplicates are not; rows are
+ * summed whole, so the longest row sets the count at which a batch moves to
+ * the extended-range form), sources[nsrc] (original ids, BC_E_SOURCE outside
+ * [0, n)), and out_bc[n] (overwritten with the same raw BC as bc_compute,
+ * within 1e-9 relative).  All working state lives in one static device array
+ * of about 37 MB that every GPU loading the library holds until exit; hence
  * n <= 32768 vertices (BC_E_LIMIT beyond), batches of 32 sources.  The call
- * allocates nothing and returns when the result is final.  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress with
- * that device current): make that first call before any stream capture.
- * Every call shares the array and it keeps the last call's contents (each call
- * clears what must start at zero): calls that overlap on the GPU, from
- * several streams or threads, race and must not be issued.
+ * allocates nothing.  It is synchronous: it waits on `stream` (and reads
+ * status words back into host memory) before it returns, with the result
+ * final.  Each call looks up the array's address on the calling thread's
+ * current device (cudaGetSymbolAddress), so that device must be the one that
+ * holds the caller's buffers.  Every call shares the array and it keeps the
+ * last call's contents (each call clears what must start at zero): calls that
+ * overlap on the GPU, from several streams or threads, race and must not be
+ * issued.
  */
 bc_status bc_compute_noalloc(const int32_t* offsets, const int32_t* indices, int32_t n, int64_t m,
                              const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream);

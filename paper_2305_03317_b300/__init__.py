@@ -56,7 +56,8 @@ class bc_run_stats(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_float), ("teams", ctypes.c_int32), ("order_ms", ctypes.c_float),
                 ("arcs_visited", ctypes.c_int64), ("rows_visited", ctypes.c_int64),
-                ("mask_arcs", ctypes.c_int64), ("mask_lanes", ctypes.c_int64)]
+                ("mask_arcs", ctypes.c_int64), ("mask_lanes", ctypes.c_int64), ("dag_arcs", ctypes.c_int64),
+                ("reached", ctypes.c_int64)]
 
 
 class bc_item(ctypes.Structure):
@@ -98,6 +99,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_debug_source": [P, i32, P, P, P],
         "bc_last_trace": [P, P, i32, P],
         "bc_compute_noalloc": [P, P, i32, i64, P, i32, P, P],
+        "bc_source_batches": [P, P, i32, ctypes.POINTER(bc_options), P, ctypes.POINTER(i32), P],
+        "bc_reduce_ranks": [P, i32, i64, P, P],
         "bc_autotune": [P, P, i32, P, ctypes.POINTER(bc_options), ctypes.POINTER(ctypes.c_double)],
         "bc_tuning_cache": [ctypes.c_char_p, i32],
         "bc_many_create": [ctypes.POINTER(bc_item), i32, ctypes.POINTER(bc_options), P, ctypes.POINTER(P)],
@@ -148,6 +151,18 @@ def _stream_handle(stream) -> int:
 def tuning_cache(path: str, save: bool) -> None:
     """Load or write the autotuner's settings (JSON)."""
     _check(load().bc_tuning_cache(path.encode(), 1 if save else 0))
+
+
+def reduce_ranks(parts, out=None, stream=None):
+    """out[v] = parts[0][v] + ... + parts[R-1][v] in rank order (bc_reduce_ranks); parts: [R][n] float64 cuda."""
+    import torch
+    R, n = int(parts.shape[0]), int(parts.shape[1])
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.float64, device=parts.device)[:n]
+    parts = parts.contiguous()
+    _check(load().bc_reduce_ranks(_ptr(parts) if n else None, R, n, _ptr(out) if n else None,
+                                  _stream_handle(stream)))
+    return out
 
 
 def server_config(slots: int = 1, memory_budget: int = 0) -> None:
@@ -249,6 +264,19 @@ class Graph:
                                  _stream_handle(stream), ctypes.byref(opt))
         _check(s)
         return out, s
+
+    def source_batches(self, sources, stream=None, batch_width: int = 0, source_order: int = 0):
+        """The order in which compute() would batch ``sources`` and its batch width: (order, K)."""
+        if isinstance(sources, np.ndarray):
+            sources = np.ascontiguousarray(sources, dtype=np.int32)
+        nsrc = int(sources.shape[0]) if isinstance(sources, np.ndarray) else int(sources.numel())
+        order = np.empty(max(nsrc, 1), np.int32)
+        K = ctypes.c_int32()
+        opt = bc_options()
+        opt.batch_width, opt.source_order = batch_width, source_order
+        _check(load().bc_source_batches(self._h, _ptr(sources) if nsrc else None, nsrc, ctypes.byref(opt),
+                                        order.ctypes.data, ctypes.byref(K), _stream_handle(stream)))
+        return order[:nsrc], K.value
 
     def compute_weighted(self, sources, out=None, stream=None):
         """Weighted BC over ``sources`` (host numpy or device int32 tensor). Returns (out, status)."""

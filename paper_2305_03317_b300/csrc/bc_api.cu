@@ -629,6 +629,8 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
         s.max_levels = ro.ctl.max_levels;
         s.pull_levels += ro.ctl.pull_levels;
         s.push_levels += ro.ctl.push_levels;
+        s.dag_arcs = (int64_t)ro.ctl.dag_pairs;  // the launch that settles the call counts
+        s.reached = (int64_t)ro.ctl.reached_pairs;
         if (ro.capacity) {
             if (capf >= K) return fail(BC_E_CUDA, "internal: level-list capacity exceeded at the bound");
             capf = K;
@@ -1527,6 +1529,84 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
     buf_release(tmp, st);
     buf_release(grouped, st);
     return r;
+}
+
+bc_status bc_source_batches(bc_graph* g, const int32_t* sources, int32_t nsrc, const bc_options* opt,
+                            int32_t* order, int32_t* batch_width, bc_stream_t stream) {
+    if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
+    if (nsrc < 0) return fail(BC_E_INVALID_ARG, "nsrc < 0");
+    if (nsrc > 0 && (!sources || !order)) return fail(BC_E_INVALID_ARG, "sources or order is NULL");
+    bc_options o;
+    memset(&o, 0, sizeof o);
+    if (opt) o = *opt;
+    bc_status cs = check_opts(o);
+    if (cs != BC_OK) return cs;
+    cudaStream_t st = (cudaStream_t)stream;
+    apply_tuning(g, nsrc, o);
+    if (batch_width) *batch_width = choose_width(g->n, nsrc, o.batch_width);
+    if (nsrc == 0) return BC_OK;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->last_stream = st;
+    std::vector<int> hs(nsrc);
+    DevBuf dsrc;
+    cudaError_t e = cudaSuccess;
+    if (is_device_ptr(sources))
+        e = cudaMemcpyAsync(hs.data(), sources, sizeof(int) * (size_t)nsrc, cudaMemcpyDeviceToHost, st);
+    else
+        memcpy(hs.data(), sources, sizeof(int) * (size_t)nsrc);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "source copy");
+    for (int i = 0; i < nsrc; ++i)
+        if (hs[i] < 0 || hs[i] >= g->n) return fail(BC_E_SOURCE, "source %d (entry %d) is outside [0, %d)", hs[i], i, g->n);
+    if (want_grouping(g, nsrc, o)) {
+        if (!buf_ensure(dsrc, sizeof(int) * (size_t)nsrc, st)) return fail(BC_E_NOMEM, "source buffer");
+        e = cudaMemcpyAsync(dsrc.p, hs.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            buf_release(dsrc, st);
+            return cuda_fail(e, "source copy");
+        }
+        DevBuf grouped;
+        bc_run_stats pre{};
+        std::vector<int> go;
+        bc_status r = group_sources(g, (const int*)dsrc.p, nsrc, st, grouped, &pre, &go);
+        buf_release(grouped, st);
+        buf_release(dsrc, st);
+        if (r < 0) return r;
+        hs.swap(go);
+    }
+    memcpy(order, hs.data(), sizeof(int) * (size_t)nsrc);
+    return BC_OK;
+}
+
+}  // extern "C"
+
+// out[v] = parts[0][v] + parts[1][v] + ... + parts[nranks-1][v], added left to
+// right in rank order, so the result does not depend on how the parts arrived.
+__global__ void k_reduce_ranks(const double* __restrict__ parts, int nranks, long long n, double* __restrict__ out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        double acc = parts[v];
+        for (int r = 1; r < nranks; ++r) acc += parts[(size_t)r * (size_t)n + (size_t)v];
+        out[v] = acc;
+    }
+}
+
+extern "C" {
+
+bc_status bc_reduce_ranks(const double* parts, int32_t nranks, int64_t n, double* out, bc_stream_t stream) {
+    if (nranks < 1 || n < 0) return fail(BC_E_INVALID_ARG, "nranks < 1 or n < 0");
+    if (n == 0) return BC_OK;
+    if (!parts || !out) return fail(BC_E_INVALID_ARG, "parts or out is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (n + 255) / 256, cap = 8LL * (sms > 0 ? sms : 1);
+    k_reduce_ranks<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(parts, nranks, (long long)n, out);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "rank reduction");
+    return BC_OK;
 }
 
 bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* level, double* sigma, int32_t* sigma_exp,

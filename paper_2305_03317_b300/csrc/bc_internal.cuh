@@ -33,6 +33,8 @@ struct Ctl {
     int trace_n;               // pairs written to the trace
     unsigned int bc_next;      // global control: the next batch allowed to add into BC
     int pad[2];
+    unsigned long long dag_pairs;      // (arc, column) terms of the forward path-count sums: sum of E_dag(s)
+    unsigned long long reached_pairs;  // (vertex, column) pairs reached, sources included: sum of n_s
 };
 
 // Level bookkeeping, indexed by BFS level.

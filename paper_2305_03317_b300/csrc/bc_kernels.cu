@@ -246,6 +246,8 @@ struct __align__(16) WarpSmem {
     int av[32];                   // append staging (pull): vertex
     uint32_t am[32][W];           // append staging: mask
     long long adeg;               // append staging: degree sum
+    unsigned long long cnt_dag;   // this warp's forward sum terms (DAG arc, column), flushed at exit
+    unsigned long long cnt_reached;  // this warp's reached (vertex, column) pairs, flushed at exit
 };
 
 using WS128 = WarpSmem<128, false>;
@@ -343,6 +345,11 @@ __device__ __forceinline__ void gather_step(const KParams& p, WarpSmem<K, EXT>& 
     constexpr int PCAP = Geo<K>::PCAP;
     constexpr bool ORDERED = EXT || DIR == BWD;
     const int lane = lane_id();
+    if constexpr (DIR == FWD) {
+        // every matched (arc, column) of a forward sum is a DAG arc of that column's source
+        const unsigned int terms = __reduce_add_sync(FULL_MASK, (unsigned int)n);
+        if (lane == 0) ws.cnt_dag += terms;
+    }
     if (!__any_sync(FULL_MASK, n > 0)) return;
     if (n > 0) {
 #pragma unroll
@@ -619,7 +626,7 @@ __device__ __forceinline__ int select_col(const uint32_t* m, int k) {
 // masks[o] selects the columns of owner o (row o of the accumulator).
 // FWD writes the path counts; BWD turns rho sums into delta and rho.
 template <int K, bool EXT, int DIR>
-__device__ __forceinline__ void write_columns(const KParams& p, const WarpSmem<K, EXT>& ws, int ng,
+__device__ __forceinline__ void write_columns(const KParams& p, WarpSmem<K, EXT>& ws, int ng,
                                               const uint32_t (*masks)[Geo<K>::W]) {
     constexpr int W = Geo<K>::W;
     const int lane = lane_id();
@@ -636,6 +643,7 @@ __device__ __forceinline__ void write_columns(const KParams& p, const WarpSmem<K
     }
     const int Q = __shfl_sync(FULL_MASK, incl, 31);
     const int ex = incl - cnt;  // exclusive prefix of owner `lane`
+    if (DIR == FWD && lane == 0) ws.cnt_reached += (unsigned long long)Q;
     bool inexact = false, big = false;
     for (int r = 0; r < Q; r += 32) {
         const int q = r + lane;
@@ -1351,6 +1359,7 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
         for (int c = 0; c < K; ++c) {
             const int s = src[c];
             if (s < 0) continue;
+            ws.cnt_reached += 1;  // the source itself, level 0 of its column
             const uint32_t bit = 1u << (c & 31);
             p.V[(size_t)s * W + (c >> 5)] |= bit;
             p.F[0][(size_t)s * W + (c >> 5)] |= bit;
@@ -1529,8 +1538,18 @@ __global__ void __launch_bounds__(kThreads, 3) bc_persistent(KParams p) {
     GridTeam team{tv.ctl, tv.gctl, tv.team_blocks, tv.budget};
     int ph = 0;
     WarpSmem<K, EXT>& ws = wsm[warp_id()];
+    if (lane_id() == 0) {
+        ws.cnt_dag = 0;
+        ws.cnt_reached = 0;
+    }
+    __syncwarp();
     for (int b = tv.team; b < tv.nbatch; b += tv.nteams)
         if (!run_batch<K, EXT>(tv, b, team, ph, ws)) return;
+    __syncwarp();
+    if (lane_id() == 0) {
+        if (ws.cnt_dag) atomicAdd(&tv.gctl->dag_pairs, ws.cnt_dag);
+        if (ws.cnt_reached) atomicAdd(&tv.gctl->reached_pairs, ws.cnt_reached);
+    }
 }
 
 // ------------------------------------------------------------------ small kernels

@@ -154,6 +154,48 @@ def test_rmat12_bitwise_across_widths_and_directions(bc, rmat12):
         assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
 
 
+def test_reduce_ranks_is_the_rank_order_sum(bc):
+    import torch
+    rng = np.random.default_rng(5)
+    parts = rng.random((5, 1001)) * 10.0 ** rng.integers(-8, 8, (5, 1001))
+    got = bc.reduce_ranks(torch.from_numpy(parts).cuda()).cpu().numpy()
+    want = parts[0].copy()
+    for r in parts[1:]:
+        want = want + r
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+    one = bc.reduce_ranks(torch.from_numpy(parts[:1]).cuda()).cpu().numpy()
+    assert np.array_equal(one.view(np.uint64), parts[0].view(np.uint64))
+
+
+def test_job_split_over_emulated_ranks(bc, rmat12):
+    # the multi-GPU split run rank after rank on one GPU: each rank's share of
+    # the job's batches through bc_compute_ex, then the rank-order sum
+    import torch
+    from grouping import grouped_order
+    from paper_2305_03317_b300 import sharded
+    g, _ = rmat12
+    G = bc.Graph(g.off, g.adj)
+    src = bcgen.sample_sources(g, 700, 3)
+    order, K = G.source_batches(src)
+    assert np.array_equal(order, src[grouped_order(g, G.export()[0], src)])  # the automatic grouping
+    assert G.source_batches(src, source_order=1)[0].tolist() == src.tolist()
+    full, _ = G.compute(src, batch_width=K)
+    full = full.cpu().numpy().copy()
+    want = oracle.bc(g.off, g.adj, src)
+    for world in (1, 2, 3, 9):
+        parts = []
+        for r in range(world):
+            mine = sharded.shard_of(order, K, r, world)
+            part = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+            if len(mine):
+                G.compute(mine, out=part, batch_width=K, source_order=1)
+            parts.append(part)
+        got = bc.reduce_ranks(torch.stack(parts)).cpu().numpy()
+        assert_bc_close(got, want)
+        if world == 1:
+            assert np.array_equal(got.view(np.uint64), full.view(np.uint64))
+
+
 def test_source_grouping_order_and_widths(bc, rmat12):
     g, _ = rmat12
     src = bcgen.sample_sources(g, 300, 4)
