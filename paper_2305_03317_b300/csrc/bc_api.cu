@@ -345,9 +345,10 @@ static int bits_needed(unsigned long long x) {
 }
 
 // Matched columns from which an arc is cheaper summed column-mapped (one warp
-// step per arc) than as compacted pairs; measured on R-MAT scale 22 (one
-// batch per width): 48 of 128 and 32 of 64; at 32 columns the two forms tie.
-static int default_dense_min(int K) { return K >= 128 ? 48 : 32; }
+// step per arc) than as compacted pairs; measured on R-MAT scale 22 (4096
+// sources): 32 of 128 once the column-mapped sums stay in registers between
+// arcs of one owner (48 before), and 32 of 64; at 32 columns the two forms tie.
+static int default_dense_min(int K) { return 32; }
 
 static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_options& o, bool ext, int team_blocks) {
     KParams p;

@@ -295,7 +295,9 @@ __device__ __forceinline__ void dense_arcs(WarpSmem<K, EXT>& ws, unsigned int db
     constexpr int W = Geo<K>::W;
     static_assert(K >= 32 && !EXT, "column-mapped arcs need K >= 32 and the plain form");
     // Each lane reads its own W columns of every arc straight into registers,
-    // two arcs ahead of the one being added (three register buffers).
+    // two arcs ahead of the one being added (three register buffers).  Same
+    // additions in the same order as one read-add-write of the accumulator
+    // row per arc: only where the running sums live changes.
     const int lane = lane_id();
     const int word = (W * lane) >> 5;
     unsigned int di = db;  // arcs still to read (taken in CSR order)
@@ -311,27 +313,35 @@ __device__ __forceinline__ void dense_arcs(WarpSmem<K, EXT>& ws, unsigned int db
     unsigned long long xa[W], xb[W], xc[W];
     fetch(xa);
     fetch(xb);
+    // The running sums of the current owner stay in registers while
+    // consecutive arcs belong to it (arcs are owner-sorted), and go back to
+    // its accumulator row when the owner changes.
+    int cur = -1;
+    unsigned long long r[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) r[i] = 0ull;
     while (db) {
         fetch(xc);
         const int j = __ffs(db) - 1;
         db &= db - 1;
         const uint32_t b = lane_field<W>(ws.fw[j][word], lane);
-        if (b) {
-            unsigned long long r[W];
-            unsigned long long* a = &ws.acc[ws.so[j] * K + W * lane];
-            load_terms<W>(a, r);
-            int e = 0;
-#pragma unroll
-            for (int i = 0; i < W; ++i)
-                if ((b >> i) & 1u) acc_add<false, DIR>(r[i], e, xa[i], 0, carry);
-            store_terms<W>(a, r);
+        const int o = ws.so[j];
+        if (o != cur) {
+            if (cur >= 0) store_terms<W>(&ws.acc[cur * K + W * lane], r);
+            load_terms<W>(&ws.acc[o * K + W * lane], r);
+            cur = o;
         }
+        int e = 0;
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            if ((b >> i) & 1u) acc_add<false, DIR>(r[i], e, xa[i], 0, carry);
 #pragma unroll
         for (int i = 0; i < W; ++i) {
             xa[i] = xb[i];
             xb[i] = xc[i];
         }
     }
+    if (cur >= 0) store_terms<W>(&ws.acc[cur * K + W * lane], r);
     __syncwarp();
 }
 
