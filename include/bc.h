@@ -63,7 +63,9 @@ typedef enum {
     BC_E_CUDA = -6,            /* a CUDA runtime call failed; bc_last_error() has the CUDA message */
     BC_E_SIGMA_RANGE = -7,     /* a path count exceeded even the extended range (2^(2^31)) */
     BC_E_LIMIT = -8,           /* a size limit: BFS depth > 65534 levels, or n/m beyond int32 */
-    BC_E_BUSY = -9             /* bc_graph_destroy: a plan or an unfinished serving job still uses the graph */
+    BC_E_BUSY = -9,            /* bc_graph_destroy: a plan or an unfinished serving job still uses the graph;
+                                  bc_cancel: the job is already running or finished */
+    BC_E_CANCELLED = -10       /* bc_poll / bc_wait: the job was withdrawn by bc_cancel before it ran */
 } bc_status;
 
 /* bc_graph_create flags */
@@ -343,8 +345,17 @@ bc_status bc_poll_ex(bc_job job, double* latency_s);
  * returns and releases like bc_poll. */
 bc_status bc_wait(bc_job job, int64_t timeout_ms);
 bc_status bc_wait_ex(bc_job job, int64_t timeout_ms, double* latency_s);
-/* Serving facts: jobs admitted concurrently at peak, total completed. */
+/* Serving facts: jobs admitted concurrently at peak, total completed (since start or the last reset). */
 bc_status bc_server_stats(int32_t* peak_concurrency, int64_t* completed);
+/* Starts a new measurement window: peak = the traversals running now, completed = 0. */
+bc_status bc_server_reset_stats(void);
+/*
+ * Withdraws a job that is still queued (not yet admitted): it will not run,
+ * out_bc is not written, and its bc_poll / bc_wait then returns BC_E_CANCELLED
+ * (releasing the id).  BC_E_BUSY when the job is already running or finished
+ * (it completes normally); BC_E_INVALID_ARG for an unknown or released id.
+ */
+bc_status bc_cancel(bc_job job);
 /* Slots (traversals run concurrently, each on 1/slots of the GPU; default 1, which measured
  * best: jobs queued on the same graph are still packed into one traversal) and the device-memory
  * budget for admission (bytes; 0 = 80% of free).  While the server runs the slot count may only

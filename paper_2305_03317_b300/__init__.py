@@ -29,6 +29,7 @@ BC_E_CUDA = -6
 BC_E_SIGMA_RANGE = -7
 BC_E_LIMIT = -8
 BC_E_BUSY = -9
+BC_E_CANCELLED = -10
 
 BC_UNDIRECTED = 1
 BC_INPUT_ON_DEVICE = 2
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_wait": [u64, i64],
         "bc_wait_ex": [u64, i64, ctypes.POINTER(ctypes.c_double)],
         "bc_server_stats": [P, P],
+        "bc_server_reset_stats": [],
+        "bc_cancel": [u64],
         "bc_server_config": [i32, i64],
         "bc_debug_source": [P, i32, P, P, P],
         "bc_last_trace": [P, P, i32, P],
@@ -176,6 +179,10 @@ def server_stats():
     return int(peak.value), int(done.value)
 
 
+def server_reset_stats() -> None:
+    _check(load().bc_server_reset_stats())
+
+
 @dataclass
 class Job:
     id: int
@@ -199,6 +206,14 @@ class Job:
             return None
         _check(s)
         return s, float(lat.value)
+
+    def cancel(self) -> bool:
+        """Withdraw the job if it is still queued (True); False when it already runs or ran."""
+        s = load().bc_cancel(self.id)
+        if s == BC_E_BUSY:
+            return False
+        _check(s)
+        return True
 
 
 class Graph:

@@ -2223,6 +2223,35 @@ bc_status bc_server_stats(int32_t* peak_concurrency, int64_t* completed) {
     return BC_OK;
 }
 
+bc_status bc_server_reset_stats(void) {
+    Server& S = server();
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.peak = S.running;
+    S.completed = 0;
+    return BC_OK;
+}
+
+bc_status bc_cancel(bc_job job) {
+    Server& S = server();
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        auto it = S.jobs.find(job);
+        if (it == S.jobs.end())
+            return fail(BC_E_INVALID_ARG, "unknown or already released job %llu", (unsigned long long)job);
+        std::shared_ptr<Job> j = it->second;
+        if (j->done) return fail(BC_E_BUSY, "job %llu has already finished", (unsigned long long)job);
+        auto q = std::find(S.queue.begin(), S.queue.end(), j);
+        if (q == S.queue.end()) return fail(BC_E_BUSY, "job %llu is running; it will finish", (unsigned long long)job);
+        S.queue.erase(q);
+        j->result = BC_E_CANCELLED;  // out_bc is not written
+        j->done = true;
+        j->t_done = std::chrono::steady_clock::now();
+        j->g->users--;
+    }
+    S.cv_done.notify_all();
+    return BC_OK;
+}
+
 const char* bc_status_string(bc_status st) {
     switch (st) {
         case BC_OK: return "BC_OK";
@@ -2237,6 +2266,7 @@ const char* bc_status_string(bc_status st) {
         case BC_E_SIGMA_RANGE: return "BC_E_SIGMA_RANGE";
         case BC_E_LIMIT: return "BC_E_LIMIT";
         case BC_E_BUSY: return "BC_E_BUSY";
+        case BC_E_CANCELLED: return "BC_E_CANCELLED";
     }
     return "BC_UNKNOWN";
 }
