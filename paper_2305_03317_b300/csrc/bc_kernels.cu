@@ -1296,17 +1296,29 @@ __device__ void phase_bc(const KParams& p, int b) {
         if (!mask_any<W>(vm)) continue;
         int cur = -1;
         double acc = 0.0;
-        for (int c = 0; c < K; ++c) {
-            if (!((vm[c >> 5] >> (c & 31)) & 1u)) continue;
-            const int s = __ldg(src + c);
-            if (s == (int)v) continue;
-            const int j = cj ? __ldg(cj + c) : 0;
-            if (j != cur) {
-                if (cur >= 0) p.job_bc[cur][v] = acc;
-                cur = j;
-                acc = p.job_bc[j][v];
+        // the row's dependencies four columns (one 32-byte sector) at a time, so
+        // that each sector is read once per thread, not once per column: rows of
+        // neighbouring threads do not stay in L1 between a thread's columns
+        constexpr int Q = K >= 4 ? 4 : 1;
+        for (int c0 = 0; c0 < K; c0 += Q) {
+            const uint32_t bits = (vm[c0 >> 5] >> (c0 & 31)) & ((1u << Q) - 1u);
+            if (!bits) continue;
+            unsigned long long d[Q];
+            load_terms<Q>(p.sig + (size_t)v * K + c0, d);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (!((bits >> i) & 1u)) continue;
+                const int c = c0 + i;
+                const int s = __ldg(src + c);
+                if (s == (int)v) continue;
+                const int j = cj ? __ldg(cj + c) : 0;
+                if (j != cur) {
+                    if (cur >= 0) p.job_bc[cur][v] = acc;
+                    cur = j;
+                    acc = p.job_bc[j][v];
+                }
+                acc += __longlong_as_double((long long)d[i]);
             }
-            acc += __longlong_as_double((long long)p.sig[(size_t)v * K + c]);
         }
         if (cur >= 0) p.job_bc[cur][v] = acc;
     }
@@ -1353,10 +1365,26 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
     active_mask<K>(p, b, act);
 
     // init A: clear masks and stamps, zero the first level slots and the batch flags
-    for (long long i = tid; i < (long long)p.n * W; i += nthr) {
-        p.V[i] = 0; p.F[0][i] = 0; p.F[1][i] = 0; p.F[2][i] = 0;
+    {
+        // 16-byte stores (the per-team arrays start 256-byte aligned); a scalar tail
+        const long long words = (long long)p.n * W, quads = words >> 2;
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (long long i = tid; i < quads; i += nthr) {
+            reinterpret_cast<uint4*>(p.V)[i] = z;
+            reinterpret_cast<uint4*>(p.F[0])[i] = z;
+            reinterpret_cast<uint4*>(p.F[1])[i] = z;
+            reinterpret_cast<uint4*>(p.F[2])[i] = z;
+        }
+        for (long long i = (quads << 2) + tid; i < words; i += nthr) {
+            p.V[i] = 0; p.F[0][i] = 0; p.F[1][i] = 0; p.F[2][i] = 0;
+        }
     }
-    for (long long i = tid; i < p.n; i += nthr) p.stamp[i] = -1;
+    {
+        const long long quads = (long long)p.n >> 2;
+        const int4 m1 = make_int4(-1, -1, -1, -1);
+        for (long long i = tid; i < quads; i += nthr) reinterpret_cast<int4*>(p.stamp)[i] = m1;
+        for (long long i = (quads << 2) + tid; i < p.n; i += nthr) p.stamp[i] = -1;
+    }
     if (tid < 3) {
         p.la.cnt[tid] = 0; p.la.hcnt[tid] = 0; p.la.dsum[tid] = 0; p.la.fulldeg[tid] = 0;
     }
