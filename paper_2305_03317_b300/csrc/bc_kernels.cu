@@ -900,11 +900,10 @@ __device__ void clear_level_masks(const KParams& p, uint32_t* F, int lev) {
     const long long s = p.la.start[lev], c = p.la.cnt[lev], hs = p.la.hstart[lev], hc = p.la.hcnt[lev];
     const long long nthr = (long long)p.team_blocks * blockDim.x;
     const long long tid = (long long)p.rank * blockDim.x + threadIdx.x;
-    for (long long i = tid; i < (c + hc) * W; i += nthr) {
-        const long long j = i / W;
-        const int t = (int)(i % W);
+    const uint32_t zero[W] = {};
+    for (long long j = tid; j < c + hc; j += nthr) {
         const int v = j < c ? p.ent[s + j] : p.hent[hs + (j - c)];
-        F[(size_t)v * W + t] = 0;
+        store_mask_full<W>(F, v, zero);  // the entry's W words in one store
     }
 }
 
