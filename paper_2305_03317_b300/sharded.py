@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import BC_OK, BCError, load, reduce_ranks, status_string
+from . import BC_E_CUDA, BC_OK, BCError, reduce_ranks, status_string
 
 
 def shard_of(order: np.ndarray, K: int, rank: int, world: int) -> np.ndarray:
@@ -70,16 +70,20 @@ def compute(graph, sources, out=None, group=None, stream=None, **opts):
                                     source_order=opts.get("source_order", 0))
     mine = shard_of(order, K, rank, world)
     run = dict(opts, batch_width=K, source_order=1)
-    part = torch.zeros(graph.n, dtype=torch.float64, device="cuda")
-    status = BC_OK
+    status, local_error = BC_OK, None
     try:
+        part = torch.zeros(graph.n, dtype=torch.float64, device="cuda")
         if len(mine):
             _, status = graph.compute(mine, out=part, stream=stream, **run)
     except BCError as err:
-        status = err.status
+        status, local_error = err.status, err
+    except Exception as err:  # anything else still reaches the other ranks as a failed status
+        status, local_error = BC_E_CUDA, err
     job = exchange_statuses(status, group, device="cuda")
     if job < 0:
-        raise BCError(job, f"a rank failed: {status_string(job)}")
+        if local_error is not None:
+            raise local_error
+        raise BCError(job, f"another rank failed: {status_string(job)}")
     parts = gather_partials(part, group)
     out = reduce_ranks(parts, out=out, stream=stream)
     return out, job
