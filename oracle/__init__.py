@@ -16,6 +16,10 @@ Contents:
     shortest path (tiny graphs only; undirected or directed, paths follow arcs);
     the definition
     BC(v) = sum_s sum_{t != s, v} sigma_st(v) / sigma_st written out.
+  * ``sum_dm1`` -- per source, the sum of (d(s,t) - 1) over reached t != s, by
+    breadth-first search alone (distances, no path counts; threads over
+    sources): the sum of the raw BC over all vertices, at any graph size;
+    ``sum_dm1_bits`` the same by bit-parallel search, 64 sources per pass.
   * ``relabel`` / ``validate`` -- the ingest rules (degree-descending stable
     relabelling; CSR validity) in their plain definitions.
   * ``wbc`` / ``wsource_detail`` -- weighted BC (positive integer arc
@@ -82,6 +86,10 @@ def _L():
             lib.oracle_source_ld.argtypes = [i32, P, P, i32, P, P, P, P]
             lib.oracle_bc_f64_threads.restype = ctypes.c_int
             lib.oracle_bc_f64_threads.argtypes = [i32, P, P, i32, P, P, ctypes.c_int]
+            lib.oracle_sum_dm1_threads.restype = ctypes.c_int
+            lib.oracle_sum_dm1_threads.argtypes = [i32, P, P, i32, P, P, ctypes.c_int]
+            lib.oracle_sum_dm1_bits.restype = ctypes.c_int
+            lib.oracle_sum_dm1_bits.argtypes = [i32, P, P, i32, P, P, ctypes.c_int]
             lib.oracle_relabel.restype = None
             lib.oracle_relabel.argtypes = [i32, P, P, P, P, P, P]
             lib.oracle_validate_csr.restype = ctypes.c_int
@@ -117,6 +125,31 @@ def bc(off, adj, sources, threads: int = 1) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle rc={rc}")
     return out[:n]
+
+
+def sum_dm1(off, adj, sources, threads: int = 1) -> np.ndarray:
+    """Per source s: sum over the vertices t != s reached from s of (d(s,t) - 1), by BFS
+    (int64).  Summed over a source list it equals the sum of the raw BC over all vertices."""
+    off, adj = _csr(off, adj)
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    n = off.shape[0] - 1
+    out = np.zeros(max(src.shape[0], 1), dtype=np.int64)
+    rc = _L().oracle_sum_dm1_threads(n, _p(off), _p(adj), src.shape[0], _p(src), _p(out), max(1, threads))
+    if rc:
+        raise ValueError(f"oracle rc={rc}")
+    return out[: src.shape[0]]
+
+
+def sum_dm1_bits(off, adj, sources, threads: int = 1) -> np.ndarray:
+    """sum_dm1 by bit-parallel breadth-first search, 64 sources per pass (for full-size graphs)."""
+    off, adj = _csr(off, adj)
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    n = off.shape[0] - 1
+    out = np.zeros(max(src.shape[0], 1), dtype=np.int64)
+    rc = _L().oracle_sum_dm1_bits(n, _p(off), _p(adj), src.shape[0], _p(src), _p(out), max(1, threads))
+    if rc:
+        raise ValueError(f"oracle rc={rc}")
+    return out[: src.shape[0]]
 
 
 def bc_ld(off, adj, sources) -> np.ndarray:

@@ -184,6 +184,162 @@ int oracle_bc_f64_threads(int32_t n, const int32_t* off, const int32_t* adj, int
     return rc;
 }
 
+/* ---------------- per-source path-length sums (breadth-first search only) ----------------
+ * For each source s: the sum over the vertices t != s reached from s of
+ * (d(s,t) - 1).  A shortest s-t path has d(s,t) - 1 interior vertices, and
+ * delta_s(v) is v's share of them over all t, so this equals the sum over
+ * v != s of delta_s(v): summed over a source list it is the sum of the raw BC
+ * over all vertices.  Distances only (no path counts), so it is cheap enough
+ * to check a full-size call; sources are split over threads. */
+typedef struct {
+    int32_t n;
+    const int32_t* off;
+    const int32_t* adj;
+    int32_t nsrc;
+    const int32_t* src;
+    int64_t* out;
+    int rc;
+} dsum_slice;
+
+static void* dsum_run(void* arg) {
+    dsum_slice* d = (dsum_slice*)arg;
+    const int32_t n = d->n;
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!dist || !queue) { d->rc = -4; free(dist); free(queue); return NULL; }
+    for (int32_t i = 0; i < d->nsrc; ++i) {
+        const int32_t s = d->src[i];
+        if (s < 0 || s >= n) { d->rc = -3; break; }
+        for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+        int32_t head = 0, tail = 0;
+        dist[s] = 0;
+        queue[tail++] = s;
+        int64_t sum = 0;
+        while (head < tail) {
+            const int32_t v = queue[head++];
+            if (v != s) sum += dist[v] - 1;
+            for (int32_t e = d->off[v]; e < d->off[v + 1]; ++e) {
+                const int32_t w = d->adj[e];
+                if (dist[w] < 0) { dist[w] = dist[v] + 1; queue[tail++] = w; }
+            }
+        }
+        d->out[i] = sum;
+    }
+    free(dist); free(queue);
+    return NULL;
+}
+
+/* out[i] for src[i]; returns 0, -3 for a source out of range, -4 when memory runs out. */
+int oracle_sum_dm1_threads(int32_t n, const int32_t* off, const int32_t* adj, int32_t nsrc, const int32_t* src,
+                           int64_t* out, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nsrc) nthreads = nsrc > 0 ? nsrc : 1;
+    dsum_slice* sl = (dsum_slice*)calloc((size_t)nthreads, sizeof(dsum_slice));
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!sl || !th) { free(sl); free(th); return -4; }
+    int32_t base = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        const int32_t cnt = nsrc / nthreads + (t < nsrc % nthreads ? 1 : 0);
+        sl[t].n = n; sl[t].off = off; sl[t].adj = adj; sl[t].nsrc = cnt; sl[t].src = src + base;
+        sl[t].out = out + base;
+        base += cnt;
+        pthread_create(&th[t], NULL, dsum_run, &sl[t]);
+    }
+    int rc = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        if (sl[t].rc) rc = sl[t].rc;
+    }
+    free(sl); free(th);
+    return rc;
+}
+
+/* The same sums, 64 sources per breadth-first pass: bit j of a vertex's word
+ * marks source j of the group.  Each level pushes the frontier words along
+ * every arc; a vertex's bits that are new at level L add L - 1 to their
+ * sources' sums.  Groups of sources are split over threads, each with its
+ * own words. */
+typedef struct {
+    int32_t n;
+    const int32_t* off;
+    const int32_t* adj;
+    int32_t nsrc;
+    const int32_t* src;
+    int64_t* out;
+    int rc;
+} dsum64_slice;
+
+static void* dsum64_run(void* arg) {
+    dsum64_slice* d = (dsum64_slice*)arg;
+    const int32_t n = d->n;
+    uint64_t* seen = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    uint64_t* front = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    uint64_t* next = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    if (!seen || !front || !next) { d->rc = -4; free(seen); free(front); free(next); return NULL; }
+    for (int32_t g0 = 0; g0 < d->nsrc; g0 += 64) {
+        const int32_t gs = d->nsrc - g0 < 64 ? d->nsrc - g0 : 64;
+        memset(seen, 0, sizeof(uint64_t) * (size_t)n);
+        memset(front, 0, sizeof(uint64_t) * (size_t)n);
+        for (int32_t j = 0; j < gs; ++j) {
+            const int32_t s = d->src[g0 + j];
+            if (s < 0 || s >= n) { d->rc = -3; goto done; }
+            seen[s] |= 1ull << j;
+            front[s] |= 1ull << j;
+            d->out[g0 + j] = 0;
+        }
+        for (int32_t level = 1;; ++level) {
+            memset(next, 0, sizeof(uint64_t) * (size_t)n);
+            int any = 0;
+            for (int32_t v = 0; v < n; ++v) {
+                const uint64_t f = front[v];
+                if (!f) continue;
+                for (int32_t e = d->off[v]; e < d->off[v + 1]; ++e) next[d->adj[e]] |= f;
+            }
+            for (int32_t w = 0; w < n; ++w) {
+                uint64_t nw = next[w] & ~seen[w];
+                front[w] = nw;
+                if (!nw) continue;
+                any = 1;
+                seen[w] |= nw;
+                while (nw) {
+                    const int j = __builtin_ctzll(nw);
+                    nw &= nw - 1;
+                    d->out[g0 + j] += level - 1;
+                }
+            }
+            if (!any) break;
+        }
+    }
+done:
+    free(seen); free(front); free(next);
+    return NULL;
+}
+
+int oracle_sum_dm1_bits(int32_t n, const int32_t* off, const int32_t* adj, int32_t nsrc, const int32_t* src,
+                        int64_t* out, int nthreads) {
+    const int32_t groups = (nsrc + 63) / 64;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > groups) nthreads = groups > 0 ? groups : 1;
+    dsum64_slice* sl = (dsum64_slice*)calloc((size_t)nthreads, sizeof(dsum64_slice));
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!sl || !th) { free(sl); free(th); return -4; }
+    int32_t gbase = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        const int32_t cnt = groups / nthreads + (t < groups % nthreads ? 1 : 0);
+        const int32_t b = gbase * 64, e = (gbase + cnt) * 64 < nsrc ? (gbase + cnt) * 64 : nsrc;
+        sl[t].n = n; sl[t].off = off; sl[t].adj = adj; sl[t].nsrc = e - b; sl[t].src = src + b; sl[t].out = out + b;
+        gbase += cnt;
+        pthread_create(&th[t], NULL, dsum64_run, &sl[t]);
+    }
+    int rc = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        if (sl[t].rc) rc = sl[t].rc;
+    }
+    free(sl); free(th);
+    return rc;
+}
+
 /* ---------------- ingest: relabelling and validation ---------------- */
 
 static const int32_t* g_deg_for_cmp;

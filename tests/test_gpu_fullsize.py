@@ -7,8 +7,10 @@ benchmark times, on outputs the oracle can compute in bounded time.
 * R-MAT scale 22, edge factor 16: the benchmark's first 128-source batch
   (K = 128, the width the benchmark runs; the first 128 of its 4096 sources
   once grouped by hub distances, as bc_compute groups them) against the oracle
-  on the host cores; and three of its batches (the first two and the last of
-  the grouped order) in one call on two teams, as the benchmark runs its 32.
+  on the host cores; three of its batches (the first two and the last of
+  the grouped order) in one call on two teams, as the benchmark runs its 32;
+  and the benchmark's whole 4096-source call by its BC sum (against the
+  oracle's breadth-first path-length sums) and its exact zeros.
 * The 2000-graph pool of uneven R-MAT graphs: sampled items (the smallest
   graph, the largest all-sources graph, the largest graph) recorded into one
   plan as the benchmark records the pool, each against the oracle.
@@ -92,6 +94,26 @@ def test_rmat22_batches_on_two_teams_with_the_last_grouped_batch(bc):
     s = G.stats()
     assert s["batches"] == 3 and s["teams"] == 2
     assert_bc_close(out.cpu().numpy(), oracle.bc(g.off, g.adj, src, threads=THREADS))
+
+
+def test_rmat22_benchmark_call_sums_and_zeros(bc):
+    # the benchmark's whole call (4096 grouped sources, 32 batches of 128 on two
+    # teams) checked by properties that hold at any size: the raw BC summed over
+    # all vertices is the sum over sources of (d(s,t) - 1) over reached t (the
+    # oracle's breadth-first distances), and a vertex of degree at most 1 lies
+    # inside no shortest path
+    g = bcgen.rmat(22, 16, 1)
+    G = bc.Graph(g.off, g.adj)
+    src = bcgen.sample_sources(g, 4096, 1)
+    out, st = G.compute(src)
+    assert st == bc.BC_OK
+    s = G.stats()
+    assert s["batches"] == 32 and s["batch_width"] == 128 and s["teams"] == 2
+    got = out.cpu().numpy()
+    want = float(oracle.sum_dm1_bits(g.off, g.adj, src, threads=THREADS).sum())
+    assert abs(got.sum() - want) <= 1e-9 * want
+    assert np.all(got >= 0)
+    assert np.all(got[np.diff(g.off) <= 1] == 0)
 
 
 def test_pool_of_2000_sampled_items_in_one_plan(bc):

@@ -229,6 +229,24 @@ def test_grid_dag_arcs_are_half_the_component_arcs():
         assert d["reached"] == g.n and d["edag"] * 2 == g.m
 
 
+@pytest.mark.parametrize("g", [bcgen.rmat(10, 8, 3), bcgen.grid(20, 23, 0.1, 4),
+                               bcgen.disjoint_union(bcgen.path(7), bcgen.star(9), bcgen.empty_graph(3)),
+                               bcgen.orient(bcgen.rmat(9, 8, 2), seed=2)], ids=lambda g: g.name)
+def test_sum_dm1_against_scipy_distances(g):
+    # the BFS-only path-length sum, from scipy's own unweighted shortest paths
+    a = sp.csr_matrix((np.ones(g.m), g.adj, g.off), shape=(g.n, g.n))
+    src = np.concatenate([np.arange(0, g.n, 3), [0, 0]]).astype(np.int32)  # repeats count per entry
+    d = shortest_path(a, directed=True, unweighted=True, indices=src)
+    want = np.array([np.sum(np.where(np.isfinite(row) & (row > 0), row - 1, 0)) for row in d], dtype=np.int64)
+    got = oracle.sum_dm1(g.off, g.adj, src, threads=3)
+    assert np.array_equal(got, want)
+    assert np.array_equal(oracle.sum_dm1_bits(g.off, g.adj, src, threads=2), want)
+    many = np.resize(src, 150)  # several 64-source groups, the last ragged, over 2 threads
+    assert np.array_equal(oracle.sum_dm1_bits(g.off, g.adj, many, threads=2), oracle.sum_dm1(g.off, g.adj, many))
+    # summed over the sources it is the sum of the raw BC over all vertices
+    assert oracle.bc(g.off, g.adj, src).sum() == pytest.approx(float(got.sum()), rel=1e-12)
+
+
 def test_long_double_and_double_agree_where_counts_fit():
     g = bcgen.rmat(11, 8, 2)
     srcs = bcgen.sample_sources(g, 64, 3)
