@@ -122,7 +122,7 @@ typedef struct {
     float beta;              /* back to push when frontier vertices * beta < non-isolated vertices (0 = 24) */
     int32_t group_vertices;  /* rows of degree <= 1024 handled per warp task, 1..32 (0 = 32); results do not
                                 depend on it (sums follow fixed 1024-arc chunks of each row) */
-    int32_t blocks_per_sm;   /* persistent-grid residency (0 = occupancy maximum) */
+    int32_t blocks_per_sm;   /* persistent-grid residency, also of the per-source form (0 = occupancy maximum) */
     int64_t barrier_budget;  /* device cycles a grid-barrier wait may spin before BC_E_TIMEOUT
                                 (0 = about 20 s; tests may set 1 to force a timeout) */
     int32_t trace;           /* 1 = record a device timestamp at the end of every grid-wide phase */
@@ -143,6 +143,14 @@ typedef struct {
                                 grouping depends on the graph and the source list alone, so results stay the
                                 same for every batch width and direction setting.  The landmark levels are
                                 kept with the graph ([n][32] uint16), built on the first grouped call */
+    int32_t deep_form;       /* bc_compute / bc_compute_ex: 1 = always the batched traversal; 2 = the per-source
+                                form for graphs of large diameter: every block of one launch runs whole sources
+                                alone, level by level with block barriers only, so that thousands of levels of a
+                                few thousand vertices do not each cost grid-wide barriers; 0 = auto: 2 when
+                                batch_width is 0 and the graph's BFS depth is known to be at least 512 levels
+                                (from an earlier call, or from a one-source probe that the first call with at
+                                least 64 sources on a graph of mean degree at most 8 runs), else 1.  Same
+                                arithmetic, same sums in the same order: the two forms give the same bits */
 } bc_options;
 
 /*
@@ -273,6 +281,7 @@ typedef struct {
                                 call's sources of E_dag(s) = #{arcs (v, w): d_s(w) = d_s(v) + 1} (last launch) */
     int64_t reached;         /* unweighted calls: sum over the call's sources of the vertices reached, source
                                 included (last launch) */
+    int32_t deep_sources;    /* sources run in the per-source form of bc_options.deep_form (0: batched form) */
 } bc_run_stats;
 bc_status bc_last_run_stats(const bc_graph* g, bc_run_stats* st);
 

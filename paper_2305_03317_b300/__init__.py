@@ -48,7 +48,8 @@ class bc_options(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("direction", ctypes.c_int32), ("alpha", ctypes.c_float),
                 ("beta", ctypes.c_float), ("group_vertices", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("barrier_budget", ctypes.c_int64), ("trace", ctypes.c_int32), ("teams", ctypes.c_int32),
-                ("dense_min", ctypes.c_int32), ("source_order", ctypes.c_int32)]
+                ("dense_min", ctypes.c_int32), ("source_order", ctypes.c_int32),
+                ("deep_form", ctypes.c_int32)]
 
 
 class bc_run_stats(ctypes.Structure):
@@ -58,7 +59,7 @@ class bc_run_stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_float), ("teams", ctypes.c_int32), ("order_ms", ctypes.c_float),
                 ("arcs_visited", ctypes.c_int64), ("rows_visited", ctypes.c_int64),
                 ("mask_arcs", ctypes.c_int64), ("mask_lanes", ctypes.c_int64), ("dag_arcs", ctypes.c_int64),
-                ("reached", ctypes.c_int64)]
+                ("reached", ctypes.c_int64), ("deep_sources", ctypes.c_int32)]
 
 
 class bc_item(ctypes.Structure):
@@ -265,7 +266,7 @@ class Graph:
     def compute(self, sources, out=None, stream=None, batch_width: int = 0, direction: int = 0,
                 alpha: float = 0.0, beta: float = 0.0, group_vertices: int = 0, blocks_per_sm: int = 0,
                 barrier_budget: int = 0, trace: bool = False, teams: int = 0, dense_min: int = 0,
-                source_order: int = 0):
+                source_order: int = 0, deep_form: int = 0):
         """BC over ``sources`` (host numpy or device int32 tensor). Returns (out, status)."""
         import torch
         if out is None:
@@ -274,7 +275,7 @@ class Graph:
             sources = np.ascontiguousarray(sources, dtype=np.int32)
         nsrc = int(sources.shape[0]) if isinstance(sources, np.ndarray) else int(sources.numel())
         opt = bc_options(batch_width, direction, alpha, beta, group_vertices, blocks_per_sm, barrier_budget,
-                         1 if trace else 0, teams, dense_min, source_order)
+                         1 if trace else 0, teams, dense_min, source_order, deep_form)
         s = load().bc_compute_ex(self._h, _ptr(sources) if nsrc else None, nsrc, _ptr(out) if self.n else None,
                                  _stream_handle(stream), ctypes.byref(opt))
         _check(s)

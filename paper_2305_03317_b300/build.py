@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["bc_api.cu", "bc_kernels.cu", "ingest.cu", "noalloc.cu", "pagerank.cu", "weighted.cu"]
+SOURCES = ["bc_api.cu", "bc_kernels.cu", "deep.cu", "ingest.cu", "noalloc.cu", "pagerank.cu", "weighted.cu"]
 LIB = os.path.join(HERE, "libbc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -253,6 +253,8 @@ struct bc_graph {
     int lm_levels = -1;         // levels of that BFS; -1 = not built
     // PageRank facts and buffers (under mu, built on first use): row classes,
     // the chunk prefix of the long rows, rank / scratch / chunk sums / counters
+    int depth_seen = -1;  // deepest BFS (levels) of any completed traversal on the graph; -1 = none yet
+    DevBuf deep_state, deep_delta, deep_aux;  // per-source form: per-block slices, dependency rows, status
     int pr_cls[2] = {-1, -1};
     long long pr_nchunks = 0;
     DevBuf pr_ccum, pr_rank, pr_scratch, pr_cpart, pr_carr, pr_ctl, pr_small;
@@ -446,6 +448,7 @@ static bc_status check_opts(const bc_options& o) {
     if (o.blocks_per_sm < 0 || o.barrier_budget < 0 || o.alpha < 0 || o.beta < 0 || o.teams < 0 || o.dense_min < 0)
         return fail(BC_E_INVALID_ARG, "negative option value");
     if (o.source_order < 0 || o.source_order > 2) return fail(BC_E_INVALID_ARG, "source_order must be 0, 1 or 2");
+    if (o.deep_form < 0 || o.deep_form > 2) return fail(BC_E_INVALID_ARG, "deep_form must be 0, 1 or 2");
     return BC_OK;
 }
 
@@ -653,6 +656,10 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
         }
         if (ro.need_ext) return fail(BC_E_SIGMA_RANGE, "path count beyond the extended range");
         if (ext) s.ext_batches = nbatch;
+        {
+            std::lock_guard<std::mutex> lk(g->state_mu);
+            g->depth_seen = std::max(g->depth_seen, ro.ctl.max_levels);
+        }
         if (stats) *stats = s;
         if (K_out) *K_out = K;
         if (ext_out) *ext_out = ext;
@@ -1107,6 +1114,7 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->ioff, st);
     buf_release(g->iadj, st);
     buf_release(g->landmark, st);
+    for (DevBuf* b : {&g->deep_state, &g->deep_delta, &g->deep_aux}) buf_release(*b, st);
     for (DevBuf* b : {&g->pr_ccum, &g->pr_rank, &g->pr_scratch, &g->pr_cpart, &g->pr_carr, &g->pr_ctl, &g->pr_small})
         buf_release(*b, st);
     for (DevBuf* b : {&g->w, &g->wdist, &g->wsig, &g->winv, &g->wdel,
@@ -1459,6 +1467,172 @@ static bc_status group_sources(bc_graph* g, const int* d_src, int nsrc, cudaStre
     return BC_OK;
 }
 
+// ------------------------------------------------------------------ per-source form (deep graphs)
+constexpr int kDeepMinDepth = 512;  // automatic rule: BFS depth (levels) from which the per-source form runs
+
+// The per-source form (deep.cu) over a source list (original ids, device):
+// rounds of R sources, each one launch of `blocks` blocks (one source at a
+// time per block) writing R dependency rows, then the rows added to bc_rel
+// (relabelled, cleared first) in list order.  Memory: per block 32 bytes per
+// vertex plus its level starts; per source of a round 8 bytes per vertex;
+// together within min(30% of free memory, 24 GB).
+static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_options& o, cudaStream_t st,
+                          double* bc_rel, bc_run_stats* out) {
+    const int n = g->n;
+    bc_status hr = ensure_heavy(g, st);
+    if (hr != BC_OK) return hr;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+    // the widest block whose resident grid still covers the sources
+    int threads = 256, per_sm = deep_blocks_per_sm(256);
+    for (int t : {1024, 512}) {
+        const int b = deep_blocks_per_sm(t);
+        if (b > 0 && (long long)b * sms >= nsrc) {
+            threads = t;
+            per_sm = b;
+            break;
+        }
+    }
+    if (per_sm < 1) return fail(BC_E_CUDA, "per-source kernel cannot be resident (occupancy 0)");
+    if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
+    const long long stride = ((long long)n + 31) & ~31LL;
+    const int slots = (int)std::min<long long>(kLevelSlots, (long long)n + 3);
+    const double per_block = 32.0 * (double)stride + 4.0 * (double)slots, per_src = 8.0 * (double)n;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        fr = 0;
+    }
+    const double budget = std::min(0.3 * (double)(fr + g->deep_state.bytes + g->deep_delta.bytes), 24e9);
+    long long blocks = std::min<long long>((long long)per_sm * sms, nsrc);
+    blocks = std::min<long long>(blocks, (long long)(budget / (per_block + per_src)));
+    if (blocks < 1) return fail(BC_E_NOMEM, "per-source form: no room for one block's state");
+    long long R = (long long)((budget - (double)blocks * per_block) / per_src);
+    R = std::max<long long>(blocks, std::min<long long>(R, nsrc));
+    const size_t b8 = sizeof(double) * (size_t)blocks * (size_t)stride;
+    const size_t b4 = sizeof(int) * (size_t)blocks * (size_t)stride;
+    const size_t state_bytes = 2 * b8 + 4 * b4 + sizeof(int) * (size_t)blocks * (size_t)slots;
+    const size_t aux_bytes = 2 * sizeof(unsigned long long) + sizeof(int) * ((size_t)nsrc + 2 * (size_t)R + 1);
+    if (!buf_ensure(g->deep_state, state_bytes, st) || !buf_ensure(g->deep_delta, sizeof(double) * (size_t)R * n, st) ||
+        !buf_ensure(g->deep_aux, aux_bytes, st))
+        return fail(BC_E_NOMEM, "per-source form buffers");
+    char* sp = (char*)g->deep_state.p;
+    char* ap = (char*)g->deep_aux.p;
+    unsigned long long* ctr = (unsigned long long*)ap;
+    int* src_rel = (int*)(ap + 2 * sizeof(unsigned long long));
+    int* status = src_rel + nsrc;
+    int* depth = status + R;
+    int* bad = depth + R;
+    cudaError_t e = cudaMemsetAsync(ap, 0, aux_bytes, st);
+    if (e == cudaSuccess) e = launch_map_sources(d_src, nsrc, (const int*)g->inv.p, n, 1, src_rel, nsrc, bad, st);
+    int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "per-source form setup");
+    if (hbad) return fail(BC_E_SOURCE, "a source id is outside [0, %d)", n);
+    if ((e = cudaMemsetAsync(bc_rel, 0, sizeof(double) * (size_t)n, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    DeepParams p{};
+    p.n = n;
+    p.off = (const int*)g->off.p;
+    p.adj = (const int*)g->adj.p;
+    p.ioff = g->directed ? (const int*)g->ioff.p : nullptr;
+    p.iadj = g->directed ? (const int*)g->iadj.p : nullptr;
+    p.n_heavy = g->n_heavy;
+    p.stride = stride;
+    p.sm = (unsigned long long*)sp;
+    p.rho = (double*)(sp + b8);
+    p.dist = (int*)(sp + 2 * b8);
+    p.order = (int*)(sp + 2 * b8 + b4);
+    p.se = (int*)(sp + 2 * b8 + 2 * b4);
+    p.re = (int*)(sp + 2 * b8 + 3 * b4);
+    p.lvl = (int*)(sp + 2 * b8 + 4 * b4);
+    p.level_slots = slots;
+    p.delta = (double*)g->deep_delta.p;
+    p.status = status;
+    p.depth = depth;
+    p.dag_pairs = ctr;
+    p.reached_pairs = ctr + 1;
+    bc_run_stats s{};
+    s.batch_width = 1;
+    s.batches = nsrc;
+    s.grid_blocks = (int)blocks;
+    s.teams = (int)blocks;
+    s.deep_sources = nsrc;
+    s.kernel_launches = 1;  // source mapping
+    bool inexact = false;
+    std::vector<int> hst((size_t)R), hdp((size_t)R);
+    for (long long r0 = 0; r0 < nsrc; r0 += R) {
+        const int cnt = (int)std::min<long long>(R, nsrc - r0);
+        p.src = src_rel + r0;
+        p.nsrc = cnt;
+        cudaEvent_t ev[2];
+        cudaEventCreate(&ev[0]);
+        cudaEventCreate(&ev[1]);
+        cudaEventRecord(ev[0], st);
+        e = launch_deep(p, (int)std::min<long long>(blocks, cnt), threads, st);
+        cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = launch_deep_accumulate(p.delta, cnt, n, bc_rel, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), status, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hdp.data(), depth, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        float ms = 0.f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        if (e != cudaSuccess) return cuda_fail(e, "per-source kernel");
+        s.kernel_ms += ms;
+        s.kernel_launches += 2;
+        for (int i = 0; i < cnt; ++i) {
+            if (hst[i] == (ERR_LIMIT << 8)) return fail(BC_E_LIMIT, "BFS deeper than %d levels", kMaxLevel);
+            if (!(hst[i] & BST_DONE)) return fail(BC_E_CUDA, "internal: source %lld not completed", r0 + i);
+            inexact |= (hst[i] & BST_INEXACT) != 0;
+            s.max_levels = std::max(s.max_levels, hdp[i]);
+        }
+    }
+    unsigned long long hc[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(hc, ctr, sizeof hc, cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "per-source counters");
+    s.dag_arcs = (int64_t)hc[0];
+    s.reached = (int64_t)hc[1];
+    {
+        std::lock_guard<std::mutex> lk(g->state_mu);
+        g->depth_seen = std::max(g->depth_seen, s.max_levels);
+    }
+    *out = s;
+    return inexact ? BC_W_SIGMA_INEXACT : BC_OK;
+}
+
+// Automatic choice of the per-source form (bc_options.deep_form = 0): the
+// graph's depth as seen by earlier traversals; on a sparse graph with no
+// depth yet, one source (relabelled vertex 0, the highest degree) is run in
+// the per-source form first, into `scratch` (n doubles), to learn it.
+static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t st, double* scratch,
+                      bc_run_stats* pre) {
+    if (o.deep_form == 1) return false;
+    if (o.deep_form == 2) return true;
+    if (o.batch_width != 0) return false;
+    int seen;
+    {
+        std::lock_guard<std::mutex> lk(g->state_mu);
+        seen = g->depth_seen;
+    }
+    if (seen < 0 && nsrc >= 64 && g->n_nz >= 4096 && g->m <= 8LL * g->n_nz) {
+        bc_run_stats ps{};
+        bc_options po;
+        memset(&po, 0, sizeof po);
+        if (run_deep(g, (const int*)g->perm.p, 1, po, st, scratch, &ps) >= 0) {
+            seen = ps.max_levels;
+            pre->kernel_launches += ps.kernel_launches;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return seen >= kDeepMinDepth;
+}
+
 bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream,
                         const bc_options* opt) {
     if (!g) return fail(BC_E_INVALID_ARG, "graph is NULL");
@@ -1471,6 +1645,7 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
     bc_status cs = check_opts(o);
     if (cs != BC_OK) return cs;
     cudaStream_t st = (cudaStream_t)stream;
+    const bc_options given = o;  // the form choice follows the caller's knobs, not tuned ones
     apply_tuning(g, nsrc, o);
     std::lock_guard<std::mutex> lk(g->mu);
     g->last_stream = st;
@@ -1517,7 +1692,11 @@ bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, doubl
     }
     std::vector<double*> jb{(double*)w->bc.p};
     bc_run_stats stats{};
-    bc_status r = run_jobs(g, w, d_src, nsrc, o, 1, jb, nullptr, false, st, &stats, nullptr, nullptr, nullptr);
+    bc_status r;
+    if (want_deep(g, nsrc, given, st, (double*)w->bc.p, &pre))
+        r = run_deep(g, d_src, nsrc, o, st, (double*)w->bc.p, &stats);
+    else
+        r = run_jobs(g, w, d_src, nsrc, o, 1, jb, nullptr, false, st, &stats, nullptr, nullptr, nullptr);
     stats.kernel_launches += pre.kernel_launches;
     stats.order_ms = pre.kernel_ms;
     if (r >= 0) {

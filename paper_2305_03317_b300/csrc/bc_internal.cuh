@@ -106,6 +106,41 @@ struct KParams {
     int level_slots;           // entries of each level array (>= levels + 3)
 };
 
+// ------------------------------------------------------------------ extended-range arithmetic
+// Path count as m * 2^e with a 64-bit integer mantissa; values below 2^64 keep
+// e == 0 and are exact.  A nonzero e implies the top mantissa bit is set.
+__device__ __forceinline__ void xu_add(unsigned long long& am, int& ae, unsigned long long xm, int xe) {
+    if (xm == 0) return;
+    if (am == 0) { am = xm; ae = xe; return; }
+    if (xe > ae) {
+        int d = xe - ae;
+        am = d >= 64 ? 0ull : (am >> d);
+        ae = xe;
+    } else if (xe < ae) {
+        int d = ae - xe;
+        xm = d >= 64 ? 0ull : (xm >> d);
+    }
+    unsigned long long s = am + xm;
+    if (s < am) {  // carry out of bit 63
+        s = (s >> 1) | (1ull << 63);
+        ae += 1;
+    }
+    am = s;
+}
+
+// Real value r * 2^e (r a double) summed with alignment to the larger exponent.
+__device__ __forceinline__ void xd_add(double& ar, int& ae, double xr, int xe) {
+    if (xr == 0.0) return;
+    if (ar == 0.0) { ar = xr; ae = xe; return; }
+    if (xe > ae) {
+        ar = scalbn(ar, ae - xe);
+        ae = xe;
+        ar += xr;
+    } else {
+        ar += scalbn(xr, xe - ae);
+    }
+}
+
 // ------------------------------------------------------------------ barrier
 // Barrier over the blocks of one team (a plain block barrier for one-block
 // teams); errors are read from the launch-wide control block.
@@ -206,6 +241,43 @@ cudaError_t launch_pagerank(int n, const int* off, const int* roff, const int* r
                             long long nchunks, const int* ccum, double* cpart, int* carr,
                             double delta, double beta, int max_iter, double* rank, double* scratch, Ctl* ctl, int* iters,
                             double* diff_out, int* go, long long budget, int blocks, cudaStream_t st);
+
+// Graphs of large diameter (deep.cu): one source per block, block barriers
+// only.  Per-block slices of `stride` elements: dist, order, the extended-form
+// path count (sm mantissa, se exponent) and rho (rho mantissa, re exponent);
+// lvl: level_slots level starts per block.  delta: [nsrc][n] dependencies
+// (0 where unreached and at the source).  status[i]: BST_DONE | BST_INEXACT,
+// or ERR_LIMIT << 8; depth[i]: levels of source i.  The counters add sum
+// E_dag and sum n_s over the launch.
+struct DeepParams {
+    int n;
+    const int* off;
+    const int* adj;
+    const int* ioff;   // directed: in-CSR for the path-count sums; null = undirected
+    const int* iadj;
+    int n_heavy;       // rows above kChunk arcs: ids [0, n_heavy), summed per chunk
+    const int* src;    // [nsrc] relabelled ids
+    int nsrc;
+    long long stride;
+    int* dist;
+    int* order;
+    unsigned long long* sm;
+    int* se;
+    double* rho;
+    int* re;
+    int* lvl;
+    int level_slots;   // lvl entries per block (>= deepest level + 3)
+    double* delta;
+    int* status;
+    int* depth;
+    unsigned long long* dag_pairs;
+    unsigned long long* reached_pairs;
+};
+// blocks x threads (a multiple of 32, at most 1024); block b owns slice b
+cudaError_t launch_deep(const DeepParams& p, int blocks, int threads, cudaStream_t st);
+int deep_blocks_per_sm(int threads);  // resident blocks of k_deep per SM (0 on error)
+// bc[v] += delta[0][v] + ... + delta[nsrc-1][v], in that order
+cudaError_t launch_deep_accumulate(const double* delta, int nsrc, long long n, double* bc, cudaStream_t st);
 
 // Thread-local detail returned by bc_last_error() (bc_api.cu)
 void set_last_error(const char* msg);

@@ -159,41 +159,6 @@ __device__ __forceinline__ uint32_t pick(const uint32_t (&m)[W], int t) {
     return x;
 }
 
-// ------------------------------------------------------------------ extended-range arithmetic
-// Path count as m * 2^e with a 64-bit integer mantissa; values below 2^64 keep
-// e == 0 and are exact.  A nonzero e implies the top mantissa bit is set.
-__device__ __forceinline__ void xu_add(unsigned long long& am, int& ae, unsigned long long xm, int xe) {
-    if (xm == 0) return;
-    if (am == 0) { am = xm; ae = xe; return; }
-    if (xe > ae) {
-        int d = xe - ae;
-        am = d >= 64 ? 0ull : (am >> d);
-        ae = xe;
-    } else if (xe < ae) {
-        int d = ae - xe;
-        xm = d >= 64 ? 0ull : (xm >> d);
-    }
-    unsigned long long s = am + xm;
-    if (s < am) {  // carry out of bit 63
-        s = (s >> 1) | (1ull << 63);
-        ae += 1;
-    }
-    am = s;
-}
-
-// Real value r * 2^e (r a double) summed with alignment to the larger exponent.
-__device__ __forceinline__ void xd_add(double& ar, int& ae, double xr, int xe) {
-    if (xr == 0.0) return;
-    if (ar == 0.0) { ar = xr; ae = xe; return; }
-    if (xe > ae) {
-        ar = scalbn(ar, ae - xe);
-        ae = xe;
-        ar += xr;
-    } else {
-        ar += scalbn(xr, xe - ae);
-    }
-}
-
 // ------------------------------------------------------------------ accumulation
 // A running sum per (owner, column): FWD path counts (u64, or 64-bit mantissa
 // with exponent), BWD sums of rho (double bits, or double with exponent).

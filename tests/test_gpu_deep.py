@@ -1,0 +1,160 @@
+"""GPU parity of the per-source form for graphs of large diameter (deep.cu).
+
+The per-source form runs each source alone in one block with the batched
+traversal's arithmetic and order of summation (extended-form path counts
+summed over in-neighbours in CSR order, per 1024-arc chunk on heavy
+undirected rows; rho sums over out-neighbours in CSR order; dependencies
+added to BC in source-list order), so its BC must equal the batched form's
+bit for bit, and the oracle within the parity tolerance of the batched tests.
+"""
+import numpy as np
+import pytest
+
+import bcgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def bc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_03317_b300 as m
+    m.load()
+    return m
+
+
+def close(got, want, rel=REL):
+    zero = want == 0
+    assert np.all(got[zero] == 0), "exact zeros must stay zero"
+    err = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    assert np.all(err[~zero] <= rel), f"max rel err {err[~zero].max()}"
+
+
+def both_forms(bc, G, src, **kw):
+    out, st_deep = G.compute(src, deep_form=2, **kw)
+    deep = out.cpu().numpy().copy()
+    s_deep = G.stats()
+    out, st_b = G.compute(src, deep_form=1, **kw)
+    batched = out.cpu().numpy().copy()
+    s_b = G.stats()
+    assert st_deep == st_b
+    assert s_deep["deep_sources"] == len(src) and s_b["deep_sources"] == 0
+    assert np.array_equal(deep.view(np.uint64), batched.view(np.uint64))
+    assert s_deep["max_levels"] == s_b["max_levels"]
+    assert s_deep["dag_arcs"] == s_b["dag_arcs"] and s_deep["reached"] == s_b["reached"]
+    return deep, st_deep
+
+
+@pytest.mark.parametrize("g", [bcgen.grid(64, 64, 0.05, 3), bcgen.random_tree(3000, 2),
+                               bcgen.disjoint_union(bcgen.path(300), bcgen.empty_graph(5), bcgen.cycle(401),
+                                                    bcgen.grid(20, 30, 0.1, 4)),
+                               bcgen.rmat(12, 8, 1)], ids=lambda g: g.name)
+def test_deep_form_equals_batched_and_oracle(bc, g):
+    src = bcgen.sample_sources(g, 150, 7)
+    src = np.concatenate([src, src[:5]])  # repeated sources count once per occurrence
+    G = bc.Graph(g.off, g.adj)
+    got, st = both_forms(bc, G, src)
+    if g.name.startswith("grid64"):  # corner-to-corner counts near C(126, 63) ~ 2^122
+        assert st == bc.BC_W_SIGMA_INEXACT
+        close(got, oracle.bc_ld(g.off, g.adj, src).astype(np.float64))
+    else:
+        assert st == bc.BC_OK
+        close(got, oracle.bc(g.off, g.adj, src))
+
+
+def test_deep_form_blocks_reused_across_sources(bc):
+    """One block per SM: every block runs several sources in turn on the same slices."""
+    g = bcgen.grid(40, 50, 0.05, 9)
+    src = np.arange(g.n, dtype=np.int32)
+    G = bc.Graph(g.off, g.adj)
+    got, st = both_forms(bc, G, src, blocks_per_sm=1)
+    assert G.stats()["grid_blocks"] < len(src)
+    close(got, oracle.bc_ld(g.off, g.adj, src).astype(np.float64))
+
+
+def test_deep_form_extended_range(bc):
+    """Path counts up to C(238,119) ~ 2^233 on a full grid: the extended form, in both forms."""
+    g = bcgen.grid(120, 120, 0.0)
+    src = np.array([0, 121, 120 * 60 + 60, g.n - 1], np.int32)
+    G = bc.Graph(g.off, g.adj)
+    got, st = both_forms(bc, G, src)
+    assert st == bc.BC_W_SIGMA_INEXACT
+    close(got, oracle.bc_ld(g.off, g.adj, src).astype(np.float64))
+
+
+def test_deep_form_heavy_rows(bc):
+    """Rows above 1024 arcs: chunked sums in the same chunk order as the batched form."""
+    g = bcgen.rmat(14, 32, 2)
+    assert int(np.diff(g.off).max()) > 2 * 1024
+    src = bcgen.sample_sources(g, 70, 3)
+    G = bc.Graph(g.off, g.adj)
+    got, st = both_forms(bc, G, src)
+    close(got, oracle.bc(g.off, g.adj, src))
+
+
+def test_deep_form_directed(bc):
+    g = bcgen.orient(bcgen.rmat(13, 48, 3), 2, 0.5)  # heavy out-rows and in-rows
+    assert int(np.diff(g.off).max()) > 1024
+    src = bcgen.sample_sources(g, 80, 4)
+    G = bc.Graph(g.off, g.adj, directed=True)
+    got, st = both_forms(bc, G, src)
+    close(got, oracle.bc(g.off, g.adj, src))
+    n = 500
+    dpath = bcgen.directed_csr(n, np.arange(n - 1), np.arange(1, n))
+    D = bc.Graph(dpath.off, dpath.adj, directed=True)
+    got, _ = both_forms(bc, D, np.arange(n, dtype=np.int32))
+    close(got, np.array([i * (n - 1 - i) for i in range(n)], np.float64), rel=1e-12)
+
+
+def test_deep_form_closed_forms_and_limit(bc):
+    n = 65000  # depth 64999 from an end: inside the 65534-level limit
+    g = bcgen.path(n)
+    G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(np.array([0], np.int32), deep_form=2)
+    assert st == bc.BC_OK and G.stats()["max_levels"] == n
+    want = np.array([0.0] + [float(n - 1 - v) for v in range(1, n - 1)] + [0.0])
+    assert np.array_equal(out.cpu().numpy(), want)
+    deep = bcgen.path(70000)
+    D = bc.Graph(deep.off, deep.adj)
+    with pytest.raises(bc.BCError) as ei:
+        D.compute(np.array([0], np.int32), deep_form=2)
+    assert ei.value.status == bc.BC_E_LIMIT
+    s0, nd = 35000, deep.n
+    mid, st = D.compute(np.array([s0], np.int32), deep_form=2)
+    v = np.arange(nd, dtype=np.float64)
+    want_mid = np.where(v < s0, v, nd - 1 - v)
+    want_mid[s0] = 0.0
+    assert st == bc.BC_OK and np.array_equal(mid.cpu().numpy(), want_mid)
+    with pytest.raises(bc.BCError) as ei:
+        G.compute(np.array([0, n], np.int32), deep_form=2)
+    assert ei.value.status == bc.BC_E_SOURCE
+    with pytest.raises(bc.BCError):
+        G.compute(np.array([0], np.int32), deep_form=3)
+
+
+def test_automatic_form_choice(bc):
+    """Auto: a sparse graph whose probe finds 512+ levels runs per source; shallow ones stay batched."""
+    g = bcgen.grid(300, 300, 0.05, 5)  # depth about 600 from a corner region
+    src = bcgen.sample_sources(g, 128, 2)
+    G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(src)
+    auto = out.cpu().numpy().copy()
+    s = G.stats()
+    assert s["deep_sources"] == len(src) and s["max_levels"] >= 512
+    out, _ = G.compute(src, deep_form=1)
+    assert np.array_equal(auto.view(np.uint64), out.cpu().numpy().view(np.uint64))
+    out, _ = G.compute(src, batch_width=64)  # a width given by the caller keeps the batched form
+    assert G.stats()["deep_sources"] == 0
+    small = bcgen.grid(100, 100, 0.05, 5)  # about 200 levels
+    S = bc.Graph(small.off, small.adj)
+    S.compute(bcgen.sample_sources(small, 128, 2))
+    assert S.stats()["deep_sources"] == 0
+    r = bcgen.rmat(12, 8, 1)
+    R = bc.Graph(r.off, r.adj)
+    R.compute(bcgen.sample_sources(r, 128, 2))
+    assert R.stats()["deep_sources"] == 0
