@@ -9,8 +9,10 @@ Metric: BC traversed edges/s = sources x m / time, m = CSR arcs (each
 undirected edge counted twice).  `value` times bc_compute with sources and
 output already on the device; `e2e` times the same call from pinned host
 sources to a pinned host copy of the result.  The roofline object reports the
-persistent traversal kernel against the measured HBM copy bandwidth using the
-algorithmic byte model B_s = 8m/k + m/4 + 16 E_dag(s) + 24 n_s per source.
+traversal kernel against the measured HBM copy bandwidth using an algorithmic
+byte model per source: B_s = 8m/k + m/4 + 16 E_dag(s) + 24 n_s for the batched
+persistent kernel (width k), B_s = 16m + 16 E_dag(s) + 40 n_s for the
+per-source kernel the library picks on deep graphs (--workload grid).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload rmat22|rmat12|grid|serve] [--sources S] [--batch-width K]
@@ -46,6 +48,7 @@ def parse():
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--ef", type=float, default=16)
     ap.add_argument("--sources", type=int, default=0)
+    ap.add_argument("--grid-side", type=int, default=1024, help="grid: vertices per side")
     ap.add_argument("--batch-width", type=int, default=0)
     ap.add_argument("--direction", type=int, default=0)
     ap.add_argument("--source-order", type=int, default=0,
@@ -78,10 +81,12 @@ def make_workload(a):
         desc = dict(workload="rmat12_ef8_all_sources", graph="undirected R-MAT scale 12, edge factor 8, seed 1",
                     sources=int(g.n), source_sampling="every vertex")
     else:  # grid
-        g = bcgen.grid(1024, 1024, 0.05, 1)
+        side = a.grid_side
+        g = bcgen.grid(side, side, 0.05, 1)
         S = a.sources or 256
         src = bcgen.sample_sources(g, S, 1)
-        desc = dict(workload="grid1024x1024_rm5pct", graph="1024x1024 4-neighbour grid, 5% of edges removed (seed 1)",
+        desc = dict(workload=f"grid{side}x{side}_rm5pct",
+                    graph=f"{side}x{side} 4-neighbour grid, 5% of edges removed (seed 1)",
                     sources=int(len(src)), source_sampling="uniform without replacement over degree>=1, seed 1")
     desc.update(n=g.n, m=g.m)
     return g, src, desc
@@ -99,17 +104,20 @@ def measured_peak():
 
 
 def committed_traffic(kernel_name, workload):
-    """Per-source DRAM bytes from the committed ncu summary, or None if absent/stale."""
+    """Per-source DRAM bytes from the committed ncu summary, or None if absent or if any source file
+    of the kernel has changed since the capture (sha256 per file)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
-        d = json.load(open(p))
-        src = open(os.path.join(ROOT, "paper_2305_03317_b300", "csrc", "bc_kernels.cu"), "rb").read()
-        if d.get("kernel_source_sha256") != hashlib.sha256(src).hexdigest():
+        e = json.load(open(p)).get("entries", {}).get(f"{kernel_name}|{workload}")
+        if e is None:
             return None
-        e = d.get("entries", {}).get(f"{kernel_name}|{workload}")
-        return None if e is None else float(e["dram_bytes_per_source"])
+        for name, sha in e["sources"].items():
+            src = open(os.path.join(ROOT, "paper_2305_03317_b300", "csrc", name), "rb").read()
+            if hashlib.sha256(src).hexdigest() != sha:
+                return None
+        return float(e["dram_bytes_per_source"])
     except Exception:
         return None
 
@@ -271,7 +279,9 @@ def run_ours(a):
     stream = torch.cuda.current_stream()
     opts = dict(batch_width=a.batch_width, direction=a.direction, source_order=a.source_order)
     tuned = None
-    if a.batch_width == 0 and not a.no_tune:
+    # the grid's levels are narrow and thousands deep: the library picks its per-source form
+    # there, which has no knobs to tune
+    if a.batch_width == 0 and not a.no_tune and a.workload != "grid":
         t_tune = time.perf_counter()
         tuned = G.autotune(src)  # per size bucket; knobs left at 0 below come from it
         tuned["seconds"] = round(time.perf_counter() - t_tune, 2)
@@ -339,22 +349,30 @@ def run_ours(a):
         if dist:
             dist.destroy_process_group()
         return
-    # roofline of the persistent traversal kernel
+    # roofline of the traversal kernel
     K = stats["batch_width"]
     nb = stats["batches"]
+    deep = stats["deep_sources"] > 0
     # this rank's launch: sum over its sources of E_dag(s) and n_s, counted exactly by the kernel
     dag, reached = stats["dag_arcs"], stats["reached"]
-    model_bytes = nb * (8.0 * g.m + K * g.m / 4.0) + 16.0 * dag + 24.0 * reached
+    if deep:  # per source: rows and level tags in both sweeps, a term per DAG arc each way, 40 B per vertex
+        model_bytes = n_rank_src * 16.0 * g.m + 16.0 * dag + 40.0 * reached
+        model_txt = "per source 16m + 16*E_dag + 40*n_s (per-source form)"
+        kname = "k_deep"
+    else:
+        model_bytes = nb * (8.0 * g.m + K * g.m / 4.0) + 16.0 * dag + 24.0 * reached
+        model_txt = "per source 8m/k + m/4 + 16*E_dag + 24*n_s"
+        kname = f"bc_persistent<{K}>"
     kms = float(np.mean(kern_ms))
     peak, peak_src = measured_peak()
     achieved = model_bytes / (kms / 1e3) / 1e9
-    kname = f"bc_persistent<{K}>"
     tr = committed_traffic(kname, desc["workload"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": dict(desc, step="one bc_compute over all sources on the resident graph",
+                       form="per-source (deep graphs)" if deep else "batched",
                        batch_width=K, batches=nb, levels=stats["max_levels"], pull_levels=stats["pull_levels"],
                        push_levels=stats["push_levels"], teams=stats["teams"], ingest_s=round(ingest_s, 3),
                        source_grouping_ms=round(stats["order_ms"], 3),
@@ -369,7 +387,7 @@ def run_ours(a):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (tr * n_rank_src) if tr is not None else None,
                      "kernel": kname, "kernel_ms": kms, "model_bytes": model_bytes,
-                     "model": f"per source 8m/k + m/4 + 16*E_dag + 24*n_s over the launch's {n_rank_src} sources; "
+                     "model": f"{model_txt} over the launch's {n_rank_src} sources; "
                               f"E_dag={dag / n_rank_src:.0f}, n_s={reached / n_rank_src:.0f} per source (exact "
                               f"kernel counts: sum E_dag {dag}, sum n_s {reached})", "peak_source": peak_src},
         "e2e": {"value": len(src) * g.m / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(4 * len(src)),

@@ -147,10 +147,11 @@ typedef struct {
                                 form for graphs of large diameter: every block of one launch runs whole sources
                                 alone, level by level with block barriers only, so that thousands of levels of a
                                 few thousand vertices do not each cost grid-wide barriers; 0 = auto: 2 when
-                                batch_width is 0 and the graph's BFS depth is known to be at least 512 levels
-                                (from an earlier call, or from a one-source probe that the first call with at
-                                least 64 sources on a graph of mean degree at most 8 runs), else 1.  Same
-                                arithmetic, same sums in the same order: the two forms give the same bits */
+                                batch_width is 0, the graph's BFS depth is known to be at least 48 levels of
+                                at most 8192 vertices on average (from an earlier call, or from a one-source
+                                probe that the first call with at least 64 sources on a graph of mean degree at
+                                most 8 runs) and the memory budget leaves a block per source or SM, else 1.
+                                Same arithmetic, same sums in the same order: the two forms give the same bits */
 } bc_options;
 
 /*

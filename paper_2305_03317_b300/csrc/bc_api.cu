@@ -254,7 +254,12 @@ struct bc_graph {
     // PageRank facts and buffers (under mu, built on first use): row classes,
     // the chunk prefix of the long rows, rank / scratch / chunk sums / counters
     int depth_seen = -1;  // deepest BFS (levels) of any completed traversal on the graph; -1 = none yet
-    DevBuf deep_state, deep_delta, deep_aux;  // per-source form: per-block slices, dependency rows, status
+    // per-source form: per-block records, per-block BFS order and level starts, dependency rows, status;
+    // the records of blocks [0, deep_blocks) at stride deep_stride hold tags of epochs below deep_epoch
+    DevBuf deep_state, deep_order, deep_delta, deep_aux;
+    unsigned int deep_epoch = 1;
+    long long deep_stride = -1;
+    long long deep_blocks = 0;
     int pr_cls[2] = {-1, -1};
     long long pr_nchunks = 0;
     DevBuf pr_ccum, pr_rank, pr_scratch, pr_cpart, pr_carr, pr_ctl, pr_small;
@@ -1114,7 +1119,7 @@ bc_status bc_graph_destroy(bc_graph* g) {
     buf_release(g->ioff, st);
     buf_release(g->iadj, st);
     buf_release(g->landmark, st);
-    for (DevBuf* b : {&g->deep_state, &g->deep_delta, &g->deep_aux}) buf_release(*b, st);
+    for (DevBuf* b : {&g->deep_state, &g->deep_order, &g->deep_delta, &g->deep_aux}) buf_release(*b, st);
     for (DevBuf* b : {&g->pr_ccum, &g->pr_rank, &g->pr_scratch, &g->pr_cpart, &g->pr_carr, &g->pr_ctl, &g->pr_small})
         buf_release(*b, st);
     for (DevBuf* b : {&g->w, &g->wdist, &g->wsig, &g->winv, &g->wdel,
@@ -1468,24 +1473,28 @@ static bc_status group_sources(bc_graph* g, const int* d_src, int nsrc, cudaStre
 }
 
 // ------------------------------------------------------------------ per-source form (deep graphs)
-constexpr int kDeepMinDepth = 512;  // automatic rule: BFS depth (levels) from which the per-source form runs
 
 // The per-source form (deep.cu) over a source list (original ids, device):
 // rounds of R sources, each one launch of `blocks` blocks (one source at a
 // time per block) writing R dependency rows, then the rows added to bc_rel
-// (relabelled, cleared first) in list order.  Memory: per block 32 bytes per
+// (relabelled, cleared first) in list order.  Memory: per block 44 bytes per
 // vertex plus its level starts; per source of a round 8 bytes per vertex;
 // together within min(30% of free memory, 24 GB).
-static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_options& o, cudaStream_t st,
-                          double* bc_rel, bc_run_stats* out) {
+struct DeepPlan {
+    int threads = 0, sms = 0;
+    long long blocks = 0, R = 0, stride = 0;
+    int slots = 0;
+};
+
+// Launch shape of the per-source form: the widest block (1024, 512 or 256
+// threads) whose resident grid still covers the sources, as many blocks as
+// are resident (or wanted), and rounds of R sources within the memory budget.
+static bc_status deep_plan(const bc_graph* g, int nsrc, const bc_options& o, DeepPlan* pl) {
     const int n = g->n;
-    bc_status hr = ensure_heavy(g, st);
-    if (hr != BC_OK) return hr;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms < 1) sms = 1;
-    // the widest block whose resident grid still covers the sources
     int threads = 256, per_sm = deep_blocks_per_sm(256);
     for (int t : {1024, 512}) {
         const int b = deep_blocks_per_sm(t);
@@ -1499,26 +1508,47 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
     if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
     const long long stride = ((long long)n + 31) & ~31LL;
     const int slots = (int)std::min<long long>(kLevelSlots, (long long)n + 3);
-    const double per_block = 32.0 * (double)stride + 4.0 * (double)slots, per_src = 8.0 * (double)n;
+    const double per_block = 44.0 * (double)stride + 4.0 * (double)slots, per_src = 8.0 * (double)n;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
         cudaGetLastError();
         fr = 0;
     }
-    const double budget = std::min(0.3 * (double)(fr + g->deep_state.bytes + g->deep_delta.bytes), 24e9);
+    const double held = (double)(g->deep_state.bytes + g->deep_order.bytes + g->deep_delta.bytes);
+    const double budget = std::min(0.3 * ((double)fr + held), 24e9);
     long long blocks = std::min<long long>((long long)per_sm * sms, nsrc);
     blocks = std::min<long long>(blocks, (long long)(budget / (per_block + per_src)));
     if (blocks < 1) return fail(BC_E_NOMEM, "per-source form: no room for one block's state");
     long long R = (long long)((budget - (double)blocks * per_block) / per_src);
     R = std::max<long long>(blocks, std::min<long long>(R, nsrc));
-    const size_t b8 = sizeof(double) * (size_t)blocks * (size_t)stride;
-    const size_t b4 = sizeof(int) * (size_t)blocks * (size_t)stride;
-    const size_t state_bytes = 2 * b8 + 4 * b4 + sizeof(int) * (size_t)blocks * (size_t)slots;
+    R = std::min<long long>(R, blocks * 0x8000LL);  // epochs of one launch stay below 2^16
+    pl->threads = threads;
+    pl->sms = sms;
+    pl->blocks = blocks;
+    pl->R = R;
+    pl->stride = stride;
+    pl->slots = slots;
+    return BC_OK;
+}
+
+static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_options& o, cudaStream_t st,
+                          double* bc_rel, bc_run_stats* out) {
+    const int n = g->n;
+    bc_status hr = ensure_heavy(g, st);
+    if (hr != BC_OK) return hr;
+    DeepPlan pl;
+    if ((hr = deep_plan(g, nsrc, o, &pl)) != BC_OK) return hr;
+    const int threads = pl.threads, slots = pl.slots;
+    const long long blocks = pl.blocks, R = pl.R, stride = pl.stride;
+    const size_t rec_bytes = sizeof(DeepRec) * (size_t)blocks * (size_t)stride;
+    const size_t ord_bytes = (sizeof(int) + sizeof(int2)) * (size_t)blocks * (size_t)stride;
+    const size_t lvl_bytes = sizeof(int) * (size_t)blocks * (size_t)slots;
     const size_t aux_bytes = 2 * sizeof(unsigned long long) + sizeof(int) * ((size_t)nsrc + 2 * (size_t)R + 1);
-    if (!buf_ensure(g->deep_state, state_bytes, st) || !buf_ensure(g->deep_delta, sizeof(double) * (size_t)R * n, st) ||
-        !buf_ensure(g->deep_aux, aux_bytes, st))
+    void* old_state = g->deep_state.p;
+    if (!buf_ensure(g->deep_state, rec_bytes, st) || !buf_ensure(g->deep_order, ord_bytes + lvl_bytes, st) ||
+        !buf_ensure(g->deep_delta, sizeof(double) * (size_t)R * n, st) || !buf_ensure(g->deep_aux, aux_bytes, st))
         return fail(BC_E_NOMEM, "per-source form buffers");
-    char* sp = (char*)g->deep_state.p;
+    if (g->deep_state.p != old_state) g->deep_stride = -1;  // fresh memory: clear before use
     char* ap = (char*)g->deep_aux.p;
     unsigned long long* ctr = (unsigned long long*)ap;
     int* src_rel = (int*)(ap + 2 * sizeof(unsigned long long));
@@ -1541,13 +1571,10 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
     p.iadj = g->directed ? (const int*)g->iadj.p : nullptr;
     p.n_heavy = g->n_heavy;
     p.stride = stride;
-    p.sm = (unsigned long long*)sp;
-    p.rho = (double*)(sp + b8);
-    p.dist = (int*)(sp + 2 * b8);
-    p.order = (int*)(sp + 2 * b8 + b4);
-    p.se = (int*)(sp + 2 * b8 + 2 * b4);
-    p.re = (int*)(sp + 2 * b8 + 3 * b4);
-    p.lvl = (int*)(sp + 2 * b8 + 4 * b4);
+    p.rec = (DeepRec*)g->deep_state.p;
+    p.order = (int*)g->deep_order.p;
+    p.orow = (int2*)((char*)g->deep_order.p + sizeof(int) * (size_t)blocks * (size_t)stride);
+    p.lvl = (int*)((char*)g->deep_order.p + ord_bytes);
     p.level_slots = slots;
     p.delta = (double*)g->deep_delta.p;
     p.status = status;
@@ -1565,13 +1592,27 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
     std::vector<int> hst((size_t)R), hdp((size_t)R);
     for (long long r0 = 0; r0 < nsrc; r0 += R) {
         const int cnt = (int)std::min<long long>(R, nsrc - r0);
+        const int nb = (int)std::min<long long>(blocks, cnt);
+        const unsigned iters = (unsigned)((cnt + nb - 1) / nb);  // sources (epochs) per block
+        if (g->deep_stride != stride || g->deep_blocks < nb || g->deep_epoch + iters - 1 > 0xFFFFu) {
+            // records of another layout, fresh memory or every epoch used: tag 0 everywhere
+            if ((e = cudaMemsetAsync(p.rec, 0, rec_bytes, st)) != cudaSuccess) return cuda_fail(e, "memset");
+            g->deep_stride = stride;
+            g->deep_blocks = blocks;
+            g->deep_epoch = 1;
+            s.kernel_launches += 1;
+        }
+        p.epoch0 = g->deep_epoch;
+        g->deep_epoch += iters;
         p.src = src_rel + r0;
         p.nsrc = cnt;
+        if ((e = cudaMemsetAsync(p.delta, 0, sizeof(double) * (size_t)cnt * (size_t)n, st)) != cudaSuccess)
+            return cuda_fail(e, "memset");
         cudaEvent_t ev[2];
         cudaEventCreate(&ev[0]);
         cudaEventCreate(&ev[1]);
         cudaEventRecord(ev[0], st);
-        e = launch_deep(p, (int)std::min<long long>(blocks, cnt), threads, st);
+        e = launch_deep(p, nb, threads, st);
         cudaEventRecord(ev[1], st);
         if (e == cudaSuccess) e = launch_deep_accumulate(p.delta, cnt, n, bc_rel, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), status, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st);
@@ -1605,10 +1646,15 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
     return inexact ? BC_W_SIGMA_INEXACT : BC_OK;
 }
 
-// Automatic choice of the per-source form (bc_options.deep_form = 0): the
-// graph's depth as seen by earlier traversals; on a sparse graph with no
-// depth yet, one source (relabelled vertex 0, the highest degree) is run in
-// the per-source form first, into `scratch` (n doubles), to learn it.
+// Automatic choice of the per-source form (bc_options.deep_form = 0), for a
+// width left to the library: the graph's depth as seen by earlier
+// traversals (on a sparse graph with none yet, one source, relabelled vertex
+// 0, is first run in the per-source form into `scratch`, n doubles, to learn
+// it).  The per-source form runs when the BFS is deep (kDeepMinDepth levels
+// or more), its levels are narrow (on average at most kDeepMaxWidth
+// vertices), and the memory budget leaves a block for every source or SM.
+constexpr int kDeepMinDepth = 48;
+constexpr int kDeepMaxWidth = 8192;
 static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t st, double* scratch,
                       bc_run_stats* pre) {
     if (o.deep_form == 1) return false;
@@ -1619,7 +1665,7 @@ static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t s
         std::lock_guard<std::mutex> lk(g->state_mu);
         seen = g->depth_seen;
     }
-    if (seen < 0 && nsrc >= 64 && g->n_nz >= 4096 && g->m <= 8LL * g->n_nz) {
+    if (seen < 0 && nsrc >= 64 && g->n_nz >= 256 && g->m <= 8LL * g->n_nz) {
         bc_run_stats ps{};
         bc_options po;
         memset(&po, 0, sizeof po);
@@ -1630,7 +1676,13 @@ static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t s
             cudaGetLastError();
         }
     }
-    return seen >= kDeepMinDepth;
+    if (seen < kDeepMinDepth || (double)g->n_nz > (double)kDeepMaxWidth * seen) return false;
+    DeepPlan pl;
+    if (deep_plan(g, nsrc, o, &pl) != BC_OK) {
+        cudaGetLastError();
+        return false;
+    }
+    return pl.blocks >= std::min<long long>(nsrc, pl.sms);
 }
 
 bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream,

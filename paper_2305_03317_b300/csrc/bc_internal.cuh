@@ -243,12 +243,27 @@ cudaError_t launch_pagerank(int n, const int* off, const int* roff, const int* r
                             double* diff_out, int* go, long long budget, int blocks, cudaStream_t st);
 
 // Graphs of large diameter (deep.cu): one source per block, block barriers
-// only.  Per-block slices of `stride` elements: dist, order, the extended-form
-// path count (sm mantissa, se exponent) and rho (rho mantissa, re exponent);
-// lvl: level_slots level starts per block.  delta: [nsrc][n] dependencies
-// (0 where unreached and at the source).  status[i]: BST_DONE | BST_INEXACT,
-// or ERR_LIMIT << 8; depth[i]: levels of source i.  The counters add sum
-// E_dag and sum n_s over the launch.
+// only.  Per-block slices of `stride` entries: rec (one 32-byte record per
+// vertex: the extended-form path count sm x 2^se, rho x 2^re and the level
+// tag, so that one sector holds what a neighbour test reads), order (the
+// vertices in BFS order) and orow (their out-row bounds); lvl: level_slots
+// level starts per block.  A tag is
+// epoch << 16 | level; tags of older epochs read as unseen, so a slice needs
+// no reset between sources: source j (0-based) of block b in a launch uses
+// epoch epoch0 + j, and the host keeps every epoch of a launch below 2^16,
+// clearing the records (tag 0) when the count wraps.  delta: [nsrc][n]
+// dependencies, cleared by the host (only reached vertices other than the
+// source are written).  status[i]: BST_DONE | BST_INEXACT, or ERR_LIMIT << 8;
+// depth[i]: levels of source i.  The counters add sum E_dag and sum n_s over
+// the launch.
+struct __align__(32) DeepRec {
+    unsigned long long sm;  // path count mantissa
+    double rho;             // rho mantissa
+    unsigned int tag;       // epoch << 16 | level
+    int se;                 // path count exponent
+    int re;                 // rho exponent
+    int pad;
+};
 struct DeepParams {
     int n;
     const int* off;
@@ -259,21 +274,18 @@ struct DeepParams {
     const int* src;    // [nsrc] relabelled ids
     int nsrc;
     long long stride;
-    int* dist;
+    DeepRec* rec;
     int* order;
-    unsigned long long* sm;
-    int* se;
-    double* rho;
-    int* re;
+    int2* orow;        // [k]: out-row bounds (off[v], off[v + 1]) of order[k], stored by its claimer
     int* lvl;
     int level_slots;   // lvl entries per block (>= deepest level + 3)
+    unsigned int epoch0;
     double* delta;
     int* status;
     int* depth;
     unsigned long long* dag_pairs;
     unsigned long long* reached_pairs;
 };
-// blocks x threads (a multiple of 32, at most 1024); block b owns slice b
 cudaError_t launch_deep(const DeepParams& p, int blocks, int threads, cudaStream_t st);
 int deep_blocks_per_sm(int threads);  // resident blocks of k_deep per SM (0 on error)
 // bc[v] += delta[0][v] + ... + delta[nsrc-1][v], in that order

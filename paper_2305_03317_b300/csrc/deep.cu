@@ -8,6 +8,15 @@
 // with block barriers only: the levels of all sources in flight advance
 // independently, and nothing waits on another block.
 //
+// State per block and vertex is one 32-byte record (path count, rho, their
+// exponents and the level tag), so the neighbour test and the term it selects
+// come from one sector, and the records of kWin arcs of a row are loaded
+// together before they are used, in CSR order.  Level tags carry an epoch:
+// a new source needs no clearing of its block's slice.  The forward sweep
+// is one pass per level: each vertex of level l + 1 sums its count over its
+// level-l neighbours and, in the same sweep of its row, claims its unseen
+// neighbours for level l + 2.
+//
 // The arithmetic is the batched traversal's, in the same order, so results
 // are bit for bit those of bc_compute's batched form:
 //   * path counts in the extended form (64-bit mantissa x 2^e, exact and equal
@@ -19,7 +28,7 @@
 //     CSR order (chunked the same way for rows above kChunk arcs), and
 //     delta = sigma * S, in the extended form's scaling;
 //   * BC adds the sources' dependencies in the order of the source list
-//     (k_deep_accumulate, one thread per vertex).
+//     (k_sum_dependency_rows, one thread per vertex).
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -29,25 +38,36 @@ namespace bcx {
 namespace {
 
 constexpr int kDeepMaxThreads = 1024;
+constexpr int kWin = 4;  // arcs of a row whose records are loaded together (divides kChunk)
+static_assert(kChunk % kWin == 0, "windows must not straddle chunks");
 
-// Path count of w (level l + 1): the extended-form sum over the in-row of w
-// of the counts at level l, per kChunk-arc chunk when `chunked`.
-__device__ __forceinline__ void deep_sigma(const int* __restrict__ rowp, int rb, int rend, bool chunked,
-                                           const int* dist, const unsigned long long* sm, const int* se, int l,
-                                           unsigned long long& am, int& ae, unsigned long long& dag) {
-    const int step = chunked ? kChunk : (rend - rb);
-    for (int c0 = rb; c0 < rend; c0 += step) {
-        const int c1 = c0 + step < rend ? c0 + step : rend;
-        unsigned long long cm = 0ull;
-        int ce = 0;
-        for (int e = c0; e < c1; ++e) {
-            const int u = rowp[e];
-            if (dist[u] == l) {
-                xu_add(cm, ce, sm[u], se[u]);
-                ++dag;
-            }
+__device__ __forceinline__ bool unseen(unsigned tag, unsigned E) { return (tag & 0xFFFF0000u) != E; }
+
+// Path-count view of a record: {tag, se} and sm (one sector).
+__device__ __forceinline__ void rec_fwd(const DeepRec* r, unsigned& tag, int& se, unsigned long long& sm) {
+    const uint2 q = *reinterpret_cast<const uint2*>(&r->tag);
+    tag = q.x;
+    se = (int)q.y;
+    sm = r->sm;
+}
+
+// Claim the vertices u[j] whose tags t[j] read as unseen for level `lv`: the
+// compare-and-swaps are issued together, then the winners append themselves
+// (with their out-row bounds ob[j]) to the level list.
+__device__ __forceinline__ void claim_win(const int (&u)[kWin], const unsigned (&t)[kWin], const int2 (&ob)[kWin],
+                                          DeepRec* rec, unsigned E, int lv, int* order, int2* orow, int base,
+                                          int* rel) {
+    bool won[kWin];
+#pragma unroll
+    for (int j = 0; j < kWin; ++j)
+        won[j] = unseen(t[j], E) && atomicCAS(&rec[u[j]].tag, t[j], E | (unsigned)lv) == t[j];
+#pragma unroll
+    for (int j = 0; j < kWin; ++j) {
+        if (won[j]) {
+            const int k = base + atomicAdd(rel, 1);
+            order[k] = u[j];
+            orow[k] = ob[j];
         }
-        xu_add(am, ae, cm, ce);
     }
 }
 
@@ -57,40 +77,38 @@ __global__ void __launch_bounds__(kDeepMaxThreads) k_deep(DeepParams p) {
     __shared__ unsigned long long s_dag, s_reached;
     const int tid = threadIdx.x, bd = blockDim.x;
     const long long b = blockIdx.x;
-    int* dist = p.dist + b * p.stride;
+    DeepRec* rec = p.rec + b * p.stride;
     int* order = p.order + b * p.stride;
-    unsigned long long* sm = p.sm + b * p.stride;
-    int* se = p.se + b * p.stride;
-    double* rho = p.rho + b * p.stride;
-    int* re = p.re + b * p.stride;
+    int2* orow = p.orow + b * p.stride;
     int* lvl = p.lvl + b * (long long)p.level_slots;
     const bool directed = p.ioff != nullptr;
     if (tid == 0) { s_dag = 0; s_reached = 0; }
-    for (int i = blockIdx.x; i < p.nsrc; i += gridDim.x) {
+    for (int i = blockIdx.x, j = 0; i < p.nsrc; i += gridDim.x, ++j) {
+        const unsigned E = (p.epoch0 + (unsigned)j) << 16;
         const int s = p.src[i];
         double* dl = p.delta + (size_t)i * (size_t)p.n;
-        for (int v = tid; v < p.n; v += bd) {
-            dist[v] = -1;
-            dl[v] = 0.0;
-        }
         if (tid == 0) {
             s_rel[0] = s_rel[1] = s_rel[2] = 0;
             s_flags = 0;
-        }
-        __syncthreads();
-        if (tid == 0) {
             order[0] = s;
-            dist[s] = 0;
-            sm[s] = 1ull;
-            se[s] = 0;
+            orow[0] = make_int2(p.off[s], p.off[s + 1]);
+            rec[s].sm = 1ull;
+            rec[s].se = 0;
+            rec[s].tag = E;  // level 0
             lvl[0] = 0;
             lvl[1] = 1;
         }
         __syncthreads();
-        // level 1: the out-neighbours of the source
+        // level 1: the out-neighbours of the source, one arc per thread
         for (int e = p.off[s] + tid; e < p.off[s + 1]; e += bd) {
             const int w = p.adj[e];
-            if (dist[w] < 0 && atomicCAS(&dist[w], -1, 1) == -1) order[1 + atomicAdd(&s_rel[2], 1)] = w;
+            const unsigned t = rec[w].tag;
+            const int2 ob = make_int2(p.off[w], p.off[w + 1]);
+            if (unseen(t, E) && atomicCAS(&rec[w].tag, t, E | 1u) == t) {
+                const int k = 1 + atomicAdd(&s_rel[2], 1);
+                order[k] = w;
+                orow[k] = ob;
+            }
         }
         __syncthreads();
         int beg = 1, end = 1 + s_rel[2], L = 0;
@@ -110,41 +128,71 @@ __global__ void __launch_bounds__(kDeepMaxThreads) k_deep(DeepParams p) {
             }
             int* rel = &s_rel[l % 3];
             if (tid == 0) s_rel[(l + 1) % 3] = 0;  // last read after the barrier ending pass l - 2
+            const unsigned want = E | (unsigned)l;
             for (int k = beg + tid; k < end; k += bd) {
                 const int w = order[k];
-                const bool chunked = !directed && w < p.n_heavy;
+                const int2 orw = orow[k];
+                const int* __restrict__ radj = directed ? p.iadj : p.adj;
+                const int rb = directed ? p.ioff[w] : orw.x;
+                const int rend = directed ? p.ioff[w + 1] : orw.y;
+                const int step = (!directed && w < p.n_heavy) ? kChunk : (rend - rb);
                 unsigned long long am = 0ull;
                 int ae = 0;
-                if (directed) {
-                    deep_sigma(p.iadj, p.ioff[w], p.ioff[w + 1], false, dist, sm, se, l, am, ae, dag);
-                    for (int e = p.off[w]; e < p.off[w + 1]; ++e) {
-                        const int u = p.adj[e];
-                        if (dist[u] < 0 && atomicCAS(&dist[u], -1, l + 2) == -1) order[end + atomicAdd(rel, 1)] = u;
-                    }
-                } else {
-                    // one sweep of the row: level-l neighbours add to the count,
-                    // unseen ones are claimed for level l + 2
-                    const int rb = p.off[w], rend = p.off[w + 1];
-                    const int step = chunked ? kChunk : (rend - rb);
-                    for (int c0 = rb; c0 < rend; c0 += step) {
-                        const int c1 = c0 + step < rend ? c0 + step : rend;
-                        unsigned long long cm = 0ull;
-                        int ce = 0;
-                        for (int e = c0; e < c1; ++e) {
-                            const int u = p.adj[e];
-                            const int du = dist[u];
-                            if (du == l) {
-                                xu_add(cm, ce, sm[u], se[u]);
-                                ++dag;
-                            } else if (du < 0 && atomicCAS(&dist[u], -1, l + 2) == -1) {
-                                order[end + atomicAdd(rel, 1)] = u;
+                for (int c0 = rb; c0 < rend; c0 += step) {
+                    const int c1 = c0 + step < rend ? c0 + step : rend;
+                    unsigned long long cm = 0ull;
+                    int ce = 0;
+                    for (int e = c0; e < c1; e += kWin) {
+                        int u[kWin];
+                        unsigned t[kWin];
+                        int se[kWin];
+                        unsigned long long sm[kWin];
+                        int2 ob[kWin];
+#pragma unroll
+                        for (int jj = 0; jj < kWin; ++jj) u[jj] = e + jj < c1 ? radj[e + jj] : -1;
+#pragma unroll
+                        for (int jj = 0; jj < kWin; ++jj) {
+                            if (u[jj] >= 0) {
+                                rec_fwd(rec + u[jj], t[jj], se[jj], sm[jj]);
+                                // out-row bounds, ready in case this arc claims u (undirected rows)
+                                ob[jj] = directed ? make_int2(0, 0) : make_int2(p.off[u[jj]], p.off[u[jj] + 1]);
+                            } else {
+                                t[jj] = E | 0xFFFFu;  // reads as seen, at no level in use
+                                se[jj] = 0;
+                                sm[jj] = 0ull;
+                                ob[jj] = make_int2(0, 0);
                             }
                         }
-                        xu_add(am, ae, cm, ce);
+                        // in CSR order: level-l neighbours add to the count
+#pragma unroll
+                        for (int jj = 0; jj < kWin; ++jj) {
+                            if (t[jj] == want) {
+                                xu_add(cm, ce, sm[jj], se[jj]);
+                                ++dag;
+                            }
+                        }
+                        // undirected rows are also the out-rows: claim their unseen neighbours
+                        if (!directed) claim_win(u, t, ob, rec, E, l + 2, order, orow, end, rel);
+                    }
+                    xu_add(am, ae, cm, ce);
+                }
+                if (directed) {
+                    for (int e = orw.x; e < orw.y; e += kWin) {
+                        int u[kWin];
+                        unsigned t[kWin];
+                        int2 ob[kWin];
+#pragma unroll
+                        for (int jj = 0; jj < kWin; ++jj) u[jj] = e + jj < orw.y ? p.adj[e + jj] : -1;
+#pragma unroll
+                        for (int jj = 0; jj < kWin; ++jj) {
+                            t[jj] = u[jj] >= 0 ? rec[u[jj]].tag : E;
+                            ob[jj] = u[jj] >= 0 ? make_int2(p.off[u[jj]], p.off[u[jj] + 1]) : make_int2(0, 0);
+                        }
+                        claim_win(u, t, ob, rec, E, l + 2, order, orow, end, rel);
                     }
                 }
-                sm[w] = am;
-                se[w] = ae;
+                rec[w].sm = am;
+                rec[w].se = ae;
                 inexact |= (ae > 0 || am >= (1ull << 53));
             }
             __syncthreads();
@@ -157,9 +205,13 @@ __global__ void __launch_bounds__(kDeepMaxThreads) k_deep(DeepParams p) {
         // reverse: levels L .. 1
         for (int l = L; l >= 1 && s_flags == 0; --l) {
             const int lb = lvl[l], le = lvl[l + 1];
+            const unsigned want = E | (unsigned)(l + 1);
             for (int k = lb + tid; k < le; k += bd) {
                 const int v = order[k];
-                const int rb = p.off[v], rend = p.off[v + 1];
+                const int2 orv = orow[k];
+                const int rb = orv.x, rend = orv.y;
+                const unsigned long long smv = rec[v].sm;
+                const int sv = rec[v].se;
                 double sr = 0.0;
                 int sx = 0;
                 const int step = v < p.n_heavy ? kChunk : (rend - rb);
@@ -167,17 +219,35 @@ __global__ void __launch_bounds__(kDeepMaxThreads) k_deep(DeepParams p) {
                     const int c1 = c0 + step < rend ? c0 + step : rend;
                     double cr = 0.0;
                     int cx = 0;
-                    for (int e = c0; e < c1; ++e) {
-                        const int w = p.adj[e];
-                        if (dist[w] == l + 1) xd_add(cr, cx, rho[w], re[w]);
+                    for (int e = c0; e < c1; e += kWin) {
+                        int w[kWin];
+                        unsigned t[kWin];
+                        int re[kWin];
+                        double rh[kWin];
+#pragma unroll
+                        for (int jj = 0; jj < kWin; ++jj) w[jj] = e + jj < c1 ? p.adj[e + jj] : -1;
+#pragma unroll
+                        for (int jj = 0; jj < kWin; ++jj) {
+                            if (w[jj] >= 0) {
+                                t[jj] = rec[w[jj]].tag;
+                                re[jj] = rec[w[jj]].re;
+                                rh[jj] = rec[w[jj]].rho;
+                            } else {
+                                t[jj] = 0u;
+                                re[jj] = 0;
+                                rh[jj] = 0.0;
+                            }
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < kWin; ++jj)
+                            if (w[jj] >= 0 && t[jj] == want) xd_add(cr, cx, rh[jj], re[jj]);
                     }
                     xd_add(sr, sx, cr, cx);
                 }
-                const double sd = (double)sm[v];  // rounds only when the mantissa is >= 2^53
-                const int sv = se[v];
+                const double sd = (double)smv;  // rounds only when the mantissa is >= 2^53
                 dl[v] = scalbn(sd * sr, sv + sx);
-                rho[v] = __drcp_rn(sd) + scalbn(sr, sv + sx);
-                re[v] = -sv;
+                rec[v].rho = __drcp_rn(sd) + scalbn(sr, sv + sx);
+                rec[v].re = -sv;
             }
             __syncthreads();
         }
@@ -199,7 +269,7 @@ __global__ void __launch_bounds__(kDeepMaxThreads) k_deep(DeepParams p) {
 }
 
 // bc[v] += delta[0][v] + delta[1][v] + ..., added one source at a time in list order.
-__global__ void k_deep_accumulate(const double* __restrict__ delta, int nsrc, long long n, double* bc) {
+__global__ void k_sum_dependency_rows(const double* __restrict__ delta, int nsrc, long long n, double* bc) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         double acc = bc[v];
@@ -232,7 +302,7 @@ cudaError_t launch_deep_accumulate(const double* delta, int nsrc, long long n, d
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long want = (n + 255) / 256, cap = 8LL * (sms > 0 ? sms : 1);
-    k_deep_accumulate<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(delta, nsrc, n, bc);
+    k_sum_dependency_rows<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(delta, nsrc, n, bc);
     return cudaGetLastError();
 }
 

@@ -138,23 +138,28 @@ def test_deep_form_closed_forms_and_limit(bc):
 
 
 def test_automatic_form_choice(bc):
-    """Auto: a sparse graph whose probe finds 512+ levels runs per source; shallow ones stay batched."""
-    g = bcgen.grid(300, 300, 0.05, 5)  # depth about 600 from a corner region
+    """Auto: a sparse graph whose probe finds 48+ narrow levels runs per source; shallow ones stay batched."""
+    g = bcgen.grid(300, 300, 0.05, 5)  # about 600 levels from the probe's vertex
     src = bcgen.sample_sources(g, 128, 2)
     G = bc.Graph(g.off, g.adj)
     out, st = G.compute(src)
     auto = out.cpu().numpy().copy()
     s = G.stats()
-    assert s["deep_sources"] == len(src) and s["max_levels"] >= 512
+    assert s["deep_sources"] == len(src) and s["max_levels"] >= 300
     out, _ = G.compute(src, deep_form=1)
     assert np.array_equal(auto.view(np.uint64), out.cpu().numpy().view(np.uint64))
     out, _ = G.compute(src, batch_width=64)  # a width given by the caller keeps the batched form
     assert G.stats()["deep_sources"] == 0
-    small = bcgen.grid(100, 100, 0.05, 5)  # about 200 levels
-    S = bc.Graph(small.off, small.adj)
-    S.compute(bcgen.sample_sources(small, 128, 2))
-    assert S.stats()["deep_sources"] == 0
-    r = bcgen.rmat(12, 8, 1)
+    tree = bcgen.random_tree(20000, 3)  # hundreds of levels of a few dozen vertices
+    T = bc.Graph(tree.off, tree.adj)
+    T.compute(bcgen.sample_sources(tree, 100, 2))
+    assert T.stats()["deep_sources"] == 100
+    rng = np.random.default_rng(4)  # sparse random graph: about 20 levels
+    sparse = bcgen.edges_to_csr(20000, rng.integers(0, 20000, 30000), rng.integers(0, 20000, 30000))
+    S = bc.Graph(sparse.off, sparse.adj)
+    S.compute(bcgen.sample_sources(sparse, 128, 2))
+    assert S.stats()["deep_sources"] == 0 and S.stats()["max_levels"] < 48
+    r = bcgen.rmat(12, 8, 1)  # dense enough that no probe runs
     R = bc.Graph(r.off, r.adj)
     R.compute(bcgen.sample_sources(r, 128, 2))
     assert R.stats()["deep_sources"] == 0
