@@ -59,12 +59,15 @@ def test_grid_1024_all_256_sources(bc):
     g = bcgen.grid(1024, 1024, 0.05, 1)
     src = bcgen.sample_sources(g, 256, 1)
     G = bc.Graph(g.off, g.adj)
-    out, st = G.compute(src, batch_width=32)  # the width the autotuner picks for this graph
+    out, st = G.compute(src)  # the benchmark's call: the library picks its per-source form here
     assert st == bc.BC_W_SIGMA_INEXACT
-    got = out.cpu().numpy()
+    assert G.stats()["deep_sources"] == 256
+    got = out.cpu().numpy().copy()
     assert_bc_close(got, oracle.bc_ld(g.off, g.adj, src).astype(np.float64))
-    plain, _ = G.compute(src, batch_width=1)
-    assert np.array_equal(plain.cpu().numpy().view(np.uint64), got.view(np.uint64))
+    for kw in (dict(batch_width=32), dict(batch_width=1)):  # the batched and plain forms: the same bits
+        other, st2 = G.compute(src, **kw)
+        assert st2 == st and G.stats()["deep_sources"] == 0
+        assert np.array_equal(other.cpu().numpy().view(np.uint64), got.view(np.uint64)), kw
 
 
 def test_rmat22_first_benchmark_batch(bc):
