@@ -207,12 +207,16 @@ struct __align__(16) WarpSmem {
     int sv[32];                   // neighbour of each arc of the current step
     int so[32];                   // owner of each arc of the current step
     uint32_t fw[32][W];           // matched columns of each arc of the step; slot tags in the rounds
-    uint32_t pr[Geo<K>::PCAP];    // expanded pairs: arc << 16 | column
+    alignas(16) uint32_t pr[Geo<K>::PCAP];  // expanded pairs: arc << 16 | column; during the
+                                            // column-mapped arcs, a ring of two staged rows
     int av[32];                   // append staging (pull): vertex
     uint32_t am[32][W];           // append staging: mask
     long long adeg;               // append staging: degree sum
     unsigned long long cnt_dag;   // this warp's forward sum terms (DAG arc, column), flushed at exit
     unsigned long long cnt_reached;  // this warp's reached (vertex, column) pairs, flushed at exit
+    alignas(8) unsigned long long mbar[2];  // completion barriers of the two staged-row slots
+    uint32_t mph;                 // their phase bits (bit s: parity of slot s's next completion)
+    int berr;                     // a staged-row wait gave up (reported as an internal error)
 };
 
 using WS128 = WarpSmem<128, false>;
@@ -254,42 +258,72 @@ __device__ __forceinline__ int set_owners(WarpSmem<K, EXT>& ws, int ng, int v, i
 // one vector load, into its own accumulator slots.  No two lanes share a slot,
 // so no atomics and no ordering rounds are needed.  Each lane's slots take
 // the arcs in order, so ordered (floating-point) sums stay in CSR order.
+//
+// The neighbours' rows (K terms, 8 bytes each) are staged in shared memory by
+// 1-D bulk asynchronous copies (cp.async.bulk, completion on an mbarrier),
+// one instruction of one lane per row, into a ring of two slots in the pair
+// buffer, which is idle until the step's pairs are expanded: one row is
+// added while the next is in flight.  Rows are 16-byte aligned (their arrays
+// start on 256-byte boundaries and a row is 8K bytes).
 template <int K, bool EXT, int DIR>
 __device__ __forceinline__ void dense_arcs(WarpSmem<K, EXT>& ws, unsigned int db,
                                            const unsigned long long* __restrict__ termv, bool& carry) {
     constexpr int W = Geo<K>::W;
+    constexpr unsigned ROW = K * 8;
     static_assert(K >= 32 && !EXT, "column-mapped arcs need K >= 32 and the plain form");
-    // Each lane reads its own W columns of every arc straight into registers,
-    // two arcs ahead of the one being added (three register buffers).  Same
-    // additions in the same order as one read-add-write of the accumulator
-    // row per arc: only where the running sums live changes.
+    static_assert(2 * ROW <= sizeof(ws.pr), "two rows fit the pair buffer");
     const int lane = lane_id();
     const int word = (W * lane) >> 5;
-    unsigned int di = db;  // arcs still to read (taken in CSR order)
-    auto fetch = [&](unsigned long long (&x)[W]) {
-#pragma unroll
-        for (int i = 0; i < W; ++i) x[i] = 0ull;
-        if (di) {
-            const int j = __ffs(di) - 1;
-            di &= di - 1;
-            if (lane_field<W>(ws.fw[j][word], lane)) load_terms<W>(termv + (size_t)ws.sv[j] * K + W * lane, x);
+    unsigned int di = db;
+    unsigned char* ring = reinterpret_cast<unsigned char*>(ws.pr);
+    unsigned ph = ws.mph;
+    // stage the next arc's row (CSR order) into slot s
+    auto issue = [&](int s) {
+        if (!di) return;
+        const int j = __ffs(di) - 1;
+        di &= di - 1;
+        if (lane == 0) {
+            const unsigned long long* src = termv + (size_t)ws.sv[j] * K;
+            const unsigned mb = (unsigned)__cvta_generic_to_shared(&ws.mbar[s]);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(ring + s * ROW);
+            // the warp's reads of the slot's previous row (generic proxy) before the
+            // copy overwrites it (the rows' own writes are ordered by the phase prologue)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(ROW) : "memory");
+            asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(dst), "l"(src), "r"(ROW), "r"(mb) : "memory");
         }
     };
-    unsigned long long xa[W], xb[W], xc[W];
-    fetch(xa);
-    fetch(xb);
-    // The running sums of the current owner stay in registers while
-    // consecutive arcs belong to it (arcs are owner-sorted), and go back to
-    // its accumulator row when the owner changes.
-    int cur = -1;
+    issue(0);
+    issue(1);
+    int cur = -1, s = 0;
     unsigned long long r[W];
 #pragma unroll
     for (int i = 0; i < W; ++i) r[i] = 0ull;
     while (db) {
-        fetch(xc);
         const int j = __ffs(db) - 1;
         db &= db - 1;
+        {  // wait (bounded) for slot s's row
+            const unsigned mb = (unsigned)__cvta_generic_to_shared(&ws.mbar[s]);
+            const unsigned par = (ph >> s) & 1u;
+            bool ok = false;
+            for (int it = 0; it < (1 << 22) && !ok; ++it) {
+                unsigned done;
+                asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                             : "=r"(done) : "r"(mb), "r"(par) : "memory");
+                ok = done != 0;
+            }
+            if (!ok && lane == 0) ws.berr = 1;
+            ph ^= 1u << s;
+        }
         const uint32_t b = lane_field<W>(ws.fw[j][word], lane);
+        unsigned long long xa[W];
+        if (b) {
+            load_terms<W>(reinterpret_cast<const unsigned long long*>(ring + s * ROW) + W * lane, xa);
+        } else {
+#pragma unroll
+            for (int i = 0; i < W; ++i) xa[i] = 0ull;
+        }
         const int o = ws.so[j];
         if (o != cur) {
             if (cur >= 0) store_terms<W>(&ws.acc[cur * K + W * lane], r);
@@ -300,13 +334,12 @@ __device__ __forceinline__ void dense_arcs(WarpSmem<K, EXT>& ws, unsigned int db
 #pragma unroll
         for (int i = 0; i < W; ++i)
             if ((b >> i) & 1u) acc_add<false, DIR>(r[i], e, xa[i], 0, carry);
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-            xa[i] = xb[i];
-            xb[i] = xc[i];
-        }
+        __syncwarp();  // every lane has read slot s: it takes the row after next
+        issue(s);
+        s ^= 1;
     }
     if (cur >= 0) store_terms<W>(&ws.acc[cur * K + W * lane], r);
+    if (lane == 0) ws.mph = ph;
     __syncwarp();
 }
 
@@ -853,6 +886,9 @@ __device__ __forceinline__ unsigned int* wq(const KParams& p, int ph, int which)
     return &p.ctl->wq[(ph & 3) * 2 + which];
 }
 __device__ __forceinline__ void phase_prologue(const KParams& p, int ph) {
+    // the rows this phase stages by bulk copies (async proxy) were written before
+    // the barrier that opened it: order the issuing lanes' acquire before them
+    if ((threadIdx.x & 31) == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
     if (p.rank == 0 && threadIdx.x == 0) {
         p.ctl->wq[((ph + 2) & 3) * 2] = 0;
         p.ctl->wq[((ph + 2) & 3) * 2 + 1] = 0;
@@ -1543,6 +1579,12 @@ __global__ void __launch_bounds__(kThreads, 3) bc_persistent(KParams p) {
     if (lane_id() == 0) {
         ws.cnt_dag = 0;
         ws.cnt_reached = 0;
+        ws.mph = 0;
+        ws.berr = 0;
+        // the staged-row slots' completion barriers (one arrival each: the issuing lane)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"((unsigned)__cvta_generic_to_shared(&ws.mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"((unsigned)__cvta_generic_to_shared(&ws.mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
     for (int b = tv.team; b < tv.nbatch; b += tv.nteams)
@@ -1551,6 +1593,7 @@ __global__ void __launch_bounds__(kThreads, 3) bc_persistent(KParams p) {
     if (lane_id() == 0) {
         if (ws.cnt_dag) atomicAdd(&tv.gctl->dag_pairs, ws.cnt_dag);
         if (ws.cnt_reached) atomicAdd(&tv.gctl->reached_pairs, ws.cnt_reached);
+        if (ws.berr) atomicOr(&tv.gctl->err, ERR_INTERNAL);
     }
 }
 
