@@ -128,16 +128,30 @@ __device__ __forceinline__ void xu_add(unsigned long long& am, int& ae, unsigned
     am = s;
 }
 
+// x * 2^n, the value of scalbn(x, n): for a normal x whose scaled value is
+// normal too, the exponent field moves by n (integer arithmetic, exact);
+// zeros, subnormals, infinities and results outside the normal range take
+// scalbn itself.
+__device__ __forceinline__ double scale2(double x, int n) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e != 0 && e != 0x7FF && n > -0x7FF && n < 0x7FF) {
+        const int ne = e + n;
+        if (ne > 0 && ne < 0x7FF) return __longlong_as_double(b + (long long)n * (1LL << 52));
+    }
+    return scalbn(x, n);
+}
+
 // Real value r * 2^e (r a double) summed with alignment to the larger exponent.
 __device__ __forceinline__ void xd_add(double& ar, int& ae, double xr, int xe) {
     if (xr == 0.0) return;
     if (ar == 0.0) { ar = xr; ae = xe; return; }
     if (xe > ae) {
-        ar = scalbn(ar, ae - xe);
+        ar = scale2(ar, ae - xe);
         ae = xe;
         ar += xr;
     } else {
-        ar += scalbn(xr, xe - ae);
+        ar += scale2(xr, xe - ae);
     }
 }
 

@@ -688,8 +688,8 @@ __device__ __forceinline__ void write_columns(const KParams& p, WarpSmem<K, EXT>
                 double delta, rho;
                 if constexpr (EXT) {
                     const int se = p.sig_e[idx];
-                    delta = scalbn(sd * sr, se + ws.acce[slot]);
-                    rho = __drcp_rn(sd) + scalbn(sr, se + ws.acce[slot]);
+                    delta = scale2(sd * sr, se + ws.acce[slot]);
+                    rho = __drcp_rn(sd) + scale2(sr, se + ws.acce[slot]);
                     p.rho_e[idx] = -se;
                 } else {
                     delta = sd * sr;

@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(kDeepMaxThreads) k_deep(DeepParams p) {
                     xd_add(sr, sx, cr, cx);
                 }
                 const double sd = (double)smv;  // rounds only when the mantissa is >= 2^53
-                dl[v] = scalbn(sd * sr, sv + sx);
-                rec[v].rho = __drcp_rn(sd) + scalbn(sr, sv + sx);
+                dl[v] = scale2(sd * sr, sv + sx);
+                rec[v].rho = __drcp_rn(sd) + scale2(sr, sv + sx);
                 rec[v].re = -sv;
             }
             __syncthreads();
