@@ -196,7 +196,8 @@ bc_status bc_reduce_ranks(const double* parts, int32_t nranks, int64_t n, double
 /*
  * Multi-source BFS: the forward sweep of bc_compute alone (Section 2.3.2,
  * iterateInBFS: levels and shortest-path counts) for each listed source, the
- * same kernels and batching.  sources: nsrc original ids (host or device).
+ * same kernels and batching (on deep graphs, by bc_compute's automatic rule of
+ * bc_options.deep_form, the per-source form; the same values either way).  sources: nsrc original ids (host or device).
  * level: device int32[nsrc][n], row i = distance from sources[i] (-1 when
  * unreachable), original vertex ids; required when n > 0 and nsrc > 0.
  * sigma: device double[nsrc][n] or NULL = number of shortest paths (exact below

@@ -1489,7 +1489,7 @@ struct DeepPlan {
 // Launch shape of the per-source form: the widest block (1024, 512 or 256
 // threads) whose resident grid still covers the sources, as many blocks as
 // are resident (or wanted), and rounds of R sources within the memory budget.
-static bc_status deep_plan(const bc_graph* g, int nsrc, const bc_options& o, DeepPlan* pl) {
+static bc_status deep_plan(const bc_graph* g, int nsrc, const bc_options& o, bool forward_only, DeepPlan* pl) {
     const int n = g->n;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1508,7 +1508,8 @@ static bc_status deep_plan(const bc_graph* g, int nsrc, const bc_options& o, Dee
     if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
     const long long stride = ((long long)n + 31) & ~31LL;
     const int slots = (int)std::min<long long>(kLevelSlots, (long long)n + 3);
-    const double per_block = 44.0 * (double)stride + 4.0 * (double)slots, per_src = 8.0 * (double)n;
+    // a round's dependency rows: 8 bytes per vertex and source (none when forward only)
+    const double per_block = 44.0 * (double)stride + 4.0 * (double)slots, per_src = forward_only ? 0.0 : 8.0 * n;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
         cudaGetLastError();
@@ -1519,7 +1520,7 @@ static bc_status deep_plan(const bc_graph* g, int nsrc, const bc_options& o, Dee
     long long blocks = std::min<long long>((long long)per_sm * sms, nsrc);
     blocks = std::min<long long>(blocks, (long long)(budget / (per_block + per_src)));
     if (blocks < 1) return fail(BC_E_NOMEM, "per-source form: no room for one block's state");
-    long long R = (long long)((budget - (double)blocks * per_block) / per_src);
+    long long R = forward_only ? (long long)nsrc : (long long)((budget - (double)blocks * per_block) / per_src);
     R = std::max<long long>(blocks, std::min<long long>(R, nsrc));
     R = std::min<long long>(R, blocks * 0x8000LL);  // epochs of one launch stay below 2^16
     pl->threads = threads;
@@ -1531,13 +1532,20 @@ static bc_status deep_plan(const bc_graph* g, int nsrc, const bc_options& o, Dee
     return BC_OK;
 }
 
+// Outputs of a forward-only run (bc_bfs): [nsrc][n] rows in original ids.
+struct BfsOut {
+    int* level;
+    double* sigma;
+    int* sigma_exp;
+};
+
 static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_options& o, cudaStream_t st,
-                          double* bc_rel, bc_run_stats* out) {
+                          double* bc_rel, bc_run_stats* out, const BfsOut* bfs = nullptr) {
     const int n = g->n;
     bc_status hr = ensure_heavy(g, st);
     if (hr != BC_OK) return hr;
     DeepPlan pl;
-    if ((hr = deep_plan(g, nsrc, o, &pl)) != BC_OK) return hr;
+    if ((hr = deep_plan(g, nsrc, o, bfs != nullptr, &pl)) != BC_OK) return hr;
     const int threads = pl.threads, slots = pl.slots;
     const long long blocks = pl.blocks, R = pl.R, stride = pl.stride;
     const size_t rec_bytes = sizeof(DeepRec) * (size_t)blocks * (size_t)stride;
@@ -1546,7 +1554,8 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
     const size_t aux_bytes = 2 * sizeof(unsigned long long) + sizeof(int) * ((size_t)nsrc + 2 * (size_t)R + 1);
     void* old_state = g->deep_state.p;
     if (!buf_ensure(g->deep_state, rec_bytes, st) || !buf_ensure(g->deep_order, ord_bytes + lvl_bytes, st) ||
-        !buf_ensure(g->deep_delta, sizeof(double) * (size_t)R * n, st) || !buf_ensure(g->deep_aux, aux_bytes, st))
+        (!bfs && !buf_ensure(g->deep_delta, sizeof(double) * (size_t)R * n, st)) ||
+        !buf_ensure(g->deep_aux, aux_bytes, st))
         return fail(BC_E_NOMEM, "per-source form buffers");
     if (g->deep_state.p != old_state) g->deep_stride = -1;  // fresh memory: clear before use
     char* ap = (char*)g->deep_aux.p;
@@ -1562,7 +1571,8 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "per-source form setup");
     if (hbad) return fail(BC_E_SOURCE, "a source id is outside [0, %d)", n);
-    if ((e = cudaMemsetAsync(bc_rel, 0, sizeof(double) * (size_t)n, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if (!bfs && (e = cudaMemsetAsync(bc_rel, 0, sizeof(double) * (size_t)n, st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
     DeepParams p{};
     p.n = n;
     p.off = (const int*)g->off.p;
@@ -1576,7 +1586,8 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
     p.orow = (int2*)((char*)g->deep_order.p + sizeof(int) * (size_t)blocks * (size_t)stride);
     p.lvl = (int*)((char*)g->deep_order.p + ord_bytes);
     p.level_slots = slots;
-    p.delta = (double*)g->deep_delta.p;
+    p.delta = bfs ? nullptr : (double*)g->deep_delta.p;
+    p.inv = (const int*)g->inv.p;
     p.status = status;
     p.depth = depth;
     p.dag_pairs = ctr;
@@ -1606,15 +1617,21 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
         g->deep_epoch += iters;
         p.src = src_rel + r0;
         p.nsrc = cnt;
-        if ((e = cudaMemsetAsync(p.delta, 0, sizeof(double) * (size_t)cnt * (size_t)n, st)) != cudaSuccess)
+        if (bfs) {
+            const size_t row0 = (size_t)r0 * (size_t)n;
+            p.level_out = bfs->level + row0;
+            p.sig_out = bfs->sigma ? bfs->sigma + row0 : nullptr;
+            p.exp_out = bfs->sigma_exp ? bfs->sigma_exp + row0 : nullptr;
+        } else if ((e = cudaMemsetAsync(p.delta, 0, sizeof(double) * (size_t)cnt * (size_t)n, st)) != cudaSuccess) {
             return cuda_fail(e, "memset");
+        }
         cudaEvent_t ev[2];
         cudaEventCreate(&ev[0]);
         cudaEventCreate(&ev[1]);
         cudaEventRecord(ev[0], st);
         e = launch_deep(p, nb, threads, st);
         cudaEventRecord(ev[1], st);
-        if (e == cudaSuccess) e = launch_deep_accumulate(p.delta, cnt, n, bc_rel, st);
+        if (e == cudaSuccess && !bfs) e = launch_deep_accumulate(p.delta, cnt, n, bc_rel, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), status, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hdp.data(), depth, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1624,7 +1641,7 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
         cudaEventDestroy(ev[1]);
         if (e != cudaSuccess) return cuda_fail(e, "per-source kernel");
         s.kernel_ms += ms;
-        s.kernel_launches += 2;
+        s.kernel_launches += bfs ? 1 : 2;
         for (int i = 0; i < cnt; ++i) {
             if (hst[i] == (ERR_LIMIT << 8)) return fail(BC_E_LIMIT, "BFS deeper than %d levels", kMaxLevel);
             if (!(hst[i] & BST_DONE)) return fail(BC_E_CUDA, "internal: source %lld not completed", r0 + i);
@@ -1656,7 +1673,7 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
 constexpr int kDeepMinDepth = 48;
 constexpr int kDeepMaxWidth = 8192;
 static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t st, double* scratch,
-                      bc_run_stats* pre) {
+                      bc_run_stats* pre, bool forward_only = false) {
     if (o.deep_form == 1) return false;
     if (o.deep_form == 2) return true;
     if (o.batch_width != 0) return false;
@@ -1678,7 +1695,7 @@ static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t s
     }
     if (seen < kDeepMinDepth || (double)g->n_nz > (double)kDeepMaxWidth * seen) return false;
     DeepPlan pl;
-    if (deep_plan(g, nsrc, o, &pl) != BC_OK) {
+    if (deep_plan(g, nsrc, o, forward_only, &pl) != BC_OK) {
         cudaGetLastError();
         return false;
     }
@@ -1876,10 +1893,29 @@ bc_status bc_bfs(bc_graph* g, const int32_t* sources, int32_t nsrc, int32_t* lev
     auto& slot = g->ws[K];
     if (!slot) slot.reset(new Workspace());
     Workspace* w = slot.get();
+    if (!buf_ensure(w->bc, sizeof(double) * n, st)) {
+        buf_release(tmp, st);
+        return fail(BC_E_NOMEM, "buffers");
+    }
+    {
+        // deep graphs: the per-source form, forward only, writes the rows itself
+        bc_options given;
+        memset(&given, 0, sizeof given);
+        bc_run_stats pre{};
+        if (want_deep(g, nsrc, given, st, (double*)w->bc.p, &pre, true)) {
+            const BfsOut bo{level, sigma, sigma_exp};
+            bc_run_stats stats{};
+            bc_status rd = run_deep(g, d_src, nsrc, given, st, nullptr, &stats, &bo);
+            if (rd >= 0) {
+                stats.kernel_launches += pre.kernel_launches;
+                g->last = stats;
+            }
+            buf_release(tmp, st);
+            return rd;
+        }
+    }
     DevBuf lvl;  // [n][K] uint16 level table of one batch
-    bc_status r = buf_ensure(w->bc, sizeof(double) * n, st) && buf_ensure(lvl, sizeof(unsigned short) * n * (size_t)K, st)
-                      ? BC_OK
-                      : fail(BC_E_NOMEM, "buffers");
+    bc_status r = buf_ensure(lvl, sizeof(unsigned short) * n * (size_t)K, st) ? BC_OK : fail(BC_E_NOMEM, "buffers");
     bool inexact = false;
     bc_run_stats total{};
     for (int b0 = 0; r >= 0 && b0 < nsrc; b0 += K) {

@@ -299,6 +299,14 @@ struct DeepParams {
     int* depth;
     unsigned long long* dag_pairs;
     unsigned long long* reached_pairs;
+    // forward sweep only (multi-source BFS): when level_out is set, no reverse
+    // sweep runs and source i writes row i of level_out (distance or -1) and,
+    // when given, sig_out / exp_out (path counts as bc_bfs defines them), in
+    // original ids through inv; delta is unused
+    const int* inv;
+    int* level_out;
+    double* sig_out;
+    int* exp_out;
 };
 cudaError_t launch_deep(const DeepParams& p, int blocks, int threads, cudaStream_t st);
 int deep_blocks_per_sm(int threads);  // resident blocks of k_deep per SM (0 on error)

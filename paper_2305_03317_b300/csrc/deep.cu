@@ -29,6 +29,8 @@
 //     delta = sigma * S, in the extended form's scaling;
 //   * BC adds the sources' dependencies in the order of the source list
 //     (k_sum_dependency_rows, one thread per vertex).
+// Run forward only, the kernel writes each source's levels and path counts
+// instead (bc_bfs on deep graphs), converted as the batched extraction does.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(kDeepMaxThreads) k_deep(DeepParams p) {
     for (int i = blockIdx.x, j = 0; i < p.nsrc; i += gridDim.x, ++j) {
         const unsigned E = (p.epoch0 + (unsigned)j) << 16;
         const int s = p.src[i];
-        double* dl = p.delta + (size_t)i * (size_t)p.n;
+        double* dl = p.delta ? p.delta + (size_t)i * (size_t)p.n : nullptr;
         if (tid == 0) {
             s_rel[0] = s_rel[1] = s_rel[2] = 0;
             s_flags = 0;
@@ -202,8 +204,29 @@ __global__ void __launch_bounds__(kDeepMaxThreads) k_deep(DeepParams p) {
             end = nend;
         }
         __syncthreads();  // s_flags and the level starts, for every thread
+        if (p.level_out && s_flags == 0) {
+            // forward only: the source's row of levels and path counts, in original ids
+            const size_t row = (size_t)i * (size_t)p.n;
+            for (int u = tid; u < p.n; u += bd) {
+                const int v = p.inv[u];
+                const unsigned t = rec[v].tag;
+                const bool reached = !unseen(t, E);
+                p.level_out[row + u] = reached ? (int)(t & 0xFFFFu) : -1;
+                if (p.sig_out) {
+                    const unsigned long long sv = reached ? rec[v].sm : 0ull;
+                    const int ev = reached ? rec[v].se : 0;
+                    if (p.exp_out) {
+                        int e = 0;
+                        p.sig_out[row + u] = frexp((double)sv, &e);
+                        p.exp_out[row + u] = sv ? e + ev : 0;
+                    } else {
+                        p.sig_out[row + u] = ev ? ldexp((double)sv, ev) : (double)sv;
+                    }
+                }
+            }
+        }
         // reverse: levels L .. 1
-        for (int l = L; l >= 1 && s_flags == 0; --l) {
+        for (int l = L; l >= 1 && s_flags == 0 && !p.level_out; --l) {
             const int lb = lvl[l], le = lvl[l + 1];
             const unsigned want = E | (unsigned)(l + 1);
             for (int k = lb + tid; k < le; k += bd) {

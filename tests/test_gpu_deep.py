@@ -163,3 +163,32 @@ def test_automatic_form_choice(bc):
     R = bc.Graph(r.off, r.adj)
     R.compute(bcgen.sample_sources(r, 128, 2))
     assert R.stats()["deep_sources"] == 0
+
+
+def test_bfs_on_deep_graphs_runs_per_source(bc):
+    """bc_bfs on a deep graph takes the per-source form (forward only): the batched form's bits."""
+    g = bcgen.grid(100, 100, 0.05, 6)
+    src = bcgen.sample_sources(g, 80, 3)
+    G = bc.Graph(g.off, g.adj)
+    lev, mant, ex, st = G.bfs(src, exponent=True)
+    assert st == bc.BC_W_SIGMA_INEXACT  # corner-to-corner counts near C(198, 99)
+    assert G.stats()["deep_sources"] == len(src)
+    lev, mant, ex = lev.cpu().numpy(), mant.cpu().numpy(), ex.cpu().numpy()
+    for i in range(0, len(src), 8):
+        olev, omant, oex, _ = oracle.source_sigma_split(g.off, g.adj, int(src[i]))
+        assert np.array_equal(lev[i], olev)
+        reached = olev >= 0
+        assert np.all(mant[i][~reached] == 0) and np.all(ex[i][~reached] == 0)
+        rel = np.abs(mant[i][reached] * np.ldexp(1.0, ex[i][reached] - oex[reached]) - omant[reached]) / omant[reached]
+        assert rel.max() <= 1e-12
+    # fewer than 64 sources on a graph of unknown depth: the batched form, the same bits
+    B = bc.Graph(g.off, g.adj)
+    blev, bmant, bex, bst = B.bfs(src[:40], exponent=True)
+    assert B.stats()["deep_sources"] == 0 and bst == st
+    assert np.array_equal(blev.cpu().numpy(), lev[:40])
+    assert np.array_equal(bmant.cpu().numpy().view(np.uint64), mant[:40].view(np.uint64))
+    assert np.array_equal(bex.cpu().numpy(), ex[:40])
+    _, sig, _, _ = G.bfs(src, exponent=False)
+    C = bc.Graph(g.off, g.adj)
+    _, bsig, _, _ = C.bfs(src[:40], exponent=False)
+    assert np.array_equal(bsig.cpu().numpy().view(np.uint64), sig.cpu().numpy()[:40].view(np.uint64))
