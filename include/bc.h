@@ -151,7 +151,10 @@ typedef struct {
                                 at most 8192 vertices on average (from an earlier call, or from a one-source
                                 probe that the first call with at least 64 sources on a graph of mean degree at
                                 most 8 runs) and the memory budget leaves a block per source or SM, else 1.
-                                Same arithmetic, same sums in the same order: the two forms give the same bits */
+                                Same arithmetic, same sums in the same order: the two forms give the same bits.
+                                The per-source form takes blocks_per_sm and ignores the batched traversal's
+                                knobs (width, direction, alpha, beta, grouping of rows, teams, dense_min) and
+                                trace (it records no phase trace) */
 } bc_options;
 
 /*
