@@ -1677,12 +1677,23 @@ static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t s
     if (o.deep_form == 1) return false;
     if (o.deep_form == 2) return true;
     if (o.batch_width != 0) return false;
+    auto deep_enough = [&](int d) { return d >= kDeepMinDepth && (double)g->n_nz <= (double)kDeepMaxWidth * d; };
     int seen;
     {
         std::lock_guard<std::mutex> lk(g->state_mu);
         seen = g->depth_seen;
     }
-    if (seen < 0 && nsrc >= 64 && g->n_nz >= 256 && g->m <= 8LL * g->n_nz) {
+    const bool probe = seen < 0 && nsrc >= 64 && g->n_nz >= 256 && g->m <= 8LL * g->n_nz;
+    if (seen < 0 ? !probe : !deep_enough(seen)) return false;
+    // room next: a graph whose per-block state leaves too few blocks runs
+    // batched whatever its depth, and needs no probe
+    DeepPlan pl;
+    if (deep_plan(g, nsrc, o, forward_only, &pl) != BC_OK) {
+        cudaGetLastError();
+        return false;
+    }
+    if (pl.blocks < std::min<long long>(nsrc, pl.sms)) return false;
+    if (probe) {
         bc_run_stats ps{};
         bc_options po;
         memset(&po, 0, sizeof po);
@@ -1693,13 +1704,7 @@ static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t s
             cudaGetLastError();
         }
     }
-    if (seen < kDeepMinDepth || (double)g->n_nz > (double)kDeepMaxWidth * seen) return false;
-    DeepPlan pl;
-    if (deep_plan(g, nsrc, o, forward_only, &pl) != BC_OK) {
-        cudaGetLastError();
-        return false;
-    }
-    return pl.blocks >= std::min<long long>(nsrc, pl.sms);
+    return deep_enough(seen);
 }
 
 bc_status bc_compute_ex(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc, bc_stream_t stream,
