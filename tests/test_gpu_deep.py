@@ -192,3 +192,20 @@ def test_bfs_on_deep_graphs_runs_per_source(bc):
     C = bc.Graph(g.off, g.adj)
     _, bsig, _, _ = C.bfs(src[:40], exponent=False)
     assert np.array_equal(bsig.cpu().numpy().view(np.uint64), sig.cpu().numpy()[:40].view(np.uint64))
+
+
+def test_deep_form_rounds_and_epoch_wrap(bc):
+    """More than 2^15 sources per block: two rounds, and the 16-bit epochs wrap (records cleared)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 5
+    g = bcgen.path(n)
+    reps = (sms * 65536 + 1000 + n - 1) // n
+    src = np.tile(np.arange(n, dtype=np.int32), reps)  # every vertex `reps` times
+    G = bc.Graph(g.off, g.adj)
+    out, st = G.compute(src, deep_form=2, blocks_per_sm=1)
+    s = G.stats()
+    assert st == bc.BC_OK and s["deep_sources"] == len(src) and s["grid_blocks"] == sms
+    assert s["kernel_launches"] >= 7  # mapping, two rounds of (traversal, row sum), the records' clearing
+    want = np.array([2.0 * i * (n - 1 - i) * reps for i in range(n)])  # ordered pairs with i strictly between
+    assert np.array_equal(out.cpu().numpy(), want)
