@@ -1,5 +1,10 @@
 // Graphs of large diameter: one source per block.
 //
+// The same computation as the batched traversal: per source a level-
+// synchronous BFS counting shortest paths, then the dependencies accumulated
+// level by level in reverse (the BFS and reverse-BFS constructs of Section
+// 2.3.2, as the BC program of Appendix A uses them).
+//
 // A graph like a road network or a grid runs thousands of BFS levels with a
 // few thousand vertices each.  The batched traversal (bc_kernels.cu) then
 // spends each level on grid-wide phases whose work is a handful of warp tasks
