@@ -209,3 +209,32 @@ def test_deep_form_rounds_and_epoch_wrap(bc):
     assert s["kernel_launches"] >= 7  # mapping, two rounds of (traversal, row sum), the records' clearing
     want = np.array([2.0 * i * (n - 1 - i) * reps for i in range(n)])  # ordered pairs with i strictly between
     assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_deep_form_allocation_failure_then_recovers(bc):
+    """The per-source form's buffers come from the allocator hook: a refusal is BC_E_NOMEM, and the graph
+    stays usable (the next call, with the default allocator, gives the batched form's bits)."""
+    import ctypes
+    lib = bc.load()
+    g = bcgen.grid(30, 30, 0.05, 8)
+    src = bcgen.sample_sources(g, 70, 5)
+    G = bc.Graph(g.off, g.adj)
+    ref, st = G.compute(src, deep_form=1)  # the call's own buffers exist from here on
+    ref = ref.cpu().numpy().copy()
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+    asked, freed = [], []
+    hooks = (ALLOC(lambda nbytes, stream, ctx: asked.append(int(nbytes))),  # returns None: no memory
+             FREE(lambda ptr, stream, ctx: freed.append(ptr)))
+    assert lib.bc_set_allocator(ctypes.cast(hooks[0], ctypes.c_void_p), ctypes.cast(hooks[1], ctypes.c_void_p),
+                                None) == bc.BC_OK
+    try:
+        with pytest.raises(bc.BCError) as ei:
+            G.compute(src, deep_form=2)
+        assert ei.value.status == bc.BC_E_NOMEM
+        assert asked and not freed
+    finally:
+        assert lib.bc_set_allocator(None, None, None) == bc.BC_OK
+    out, st2 = G.compute(src, deep_form=2)
+    assert st2 == st and G.stats()["deep_sources"] == len(src)
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64))
