@@ -885,10 +885,12 @@ __device__ __forceinline__ bool heavy_partial(const KParams& p, WarpSmem<K, EXT>
 __device__ __forceinline__ unsigned int* wq(const KParams& p, int ph, int which) {
     return &p.ctl->wq[(ph & 3) * 2 + which];
 }
+template <bool STAGED>
 __device__ __forceinline__ void phase_prologue(const KParams& p, int ph) {
-    // the rows this phase stages by bulk copies (async proxy) were written before
-    // the barrier that opened it: order the issuing lanes' acquire before them
-    if ((threadIdx.x & 31) == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+    // the rows a phase stages by bulk copies (async proxy: the column-mapped
+    // arcs of K >= 32 in the plain form) were written before the barrier that
+    // opened it: order the issuing lanes' acquire before them
+    if (STAGED && (threadIdx.x & 31) == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
     if (p.rank == 0 && threadIdx.x == 0) {
         p.ctl->wq[((ph + 2) & 3) * 2] = 0;
         p.ctl->wq[((ph + 2) & 3) * 2 + 1] = 0;
@@ -934,7 +936,7 @@ __device__ void phase_pull(const KParams& p, int it, int ph, const uint32_t (&ac
     uint32_t* Fn = p.F[(it + 1) % 3];
     const int lev = it + 1;
     bool carry = false;
-    phase_prologue(p, ph);
+    phase_prologue<K >= 32 && !EXT>(p, ph);
     // directed graphs pull over in-rows (the transpose), whole rows: no chunk tasks
     const bool directed = p.ioff != nullptr;
     const int* roff = directed ? p.ioff : p.off;
@@ -1049,7 +1051,7 @@ __device__ void phase_push(const KParams& p, int it, int ph, WarpSmem<K, EXT>& w
     uint32_t* Fn = p.F[(it + 1) % 3];
     const int lev = it + 1;
     const int stampv = lev;
-    phase_prologue(p, ph);
+    phase_prologue<false>(p, ph);
     // claim unseen columns of the neighbours of the owner table's arcs
     auto visit = [&](int ng, int T) {
         for (int base = 0; base < T; base += 32) {
@@ -1158,7 +1160,7 @@ __device__ void phase_sigma(const KParams& p, int it, int ph, const uint32_t (&a
     const uint32_t* Fn = p.F[(it + 1) % 3];
     const int lev = it + 1;
     bool carry = false;
-    phase_prologue(p, ph);
+    phase_prologue<K >= 32 && !EXT>(p, ph);
     // directed graphs sum over in-rows (the transpose), whole rows: heavy entries
     // (heavy by out-degree) join the grouped path below
     const bool directed = p.ioff != nullptr;
@@ -1230,7 +1232,7 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
     const uint32_t* Fd = p.F[(l + 1) % 3];  // level l+1 masks
     uint32_t* Fl = p.F[l % 3];              // level l masks (read by level l-1)
     bool carry = false;
-    phase_prologue(p, ph);
+    phase_prologue<K >= 32 && !EXT>(p, ph);
     const int HT = p.la.hcnt[l] > 0 ? p.la.hchunks[l] : 0;
     for (bool fst = true;;) {
         const long long t0 = next_task(p, wq(p, ph, 0), HT, fst);
