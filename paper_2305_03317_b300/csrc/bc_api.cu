@@ -229,6 +229,7 @@ struct bc_graph {
     int max_deg = 0;
     int n_nz = 0;
     int n_heavy = -1;      // rows with degree > kChunk (a prefix of the new ids); -1 = not yet counted
+    int first_leaf = 1 << 30;  // first new id of degree 1 (degrees are non-increasing); set with n_heavy
     long long hchunk_total = 0;
     bool directed = false;
     int max_in_deg = 0;  // directed: longest in-row (forward sums run over whole in-rows)
@@ -293,6 +294,17 @@ static bc_status ensure_heavy(bc_graph* g, cudaStream_t st) {
         else hi = mid;
     }
     const int nh = lo;
+    // rows of degree 1 follow every longer row: the first of them
+    int llo = nh, lhi = g->n_nz;
+    while (llo < lhi) {
+        int mid = (llo + lhi) / 2;
+        int two[2];
+        cudaError_t e = cudaMemcpyAsync(two, off + mid, sizeof two, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "degree-1 row count");
+        if (two[1] - two[0] > 1) llo = mid + 1;
+        else lhi = mid;
+    }
     std::vector<int> ho((size_t)nh + 1), cum((size_t)nh + 1);
     cudaError_t e = cudaMemcpyAsync(ho.data(), off, sizeof(int) * ((size_t)nh + 1), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -303,6 +315,7 @@ static bc_status ensure_heavy(bc_graph* g, cudaStream_t st) {
     e = cudaMemcpyAsync(g->hcum.p, cum.data(), sizeof(int) * ((size_t)nh + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "heavy-row table");
+    g->first_leaf = llo;
     g->n_heavy = nh;
     g->hchunk_total = cum[nh];
     return BC_OK;
@@ -364,6 +377,7 @@ static KParams make_params(bc_graph* g, Workspace* w, int nbatch, const bc_optio
     p.n = g->n;
     p.n_nz = g->n_nz;
     p.n_heavy = g->n_heavy;
+    p.first_leaf = g->directed ? g->n : g->first_leaf;  // undirected only: a directed out-degree 1 may lead on
     p.m_nz = g->m;
     p.off = (const int*)g->off.p;
     p.adj = (const int*)g->adj.p;

@@ -51,6 +51,9 @@ struct LevelArrays {
 struct KParams {
     // graph (relabelled: ids sorted by degree descending, heavy rows first, isolated last)
     int n, n_nz, n_heavy;
+    // undirected graphs: ids [first_leaf, n_nz) have degree 1 (their one neighbour
+    // is their parent, so no successor at any level >= 1); n when not used
+    int first_leaf;
     long long m_nz;
     const int* off;
     const int* adj;

@@ -1260,23 +1260,26 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
         const int first = (int)(g0 * group);
         const int ng = min(group, lc - first);
         int v = 0, beg = 0, len = 0;
-        uint32_t mk[W];
+        uint32_t mk[W], fin[W];
 #pragma unroll
-        for (int t = 0; t < W; ++t) mk[t] = 0;
+        for (int t = 0; t < W; ++t) mk[t] = fin[t] = 0;
         if (lane < ng) {
             v = p.ent[ls + first + lane];
             load_mask<W>(p.emask, ls + first + lane, mk);
-            beg = p.off[v];
-            len = p.off[v + 1] - beg;
+            // a vertex of degree 1 at a level >= 1 has no successor: its delta is 0
+            // and its rho the 1/sigma the forward sweep stored, so it is not
+            // gathered or finished (plain form; phase_bc leaves it out too)
+            if (EXT || v < p.first_leaf) {
+                beg = p.off[v];
+                len = p.off[v + 1] - beg;
+#pragma unroll
+                for (int t = 0; t < W; ++t) fin[t] = mk[t];
+            }
         }
-        const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, mk);
+        const int T = set_owners<K, EXT>(ws, ng, v, beg, len, ls + first + lane, fin);
         group_gather<K, EXT, BWD>(p, ws, ng, T, Fd, p.adj, carry);
         write_columns<K, EXT, BWD>(p, ws, ng, ws.owant);
-        if (lane < ng) {
-            uint32_t want[W];
-            read_mask_s<W>(ws.owant[lane], want);
-            store_mask_full<W>(Fl, ws.ov[lane], want);
-        }
+        if (lane < ng) store_mask_full<W>(Fl, v, mk);  // level-l tags for level l-1's gathers
     }
     clear_level_masks<W>(p, p.F[(l + 2) % 3], l + 2);
 }
@@ -1286,13 +1289,15 @@ __device__ void phase_back(const KParams& p, int l, int ph, WarpSmem<K, EXT>& ws
 // contiguous; a job's sum is carried sequentially across its columns and its
 // batches, so the additions happen in the job's source-list order whatever
 // else shares the batch.
-template <int K>
+template <int K, bool EXT>
 __device__ void phase_bc(const KParams& p, int b) {
     constexpr int W = Geo<K>::W;
     const long long nthr = (long long)p.team_blocks * blockDim.x;
     const int* src = p.src + (size_t)b * K;
     const int* cj = p.col_job ? p.col_job + (size_t)b * K : nullptr;
-    for (long long v = (long long)p.rank * blockDim.x + threadIdx.x; v < p.n_nz; v += nthr) {
+    // vertices of degree 1 (ids [first_leaf, n_nz)) add nothing: their dependency is 0
+    const long long vend = EXT ? p.n_nz : min((long long)p.n_nz, (long long)p.first_leaf);
+    for (long long v = (long long)p.rank * blockDim.x + threadIdx.x; v < vend; v += nthr) {
         uint32_t vm[W];
         load_mask<W>(p.V, v, vm);
         if (!mask_any<W>(vm)) continue;
@@ -1521,7 +1526,7 @@ __device__ bool run_batch(const KParams& p, int b, GridTeam& team, int& ph, Warp
     }
     // batches add into BC in batch order, whichever team ran them
     if (!bc_turn_wait(p, team, b)) return false;
-    phase_bc<K>(p, b);
+    phase_bc<K, EXT>(p, b);
     if (tid == 0) p.batch_status[b] = BST_DONE | (p.ctl->flags & BST_INEXACT);
     const bool ok = team.sync();
     bc_turn_pass(p, b);

@@ -185,6 +185,7 @@ extern "C" bc_status bc_compute_noalloc(const int32_t* offsets, const int32_t* i
     p.n = n;
     p.n_nz = n;       // no relabelling: isolated vertices stay where they are
     p.n_heavy = 0;    // every row runs on the grouped path
+    p.first_leaf = n; // no relabelling: degree-1 rows are not a suffix, none is left out
     p.m_nz = m;
     p.off = offsets;
     p.adj = indices;
