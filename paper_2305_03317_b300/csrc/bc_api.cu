@@ -489,20 +489,23 @@ static int grid_blocks(int K, bool ext, int blocks_per_sm, int share) {
 // block per 2^19 arcs, so small graphs run one team per SM-sized group and the
 // largest graphs one team over the whole grid); no more teams than batches,
 // and the per-team arenas within a memory budget.
-static void choose_teams(long long m, int nbatch, int blocks, size_t team_bytes, int forced, int* nteams,
+static void choose_teams(long long m, int K, int nbatch, int blocks, size_t team_bytes, int forced, int* nteams,
                          int* team_blocks) {
     int T;
     if (forced > 0) {
         T = forced;
     } else {
         // blocks per team: about one per 2^19 arcs on large graphs, and on
-        // smaller ones about 0.7 * m^0.24 (measured optimum with many batches:
-        // 7 blocks at R-MAT 10, 11 at 12, 15 at 14, 18 at 16, 27 at 18; one
-        // team per batch on a whole grid ran R-MAT 16 with 316 batches in
-        // 457 ms against 175-191 ms with 16-32 teams); at least two teams when
-        // there are two batches (a second batch in flight hides the first's
-        // level-barrier waits: R-MAT 22, 1261 -> 1245 ms)
-        long long per = std::max<long long>((m >> 19) + 1, (long long)(0.7 * std::pow((double)m, 0.24)));
+        // smaller ones about 0.7 * m^0.24 at width 128, in proportion to the
+        // width (measured optimum with many 128-wide batches: 7 blocks at R-MAT
+        // 10, 11 at 12, 15 at 14, 18 at 16, 27 at 18; one team per batch on a
+        // whole grid ran R-MAT 16 with 316 batches in 457 ms against 175-191 ms
+        // with 16-32 teams; one-source batches of R-MAT 12 run best one block
+        // each: 45.7 ms against 67.3 ms on 9-block teams); at least two teams
+        // when there are two batches (a second batch in flight hides the
+        // first's level-barrier waits: R-MAT 22, 1261 -> 1245 ms)
+        long long per = std::max<long long>((m >> 19) + 1,
+                                            (long long)(0.7 * std::pow((double)m, 0.24) * K / 128.0));
         if (per < 1) per = 1;
         T = (int)std::max<long long>(1, blocks / std::min<long long>(per, blocks));
         if (nbatch >= 2) T = std::max(T, 2);
@@ -640,7 +643,7 @@ static bc_status run_jobs(bc_graph* g, Workspace* w, const int* d_src, int nsrc,
         if (blocks < 1) return fail(BC_E_CUDA, "persistent kernel cannot be resident (occupancy 0)");
         int nteams = 1, team_blocks = blocks;
         const TeamLayout L = team_layout(g->n, g->n_heavy, g->hchunk_total, K, ext, capf);
-        choose_teams(g->m, nbatch, blocks, L.bytes, o.teams, &nteams, &team_blocks);
+        choose_teams(g->m, K, nbatch, blocks, L.bytes, o.teams, &nteams, &team_blocks);
         s.grid_blocks = nteams * team_blocks;
         s.teams = nteams;
         if (!ws_ensure(w, g, K, ext, nbatch, (int)job_bc.size(), capf, nteams, st)) return BC_E_NOMEM;
@@ -1001,7 +1004,7 @@ static bc_status many_record(bc_many_plan* pl) {
         const int blocks = grid_blocks(it.K, false, pl->opt.blocks_per_sm, 1);
         // this item's teams: as many as its batches and the workspace's slices allow
         int nteams = 1, team_blocks = blocks;
-        choose_teams(g->m, it.nbatch, blocks, w->lay.bytes, pl->opt.teams, &nteams, &team_blocks);
+        choose_teams(g->m, it.K, it.nbatch, blocks, w->lay.bytes, pl->opt.teams, &nteams, &team_blocks);
         nteams = std::min(nteams, w->nteams);
         team_blocks = blocks / nteams;
         const int saved = w->nteams;
@@ -2213,7 +2216,7 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
             const int blocks = grid_blocks(it.K, false, o.blocks_per_sm, 1);
             int T = 1, B = blocks;
             const TeamLayout L = team_layout(g->n, g->n_heavy, g->hchunk_total, it.K, false, cap_factor(it.K, 0));
-            choose_teams(g->m, it.nbatch, blocks, L.bytes, o.teams, &T, &B);
+            choose_teams(g->m, it.K, it.nbatch, blocks, L.bytes, o.teams, &T, &B);
             d.teams = std::max(d.teams, T);
         }
         pl->items.push_back(std::move(it));
