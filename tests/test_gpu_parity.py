@@ -154,6 +154,27 @@ def test_rmat12_bitwise_across_widths_and_directions(bc, rmat12):
         assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), kw
 
 
+def test_many_batches_team_counts_and_degree1_rule_keep_bits(bc):
+    """Hundreds of batches on a medium graph: the automatic team count (several blocks per team),
+    one team per batch and a few large teams give the same bits, with degree-1 vertices (left out of
+    the reverse sweep) exactly 0 and the whole against the oracle."""
+    g = bcgen.rmat(13, 8, 5)
+    deg = np.diff(g.off)
+    assert (deg == 1).sum() > 500  # many degree-1 vertices
+    src = np.tile(np.nonzero(deg)[0].astype(np.int32), 2)[:9000]  # repeated sources: 71 batches of 128
+    G = bc.Graph(g.off, g.adj)
+    ref, st = G.compute(src)
+    ref = ref.cpu().numpy().copy()
+    auto_teams = G.stats()["teams"]
+    assert 1 < auto_teams < 71
+    for kw in (dict(teams=71), dict(teams=4), dict(batch_width=32), dict(batch_width=1), dict(deep_form=2)):
+        out, st2 = G.compute(src, **kw)
+        assert st2 == st
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64)), kw
+    assert np.all(ref[deg == 1] == 0.0)
+    assert_bc_close(ref, oracle.bc(g.off, g.adj, src))
+
+
 def test_reduce_ranks_is_the_rank_order_sum(bc):
     import torch
     rng = np.random.default_rng(5)
