@@ -324,8 +324,11 @@ bc_status bc_tuning_cache(const char* path, int32_t save);
  * unpermute) into a CUDA graph; bc_many_run replays it on `stream`, then
  * redoes alone any item that needed the extended path-count form or larger
  * level lists, and returns the worst status (per item in item_status[nitems],
- * may be NULL).  Outputs must stay alive while the plan is run.  Results are
- * bitwise those of bc_compute on each item.
+ * may be NULL).  Items on graphs that bc_compute's automatic rule sends to the
+ * per-source form (bc_options.deep_form; decided at create, a depth probe
+ * included) are not recorded: bc_many_run runs them after the replay through
+ * bc_compute_ex in that form.  Outputs must stay alive while the plan is run.
+ * Results are bitwise those of bc_compute on each item.
  */
 typedef struct bc_many_plan bc_many_plan;
 typedef struct {

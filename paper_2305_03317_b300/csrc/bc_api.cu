@@ -963,6 +963,7 @@ struct ManyItem {
     long long src_off = 0;     // into the plan's device source buffer
     double* out = nullptr;
     int K = 0, nbatch = 0;
+    bool deep = false;         // the per-source form: run at each replay by bc_compute_ex, not recorded
 };
 
 struct bc_many_plan {
@@ -999,6 +1000,7 @@ static bc_status many_record(bc_many_plan* pl) {
     int launches = 0;
     for (size_t i = 0; i < pl->items.size() && r == BC_OK; ++i) {
         ManyItem& it = pl->items[i];
+        if (it.deep) continue;  // run at replay time, outside the recorded graph
         bc_graph* g = it.g;
         Workspace* w = pl->ws[it.K].get();
         const int blocks = grid_blocks(it.K, false, pl->opt.blocks_per_sm, 1);
@@ -2207,6 +2209,20 @@ bc_status bc_many_create(const bc_item* items, int32_t nitems, const bc_options*
         it.nbatch = (x.nsrc + it.K - 1) / it.K;
         it.src_off = total_src;
         total_src += x.nsrc;
+        if (g->n > 0 && x.nsrc > 0) {
+            // deep graphs take the per-source form, by bc_compute's rule (a depth probe included)
+            std::lock_guard<std::mutex> lk(g->mu);
+            DevBuf scratch;
+            bc_run_stats pre{};
+            if (!buf_ensure(scratch, sizeof(double) * (size_t)g->n, ust)) return fail(BC_E_NOMEM, "probe buffer");
+            it.deep = want_deep(g, x.nsrc, o, ust, (double*)scratch.p, &pre);
+            cudaStreamSynchronize(ust);
+            buf_release(scratch, ust);
+        }
+        if (it.deep) {
+            pl->items.push_back(std::move(it));
+            continue;
+        }
         Dims& d = dims[it.K];
         d.n = std::max(d.n, g->n);
         d.nh = std::max(d.nh, g->n_heavy);
@@ -2279,7 +2295,14 @@ bc_status bc_many_run(bc_many_plan* pl, bc_stream_t stream, bc_status* item_stat
     for (size_t i = 0; i < ni; ++i) {
         const int w = status[i];
         bc_status r;
-        if ((w >> 8) & ERR_TIMEOUT) {
+        if (pl->items[i].deep) {
+            // the per-source form, in the item's fixed source order
+            ManyItem& it = pl->items[i];
+            bc_options od = pl->opt;
+            od.deep_form = 2;
+            od.source_order = 1;
+            r = bc_compute_ex(it.g, it.src.data(), (int)it.src.size(), it.out, stream, &od);
+        } else if ((w >> 8) & ERR_TIMEOUT) {
             r = fail(BC_E_TIMEOUT, "item %zu: a grid-barrier wait exceeded its cycle budget", i);
         } else if ((w >> 8) & ERR_LIMIT) {
             r = fail(BC_E_LIMIT, "item %zu: BFS deeper than %d levels", i, kMaxLevel);

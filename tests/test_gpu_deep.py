@@ -238,3 +238,26 @@ def test_deep_form_allocation_failure_then_recovers(bc):
     out, st2 = G.compute(src, deep_form=2)
     assert st2 == st and G.stats()["deep_sources"] == len(src)
     assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64))
+
+
+def test_plan_runs_deep_items_per_source(bc):
+    """A many-graph plan with a deep item: that item runs in the per-source form at each replay,
+    the others from the recorded graph; every output equals the direct call bit for bit."""
+    import torch
+    graphs = [bcgen.rmat(11, 8, 3), bcgen.grid(200, 200, 0.05, 7), bcgen.random_tree(5000, 4)]
+    items, refs = [], []
+    for i, g in enumerate(graphs):
+        src = bcgen.sample_sources(g, 100, 11 + i)
+        out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        items.append((bc.Graph(g.off, g.adj), src, out))
+        R = bc.Graph(g.off, g.adj)
+        ref, _ = R.compute(src)
+        refs.append((ref.cpu().numpy().copy(), R.stats()["deep_sources"]))
+    assert refs[0][1] == 0 and refs[1][1] == 100 and refs[2][1] == 100  # R-MAT batched, grid and tree per source
+    plan = bc.ManyPlan(items)
+    for _ in range(2):
+        st = plan.run()
+        assert all(int(x) in (bc.BC_OK, bc.BC_W_SIGMA_INEXACT) for x in st)
+        for (G, src, out), (ref, _) in zip(items, refs):
+            assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64))
+    close(items[2][2].cpu().numpy(), oracle.bc(graphs[2].off, graphs[2].adj, items[2][1]))

@@ -473,7 +473,7 @@ def test_many_graphs_plan_matches_single_calls(bc):
             got = out.cpu().numpy()
             assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
             assert_bc_close(got, want)
-    # the 70x70 full grid needs the extended form: its item is redone alone
+    # the 70x70 full grid needs the extended form (and, 138 levels deep, runs in the per-source form)
     assert int(st[len(sizes)]) == bc.BC_W_SIGMA_INEXACT
     G, src, _ = items[-1]
     G.compute(src)
