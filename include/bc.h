@@ -352,6 +352,10 @@ bc_status bc_many_info(const bc_many_plan* plan, int32_t* items, int32_t* kernel
  * admitted jobs run concurrently on their own streams.  bc_poll returns
  * BC_PENDING until done, then the job's final status once, releasing the id.
  * A job's result is bitwise the same whether it runs alone or among others.
+ * Jobs on a graph that an earlier traversal showed deep (bc_options.deep_form's
+ * depth rule) run one by one through bc_compute_ex, which picks the per-source
+ * form; its per-source state is the graph's and is not part of the admission
+ * budget.
  */
 bc_status bc_batch_submit(bc_graph* g, const int32_t* sources, int32_t nsrc, double* out_bc,
                           bc_job* job);

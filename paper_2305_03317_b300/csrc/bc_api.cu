@@ -266,6 +266,14 @@ struct bc_graph {
     DevBuf pr_ccum, pr_rank, pr_scratch, pr_cpart, pr_carr, pr_ctl, pr_small;
 };
 
+// The per-source form's depth rule (see want_deep): at least kDeepMinDepth
+// levels of at most kDeepMaxWidth vertices on average.
+constexpr int kDeepMinDepth = 48;
+constexpr int kDeepMaxWidth = 8192;
+static bool deep_by_depth(const bc_graph* g, int depth) {
+    return depth >= kDeepMinDepth && (double)g->n_nz <= (double)kDeepMaxWidth * depth;
+}
+
 // ------------------------------------------------------------------ helpers
 static bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
@@ -860,9 +868,23 @@ void worker_main(int slot) {
         apply_tuning(g, nsrc, o);
         const int K = choose_width(g->n, nsrc, o.batch_width);
         bc_status r = BC_OK;
+        // a graph known to be deep: every job through the direct call, which picks
+        // the per-source form by the same rule, so each result is the direct call's
+        int seen;
+        {
+            std::lock_guard<std::mutex> lk(g->state_mu);
+            seen = g->depth_seen;
+        }
+        const bool deep = deep_by_depth(g, seen);
+        std::vector<bc_status> jr(batch.size(), BC_OK);
+        if (deep) {
+            for (size_t k = 0; k < batch.size(); ++k)
+                jr[k] = bc_compute_ex(g, batch[k]->src.data(), (int)batch[k]->src.size(), batch[k]->out, st, nullptr);
+        }
         // each job's sources in the order bc_compute would take them, so that a
         // job's result is the same alone, packed or computed directly
         for (auto& j : batch) {
+            if (deep) break;
             if (r != BC_OK || j->grouped || !want_grouping(g, (int)j->src.size(), o)) continue;
             const int n1 = (int)j->src.size();
             DevBuf tmp;
@@ -881,44 +903,47 @@ void worker_main(int slot) {
                 j->grouped = true;
             }
         }
-        std::vector<int> all;
-        std::vector<int> owner;  // job index per source
-        for (size_t j = 0; j < batch.size(); ++j) {
-            all.insert(all.end(), batch[j]->src.begin(), batch[j]->src.end());
-            owner.insert(owner.end(), batch[j]->src.size(), (int)j);
-        }
-        const int nbatch = (nsrc + K - 1) / K;
-        std::vector<int> col_job((size_t)nbatch * K, 0);
-        for (int i = 0; i < nbatch * K; ++i) col_job[i] = i < nsrc ? owner[i] : (int)batch.size() - 1;
-        const size_t nn = (size_t)(g->n > 0 ? g->n : 1);
-        if (r == BC_OK && (!buf_ensure(dsrc, sizeof(int) * (size_t)nsrc, st) ||
-                           !buf_ensure(jobbufs, sizeof(double) * nn * batch.size(), st))) {
-            r = fail(BC_E_NOMEM, "serving buffers");
-        }
-        if (r == BC_OK) {
-            cudaError_t e = cudaMemcpyAsync(dsrc.p, all.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) r = cuda_fail(e, "source copy");
-        }
-        std::vector<double*> jb;
-        for (size_t j = 0; j < batch.size(); ++j) jb.push_back((double*)jobbufs.p + nn * j);
-        if (r == BC_OK) {  // runs on the same graph proceed concurrently (own workspace and stream)
-            r = run_jobs(g, &ws, (const int*)dsrc.p, nsrc, o, share, jb, &col_job, false, st, nullptr, nullptr,
-                         nullptr, nullptr);
-        }
-        if (r >= 0) {
+        if (!deep) {
+            std::vector<int> all;
+            std::vector<int> owner;  // job index per source
             for (size_t j = 0; j < batch.size(); ++j) {
-                cudaError_t e = launch_unpermute(jb[j], (const int*)g->inv.p, batch[j]->out, g->n, st);
-                if (e != cudaSuccess) { r = cuda_fail(e, "unpermute"); break; }
+                all.insert(all.end(), batch[j]->src.begin(), batch[j]->src.end());
+                owner.insert(owner.end(), batch[j]->src.size(), (int)j);
             }
-            cudaError_t e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess && r >= 0) r = cuda_fail(e, "serving run");
+            const int nbatch = (nsrc + K - 1) / K;
+            std::vector<int> col_job((size_t)nbatch * K, 0);
+            for (int i = 0; i < nbatch * K; ++i) col_job[i] = i < nsrc ? owner[i] : (int)batch.size() - 1;
+            const size_t nn = (size_t)(g->n > 0 ? g->n : 1);
+            if (r == BC_OK && (!buf_ensure(dsrc, sizeof(int) * (size_t)nsrc, st) ||
+                               !buf_ensure(jobbufs, sizeof(double) * nn * batch.size(), st))) {
+                r = fail(BC_E_NOMEM, "serving buffers");
+            }
+            if (r == BC_OK) {
+                cudaError_t e = cudaMemcpyAsync(dsrc.p, all.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) r = cuda_fail(e, "source copy");
+            }
+            std::vector<double*> jb;
+            for (size_t j = 0; j < batch.size(); ++j) jb.push_back((double*)jobbufs.p + nn * j);
+            if (r == BC_OK) {  // runs on the same graph proceed concurrently (own workspace and stream)
+                r = run_jobs(g, &ws, (const int*)dsrc.p, nsrc, o, share, jb, &col_job, false, st, nullptr, nullptr,
+                             nullptr, nullptr);
+            }
+            if (r >= 0) {
+                for (size_t j = 0; j < batch.size(); ++j) {
+                    cudaError_t e = launch_unpermute(jb[j], (const int*)g->inv.p, batch[j]->out, g->n, st);
+                    if (e != cudaSuccess) { r = cuda_fail(e, "unpermute"); break; }
+                }
+                cudaError_t e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess && r >= 0) r = cuda_fail(e, "serving run");
+            }
         }
         const long long have = (long long)(ws.bytes() + dsrc.bytes + jobbufs.bytes);
         {
             std::lock_guard<std::mutex> lk(S.mu);
             const auto now = std::chrono::steady_clock::now();
-            for (auto& j : batch) {
-                j->result = r;
+            for (size_t k = 0; k < batch.size(); ++k) {
+                auto& j = batch[k];
+                j->result = deep ? jr[k] : r;
                 j->done = true;
                 j->t_done = now;
                 j->g->users--;
@@ -1693,14 +1718,12 @@ static bc_status run_deep(bc_graph* g, const int* d_src, int nsrc, const bc_opti
 // it).  The per-source form runs when the BFS is deep (kDeepMinDepth levels
 // or more), its levels are narrow (on average at most kDeepMaxWidth
 // vertices), and the memory budget leaves a block for every source or SM.
-constexpr int kDeepMinDepth = 48;
-constexpr int kDeepMaxWidth = 8192;
 static bool want_deep(bc_graph* g, int nsrc, const bc_options& o, cudaStream_t st, double* scratch,
                       bc_run_stats* pre, bool forward_only = false) {
     if (o.deep_form == 1) return false;
     if (o.deep_form == 2) return true;
     if (o.batch_width != 0) return false;
-    auto deep_enough = [&](int d) { return d >= kDeepMinDepth && (double)g->n_nz <= (double)kDeepMaxWidth * d; };
+    auto deep_enough = [&](int d) { return deep_by_depth(g, d); };
     int seen;
     {
         std::lock_guard<std::mutex> lk(g->state_mu);

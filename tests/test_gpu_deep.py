@@ -261,3 +261,25 @@ def test_plan_runs_deep_items_per_source(bc):
         for (G, src, out), (ref, _) in zip(items, refs):
             assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64))
     close(items[2][2].cpu().numpy(), oracle.bc(graphs[2].off, graphs[2].adj, items[2][1]))
+
+
+def test_serving_deep_graph_jobs_equal_direct_calls(bc):
+    """Jobs served on a graph known to be deep run through the direct call (per-source form):
+    each result equals the direct call bit for bit, alone or with other jobs in the queue."""
+    import torch
+    g = bcgen.grid(150, 150, 0.05, 12)
+    G = bc.Graph(g.off, g.adj)
+    G.compute(bcgen.sample_sources(g, 80, 1))  # learns the depth (a probe, then the per-source form)
+    assert G.stats()["deep_sources"] == 80
+    lists = [bcgen.sample_sources(g, k, 20 + k) for k in (5, 70, 130, 33)]
+    refs = []
+    for src in lists:
+        ref, _ = G.compute(src)
+        refs.append(ref.cpu().numpy().copy())
+    outs = [torch.empty(g.n, dtype=torch.float64, device="cuda") for _ in lists]
+    jobs = [G.submit(src, out) for src, out in zip(lists, outs)]
+    for job, out, ref in zip(jobs, outs, refs):
+        st, lat = job.wait(60000)
+        assert st in (bc.BC_OK, bc.BC_W_SIGMA_INEXACT) and lat >= 0
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64))
+    close(outs[0].cpu().numpy(), oracle.bc_ld(g.off, g.adj, lists[0]).astype(np.float64))
