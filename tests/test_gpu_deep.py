@@ -283,3 +283,13 @@ def test_serving_deep_graph_jobs_equal_direct_calls(bc):
         assert st in (bc.BC_OK, bc.BC_W_SIGMA_INEXACT) and lat >= 0
         assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64))
     close(outs[0].cpu().numpy(), oracle.bc_ld(g.off, g.adj, lists[0]).astype(np.float64))
+
+
+@pytest.mark.parametrize("g", [bcgen.empty_graph(1), bcgen.path(2), bcgen.path(3), bcgen.star(6),
+                               bcgen.disjoint_union(bcgen.empty_graph(3), bcgen.path(2))], ids=lambda g: g.name)
+def test_deep_form_tiny_graphs(bc, g):
+    src = np.arange(g.n, dtype=np.int32)
+    G = bc.Graph(g.off, g.adj)
+    got, st = both_forms(bc, G, src)
+    assert st == bc.BC_OK
+    assert np.array_equal(got, oracle.bc(g.off, g.adj, src))
