@@ -400,7 +400,7 @@ class ManyPlan:
         for i, (g, s, o) in enumerate(self._keep):
             arr[i] = bc_item(g._h, s.ctypes.data if s.size else None, int(s.size), _ptr(o) if g.n else None)
         opt = bc_options(opts.get("batch_width", 0), opts.get("direction", 0), 0.0, 0.0, 0, opts.get("blocks_per_sm", 0),
-                         0, 0, opts.get("teams", 0), 0, opts.get("source_order", 0))
+                         0, 0, opts.get("teams", 0), 0, opts.get("source_order", 0), opts.get("deep_form", 0))
         self._h = ctypes.c_void_p()
         _check(lib.bc_many_create(arr, len(items), ctypes.byref(opt), _stream_handle(stream), ctypes.byref(self._h)))
 
