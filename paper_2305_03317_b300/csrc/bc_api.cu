@@ -514,6 +514,11 @@ static void choose_teams(long long m, int K, int nbatch, int blocks, size_t team
         // first's level-barrier waits: R-MAT 22, 1261 -> 1245 ms)
         long long per = std::max<long long>((m >> 19) + 1,
                                             (long long)(0.7 * std::pow((double)m, 0.24) * K / 128.0));
+        // a one-source batch gains little from a team past 32 blocks: R-MAT 22
+        // with 256 sources ran 1493 ms on 2 teams of 222 blocks and 969 ms on 13
+        // of 34 (9-20 teams within 0.3%); R-MAT 20 with 512 sources 583 ms on 6
+        // teams, 492 on 13, 481 on 27 (R-MAT 18 and below keep their teams)
+        if (K == 1) per = std::min<long long>(per, 32);
         if (per < 1) per = 1;
         T = (int)std::max<long long>(1, blocks / std::min<long long>(per, blocks));
         if (nbatch >= 2) T = std::max(T, 2);
