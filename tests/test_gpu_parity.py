@@ -8,6 +8,8 @@ the two differ by a few ulps per level of the DAG; 1e-9 relative per vertex
 is far above that and exact zeros must stay exact zeros.  Levels and path
 counts below 2^53 are compared bit for bit.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -173,6 +175,31 @@ def test_many_batches_team_counts_and_degree1_rule_keep_bits(bc):
         assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64)), kw
     assert np.all(ref[deg == 1] == 0.0)
     assert_bc_close(ref, oracle.bc(g.off, g.adj, src))
+
+
+def test_one_source_batches_on_a_large_graph_keep_bits(bc):
+    """One-source batches on a graph large enough that their teams are capped
+    (R-MAT 20: about one block per 2^19 arcs would give teams of 64 blocks; one-
+    source batches keep at most about 32): the same bits as one 128-wide batch
+    and as fewer, larger teams; over 8 of the sources, the oracle's values."""
+    g = bcgen.rmat(20, 16, 1)
+    src = bcgen.sample_sources(g, 64, 3)
+    G = bc.Graph(g.off, g.adj)
+    ref, st = G.compute(src, batch_width=128)
+    assert st == bc.BC_OK
+    ref = ref.cpu().numpy().copy()
+    out, st1 = G.compute(src, batch_width=1)
+    s = G.stats()
+    assert st1 == st and s["batches"] == 64
+    assert s["teams"] >= 12 and s["grid_blocks"] // s["teams"] <= 40, s
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64))
+    out, st2 = G.compute(src, batch_width=1, teams=4)
+    assert st2 == st and G.stats()["teams"] == 4
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), ref.view(np.uint64))
+    few = src[:8]
+    got, st3 = G.compute(few, batch_width=1)
+    assert st3 == bc.BC_OK
+    assert_bc_close(got.cpu().numpy(), oracle.bc(g.off, g.adj, few, threads=max(1, min(os.cpu_count() or 1, 64))))
 
 
 def test_reduce_ranks_is_the_rank_order_sum(bc):
