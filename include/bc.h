@@ -384,6 +384,23 @@ bc_status bc_cancel(bc_job job);
 bc_status bc_server_config(int32_t slots, int64_t memory_budget);
 
 /*
+ * Inspection: the team split that bc_compute and plans use for a traversal
+ * (host arithmetic only, no device work; the calls pass their graph's arc
+ * count m, the batch width, the batch count, the cooperative grid's blocks,
+ * the arena bytes of one team and the device's free bytes at the call).
+ * A team has about one block per 2^19 arcs on large graphs, at least about
+ * 0.7 * m^0.24 * batch_width / 128 blocks on smaller ones, at most 32 when
+ * batch_width is 1; at least two teams when there are two batches; no more
+ * teams than batches or blocks; the teams' slices within 30% of free_bytes
+ * (and 24 GB); then the fewest teams that need the same number of rounds.
+ * teams > 0 asks for that many (still capped by batches, blocks and memory).
+ * Writes nteams and team_blocks (blocks / nteams).  BC_E_INVALID_ARG for
+ * m < 0, batch_width < 1, nbatch < 0, blocks < 1, teams < 0 or NULL outputs.
+ */
+bc_status bc_team_rule(int64_t m, int32_t batch_width, int32_t nbatch, int32_t blocks, uint64_t team_bytes,
+                       uint64_t free_bytes, int32_t teams, int32_t* nteams, int32_t* team_blocks);
+
+/*
  * Test/inspection: levels and path counts of ONE source (original id) in
  * original ids.  level[v] = BFS depth or -1; sigma(v) = sigma_mant[v] *
  * 2^sigma_exp[v] exactly when the count is below 2^53 (mantissa in [0.5,1)).

@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bc_server_reset_stats": [],
         "bc_cancel": [u64],
         "bc_server_config": [i32, i64],
+        "bc_team_rule": [i64, i32, i32, i32, u64, u64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "bc_debug_source": [P, i32, P, P, P],
         "bc_last_trace": [P, P, i32, P],
         "bc_compute_noalloc": [P, P, i32, i64, P, i32, P, P],
@@ -171,6 +172,16 @@ def reduce_ranks(parts, out=None, stream=None):
 
 def server_config(slots: int = 1, memory_budget: int = 0) -> None:
     _check(load().bc_server_config(slots, memory_budget))
+
+
+def team_rule(m: int, batch_width: int, nbatch: int, blocks: int, team_bytes: int, free_bytes: int,
+              teams: int = 0):
+    """(teams, blocks per team) of a traversal (bc_team_rule: host arithmetic, no device work)."""
+    T = ctypes.c_int32()
+    B = ctypes.c_int32()
+    _check(load().bc_team_rule(m, batch_width, nbatch, blocks, team_bytes, free_bytes, teams, ctypes.byref(T),
+                               ctypes.byref(B)))
+    return int(T.value), int(B.value)
 
 
 def server_stats():

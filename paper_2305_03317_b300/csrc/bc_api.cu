@@ -493,12 +493,12 @@ static int grid_blocks(int K, bool ext, int blocks_per_sm, int share) {
     return blocks;
 }
 
-// Teams for a launch: blocks per team grow with the graph's arcs (about one
-// block per 2^19 arcs, so small graphs run one team per SM-sized group and the
-// largest graphs one team over the whole grid); no more teams than batches,
-// and the per-team arenas within a memory budget.
-static void choose_teams(long long m, int K, int nbatch, int blocks, size_t team_bytes, int forced, int* nteams,
-                         int* team_blocks) {
+// Teams for a launch, host arithmetic only (exported as bc_team_rule): blocks
+// per team grow with the graph's arcs m; no more teams than the nbatch batches
+// or the grid's blocks; the teams' arena slices (team_bytes each) within 30%
+// of free_bytes and 24 GB; forced > 0 asks for that many teams.
+static void team_rule(long long m, int K, int nbatch, int blocks, size_t team_bytes, size_t free_bytes, int forced,
+                      int* nteams, int* team_blocks) {
     int T;
     if (forced > 0) {
         T = forced;
@@ -525,12 +525,7 @@ static void choose_teams(long long m, int K, int nbatch, int blocks, size_t team
     }
     T = std::min(T, std::max(1, nbatch));
     T = std::min(T, blocks);
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-        cudaGetLastError();
-        fr = (size_t)16 << 30;
-    }
-    const double budget = std::min(0.3 * (double)fr, 24e9);
+    const double budget = std::min(0.3 * (double)free_bytes, 24e9);
     while (T > 1 && (double)T * (double)team_bytes > budget) --T;
     if (forced <= 0 && T > 1) {
         // the fewest teams that take the batches in the same number of rounds,
@@ -541,6 +536,16 @@ static void choose_teams(long long m, int K, int nbatch, int blocks, size_t team
     }
     *nteams = T;
     *team_blocks = blocks / T;
+}
+
+static void choose_teams(long long m, int K, int nbatch, int blocks, size_t team_bytes, int forced, int* nteams,
+                         int* team_blocks) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        fr = (size_t)16 << 30;
+    }
+    team_rule(m, K, nbatch, blocks, team_bytes, fr, forced, nteams, team_blocks);
 }
 
 // One traversal run of a source list (original ids, device) on workspace w:
@@ -2469,6 +2474,18 @@ bc_status bc_tuning_cache(const char* path, int32_t save) {
         }
     }
     fclose(f);
+    return BC_OK;
+}
+
+bc_status bc_team_rule(int64_t m, int32_t batch_width, int32_t nbatch, int32_t blocks, uint64_t team_bytes,
+                       uint64_t free_bytes, int32_t teams, int32_t* nteams, int32_t* team_blocks) {
+    if (m < 0 || batch_width < 1 || nbatch < 0 || blocks < 1 || teams < 0 || !nteams || !team_blocks)
+        return fail(BC_E_INVALID_ARG, "bc_team_rule: m >= 0, batch_width >= 1, nbatch >= 0, blocks >= 1, teams >= 0 "
+                                      "and non-NULL outputs");
+    int T = 1, B = blocks;
+    team_rule(m, batch_width, nbatch, blocks, (size_t)team_bytes, (size_t)free_bytes, teams, &T, &B);
+    *nteams = T;
+    *team_blocks = B;
     return BC_OK;
 }
 

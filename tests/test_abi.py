@@ -66,3 +66,31 @@ def test_tuning_cache_roundtrip_without_gpu(tmp_path):
     q = tmp_path / "tune2.json"
     bc.tuning_cache(str(q), True)
     assert '"batch_width": 64' in q.read_text() and '"group_vertices": 16' in q.read_text()
+
+
+def test_team_rule_without_gpu():
+    # the team split of a traversal is host arithmetic; these are the splits the
+    # measured calls ran (R-MAT 22: 128,304,910 arcs; R-MAT 12: about 6e4; a
+    # grid of 444 blocks, 3 per SM)
+    import paper_2305_03317_b300 as bc
+    m22, m12, blocks, free = 128304910, 60000, 444, 270 * 10**9
+    # R-MAT 22, 32 batches of 128: one block per 2^19 arcs would be one team;
+    # two batches in flight
+    assert bc.team_rule(m22, 128, 32, blocks, 5 * 10**9, free) == (2, 222)
+    # one-source batches: teams of at most about 32 blocks, then the fewest
+    # teams that need the same 20 rounds
+    assert bc.team_rule(m22, 1, 256, blocks, 2 * 10**8, free) == (13, 34)
+    # R-MAT 12: one block per one-source batch (4096 batches: 10 rounds of 410);
+    # 128-wide batches on teams of about 0.7 m^0.24 blocks, no more teams than batches
+    assert bc.team_rule(m12, 1, 4096, blocks, 10**6, free) == (410, 1)
+    assert bc.team_rule(m12, 128, 32, blocks, 10**7, free) == (32, 13)
+    # the slices within 30% of free memory and 24 GB
+    assert bc.team_rule(m22, 1, 256, blocks, 10 * 10**9, free) == (2, 222)
+    assert bc.team_rule(m22, 128, 32, blocks, 5 * 10**9, 10 * 10**9) == (1, 444)
+    # asked-for counts, capped by batches; nothing to run still gives one team
+    assert bc.team_rule(m22, 128, 32, blocks, 10**9, free, teams=4) == (4, 111)
+    assert bc.team_rule(m12, 128, 32, blocks, 10**6, free, teams=100) == (32, 13)
+    assert bc.team_rule(m12, 128, 0, blocks, 10**6, free) == (1, 444)
+    with pytest.raises(bc.BCError) as ei:
+        bc.team_rule(m12, 0, 32, blocks, 10**6, free)
+    assert ei.value.status == bc.BC_E_INVALID_ARG
